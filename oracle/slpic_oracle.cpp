@@ -1,0 +1,824 @@
+// SLPIC-MCC oracle: a plain, slow CPU restatement of one speed-limited
+// particle-in-cell step with Monte-Carlo collisions (Theis, Werner, Jenkins,
+// Cary, "Computing the Paschen curve for argon with speed-limited
+// particle-in-cell simulation").
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+// call this file: only the tests, the package's smoke check and the CPU
+// baseline leg of the benchmark use it.  It shares no code, header, constant
+// or table generator with the CUDA library.
+//
+// Everything is written as loops over markers in array order, one marker at a
+// time, in the order the method states.  The arithmetic type R is double for
+// the reference (FP64) mode and float for the FP32 mirror mode; the mirror
+// evaluates the same expressions left to right in IEEE single precision
+// (build with -ffp-contract=off so that no multiply-add is fused), which is
+// what lets counts and deposits be compared bit for bit against an FP32
+// implementation that makes the same choices.
+//
+// Readings of the paper that this file fixes (the paper is silent on them):
+//  * cathode at x = 0 with phi = 0, anode at x = d with phi = V (Sec. IV);
+//  * linear (cloud-in-cell) shape for gather and deposit (Eq. Ansatz);
+//  * leapfrog: the kick uses beta of the pre-kick speed, the drift beta of the
+//    post-kick speed (Eqs. slpicEOMx, slpicEOMv, betaAbrupt);
+//  * collision probability of a marker per step = beta v dt / lambda_mfp
+//    = n_g sigma(eps) beta v dt (Sec. III, the d'/lambda_mfp rule and
+//    Eq. SLPICcollisionNumber with beta_n = 1, whole-marker collisions),
+//    realised with a null-collision majorant;
+//  * Vahedi-Surendra elastic angles, isotropic excitation with the threshold
+//    removed, ionization with a uniform split of the excess energy (the
+//    Kutasi sharing rule is not given in the paper), Ar+ born with a gas
+//    temperature Maxwellian;
+//  * constant secondary-emission yield gamma (Lieberman value, Sec. V).
+//
+// Parity unpinned: the ensemble quantities (Townsend alpha of the synthetic
+// gas, multiplication, breakdown voltage) have no printed value in the paper;
+// they are pinned only by closed forms and self-consistency checks.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <vector>
+
+namespace {
+
+// CODATA 2018 constants (SI).
+const double kQe = 1.602176634e-19;     // elementary charge [C]
+const double kMe = 9.1093837015e-31;    // electron mass [kg]
+const double kKB = 1.380649e-23;        // Boltzmann constant [J/K]
+const double kEps0 = 8.8541878128e-12;  // vacuum permittivity [F/m]
+const double kTwoPi = 6.283185307179586;
+
+const int ELECTRON = 0;
+const int ION = 1;
+const uint32_t GEN_BIT = 0x80000000u;   // set on markers of later generations
+const uint32_t SEED_STEP = 0xFFFFFFFFu; // Philox "step" word used for seeding
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10, from its published definition (Salmon, Moraes, Dror, Shaw,
+// "Parallel random numbers: as easy as 1, 2, 3", SC'11): ten rounds of two
+// 32x32->64 multiplies with the round keys bumped by the Weyl constants.
+// ---------------------------------------------------------------------------
+void philox4x32_10(const uint32_t ctr_in[4], uint32_t k0, uint32_t k1,
+                   uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// 32 random bits -> uniform in (0, 1): (floor(x / 2^9) + 1/2) / 2^23.  The
+// result has at most 24 significant bits, so it is the same number in float
+// and in double.
+template <typename R>
+R uniform01(uint32_t x) {
+  return ((R)(x >> 9) + (R)0.5) * (R)(1.0 / 8388608.0);
+}
+
+template <typename R>
+struct Marker {
+  int32_t cell;
+  R off;  // position inside the cell, in [0, 1)
+  R vx, vy, vz;
+  R wj;   // flux weight w_j = w_p / beta (constant along a trajectory)
+  uint32_t id;
+};
+
+}  // namespace
+
+extern "C" {
+
+// Configuration of one instance (one gap at one (p, V)).  Mirrors nothing in
+// the CUDA library; the tests fill it from the same numbers they give the
+// library.
+typedef struct {
+  int n_cells;
+  double d;          // gap [m]
+  double V;          // anode potential [V]
+  double area;       // electrode area that the 1D weights refer to [m^2]
+  int field_mode;    // 0: vacuum field -V/d kept fixed, 1: Poisson every step
+  double p_Pa, T_K;  // background argon
+  double dt;         // time step [s]
+  double mass[2];    // [kg] electron, ion
+  double charge[2];  // [C]
+  double vlim[2];    // speed limit [m/s]; <= 0 or inf means beta = 1
+  double gamma_se;   // ion-induced secondary-electron yield at the cathode
+  int charge_shift;  // fixed-point scale: charge unit = 2^-shift flux weight
+  uint64_t seed;
+  uint32_t instance;
+  int tab_lo_exp2;   // table starts at 2^tab_lo_exp2 eV
+  int tab_log2_sub;  // 2^tab_log2_sub nodes per octave
+  int tab_octaves;   // table spans this many octaves
+  const float* sig_el;  // cross sections at the nodes [m^2]
+  const float* sig_ex;
+  const float* sig_io;
+  double e_ex, e_io;    // excitation and ionization thresholds [eV]
+  int precision;        // 64: FP64 reference, 32: FP32 mirror
+} oracle_config;
+
+// Per-step record of what happened (all sums over markers, in the step).
+typedef struct {
+  int64_t step;
+  int64_t n_live[2];       // live markers after the step
+  double w_live[2];        // sum of w_j of live markers after the step
+  int64_t n_coll[3];       // elastic, excitation, ionization
+  int64_t n_candidates;    // null-collision candidates (u1 < P0)
+  int64_t n_abs[2][2];     // [species][0: cathode, 1: anode]
+  double w_abs[2][2];
+  int64_t n_see;           // secondary electrons emitted
+  double w_see;
+  double w_ionz;           // sum of w_j of ionizing electrons
+  double w_cath_ion;       // sum of w_j of ions absorbed at the cathode
+  double w_cath_ion_gen0;  // same, ions of the first generation only
+  int64_t n_clamp;         // energies clamped at 0 after an inelastic event
+  int64_t n_majorant;      // markers whose beta*v exceeded the table's cap
+  int64_t marker_steps;    // markers pushed in the step
+} oracle_tally;
+
+}  // extern "C"
+
+namespace {
+
+template <typename R>
+struct Sim {
+  oracle_config cfg;
+  int N = 0;
+  int n_nodes_tab = 0;
+  std::vector<Marker<R>> sp[2];
+  uint32_t next_id[2] = {0, 0};
+  uint32_t step = 0;
+  // tables (cumulative cross sections, in R)
+  std::vector<R> S1, S2, S3;
+  // field at the nodes (FP64 solution, and its R copy used by the push)
+  std::vector<double> phi, E64;
+  std::vector<R> E;
+  std::vector<int64_t> charge[2];  // deposit of the last step (fixed point)
+  std::vector<oracle_tally> history;
+  // derived constants, in R
+  R qmdt[2], dtdx, vlim[2], K_E, K_V[2], ndt, P0, vb_cap, R2, e_ex, e_io;
+  R sigT_ion, gamma, two_pi, wscale;
+  bool limited[2];
+
+  void init(const oracle_config& c) {
+    cfg = c;
+    N = c.n_cells;
+    const double dx = c.d / c.n_cells;
+    for (int s = 0; s < 2; ++s) {
+      qmdt[s] = (R)((c.charge[s] / c.mass[s]) * c.dt);
+      limited[s] = c.vlim[s] > 0.0 && std::isfinite(c.vlim[s]);
+      vlim[s] = limited[s] ? (R)c.vlim[s] : std::numeric_limits<R>::infinity();
+      K_V[s] = (R)(2.0 * kQe / c.mass[s]);
+    }
+    dtdx = (R)(c.dt / dx);
+    K_E = (R)(0.5 * kMe / kQe);
+    const double n_g = c.p_Pa / (kKB * c.T_K);
+    ndt = (R)(n_g * c.dt);
+    R2 = (R)(2.0 * kMe / c.mass[ION]);
+    e_ex = (R)c.e_ex;
+    e_io = (R)c.e_io;
+    sigT_ion = (R)std::sqrt(kKB * c.T_K / c.mass[ION]);
+    gamma = (R)c.gamma_se;
+    two_pi = (R)kTwoPi;
+    wscale = (R)std::ldexp(1.0, c.charge_shift);
+
+    // Cumulative cross sections at the nodes, plus one padding node equal to
+    // the last so that interpolation at the top node reads a valid neighbour.
+    n_nodes_tab = (c.tab_octaves << c.tab_log2_sub) + 1;
+    S1.assign(n_nodes_tab + 1, 0);
+    S2.assign(n_nodes_tab + 1, 0);
+    S3.assign(n_nodes_tab + 1, 0);
+    R smax = 0;
+    for (int j = 0; j < n_nodes_tab; ++j) {
+      S1[j] = (R)c.sig_el[j];
+      S2[j] = S1[j] + (R)c.sig_ex[j];
+      S3[j] = S2[j] + (R)c.sig_io[j];
+      smax = std::max(smax, S3[j]);
+    }
+    S1[n_nodes_tab] = S1[n_nodes_tab - 1];
+    S2[n_nodes_tab] = S2[n_nodes_tab - 1];
+    S3[n_nodes_tab] = S3[n_nodes_tab - 1];
+    // Majorant of n_g sigma_tot(eps) min(v, vlim) dt over the table.  Above
+    // the table's top energy the cross sections are held at the top node and
+    // beta*v is capped at the speed of that energy (only matters for beta=1).
+    R e_top = (R)std::ldexp(1.0, c.tab_lo_exp2 + c.tab_octaves);
+    R v_top = std::sqrt(e_top * K_V[ELECTRON]);
+    vb_cap = std::min(vlim[ELECTRON], v_top);
+    P0 = (ndt * vb_cap) * smax;
+
+    phi.assign(N + 1, 0.0);
+    E64.assign(N + 1, -c.V / c.d);
+    for (int k = 0; k <= N; ++k) phi[k] = c.V * k / N;
+    E.assign(N + 1, (R)(-c.V / c.d));
+    charge[0].assign(N + 1, 0);
+    charge[1].assign(N + 1, 0);
+  }
+
+  void draws(uint32_t id, uint32_t stp, int species, uint32_t block,
+             R u[4]) const {
+    uint32_t ctr[4] = {id, stp, cfg.instance * 2u + (uint32_t)species, block};
+    uint32_t out[4];
+    philox4x32_10(ctr, (uint32_t)cfg.seed, (uint32_t)(cfg.seed >> 32), out);
+    for (int i = 0; i < 4; ++i) u[i] = uniform01<R>(out[i]);
+  }
+
+  // beta(v) = min(1, vlim / v), Eq. betaAbrupt.
+  R beta(R v, int s) const { return v > vlim[s] ? vlim[s] / v : (R)1; }
+
+  // Linear interpolation of the cumulative cross sections at eps.  Nodes sit
+  // at 2^(lo + o) (1 + m / 2^sub) eV: 2^sub equal steps inside each octave.
+  void xsec(R eps, R& s1, R& s2, R& s3) const {
+    const int L = cfg.tab_lo_exp2, sub = cfg.tab_log2_sub;
+    const R e_lo = (R)std::ldexp(1.0, L);
+    const R e_hi = (R)std::ldexp(1.0, L + cfg.tab_octaves);
+    int j;
+    R t;
+    if (!(eps >= e_lo)) {
+      j = 0;
+      t = 0;
+    } else if (eps >= e_hi) {
+      j = n_nodes_tab - 1;
+      t = 0;
+    } else {
+      int ex;
+      R m = std::frexp(eps, &ex);  // eps = m 2^ex, m in [1/2, 1)
+      int octave = ex - 1 - L;
+      R pos = (m + m - (R)1) * (R)(1 << sub);  // in [0, 2^sub), exact
+      R fl = std::floor(pos);
+      j = (octave << sub) + (int)fl;
+      t = pos - fl;
+    }
+    s1 = S1[j] + t * (S1[j + 1] - S1[j]);
+    s2 = S2[j] + t * (S2[j + 1] - S2[j]);
+    s3 = S3[j] + t * (S3[j + 1] - S3[j]);
+  }
+
+  // Isotropic direction with cos(theta) = 1 - 2 ua about x, phi = 2 pi ub.
+  void isotropic(R speed, R ua, R ub, R& vx, R& vy, R& vz) const {
+    R ct = (R)1 - (R)2 * ua;
+    R st = std::sqrt(std::max((R)0, ((R)1 - ct) * ((R)1 + ct)));
+    R ph = two_pi * ub;
+    vx = speed * ct;
+    vy = speed * (st * std::cos(ph));
+    vz = speed * (st * std::sin(ph));
+  }
+
+  // Rotate the unit vector (ux, uy, uz) by polar angle chi (given by its
+  // cosine and sine) and azimuth phi about itself.  The perpendicular basis is
+  // built from the x axis, or from the z axis when |ux| > 0.99.
+  void rotate(R& ux, R& uy, R& uz, R cc, R sc, R cp, R sp) const {
+    R nx, ny, nz;
+    if (std::fabs(ux) <= (R)0.99) {
+      R w = std::sqrt(((R)1 - ux) * ((R)1 + ux));
+      nx = ux * cc + sc * (cp * w);
+      ny = uy * cc + sc * ((uz * sp - ux * (uy * cp)) / w);
+      nz = uz * cc - sc * ((uy * sp + ux * (uz * cp)) / w);
+    } else {
+      R w = std::sqrt(((R)1 - uz) * ((R)1 + uz));
+      nx = ux * cc + sc * ((uy * sp - uz * (ux * cp)) / w);
+      ny = uy * cc - sc * ((ux * sp + uz * (uy * cp)) / w);
+      nz = uz * cc + sc * (cp * w);
+    }
+    ux = nx; uy = ny; uz = nz;
+  }
+
+  void deposit_one(const Marker<R>& m, int s, std::vector<int64_t>& q) const {
+    R v = std::sqrt(m.vx * m.vx + m.vy * m.vy + m.vz * m.vz);
+    R wp = beta(v, s) * m.wj;  // density weight w_p = beta w_j
+    int64_t Q = (int64_t)std::llrint(wp * wscale);
+    int64_t f = (int64_t)(m.off * (R)16777216.0);  // 24-bit CIC fraction
+    int64_t right = (Q * f) >> 24;
+    q[m.cell] += Q - right;
+    q[m.cell + 1] += right;
+  }
+
+  void solve_field() {
+    // (phi[k+1] - 2 phi[k] + phi[k-1]) / dx^2 = -rho_k / eps0, k = 1..N-1,
+    // phi[0] = 0, phi[N] = V; Thomas algorithm on the tridiagonal system.
+    const double dx = cfg.d / N;
+    const double unit = std::ldexp(1.0, -cfg.charge_shift);
+    std::vector<double> rhs(N + 1, 0.0), cp(N + 1, 0.0), dp(N + 1, 0.0);
+    for (int k = 1; k < N; ++k) {
+      double net = (double)(charge[ION][k] - charge[ELECTRON][k]);
+      double rho = kQe * net * unit / (cfg.area * dx);
+      rhs[k] = -rho * dx * dx / kEps0;
+    }
+    rhs[1] -= 0.0;       // phi[0]
+    rhs[N - 1] -= cfg.V; // phi[N]
+    // forward sweep: a = 1, b = -2, c = 1
+    cp[1] = 1.0 / -2.0;
+    dp[1] = rhs[1] / -2.0;
+    for (int k = 2; k < N; ++k) {
+      double den = -2.0 - cp[k - 1];
+      cp[k] = 1.0 / den;
+      dp[k] = (rhs[k] - dp[k - 1]) / den;
+    }
+    phi[0] = 0.0;
+    phi[N] = cfg.V;
+    if (N >= 2) {
+      phi[N - 1] = dp[N - 1];
+      for (int k = N - 2; k >= 1; --k) phi[k] = dp[k] - cp[k] * phi[k + 1];
+    }
+    E64[0] = -(phi[1] - phi[0]) / dx;
+    E64[N] = -(phi[N] - phi[N - 1]) / dx;
+    for (int k = 1; k < N; ++k) E64[k] = -(phi[k + 1] - phi[k - 1]) / (2.0 * dx);
+    for (int k = 0; k <= N; ++k) E[k] = (R)E64[k];
+  }
+
+  void one_step() {
+    oracle_tally t;
+    std::memset(&t, 0, sizeof(t));
+    t.step = step;
+    const uint32_t s_now = step;
+    std::vector<Marker<R>> born_e_ionz, born_i, born_e_see;
+    for (int s = 0; s < 2; ++s) {
+      std::vector<Marker<R>> survivors;
+      survivors.reserve(sp[s].size());
+      for (size_t i = 0; i < sp[s].size(); ++i) {
+        Marker<R> m = sp[s][i];
+        t.marker_steps++;
+        // Field at the marker (linear interpolation between its nodes).
+        R Ex = E[m.cell] + m.off * (E[m.cell + 1] - E[m.cell]);
+        // Speed-limited kick and drift (Eqs. slpicEOMx, slpicEOMv).
+        R s0 = m.vx * m.vx + m.vy * m.vy + m.vz * m.vz;
+        R b0 = beta(std::sqrt(s0), s);
+        m.vx = m.vx + b0 * (qmdt[s] * Ex);
+        R s1 = m.vx * m.vx + m.vy * m.vy + m.vz * m.vz;
+        R v1 = std::sqrt(s1);
+        R b1 = beta(v1, s);
+        m.off = m.off + b1 * (m.vx * dtdx);
+        R fl = std::floor(m.off);
+        m.cell += (int)fl;
+        m.off = m.off - fl;
+        if (m.off >= (R)1) {
+          m.off = 0;
+          m.cell += 1;
+        }
+        // Absorbing electrodes; the flux through each is the sum of w_j of
+        // the markers that cross it (Eq. j).
+        if (m.cell < 0) {
+          t.n_abs[s][0]++;
+          t.w_abs[s][0] += (double)m.wj;
+          if (s == ION) {
+            t.w_cath_ion += (double)m.wj;
+            if (!(m.id & GEN_BIT)) t.w_cath_ion_gen0 += (double)m.wj;
+            R u[4];
+            draws(m.id, s_now, ION, 0, u);
+            if (u[0] < gamma) {
+              Marker<R> e;
+              e.cell = 0; e.off = 0; e.vx = 0; e.vy = 0; e.vz = 0;
+              e.wj = m.wj;  // flux weight carried over to the emitted electron
+              e.id = GEN_BIT;
+              born_e_see.push_back(e);
+              t.n_see++;
+              t.w_see += (double)m.wj;
+            }
+          }
+          continue;
+        }
+        if (m.cell >= N) {
+          t.n_abs[s][1]++;
+          t.w_abs[s][1] += (double)m.wj;
+          continue;
+        }
+        if (s == ELECTRON) collide(m, s1, v1, s_now, t, born_e_ionz, born_i);
+        survivors.push_back(m);
+      }
+      sp[s].swap(survivors);
+    }
+    // Append births: ionization electrons, then emitted electrons; ions.
+    for (auto& m : born_e_ionz) {
+      m.id = (m.id & GEN_BIT) | next_id[ELECTRON]++;
+      sp[ELECTRON].push_back(m);
+    }
+    for (auto& m : born_e_see) {
+      m.id = (m.id & GEN_BIT) | next_id[ELECTRON]++;
+      sp[ELECTRON].push_back(m);
+    }
+    for (auto& m : born_i) {
+      m.id = (m.id & GEN_BIT) | next_id[ION]++;
+      sp[ION].push_back(m);
+    }
+    // Deposit every live marker with its density weight.
+    for (int s = 0; s < 2; ++s) {
+      std::fill(charge[s].begin(), charge[s].end(), 0);
+      for (const auto& m : sp[s]) deposit_one(m, s, charge[s]);
+    }
+    if (cfg.field_mode == 1) solve_field();
+    for (int s = 0; s < 2; ++s) {
+      t.n_live[s] = (int64_t)sp[s].size();
+      double w = 0;
+      for (const auto& m : sp[s]) w += (double)m.wj;
+      t.w_live[s] = w;
+    }
+    history.push_back(t);
+    step++;
+  }
+
+  // Null-collision Monte-Carlo collision of one electron (Sec. III).
+  void collide(Marker<R>& m, R s1, R v1, uint32_t s_now, oracle_tally& t,
+               std::vector<Marker<R>>& born_e, std::vector<Marker<R>>& born_i) {
+    R u[4];
+    draws(m.id, s_now, ELECTRON, 0, u);
+    if (!(u[0] < P0)) return;
+    t.n_candidates++;
+    R vb = v1 > vlim[ELECTRON] ? vlim[ELECTRON] : v1;  // beta v
+    if (vb > vb_cap) {
+      vb = vb_cap;
+      t.n_majorant++;
+    }
+    R c = ndt * vb;
+    R eps = s1 * K_E;
+    R x1, x2, x3;
+    xsec(eps, x1, x2, x3);
+    R r = u[1] * P0;
+    int proc;
+    if (r < c * x1) proc = 0;
+    else if (r < c * x2) proc = 1;
+    else if (r < c * x3) proc = 2;
+    else return;  // null collision
+    t.n_coll[proc]++;
+    const R kv = K_V[ELECTRON];
+    if (proc == 0) {
+      // Elastic, Vahedi-Surendra: cos chi = (2 + eps - 2 (1 + eps)^u) / eps,
+      // written as 1 - 2 expm1(u log1p(eps)) / eps; recoil energy loss.
+      R em = std::expm1(u[2] * std::log1p(eps));
+      R cc = (R)1 - (em + em) / eps;
+      cc = std::min((R)1, std::max((R)-1, cc));
+      R sc = std::sqrt(std::max((R)0, ((R)1 - cc) * ((R)1 + cc)));
+      R ph = two_pi * u[3];
+      R cp = std::cos(ph), spn = std::sin(ph);
+      R e_new = eps * ((R)1 - R2 * ((R)1 - cc));
+      R ux = m.vx / v1, uy = m.vy / v1, uz = m.vz / v1;
+      rotate(ux, uy, uz, cc, sc, cp, spn);
+      R v_new = std::sqrt(e_new * kv);
+      m.vx = v_new * ux;
+      m.vy = v_new * uy;
+      m.vz = v_new * uz;
+    } else if (proc == 1) {
+      R e_new = eps - e_ex;
+      if (e_new < (R)0) {
+        e_new = 0;
+        t.n_clamp++;
+      }
+      isotropic(std::sqrt(e_new * kv), u[2], u[3], m.vx, m.vy, m.vz);
+    } else {
+      R e_av = eps - e_io;
+      if (e_av < (R)0) {
+        e_av = 0;
+        t.n_clamp++;
+      }
+      t.w_ionz += (double)m.wj;
+      R b[4];
+      draws(m.id, s_now, ELECTRON, 1, b);
+      R e_sec = b[0] * e_av;
+      R e_pri = e_av - e_sec;
+      isotropic(std::sqrt(e_pri * kv), u[2], u[3], m.vx, m.vy, m.vz);
+      Marker<R> e;
+      e.cell = m.cell;
+      e.off = m.off;
+      isotropic(std::sqrt(e_sec * kv), b[1], b[2], e.vx, e.vy, e.vz);
+      e.wj = m.wj;
+      e.id = m.id & GEN_BIT;
+      born_e.push_back(e);
+      // Ion at rest in the gas frame plus a Maxwellian at the gas
+      // temperature (Box-Muller on a third block of draws).
+      R g[4];
+      draws(m.id, s_now, ELECTRON, 2, g);
+      R r1 = std::sqrt((R)-2 * std::log(g[0]));
+      R r2 = std::sqrt((R)-2 * std::log(g[2]));
+      R a1 = two_pi * g[1], a2 = two_pi * g[3];
+      Marker<R> ion;
+      ion.cell = m.cell;
+      ion.off = m.off;
+      ion.vx = sigT_ion * (r1 * std::cos(a1));
+      ion.vy = sigT_ion * (r1 * std::sin(a1));
+      ion.vz = sigT_ion * (r2 * std::cos(a2));
+      ion.wj = m.wj;
+      ion.id = m.id & GEN_BIT;
+      born_i.push_back(ion);
+    }
+  }
+
+  // Initial markers.  mode 0: at the cathode, uniform in the first cell, given
+  // energy, directions uniform on the forward (+x) hemisphere; mode 1: at the
+  // cathode at rest; mode 2: uniform in the gap, energy log-uniform in
+  // [e_lo, e_hi], isotropic; mode 3: uniform in the gap, Maxwellian at the gas
+  // temperature.
+  void seed(int s, int64_t n, int mode, double e0, double e_lo, double e_hi,
+            double wj) {
+    const R lr = (R)std::log(e_hi / e_lo);
+    const R elo = (R)e_lo;
+    const R ekin = (R)e0;
+    const R Nr = (R)N;
+    const R below1 = std::nextafter((R)1, (R)0);
+    const R sigT = (R)std::sqrt(kKB * cfg.T_K / cfg.mass[s]);
+    for (int64_t i = 0; i < n; ++i) {
+      Marker<R> m;
+      m.id = next_id[s]++;
+      m.wj = (R)wj;
+      R u[4];
+      draws(m.id, SEED_STEP, s, 0, u);
+      if (mode == 0 || mode == 1) {
+        m.cell = 0;
+        if (mode == 0) {
+          m.off = u[0];
+          R v = std::sqrt(ekin * K_V[s]);
+          R ct = u[1];
+          R st = std::sqrt(std::max((R)0, ((R)1 - ct) * ((R)1 + ct)));
+          R ph = two_pi * u[2];
+          m.vx = v * ct;
+          m.vy = v * (st * std::cos(ph));
+          m.vz = v * (st * std::sin(ph));
+        } else {
+          m.off = 0; m.vx = 0; m.vy = 0; m.vz = 0;
+        }
+      } else {
+        R p = u[0] * Nr;
+        R fl = std::floor(p);
+        m.cell = (int)fl;
+        m.off = p - fl;
+        if (m.cell >= N) {
+          m.cell = N - 1;
+          m.off = below1;
+        }
+        if (mode == 2) {
+          R e = elo * std::exp(u[1] * lr);
+          isotropic(std::sqrt(e * K_V[s]), u[2], u[3], m.vx, m.vy, m.vz);
+        } else {
+          R g[4];
+          draws(m.id, SEED_STEP, s, 1, g);
+          R r1 = std::sqrt((R)-2 * std::log(u[1]));
+          R r2 = std::sqrt((R)-2 * std::log(u[3]));
+          R a1 = two_pi * u[2], a2 = two_pi * g[0];
+          m.vx = sigT * (r1 * std::cos(a1));
+          m.vy = sigT * (r1 * std::sin(a1));
+          m.vz = sigT * (r2 * std::cos(a2));
+        }
+      }
+      sp[s].push_back(m);
+    }
+  }
+
+  void deposit_all() {
+    for (int s = 0; s < 2; ++s) {
+      std::fill(charge[s].begin(), charge[s].end(), 0);
+      for (const auto& m : sp[s]) deposit_one(m, s, charge[s]);
+    }
+  }
+};
+
+struct Handle {
+  int precision;
+  Sim<double>* d = nullptr;
+  Sim<float>* f = nullptr;
+};
+
+template <typename F>
+void visit(Handle* h, F fn) {
+  if (h->precision == 32) fn(*h->f);
+  else fn(*h->d);
+}
+
+}  // namespace
+
+extern "C" {
+
+void oracle_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1,
+                   uint32_t* out) {
+  philox4x32_10(ctr, k0, k1, out);
+}
+
+// Many blocks at once: ctr is n x 4, out is n x 4.
+void oracle_philox_many(const uint32_t* ctr, int64_t n, uint32_t k0,
+                        uint32_t k1, uint32_t* out) {
+  for (int64_t i = 0; i < n; ++i) philox4x32_10(ctr + 4 * i, k0, k1, out + 4 * i);
+}
+
+double oracle_uniform64(uint32_t x) { return uniform01<double>(x); }
+float oracle_uniform32(uint32_t x) { return uniform01<float>(x); }
+
+void* oracle_create(const oracle_config* c) {
+  if (!c || c->n_cells < 1 || !(c->d > 0) || !(c->dt >= 0)) return nullptr;
+  Handle* h = new Handle;
+  h->precision = c->precision == 32 ? 32 : 64;
+  if (h->precision == 32) {
+    h->f = new Sim<float>;
+    h->f->init(*c);
+  } else {
+    h->d = new Sim<double>;
+    h->d->init(*c);
+  }
+  return h;
+}
+
+void oracle_destroy(void* hp) {
+  Handle* h = (Handle*)hp;
+  if (!h) return;
+  delete h->d;
+  delete h->f;
+  delete h;
+}
+
+// Load n markers of species s from FP32 arrays (the storage format); in FP64
+// mode they are widened exactly.  Replaces the species' markers.
+int oracle_load(void* hp, int s, int64_t n, const int32_t* cell,
+                const float* off, const float* vx, const float* vy,
+                const float* vz, const float* wj, const uint32_t* id,
+                uint32_t next_id) {
+  Handle* h = (Handle*)hp;
+  if (!h || s < 0 || s > 1 || n < 0) return -1;
+  int bad = 0;
+  visit(h, [&](auto& sim) {
+    using R = decltype(sim.K_E);
+    sim.sp[s].clear();
+    for (int64_t i = 0; i < n; ++i) {
+      Marker<R> m;
+      m.cell = cell[i];
+      m.off = (R)off[i];
+      m.vx = (R)vx[i]; m.vy = (R)vy[i]; m.vz = (R)vz[i];
+      m.wj = (R)wj[i];
+      m.id = id[i];
+      if (m.cell < 0 || m.cell >= sim.N || !(m.off >= 0) || !(m.off < 1)) bad = 1;
+      sim.sp[s].push_back(m);
+    }
+    sim.next_id[s] = next_id;
+  });
+  return bad ? -2 : 0;
+}
+
+int oracle_seed(void* hp, int s, int64_t n, int mode, double e0, double e_lo,
+                double e_hi, double wj) {
+  Handle* h = (Handle*)hp;
+  if (!h || s < 0 || s > 1 || n < 0 || mode < 0 || mode > 3) return -1;
+  visit(h, [&](auto& sim) { sim.seed(s, n, mode, e0, e_lo, e_hi, wj); });
+  return 0;
+}
+
+int oracle_step(void* hp, int64_t nsteps) {
+  Handle* h = (Handle*)hp;
+  if (!h || nsteps < 0) return -1;
+  visit(h, [&](auto& sim) {
+    for (int64_t i = 0; i < nsteps; ++i) sim.one_step();
+  });
+  return 0;
+}
+
+// Deposit the current markers (no push), as the step's deposit would.
+int oracle_deposit(void* hp) {
+  Handle* h = (Handle*)hp;
+  if (!h) return -1;
+  visit(h, [&](auto& sim) { sim.deposit_all(); });
+  return 0;
+}
+
+int oracle_solve_field(void* hp) {
+  Handle* h = (Handle*)hp;
+  if (!h) return -1;
+  visit(h, [&](auto& sim) { sim.solve_field(); });
+  return 0;
+}
+
+int64_t oracle_count(void* hp, int s) {
+  Handle* h = (Handle*)hp;
+  int64_t n = -1;
+  if (!h || s < 0 || s > 1) return -1;
+  visit(h, [&](auto& sim) { n = (int64_t)sim.sp[s].size(); });
+  return n;
+}
+
+uint32_t oracle_next_id(void* hp, int s) {
+  Handle* h = (Handle*)hp;
+  uint32_t n = 0;
+  visit(h, [&](auto& sim) { n = sim.next_id[s]; });
+  return n;
+}
+
+int oracle_get(void* hp, int s, int32_t* cell, double* off, double* vx,
+               double* vy, double* vz, double* wj, uint32_t* id) {
+  Handle* h = (Handle*)hp;
+  if (!h || s < 0 || s > 1) return -1;
+  visit(h, [&](auto& sim) {
+    for (size_t i = 0; i < sim.sp[s].size(); ++i) {
+      const auto& m = sim.sp[s][i];
+      cell[i] = m.cell;
+      off[i] = (double)m.off;
+      vx[i] = (double)m.vx; vy[i] = (double)m.vy; vz[i] = (double)m.vz;
+      wj[i] = (double)m.wj;
+      id[i] = m.id;
+    }
+  });
+  return 0;
+}
+
+int oracle_charge(void* hp, int s, int64_t* out) {
+  Handle* h = (Handle*)hp;
+  if (!h || s < 0 || s > 1) return -1;
+  visit(h, [&](auto& sim) {
+    std::copy(sim.charge[s].begin(), sim.charge[s].end(), out);
+  });
+  return 0;
+}
+
+int oracle_field(void* hp, double* phi, double* E) {
+  Handle* h = (Handle*)hp;
+  if (!h) return -1;
+  visit(h, [&](auto& sim) {
+    std::copy(sim.phi.begin(), sim.phi.end(), phi);
+    std::copy(sim.E64.begin(), sim.E64.end(), E);
+  });
+  return 0;
+}
+
+// Set the field at the nodes (used by tests that impose a field).
+int oracle_set_field(void* hp, const double* E) {
+  Handle* h = (Handle*)hp;
+  if (!h) return -1;
+  visit(h, [&](auto& sim) {
+    using R = decltype(sim.K_E);
+    for (int k = 0; k <= sim.N; ++k) {
+      sim.E64[k] = E[k];
+      sim.E[k] = (R)E[k];
+    }
+  });
+  return 0;
+}
+
+int64_t oracle_history_len(void* hp) {
+  Handle* h = (Handle*)hp;
+  int64_t n = 0;
+  visit(h, [&](auto& sim) { n = (int64_t)sim.history.size(); });
+  return n;
+}
+
+int oracle_history(void* hp, oracle_tally* out) {
+  Handle* h = (Handle*)hp;
+  if (!h) return -1;
+  visit(h, [&](auto& sim) {
+    std::copy(sim.history.begin(), sim.history.end(), out);
+  });
+  return 0;
+}
+
+// The constants the step uses, as doubles, for tests: P0 (null-collision
+// majorant probability), vb_cap, ndt.
+int oracle_constants(void* hp, double* out3) {
+  Handle* h = (Handle*)hp;
+  if (!h) return -1;
+  visit(h, [&](auto& sim) {
+    out3[0] = (double)sim.P0;
+    out3[1] = (double)sim.vb_cap;
+    out3[2] = (double)sim.ndt;
+  });
+  return 0;
+}
+
+// Interpolated cumulative cross sections at energies eps[n] (tests).
+int oracle_xsec(void* hp, const double* eps, int64_t n, double* out) {
+  Handle* h = (Handle*)hp;
+  if (!h) return -1;
+  visit(h, [&](auto& sim) {
+    using R = decltype(sim.K_E);
+    for (int64_t i = 0; i < n; ++i) {
+      R a, b, c;
+      sim.xsec((R)eps[i], a, b, c);
+      out[3 * i] = (double)a;
+      out[3 * i + 1] = (double)b;
+      out[3 * i + 2] = (double)c;
+    }
+  });
+  return 0;
+}
+
+// Time-step and run-length rules of the paper (Sec. IV): dt = dx / v0 with
+// v0 = sqrt(2 e V / M) for SLPIC, dt = dx / vmax with vmax = sqrt(2 e V / m_e)
+// for PIC; the classification window is 30 ion crossing times
+// 30 sqrt(2 M d / (e E)), E = V / d.
+double oracle_dt_slpic(double d, int cells, double V, double M) {
+  return (d / cells) / std::sqrt(2.0 * kQe * V / M);
+}
+double oracle_dt_pic(double d, int cells, double V) {
+  return (d / cells) / std::sqrt(2.0 * kQe * V / kMe);
+}
+double oracle_ion_crossing_time(double d, double V, double M) {
+  double E = V / d;
+  return std::sqrt(2.0 * M * d / (kQe * E));
+}
+
+}  // extern "C"

@@ -1,0 +1,566 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test names the passage of the paper (section / equation / table) or the
+closed form it checks.  None of them compares the oracle with itself.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, stats
+
+from paper_2103_12194_gb300 import inputs
+from tests import scalar_reference as sref
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def load_table():
+    rows = []
+    with open(os.path.join(GOLDEN, "table_sims.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            rows.append([float(x) for x in line.split()])
+    return np.array(rows)
+
+
+def vacuum(spec):
+    s = dict(spec)
+    s["p_Pa"] = 0.0
+    return s
+
+
+# ---------------------------------------------------------------------------
+# Table tab:sims (Sec. V) and the time-step rules of Sec. IV
+# ---------------------------------------------------------------------------
+
+def test_table_step_counts_follow_dt_rules(oracle_mod):
+    """N_T of Table tab:sims = 30 ion crossing times / dt, with dt = dx/v0
+    (SLPIC) or dx/vmax (PIC), Sec. IV; printed with two significant digits."""
+    tab = load_table()
+    d = 0.01
+    for p, V, cells, nt_slpic, nt_pic, *_ in tab:
+        cells = int(cells)
+        window = 30.0 * oracle_mod.ion_crossing_time(d, V, inputs.M_AR)
+        n_slpic = window / oracle_mod.dt_slpic(d, cells, V, inputs.M_AR)
+        assert float("%.1e" % n_slpic) == pytest.approx(nt_slpic, rel=1e-9), (p, n_slpic)
+        if not math.isnan(nt_pic):
+            n_pic = window / oracle_mod.dt_pic(d, cells, V)
+            assert float("%.1e" % n_pic) == pytest.approx(nt_pic, rel=1e-9), (p, n_pic)
+        # 30 crossing times of dt = dx / v0 is exactly 60 cells' worth of steps
+        assert n_slpic == pytest.approx(60 * cells, rel=1e-12)
+
+
+def test_dt_ratio_is_270(oracle_mod):
+    """The SLPIC step is 270 times the PIC step (Sec. IV): sqrt(M/m_e)."""
+    r = oracle_mod.dt_slpic(0.01, 219, 170.0, inputs.M_AR) / oracle_mod.dt_pic(0.01, 219, 170.0)
+    assert round(r) == 270
+    assert r == pytest.approx(math.sqrt(inputs.M_AR / inputs.ME), rel=1e-12)
+
+
+def test_table_speedups_are_runtime_ratios():
+    """Speed-up column = T_PIC / T_SLPIC (Table tab:sims caption)."""
+    tab = load_table()
+    ok = ~np.isnan(tab[:, 8])
+    ratio = tab[ok, 7] / tab[ok, 6]
+    # printed speed-ups are rounded from unrounded run times
+    assert np.all(np.abs(ratio - tab[ok, 8]) / tab[ok, 8] < 0.1)
+
+
+# ---------------------------------------------------------------------------
+# Philox and the uniform map
+# ---------------------------------------------------------------------------
+
+def test_philox_matches_independent_python(oracle_mod):
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2**32, size=(200, 4), dtype=np.uint64).astype(np.uint32)
+    seed = 0x0123456789ABCDEF
+    got = oracle_mod.philox(ctr, seed)
+    for i in range(ctr.shape[0]):
+        assert list(got[i]) == sref.philox([int(c) for c in ctr[i]], seed)
+
+
+def test_philox_statistics(oracle_mod):
+    """Uniformity (chi^2 over 256 bins), per-bit balance, and no correlation
+    between neighbouring counters."""
+    n = 1 << 18
+    ctr = np.zeros((n, 4), np.uint32)
+    ctr[:, 0] = np.arange(n, dtype=np.uint32)
+    ctr[:, 1] = 7
+    out = oracle_mod.philox(ctr, 0).reshape(-1)
+    hist = np.bincount(out >> 24, minlength=256)
+    assert stats.chisquare(hist).pvalue > 1e-4
+    bits = ((out[:, None] >> np.arange(32, dtype=np.uint32)) & 1).mean(axis=0)
+    assert np.all(np.abs(bits - 0.5) < 5 * 0.5 / math.sqrt(out.size))
+    u = (out >> 9).astype(np.float64)
+    r = np.corrcoef(u[:-4], u[4:])[0, 1]
+    assert abs(r) < 5 / math.sqrt(u.size)
+
+
+def test_uniform_is_exact_in_float_and_open_interval(oracle_mod):
+    for x in (0, 1, 511, 512, 0x7FFFFFFF, 0xFFFFFFFF, 0xDEADBEEF):
+        a = oracle_mod.uniform(x, 64)
+        b = oracle_mod.uniform(x, 32)
+        assert a == b
+        assert 0.0 < a < 1.0
+        assert a == ((x >> 9) + 0.5) / 2**23
+
+
+# ---------------------------------------------------------------------------
+# Cross-section table
+# ---------------------------------------------------------------------------
+
+def test_table_interpolation_matches_analytic_shapes(oracle_mod):
+    """The octave-uniform table reproduces the analytic argon-like cross
+    sections between the nodes to linear-interpolation accuracy."""
+    spec = inputs.gap_spec(n_cells=16, V=100.0)
+    o = oracle_mod.Oracle(spec, 64)
+    eps = np.geomspace(0.02, 400.0, 3001)
+    got = o.xsec(eps)
+    el, ex, io = inputs.argon_like_xsec(eps)
+    tot = el + ex + io
+    # linear interpolation error of these smooth shapes on a 1/256-octave grid
+    smooth = (np.abs(eps - inputs.E_EXC) > 0.1) & (np.abs(eps - inputs.E_ION) > 0.1)
+    assert np.allclose(got[smooth, 0], el[smooth], rtol=2e-4, atol=1e-24)
+    assert np.allclose(got[smooth, 2], tot[smooth], rtol=2e-4, atol=1e-24)
+    # clamped outside the table
+    lo = o.xsec(np.array([1e-6, 1e6]))
+    assert lo[0, 0] == pytest.approx(float(spec["sig_el"][0]))
+    assert lo[1, 2] == pytest.approx(float(spec["sig_el"][-1] + spec["sig_ex"][-1] + spec["sig_io"][-1]), rel=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# beta = 1 is PIC (Sec. II.B), collisionless transits
+# ---------------------------------------------------------------------------
+
+def test_beta_one_reduces_to_textbook_leapfrog(oracle_mod):
+    """With no speed limit the step is the standard leapfrog PIC push
+    (Sec. II.B: beta = 1 gives exactly PIC)."""
+    spec = vacuum(inputs.gap_spec(n_cells=64, V=300.0, vlim_e=math.inf, field_mode=0))
+    spec["dt"] = 2e-12
+    st = inputs.gap_state(50, spec, rng_seed=3, e_lo=0.5, e_hi=5.0)
+    o = oracle_mod.Oracle(spec, 64)
+    o.load(0, st)
+    o.step(1)
+    got = o.particles(0)
+    dx = spec["d"] / spec["n_cells"]
+    x0 = (st["cell"] + st["off"].astype(np.float64)) * dx
+    E = -spec["V"] / spec["d"]
+    vx = st["vx"].astype(np.float64) + (spec["charge_e"] / spec["mass_e"]) * E * spec["dt"]
+    x1 = x0 + vx * spec["dt"]
+    inside = (x1 >= 0) & (x1 < spec["d"])
+    assert got["cell"].size == inside.sum()
+    xg = (got["cell"] + got["off"]) * dx
+    assert np.allclose(xg, x1[inside], rtol=0, atol=1e-12 * spec["d"])
+    assert np.allclose(got["vx"], vx[inside], rtol=1e-13)
+    assert np.array_equal(got["vy"], st["vy"][inside].astype(np.float64))
+
+
+def _first_anode_step(o, nmax):
+    for k in range(nmax):
+        o.step(1)
+        h = o.history()[-1]
+        if h["n_abs"][0][1] > 0:
+            return k + 1
+    return None
+
+
+def test_pic_transit_matches_discrete_closed_form(oracle_mod):
+    """From rest in a uniform field, leapfrog gives x_n = a dt^2 n(n+1)/2; the
+    electron reaches the anode at the first n with x_n >= d, with energy
+    e V up to O(dt)."""
+    V, N = 300.0, 64
+    spec = vacuum(inputs.gap_spec(n_cells=N, V=V, vlim_e=math.inf, field_mode=0))
+    dt = 1.3e-11
+    spec["dt"] = dt
+    o = oracle_mod.Oracle(spec, 64)
+    o.load(0, inputs.rest_state(1))
+    a = inputs.QE * V / spec["d"] / inputs.ME
+    n_exp = next(n for n in range(1, 10000) if a * dt * dt * n * (n + 1) / 2 >= spec["d"])
+    # energy check one step before arrival
+    o2 = oracle_mod.Oracle(spec, 64)
+    o2.load(0, inputs.rest_state(1))
+    o2.step(n_exp - 1)
+    v = o2.particles(0)["vx"][0]
+    assert v == pytest.approx((n_exp - 1) * a * dt, rel=1e-12)
+    assert _first_anode_step(o, n_exp + 5) == n_exp
+    e_arr = 0.5 * inputs.ME * (n_exp * a * dt) ** 2 / inputs.QE
+    assert e_arr == pytest.approx(V, rel=4.0 / n_exp)
+
+
+def test_slpic_transit_time_and_energy(oracle_mod):
+    """Speed-limited motion from rest (Eqs. slpicEOMx, slpicEOMv with
+    betaAbrupt): accelerate to v0 in v0/a, then x moves at v0, so
+    T = v0/(2a) + d/v0; the energy on arrival is still e V (same phase-space
+    path, only slower)."""
+    spec, _ = inputs.small_gap_config()
+    spec = vacuum(spec)
+    spec["field_mode"] = 0
+    o = oracle_mod.Oracle(spec, 64)
+    o.load(0, inputs.rest_state(1))
+    a = inputs.QE * spec["V"] / spec["d"] / inputs.ME
+    v0 = spec["vlim_e"]
+    T = v0 / (2 * a) + spec["d"] / v0
+    n_exp = T / spec["dt"]
+    assert n_exp == pytest.approx(256.06, abs=0.01)
+    n = _first_anode_step(o, 400)
+    assert abs(n - n_exp) <= 1.5
+    o2 = oracle_mod.Oracle(spec, 64)
+    o2.load(0, inputs.rest_state(1))
+    o2.step(n - 1)
+    p = o2.particles(0)
+    e = 0.5 * inputs.ME * p["vx"][0] ** 2 / inputs.QE
+    x = (p["cell"][0] + p["off"][0]) * spec["d"] / spec["n_cells"]
+    # O(dt) discretisation error: the first kick (beta = 1 at rest) gives
+    # a dt in one step, worth m (a dt)^2 / 2, while the marker moves one
+    # cell; the staggered velocity adds at most half a cell of field energy.
+    first_kick = 0.5 * inputs.ME * (a * spec["dt"]) ** 2 / inputs.QE
+    assert abs(e - spec["V"] * x / spec["d"]) < first_kick + 2 * spec["V"] / spec["n_cells"]
+    assert e == pytest.approx(spec["V"], rel=0.03)
+
+
+def test_displacement_bounded_by_speed_limit(oracle_mod):
+    """|dx| <= beta v dt <= v0 dt per step (Sec. II.B)."""
+    spec, _ = inputs.small_gap_config()
+    st = inputs.gap_state(3000, spec, rng_seed=5, e_lo=0.01, e_hi=300.0)
+    o = oracle_mod.Oracle(spec, 64)
+    o.load(0, st)
+    o.step(1)
+    p = o.particles(0)
+    old = p["id"] < 3000  # births sit at their parent's position
+    x0 = (st["cell"] + st["off"].astype(np.float64))
+    idx = np.searchsorted(st["id"], p["id"][old])
+    moved = np.abs((p["cell"][old] + p["off"][old]) - x0[idx])
+    bound = spec["vlim_e"] * spec["dt"] / (spec["d"] / spec["n_cells"])
+    assert np.all(moved <= bound * (1 + 1e-12))
+
+
+# ---------------------------------------------------------------------------
+# Null-collision Monte Carlo (Sec. III, Eq. SLPICcollisionNumber)
+# ---------------------------------------------------------------------------
+
+def _beam_step(oracle_mod, eps, vlim, n=200000, scale=(1, 1, 1), p_torr=1.0):
+    spec = inputs.gap_spec(n_cells=1 << 14, V=0.0, vlim_e=vlim, field_mode=0,
+                           pd_torr_cm=p_torr, table=inputs.make_table(scale=scale))
+    spec["dt"] = 4e-12
+    v = math.sqrt(2 * inputs.QE * eps / inputs.ME)
+    o = oracle_mod.Oracle(spec, 64)
+    st = inputs.beam_state(n, spec, v)
+    o.load(0, st)
+    o.step(1)
+    return spec, o, float(st["vx"][0])
+
+
+def _energy(v):
+    return 0.5 * inputs.ME * v * v / inputs.QE
+
+
+@pytest.mark.parametrize("eps,vlim", [(20.0, math.inf), (20.0, 4e5), (3.0, 2e5), (120.0, 1e6)])
+def test_collision_rate_equals_beta_nu_dt(oracle_mod, eps, vlim):
+    """Per step, a marker collides through process k with probability
+    n_g sigma_k(eps) beta v dt (the physical mean free path is kept), and the
+    null-collision candidates are drawn with the majorant probability P0."""
+    n = 200000
+    spec, o, v = _beam_step(oracle_mod, eps, vlim, n)
+    h = o.history()[0]
+    c = o.constants()
+    ng = spec["p_Pa"] / (inputs.KB * spec["T_K"])
+    vb = min(v, vlim)
+    el, ex, io = [float(s[0]) for s in inputs.argon_like_xsec(np.array([eps]))]
+    p = np.array([el, ex, io]) * ng * vb * spec["dt"]
+    for k in range(3):
+        sd = math.sqrt(n * p[k] * (1 - p[k])) + 1
+        assert abs(h["n_coll"][k] - n * p[k]) < 5 * sd, (k, h["n_coll"][k], n * p[k])
+    sd = math.sqrt(n * c["P0"] * (1 - c["P0"]))
+    assert abs(h["n_candidates"] - n * c["P0"]) < 5 * sd
+    assert c["P0"] >= p.sum()
+
+
+def test_free_path_is_exponential_and_independent_of_beta(oracle_mod):
+    """The distance to the first collision is exponential with mean
+    lambda = 1/(n_g sigma) whatever beta is (Sec. III: SLPIC preserves the
+    physical mean free path)."""
+    eps = 6.0
+    v = math.sqrt(2 * inputs.QE * eps / inputs.ME)
+    ng = 1 * inputs.TORR / (inputs.KB * 300.0)
+    sig = float(sum(inputs.argon_like_xsec(np.array([eps])))[0])
+    lam = 1.0 / (ng * sig)
+    for vlim in (math.inf, v / 4):
+        spec = inputs.gap_spec(n_cells=1 << 15, V=0.0, vlim_e=vlim, field_mode=0, d=0.2, pd_torr_cm=20.0)
+        vb = min(v, vlim)
+        spec["dt"] = 0.02 * lam / vb  # ~2% collision probability per step
+        n = 20000
+        o = oracle_mod.Oracle(spec, 64)
+        st = inputs.beam_state(n, spec, v)
+        o.load(0, st)
+        first = np.full(n, -1)
+        for k in range(1, 600):
+            o.step(1)
+            p = o.particles(0)
+            idx = p["id"][p["id"] < n]
+            changed = (p["vy"][: idx.size] != 0.0) | (p["vz"][: idx.size] != 0.0)
+            newly = idx[changed & (first[idx] < 0)]
+            first[newly] = k
+        done = first > 0
+        assert done.mean() > 0.99
+        dist = first[done] * vb * spec["dt"]
+        assert dist.mean() == pytest.approx(lam, rel=5 / math.sqrt(done.sum()))
+        # geometric in steps = discretised exponential
+        p_step = vb * spec["dt"] / lam
+        edges = np.unique(np.ceil(stats.geom(p_step).ppf(np.linspace(0, 0.99, 25))).astype(int))
+        edges = np.append(edges, 10**9)
+        obs = np.histogram(first[done], bins=edges)[0]
+        cdf = stats.geom(p_step).cdf(edges - 1)
+        expct = np.diff(cdf) / (cdf[-1] - cdf[0]) * obs.sum()
+        assert stats.chisquare(obs, expct).pvalue > 1e-3
+
+
+# ---------------------------------------------------------------------------
+# Collision kinematics (Sec. IV: Vahedi-Surendra elastic, isotropic
+# excitation with the threshold removed, ionization products)
+# ---------------------------------------------------------------------------
+
+def test_elastic_angles_follow_vahedi_surendra_cross_section(oracle_mod):
+    """Scattering angles follow the differential cross section
+    eps / (4 pi (1 + eps sin^2(chi/2)) ln(1 + eps)); the energy after the
+    collision is eps (1 - 2 m/M (1 - cos chi))."""
+    eps = 40.0
+    spec, o, v = _beam_step(oracle_mod, eps, math.inf, n=300000, scale=(1, 0, 0), p_torr=30.0)
+    p = o.particles(0)
+    hit = (p["vy"] != 0) | (p["vz"] != 0)
+    assert hit.sum() > 5000
+    speed = np.sqrt(p["vx"] ** 2 + p["vy"] ** 2 + p["vz"] ** 2)[hit]
+    cos = p["vx"][hit] / speed
+    pdf = lambda c: (eps / 2) / ((1 + eps * (1 - c) / 2) * math.log1p(eps))
+    assert integrate.quad(pdf, -1, 1)[0] == pytest.approx(1.0, rel=1e-10)
+    mean = integrate.quad(lambda c: c * pdf(c), -1, 1)[0]
+    assert cos.mean() == pytest.approx(mean, abs=5 * cos.std() / math.sqrt(cos.size))
+    cdf = lambda c: np.log1p(eps * (1 - np.clip(c, -1, 1)) / 2) / math.log1p(eps)
+    ks = stats.kstest(cos, lambda c: 1 - cdf(c))
+    assert ks.pvalue > 1e-3
+    e_new = 0.5 * inputs.ME * speed ** 2 / inputs.QE
+    e_exp = _energy(v) * (1 - 2 * inputs.ME / inputs.M_AR * (1 - cos))
+    assert np.allclose(e_new, e_exp, rtol=1e-12)
+
+
+def test_excitation_removes_threshold_isotropically(oracle_mod):
+    eps = 30.0
+    spec, o, v = _beam_step(oracle_mod, eps, math.inf, n=200000, scale=(0, 1, 0), p_torr=30.0)
+    p = o.particles(0)
+    hit = (p["vy"] != 0) | (p["vz"] != 0)
+    assert hit.sum() > 2000
+    speed2 = p["vx"] ** 2 + p["vy"] ** 2 + p["vz"] ** 2
+    e_new = 0.5 * inputs.ME * speed2[hit] / inputs.QE
+    assert np.allclose(e_new, _energy(v) - inputs.E_EXC, rtol=1e-12)
+    cos = p["vx"][hit] / np.sqrt(speed2[hit])
+    assert stats.kstest(cos, stats.uniform(-1, 2).cdf).pvalue > 1e-3
+
+
+def test_ionization_shares_energy_and_births_conserve_flux_weight(oracle_mod):
+    """Ionization: primary + secondary energies = eps - 15.76 eV; the born
+    electron and ion carry the primary's flux weight (Sec. III); the ion gets a
+    gas-temperature Maxwellian."""
+    eps = 100.0
+    spec, o, v = _beam_step(oracle_mod, eps, math.inf, n=200000, scale=(0, 0, 1), p_torr=30.0)
+    e = o.particles(0)
+    i = o.particles(1)
+    n0 = 200000
+    prim = (e["id"] < n0) & ((e["vy"] != 0) | (e["vz"] != 0))
+    born = e["id"] >= n0
+    assert born.sum() == prim.sum() == i["id"].size > 1000
+    # births are appended in parent order at the parent's position
+    assert np.array_equal(e["cell"][born], e["cell"][prim])
+    assert np.array_equal(e["off"][born], e["off"][prim])
+    ek = lambda a, m: 0.5 * inputs.ME * (a["vx"][m] ** 2 + a["vy"][m] ** 2 + a["vz"][m] ** 2) / inputs.QE
+    assert np.allclose(ek(e, prim) + ek(e, born), _energy(v) - inputs.E_ION, rtol=1e-12)
+    assert np.array_equal(e["wj"][born], e["wj"][prim])
+    h = o.history()[0]
+    assert h["w_live"][1] == pytest.approx(h["w_ionz"], rel=1e-15)
+    kT_M = inputs.KB * spec["T_K"] / inputs.M_AR
+    for comp in ("vx", "vy", "vz"):
+        var = np.var(i[comp])
+        assert var == pytest.approx(kT_M, rel=6 * math.sqrt(2.0 / i[comp].size))
+
+
+# ---------------------------------------------------------------------------
+# Ledgers: markers, flux weights and deposited charge
+# ---------------------------------------------------------------------------
+
+def test_marker_and_weight_ledger(oracle_mod):
+    spec, _ = inputs.small_gap_config()
+    spec["gamma_se"] = 0.5
+    e = inputs.gap_state(4000, spec, rng_seed=9, e_lo=1.0, e_hi=100.0, wj_spread=1.0)
+    ions = inputs.gap_state(3000, spec, rng_seed=10, e_lo=0.01, e_hi=40.0, species=1)
+    ions["vx"] = -np.abs(ions["vx"])
+    o = oracle_mod.Oracle(spec, 64)
+    o.load(0, e)
+    o.load(1, ions)
+    n_prev = [4000, 3000]
+    w_prev = [float(e["wj"].astype(np.float64).sum()), float(ions["wj"].astype(np.float64).sum())]
+    for _ in range(30):
+        o.step(1)
+        h = o.history()[-1]
+        born_e = h["n_coll"][2] + h["n_see"]
+        born_i = h["n_coll"][2]
+        assert h["n_live"][0] == n_prev[0] - h["n_abs"][0].sum() + born_e
+        assert h["n_live"][1] == n_prev[1] - h["n_abs"][1].sum() + born_i
+        assert h["w_live"][0] == pytest.approx(w_prev[0] - h["w_abs"][0].sum() + h["w_ionz"] + h["w_see"], rel=1e-12)
+        assert h["w_live"][1] == pytest.approx(w_prev[1] - h["w_abs"][1].sum() + h["w_ionz"], rel=1e-12)
+        n_prev = list(h["n_live"])
+        w_prev = list(h["w_live"])
+        for s in (0, 1):
+            q = o.charge(s)
+            p = o.particles(s)
+            vl = spec["vlim_e"] if s == 0 else math.inf
+            v = np.sqrt(p["vx"] ** 2 + p["vy"] ** 2 + p["vz"] ** 2)
+            beta = np.where(v > vl, vl / np.where(v > 0, v, 1), 1.0)
+            Q = np.rint(beta * p["wj"] * 2.0 ** spec["charge_shift"]).astype(np.int64)
+            assert int(q.sum()) == int(Q.sum())
+    hist = o.history()
+    assert hist["n_see"].sum() > 0 and hist["n_coll"][:, 2].sum() > 0
+
+
+def test_deposit_is_linear_weighting_to_24_bits(oracle_mod):
+    """Deposit (Eq. Ansatz with a linear shape): node k gets w_p (1 - f), node
+    k+1 gets w_p f, f quantised to 24 bits."""
+    spec = vacuum(inputs.gap_spec(n_cells=32, V=0.0, vlim_e=math.inf))
+    st = inputs.rest_state(1, cell=7, off=0.375)
+    o = oracle_mod.Oracle(spec, 64)
+    o.load(0, st)
+    o.deposit()
+    q = o.charge(0)
+    Q = 2 ** spec["charge_shift"]
+    assert q[7] == Q - int(Q * 0.375) and q[8] == int(Q * 0.375)
+    assert q.sum() == Q and np.count_nonzero(q) == 2
+
+
+def test_flux_is_conserved_without_collisions(oracle_mod):
+    """Without collisions every seeded electron leaves through an electrode:
+    the time-integrated flux of w_j equals what was seeded (Eq. j)."""
+    spec, _ = inputs.small_gap_config()
+    spec = vacuum(spec)
+    o = oracle_mod.Oracle(spec, 64)
+    o.seed(0, 500, 0, e0=1.0, wj=1.5)
+    o.step(400)
+    h = o.history()
+    assert h[-1]["n_live"][0] == 0
+    assert h["w_abs"][:, 0, :].sum() == pytest.approx(500 * 1.5, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Field solve
+# ---------------------------------------------------------------------------
+
+def test_poisson_vacuum_and_uniform_charge(oracle_mod):
+    """rho = 0 gives the linear potential and E = -V/d; a uniform charge gives
+    the parabola V x/d + rho x (d - x)/(2 eps0), which the discrete equations
+    reproduce exactly (the second difference of a quadratic is exact)."""
+    N, V = 40, 50.0
+    spec = vacuum(inputs.gap_spec(n_cells=N, V=V, vlim_e=math.inf, field_mode=1))
+    spec["charge_shift"] = 20
+    o = oracle_mod.Oracle(spec, 64)
+    o.load(1, inputs.rest_state(0))
+    o.deposit()
+    o.solve_field()
+    phi, E = o.field()
+    x = np.linspace(0, spec["d"], N + 1)
+    assert np.allclose(phi, V * x / spec["d"], rtol=0, atol=1e-12 * V)
+    assert np.allclose(E, -V / spec["d"], rtol=1e-12)
+    # one ion at rest on every interior node
+    st = {k: np.concatenate([inputs.rest_state(1, cell=c)[k] for c in range(1, N)]) for k in ("cell", "off", "vx", "vy", "vz", "wj")}
+    st["id"] = np.arange(N - 1, dtype=np.uint32)
+    st["wj"] = np.full(N - 1, 1e9, np.float32)
+    o.load(1, st)
+    o.deposit()
+    o.solve_field()
+    phi, E = o.field()
+    dx = spec["d"] / N
+    rho = inputs.QE * 1e9 / dx
+    exact = V * x / spec["d"] + rho * x * (spec["d"] - x) / (2 * 8.8541878128e-12)
+    assert np.allclose(phi, exact, rtol=1e-9, atol=1e-9 * np.abs(exact).max())
+    Eexact = -(V / spec["d"] + rho * (spec["d"] - 2 * x) / (2 * 8.8541878128e-12))
+    assert np.allclose(E[1:N], Eexact[1:N], rtol=1e-8, atol=1e-8 * np.abs(Eexact).max())
+
+
+# ---------------------------------------------------------------------------
+# Brute force on a handful of markers against an independent restatement
+# ---------------------------------------------------------------------------
+
+def test_tiny_brute_force_against_scalar_restatement(oracle_mod):
+    spec, _ = inputs.small_gap_config()
+    spec = dict(spec, n_cells=32, gamma_se=0.6, charge_shift=30, p_Pa=spec["p_Pa"] * 30)
+    spec["dt"] = (spec["d"] / 32) / spec["vlim_e"]
+    e = inputs.gap_state(8, spec, rng_seed=11, e_lo=5.0, e_hi=150.0)
+    ions = inputs.gap_state(8, spec, rng_seed=12, e_lo=1.0, e_hi=30.0, species=1)
+    ions["vx"] = -np.abs(ions["vx"])
+    o = oracle_mod.Oracle(spec, 64)
+    o.load(0, e)
+    o.load(1, ions)
+    ref = sref.ScalarSim(spec)
+    dx = spec["d"] / spec["n_cells"]
+    for s, st in ((0, e), (1, ions)):
+        ref.parts[s] = [[(float(st["cell"][i]) + float(st["off"][i])) * dx, float(st["vx"][i]), float(st["vy"][i]),
+                         float(st["vz"][i]), float(st["wj"][i]), int(st["id"][i])] for i in range(8)]
+        ref.next_id[s] = 8
+    events = 0
+    for _ in range(20):
+        o.step(1)
+        ref.step()
+        h = o.history()[-1]
+        r = ref.hist[-1]
+        assert list(h["n_live"]) == r["n_live"]
+        assert [list(a) for a in h["n_abs"]] == r["n_abs"]
+        assert list(h["n_coll"]) == r["n_coll"]
+        assert h["n_see"] == r["n_see"]
+        events += sum(r["n_coll"]) + r["n_see"]
+        for s in (0, 1):
+            p = o.particles(s)
+            q = np.array(ref.parts[s]).reshape(-1, 6)
+            assert np.array_equal(p["id"], q[:, 5].astype(np.uint32))
+            assert np.allclose((p["cell"] + p["off"]) * dx, q[:, 0], rtol=0, atol=1e-9 * dx)
+            for j, k in enumerate(("vx", "vy", "vz")):
+                assert np.allclose(p[k], q[:, 1 + j], rtol=1e-9, atol=1e-6)
+            assert np.array_equal(o.charge(s), ref.charge[s]) or \
+                np.abs(o.charge(s) - ref.charge[s]).max() <= 2
+        phi, E = o.field()
+        assert np.allclose(phi, ref.phi, rtol=1e-9, atol=1e-9 * spec["V"])
+    assert events > 5
+
+
+# ---------------------------------------------------------------------------
+# Townsend multiplication (Sec. II.A): anode electrons per seed grow as
+# exp(alpha d) in a uniform field without secondary emission
+# ---------------------------------------------------------------------------
+
+@pytest.mark.slow
+def test_townsend_growth_is_exponential_in_gap_length(oracle_mod):
+    E_field = 3.0e4  # V/m
+    dx = 0.01 / 256
+    vlim = 4 * inputs.ion_speed(300.0)
+    lnM = []
+    for d in (0.003, 0.006, 0.009):
+        V = E_field * d
+        N = int(round(d / dx))
+        spec = inputs.gap_spec(n_cells=N, V=V, d=d, vlim_e=vlim, gamma_se=0.0, field_mode=0)
+        spec["p_Pa"] = inputs.TORR  # 1 Torr whatever d is
+        spec["dt"] = dx / vlim
+        vals = []
+        for seed in range(4):
+            spec["seed"] = seed
+            o = oracle_mod.Oracle(spec, 64)
+            o.seed(0, 300, 0, e0=1.0)
+            for _ in range(200):  # until every electron has left the gap
+                o.step(100)
+                if o.count(0) == 0:
+                    break
+            h = o.history()
+            assert h[-1]["n_live"][0] == 0
+            vals.append(h["w_abs"][:, 0, 1].sum() / 300.0)
+        lnM.append((math.log(np.mean(vals)), np.std(np.log(vals)) / 2))
+    a1 = lnM[1][0] - lnM[0][0]
+    a2 = lnM[2][0] - lnM[1][0]
+    err = math.sqrt(lnM[0][1] ** 2 + 2 * lnM[1][1] ** 2 + lnM[2][1] ** 2) + 0.05
+    assert a1 > 0.3 and a2 > 0.3
+    assert abs(a1 - a2) < 4 * err, (a1, a2, err)
