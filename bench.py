@@ -1,0 +1,330 @@
+"""Throughput of the SLPIC-MCC step on GB300: marker-steps per second.
+
+Workload (default): the push + MCC microbenchmark gap -- 3.2e7 electrons
+uniform over a 1 cm gap of 4096 cells at 1 Torr and 300 V, energies
+log-uniform over 0.1-200 eV, isotropic, v_lim = 1/8 of the median speed,
+dt = dx / v_lim, three-process null-collision MCC on a 4096-bin table, ion
+births and secondary emission live, fixed-point deposit and the Poisson solve
+every step.  A step is one pass of the whole step over every live marker.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own
+independent instance (instances do not exchange data), so scaling is weak.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_MARKER_STEP = 48  # read 28 B of state, write the 20 B that change
+L2_BYTES = 129 * 2**20
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--markers", type=int, default=32_000_000)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        v = d.get("hbm_gbs")
+        if isinstance(v, dict):
+            v = v.get("value")
+        if v:
+            return float(v), "measured"
+    except Exception:
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def push_traffic():
+    """DRAM bytes per marker of the particle kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    src = os.path.join(ROOT, "paper_2103_12194_gb300", "csrc", "push.cu")
+    path = os.path.join(ROOT, "profiles", "push_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if d.get("push_cu_sha256_16") == h:
+            return float(d["dram_bytes_per_marker"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", "slpic_clocks_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        try:
+            rows = [l.split(",") for l in open(self.path).read().strip().splitlines()]
+        except Exception:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 7:
+                continue
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(spec, n_markers, seconds):
+    """The oracle (FP64, as it stands, one host thread) on a bounded sample of
+    the same workload: n markers drawn like the GPU's, a few steps."""
+    import oracle
+    from paper_2103_12194_gb300 import inputs
+    n = min(n_markers, 200_000)
+    st = inputs.gap_state(n, spec, rng_seed=1, e_lo=0.1, e_hi=200.0)
+    o = oracle.Oracle(spec, precision=64)
+    o.load(0, st)
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter()
+    per_step = max(t1 - t0, 1e-6)
+    k = max(1, min(200, int(seconds / per_step)))
+    t0 = time.perf_counter()
+    o.step(k)
+    dt = time.perf_counter() - t0
+    h = o.history()
+    ms = int(h["marker_steps"][1:].sum())
+    return {"value": ms / dt, "unit": "marker-steps/s", "cores": 1, "kind": "oracle",
+            "sample": "%d of the workload's electrons (same draw), %d steps, FP64 oracle, "
+                      "single host thread, %.1f s" % (n, k, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2103_12194_gb300 import inputs
+    spec, _ = inputs.microbench_config(n_markers=args.markers)
+    per_step_s = args.cpu_seconds / max(1, args.steps + args.warmup)
+    cb = cpu_baseline(spec, args.markers, max(1.0, per_step_s * args.steps))
+    line = {"impl": "reference", "metric": "marker-steps/s", "value": cb["value"],
+            "unit": "marker-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "push+MCC microbenchmark gap (CPU oracle sample)",
+                       "markers": args.markers, "cells": 4096},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "marker-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2103_12194_gb300 import build, inputs, slpic
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    stream = torch.cuda.current_stream()
+    spec, run = inputs.microbench_config(n_markers=args.markers, seed=rank)
+    spec["instance"] = 0
+    n = args.markers
+    cap_e = int(n * 1.25)
+    cap_i = max(1 << 20, n // 4)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- device-resident run ------------------------------------------
+    sim = slpic.Simulation(1, device=local, stream=stream)
+    sim.configure(0, spec, capacity=(cap_e, cap_i))
+    sim.seed(0, slpic.ELECTRON, n, slpic.SEED_GAP, e_lo=run["e_lo"], e_hi=run["e_hi"])
+    sim.step(args.warmup)
+    sim.synchronize()
+    sim.set_profiling(True)
+    t_before = sim.tallies(0)
+    ms_before = int(t_before["marker_steps"])
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        sim.step(args.steps)
+        launches += sim.launch_count()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    sim.synchronize()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    push_ms, push_launches = sim.profile()
+    t_after = sim.tallies(0)
+    marker_steps = int(t_after["marker_steps"]) - ms_before
+    times = [elapsed_ms]
+    counts = [marker_steps]
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([elapsed_ms, float(marker_steps)], device="cuda")
+        allt = [torch.zeros_like(tt) for _ in range(world)]
+        dist.all_gather(allt, tt)
+        times = [float(x[0]) for x in allt]
+        counts = [float(x[1]) for x in allt]
+    t_max = max(times) / 1e3
+    value = sum(counts) / t_max
+    avg_push_s = push_ms / 1e3 / max(1, push_launches)
+    markers_per_launch = marker_steps / max(1, push_launches)
+    achieved = BYTES_PER_MARKER_STEP * markers_per_launch / avg_push_s / 1e9
+    peak, peak_kind = peaks()
+    tr = push_traffic()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_kind,
+            "traffic": (tr * markers_per_launch if tr is not None else None),
+            "kernel": "k_push", "push_share_of_step": push_ms / elapsed_ms if elapsed_ms else None}
+    state_bytes = 28 * n
+    sim.set_profiling(False)
+    sim.close()
+    del sim
+
+    # ---- end to end through the C ABI with host buffers -----------------
+    e2e = None
+    if not args.no_e2e:
+        host = inputs.gap_state(n, spec, rng_seed=100 + rank, e_lo=run["e_lo"], e_hi=run["e_hi"])
+        pinned = {}
+        for k, a in host.items():
+            t = torch.empty(a.shape, dtype={np.int32: torch.int32, np.float32: torch.float32,
+                                            np.uint32: torch.int32}[a.dtype.type],
+                            pin_memory=True)
+            t.numpy().view(a.dtype)[:] = a
+            pinned[k] = t.numpy().view(a.dtype)
+        del host
+        sim = slpic.Simulation(1, device=local, stream=stream)
+        sim.configure(0, spec, capacity=(cap_e, cap_i))
+        sim.load(0, slpic.ELECTRON, pinned)   # build and warm the context
+        sim.step(args.warmup)
+        sim.synchronize()
+        dens = np.empty(spec["n_cells"] + 1)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.reset_counters(0)
+        sim.load(0, slpic.ELECTRON, pinned)
+        sim.load(0, slpic.ION, {k: v[:0] for k, v in pinned.items()})
+        sim.step(args.steps)
+        hist = sim.history(0, capacity=args.steps)
+        dens = sim.density(0, slpic.ELECTRON)
+        t1 = time.perf_counter()
+        barrier()
+        ms_e2e = int(hist["marker_steps"].sum())
+        d2h = hist.nbytes + dens.nbytes
+        e2e = {"value": ms_e2e / (t1 - t0), "unit": "marker-steps/s",
+               "h2d_bytes_per_step": state_bytes / args.steps,
+               "d2h_bytes_per_step": d2h / args.steps,
+               "note": "host SoA in pinned memory loaded through slpic_load_particles, "
+                       "K steps, per-step tallies and density read back"}
+        sim.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(spec, n, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": "marker-steps/s", "value": value, "unit": "marker-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "push+MCC microbenchmark gap: 3.2e7 electrons log-uniform "
+                                   "0.1-200 eV, 4096 cells, 1 Torr, 300 V, Poisson on",
+                       "markers": n, "cells": spec["n_cells"], "instances_per_gpu": 1,
+                       "parallelism": "independent instance per GPU" if world > 1 else "1 GPU",
+                       "l2": "inputs larger than L2 (%.2f GB of markers > %.0f MB)"
+                             % (state_bytes / 1e9, L2_BYTES / 2**20)},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

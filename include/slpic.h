@@ -1,0 +1,236 @@
+/*
+ * slpic.h -- C ABI of libslpic, a GB300 (sm_103a) implementation of the
+ * per-marker step of speed-limited particle-in-cell with Monte-Carlo
+ * collisions (SLPIC-MCC) for a 1D3V argon-filled parallel-plate gap
+ * (Theis, Werner, Jenkins, Cary, "Computing the Paschen curve for argon with
+ * speed-limited particle-in-cell simulation").
+ *
+ * One context holds one or more independent instances (gaps at their own
+ * pressure and voltage); every instance has an electron and an Ar+ species.
+ * All instances advance together in one batched launch per phase.
+ *
+ * Conventions used by every call:
+ *  - SI units, except energies, which are in eV.
+ *  - Cathode at x = 0 (phi = 0), anode at x = d (phi = V); E_x = -dphi/dx.
+ *  - Species index: SLPIC_ELECTRON (0) or SLPIC_ION (1).
+ *  - Marker storage (FP32 path): struct-of-arrays of int32 cell in [0, N),
+ *    float offset in [0, 1) inside the cell, float vx, vy, vz [m/s], float
+ *    flux weight w_j (physical particles represented per crossing, constant
+ *    along a trajectory, Sec. II.B), uint32 id.  Bit 31 of the id is the
+ *    generation flag (0: descends from a seeded electron without passing
+ *    through secondary emission); bits 0-30 are a serial number unique within
+ *    the species.
+ *  - Host pointers are read or written only during the call; the library
+ *    never keeps them.  Device pointers passed to *_device calls must point
+ *    to memory of the context's device and stay valid during the call.
+ *  - Every call returns SLPIC_OK (0) or a negative SLPIC_ERR_* code and then
+ *    leaves a message in slpic_last_error().  Errors raised on the GPU during
+ *    slpic_step (capacity, wait time-out) are latched in device memory and
+ *    returned by the next call that synchronises (reads, slpic_synchronize);
+ *    after such an error the markers keep the state they had before the
+ *    failed step and further steps are no-ops until slpic_clear_error().
+ *  - A context is not thread-safe; use one host thread per context.
+ */
+#ifndef SLPIC_H
+#define SLPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SLPIC_OK 0
+#define SLPIC_ERR_INVALID_ARG (-1)
+#define SLPIC_ERR_STATE (-2)
+#define SLPIC_ERR_CAPACITY (-3)
+#define SLPIC_ERR_CUDA (-4)
+#define SLPIC_ERR_TIMEOUT (-5)
+#define SLPIC_ERR_NUMERIC (-6)
+
+#define SLPIC_ELECTRON 0
+#define SLPIC_ION 1
+
+#define SLPIC_FIELD_FROZEN 0  /* vacuum field -V/d at every node, never solved */
+#define SLPIC_FIELD_POISSON 1 /* 1D Poisson solve after every step's deposit */
+
+#define SLPIC_SEED_CATHODE 0  /* uniform in cell 0, energy e0, forward hemisphere */
+#define SLPIC_SEED_REST 1     /* at x = 0 with zero velocity (the paper's seeding) */
+#define SLPIC_SEED_GAP 2      /* uniform over the gap, energy log-uniform, isotropic */
+#define SLPIC_SEED_THERMAL 3  /* uniform over the gap, gas-temperature Maxwellian */
+
+typedef struct slpic_ctx slpic_ctx;
+
+/* FP32 marker arrays (host or device pointers, as the call states). */
+typedef struct {
+  int32_t* cell;
+  float* off;
+  float* vx;
+  float* vy;
+  float* vz;
+  float* wj;
+  uint32_t* id;
+} slpic_soa_f32;
+
+/* What happened in one step of one instance (or, from slpic_read_tallies, the
+ * sums over all steps since the last seed/load).  Counts are exact; weight
+ * sums are exact integer sums of w_j in units of 2^-charge_shift converted to
+ * double at read time. */
+typedef struct {
+  int64_t step;            /* index of the step (last step for sums) */
+  int64_t n_live[2];       /* live markers after the step */
+  double w_live[2];        /* sum of w_j of live markers after the step */
+  int64_t n_coll[3];       /* real collisions: elastic, excitation, ionization */
+  int64_t n_candidates;    /* null-collision candidates (u1 < P0) */
+  int64_t n_abs[2][2];     /* absorbed [species][0 cathode, 1 anode] */
+  double w_abs[2][2];      /* their sum of w_j (flux through the electrode, Eq. j) */
+  int64_t n_see;           /* secondary electrons emitted at the cathode */
+  double w_see;
+  double w_ionz;           /* sum of w_j of ionizing electrons (= born ions) */
+  double w_cath_ion;       /* sum of w_j of ions absorbed at the cathode */
+  double w_cath_ion_gen0;  /* same, first-generation ions only */
+  int64_t n_clamp;         /* energies clamped at 0 after an inelastic event */
+  int64_t n_majorant;      /* electrons whose beta*v exceeded the majorant's cap */
+  int64_t marker_steps;    /* markers advanced (both species) */
+} slpic_tallies;
+
+/* Library version as an integer MMmmpp. */
+int slpic_version(void);
+
+/* Message of the last failed call on ctx (owned by ctx; valid until the next
+ * call).  With ctx = NULL: the last failure of slpic_create. */
+const char* slpic_last_error(const slpic_ctx* ctx);
+
+/* Create a context on CUDA device `device` with `n_instances` >= 1 instances.
+ * Nothing is allocated on the device until the first seed/load/step. */
+int slpic_create(slpic_ctx** out, int device, int n_instances);
+int slpic_destroy(slpic_ctx* ctx);
+
+/* Stream for all device work of ctx (a cudaStream_t, e.g. PyTorch's current
+ * stream); NULL = the legacy default stream. */
+int slpic_set_stream(slpic_ctx* ctx, void* cuda_stream);
+
+/* Gap of instance `inst` (Sec. IV): width d [m], n_cells >= 2 uniform cells,
+ * anode potential V [V], field mode (SLPIC_FIELD_*), electrode area [m^2]
+ * that the flux weights refer to (charge density = sum e w_p / (area dx)). */
+int slpic_set_gap(slpic_ctx* ctx, int inst, double d, int n_cells, double V,
+                  int field_mode, double area);
+/* Change only the anode potential (allowed between runs, e.g. bisection over
+ * V); the vacuum field is reset to -V/d. */
+int slpic_set_voltage(slpic_ctx* ctx, int inst, double V);
+/* Background argon at rest: pressure [Pa], temperature [K]; n_g = p/(k T). */
+int slpic_set_gas(slpic_ctx* ctx, int inst, double p_Pa, double T_K);
+/* Electron-argon cross sections [m^2] at the nodes of an octave-uniform
+ * energy grid: node j = o 2^log2_sub + m sits at 2^(lo_exp2 + o)
+ * (1 + m / 2^log2_sub) eV, j = 0 .. octaves 2^log2_sub (inclusive).  Values
+ * are interpolated linearly in energy and held constant outside the grid.
+ * Elastic (Vahedi-Surendra angles), one excitation level (threshold e_ex, eV)
+ * and ionization (threshold e_io, eV), Sec. IV.  Host arrays, copied.
+ * inst = -1 sets every instance. */
+int slpic_set_cross_sections(slpic_ctx* ctx, int inst, int lo_exp2,
+                             int log2_sub, int octaves, const float* sig_el,
+                             const float* sig_ex, double e_ex,
+                             const float* sig_io, double e_io);
+/* Species: mass [kg], charge [C], speed limit v_lim [m/s] of Eq. betaAbrupt
+ * (beta = min(1, v_lim/|v|); v_lim <= 0 or +inf gives beta = 1, i.e. PIC),
+ * capacity = maximum live markers.  Only electrons collide (Sec. IV). */
+int slpic_set_species(slpic_ctx* ctx, int inst, int species, double mass,
+                      double charge, double v_lim, int64_t capacity);
+/* Ion-induced secondary-electron yield gamma at the cathode (constant; the
+ * emitted electron starts at x = 0 with zero velocity, Sec. IV). */
+int slpic_set_emission(slpic_ctx* ctx, int inst, double gamma_se);
+/* Time step [s]. */
+int slpic_set_dt(slpic_ctx* ctx, int inst, double dt);
+/* Random stream: 64-bit Philox key of the instance. */
+int slpic_set_seed(slpic_ctx* ctx, int inst, uint64_t seed);
+/* Fixed point of the deposit: one unit of charge = 2^-shift flux weights
+ * (0 <= shift <= 40; the weights times 2^shift must stay below 2^39). */
+int slpic_set_charge_shift(slpic_ctx* ctx, int inst, int shift);
+
+/* Time-step rules of Sec. IV for a gap of n_cells cells at voltage V:
+ * mode 0 (SLPIC) dt = dx / v0 with v0 = sqrt(2 e V / m_ion); mode 1 (PIC)
+ * dt = dx / sqrt(2 e V / m_e).  Host arithmetic only. */
+int slpic_suggest_dt(double d, int n_cells, double V, double m_ion, int mode,
+                     double* dt_out);
+
+/* Seed n markers of `species` on the device (appended to the live ones),
+ * drawn from the instance's Philox stream (counter word 1 = 0xFFFFFFFF):
+ * mode SLPIC_SEED_*; e0 [eV] for SEED_CATHODE; [e_lo, e_hi] eV for SEED_GAP;
+ * every marker gets flux weight wj.  Resets the step counter and tallies. */
+int slpic_seed(slpic_ctx* ctx, int inst, int species, int64_t n, int mode,
+               double e0, double e_lo, double e_hi, double wj);
+/* Replace the markers of `species` by n markers from host arrays (FP32 SoA);
+ * next_id = serial number of the next born marker.  Cells must lie in
+ * [0, N) and offsets in [0, 1).  Resets the step counter and tallies. */
+int slpic_load_particles(slpic_ctx* ctx, int inst, int species,
+                         const slpic_soa_f32* host, int64_t n,
+                         uint32_t next_id);
+/* Same from device arrays (device-to-device copies, no host staging). */
+int slpic_load_particles_device(slpic_ctx* ctx, int inst, int species,
+                                const slpic_soa_f32* dev, int64_t n,
+                                uint32_t next_id);
+/* Reset the step counter and tallies without touching the markers. */
+int slpic_reset_counters(slpic_ctx* ctx, int inst);
+
+/* Advance every instance by n_steps steps (asynchronous on the context's
+ * stream).  One step: gather, speed-limited kick and drift, absorption and
+ * secondary emission, null-collision MCC with births, stable compaction and
+ * append, fixed-point deposit, field solve, tallies. */
+int slpic_step(slpic_ctx* ctx, int64_t n_steps);
+/* Wait for the context's work; returns the latched device error, if any. */
+int slpic_synchronize(slpic_ctx* ctx);
+/* Forget a latched device error (markers are as before the failed step). */
+int slpic_clear_error(slpic_ctx* ctx);
+
+/* Reads (synchronise first).  Host buffers are caller-owned. */
+int slpic_count(slpic_ctx* ctx, int inst, int species, int64_t* n_out);
+int slpic_read_particles(slpic_ctx* ctx, int inst, int species,
+                         const slpic_soa_f32* host, int64_t capacity,
+                         int64_t* n_out);
+/* Fixed-point deposit of the last step (n_cells + 1 int64 node values). */
+int slpic_read_charge(slpic_ctx* ctx, int inst, int species, int64_t* host,
+                      int64_t n);
+/* Number density at the nodes [m^-3] of the last step's deposit (boundary
+ * nodes count half a cell). */
+int slpic_read_density(slpic_ctx* ctx, int inst, int species, double* host,
+                       int64_t n);
+/* Potential [V] and field [V/m] at the n_cells + 1 nodes. */
+int slpic_read_field(slpic_ctx* ctx, int inst, double* phi, double* E,
+                     int64_t n);
+/* Sums over all steps since the last seed/load/reset. */
+int slpic_read_tallies(slpic_ctx* ctx, int inst, slpic_tallies* out);
+/* Per-step records of the last min(n_steps, ring) steps, oldest first. */
+int slpic_read_history(slpic_ctx* ctx, int inst, slpic_tallies* out,
+                       int64_t capacity, int64_t* n_out);
+/* Electrode currents of the last step [A]: e * (sum of w_j crossing) / dt,
+ * positive for charge flowing into the gap's external circuit direction
+ * x = 0 -> d. */
+int slpic_read_current(slpic_ctx* ctx, int inst, double* I_anode,
+                       double* I_cathode);
+/* First-generation secondary-emission gain G = gamma * (sum of w_j of
+ * first-generation ions absorbed at the cathode) / (sum of seeded w_j):
+ * expected emitted electrons per seed electron; G >= 1 is the Townsend
+ * breakdown criterion gamma (e^(alpha d) - 1) >= 1 (Sec. II.A). */
+int slpic_read_gain(slpic_ctx* ctx, int inst, double* G);
+
+/* Per-step timing of the particle kernel: when on, slpic_step launches each
+ * step without a CUDA graph and brackets every particle-kernel launch with
+ * CUDA events on the context's stream. */
+int slpic_set_profiling(slpic_ctx* ctx, int on);
+/* Total device time [ms] and number of particle-kernel launches timed since
+ * profiling was switched on (synchronises). */
+int slpic_read_profile(slpic_ctx* ctx, double* push_ms, int64_t* launches);
+/* Device-side kernel launches made by the last slpic_step call. */
+int slpic_launch_count(slpic_ctx* ctx, int64_t* launches);
+
+/* Philox4x32-10 evaluated by the device: out[4i..4i+3] = Philox(ctr[4i..],
+ * key = seed).  Host arrays; for checking the random stream. */
+int slpic_philox(int device, uint64_t seed, const uint32_t* ctr, int64_t n,
+                 uint32_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLPIC_H */

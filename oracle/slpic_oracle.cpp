@@ -187,10 +187,10 @@ struct Sim {
       K_V[s] = (R)(2.0 * kQe / c.mass[s]);
     }
     dtdx = (R)(c.dt / dx);
-    K_E = (R)(0.5 * kMe / kQe);
+    K_E = (R)(0.5 * c.mass[ELECTRON] / kQe);
     const double n_g = c.p_Pa / (kKB * c.T_K);
     ndt = (R)(n_g * c.dt);
-    R2 = (R)(2.0 * kMe / c.mass[ION]);
+    R2 = (R)(2.0 * c.mass[ELECTRON] / c.mass[ION]);
     e_ex = (R)c.e_ex;
     e_io = (R)c.e_io;
     sigT_ion = (R)std::sqrt(kKB * c.T_K / c.mass[ION]);

@@ -1,0 +1,1012 @@
+// Host side of libslpic: the C ABI declared in include/slpic.h.  Validates
+// and stores the configuration, derives the single-precision constants of
+// the step, owns the device memory, and launches the step (directly or as a
+// replayed CUDA graph of several steps).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "../../include/slpic.h"
+#include "slpic_internal.h"
+
+using namespace slpic;
+
+namespace {
+
+// CODATA 2018 (SI).
+const double kQe = 1.602176634e-19;
+const double kKB = 1.380649e-23;
+const double kEps0 = 8.8541878128e-12;
+const double kTwoPi = 6.283185307179586;
+
+constexpr int kGraphSteps = 32;  // steps captured in one CUDA graph
+constexpr int kRingLen = 4096;   // per-step records kept on the device
+
+std::string g_create_error;
+
+struct HostSpecies {
+  bool set = false;
+  double mass = 0, charge = 0, vlim = 0;
+  long long cap = 0;
+};
+
+struct HostInst {
+  bool gap_set = false, gas_set = false, xs_set = false, dt_set = false;
+  double d = 0, V = 0, area = 1;
+  int n_cells = 0, field_mode = 0;
+  double p_Pa = 0, T_K = 300;
+  int lo_exp2 = 0, log2_sub = 0, octaves = 0;
+  std::vector<float> el, ex, io;
+  double e_ex = 0, e_io = 0;
+  HostSpecies sp[2];
+  double gamma = 0, dt = 0;
+  uint64_t seed = 0;
+  int shift = 32;
+};
+
+struct DevSpeciesAlloc {
+  void* block = nullptr;
+};
+
+}  // namespace
+
+struct slpic_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  int n_inst = 0;
+  std::vector<HostInst> hi;
+  std::string err;
+  bool committed = false;
+  // device memory
+  std::vector<void*> allocs;
+  InstDev* d_inst = nullptr;
+  InstState* d_istate = nullptr;
+  SpeciesState* d_sstate = nullptr;
+  Control* d_ctrl = nullptr;
+  TileStatus* d_tiles = nullptr;
+  unsigned int* d_seg = nullptr;
+  unsigned int* d_scratch = nullptr;  // 16 bytes for small device results
+  std::vector<InstDev> h_inst;  // host copies of the device configuration
+  DeviceRefs refs{};
+  int push_grid = 0;
+  int blocks_per_sm = 0;
+  // graph of kGraphSteps steps
+  cudaGraphExec_t graph = nullptr;
+  // profiling
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;  // pairs
+  size_t ev_used = 0;
+  double prof_ms = 0;
+  long long prof_launches = 0;
+  long long last_launches = 0;
+};
+
+namespace {
+
+int fail(slpic_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  else g_create_error = buf;
+  return code;
+}
+
+int cuda_fail(slpic_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, SLPIC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                        \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+  } while (0)
+
+bool valid_inst(slpic_ctx* c, int inst) { return c && inst >= 0 && inst < c->n_inst; }
+
+int set_device(slpic_ctx* c) {
+  CK(cudaSetDevice(c->device), "cudaSetDevice");
+  return SLPIC_OK;
+}
+
+int device_error(slpic_ctx* c) {
+  Control h;
+  CK(cudaMemcpy(&h, c->d_ctrl, sizeof h, cudaMemcpyDeviceToHost), "read status");
+  switch (h.error) {
+    case kErrNone: return SLPIC_OK;
+    case kErrCapacity:
+      return fail(c, SLPIC_ERR_CAPACITY,
+                  "instance %d: live markers or births exceeded the capacity", h.error_inst);
+    case kErrTimeout:
+      return fail(c, SLPIC_ERR_TIMEOUT, "a bounded device wait timed out");
+    case kErrIdWrap:
+      return fail(c, SLPIC_ERR_CAPACITY, "instance %d: marker serial numbers exhausted (2^31)",
+                  h.error_inst);
+    default: return fail(c, SLPIC_ERR_CUDA, "unknown device error %d", h.error);
+  }
+}
+
+int sync(slpic_ctx* c) {
+  if (int rc = set_device(c)) return rc;
+  CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+  if (!c->committed) return SLPIC_OK;
+  return device_error(c);
+}
+
+// Derive the single-precision constants of instance i (everything that does
+// not need reallocation) into c->h_inst[i].
+void fill_constants(slpic_ctx* c, int i, InstDev& P) {
+  const HostInst& h = c->hi[i];
+  const double dx = h.d / h.n_cells;
+  P.n_cells = h.n_cells;
+  P.field_mode = h.field_mode;
+  P.charge_shift = h.shift;
+  P.tab_lo_exp2 = h.lo_exp2;
+  P.tab_log2_sub = h.log2_sub;
+  P.tab_nodes = (h.octaves << h.log2_sub) + 1;
+  P.key0 = (uint32_t)h.seed;
+  P.key1 = (uint32_t)(h.seed >> 32);
+  P.ctr_inst = (uint32_t)i;
+  P.dtdx = (float)(h.dt / dx);
+  const HostSpecies& E = h.sp[kElectron];
+  const HostSpecies& I = h.sp[kIon];
+  P.K_E = (float)(0.5 * E.mass / kQe);
+  const double n_g = h.p_Pa / (kKB * h.T_K);
+  P.ndt = (float)(n_g * h.dt);
+  P.R2 = (float)(2.0 * E.mass / I.mass);
+  P.e_ex = (float)h.e_ex;
+  P.e_io = (float)h.e_io;
+  P.sigT_ion = (float)std::sqrt(kKB * h.T_K / I.mass);
+  P.gamma = (float)h.gamma;
+  P.wscale = (float)std::ldexp(1.0, h.shift);
+  P.two_pi = (float)kTwoPi;
+  P.e_lo = (float)std::ldexp(1.0, h.lo_exp2);
+  P.e_hi = (float)std::ldexp(1.0, h.lo_exp2 + h.octaves);
+  P.dx = dx;
+  P.d = h.d;
+  P.V = h.V;
+  P.area = h.area;
+  P.dt = h.dt;
+  P.pois_C = kQe * dx * std::ldexp(1.0, -h.shift) / (h.area * kEps0);
+  for (int s = 0; s < 2; ++s) {
+    const HostSpecies& S = h.sp[s];
+    const bool limited = S.vlim > 0.0 && std::isfinite(S.vlim);
+    P.sp[s].qmdt = (float)((S.charge / S.mass) * h.dt);
+    P.sp[s].vlim = limited ? (float)S.vlim : std::numeric_limits<float>::infinity();
+    P.sp[s].K_V = (float)(2.0 * kQe / S.mass);
+  }
+  // majorant of n_g sigma_tot(eps) min(v, vlim) dt over the table (FP32, the
+  // same operations the step uses)
+  float smax = 0.0f;
+  const size_t nn = h.el.size();
+  for (size_t j = 0; j < nn; ++j) {
+    const float s3 = (h.el[j] + h.ex[j]) + h.io[j];
+    smax = std::max(smax, s3);
+  }
+  const float e_top = P.e_hi;
+  const float v_top = std::sqrt(e_top * P.sp[kElectron].K_V);
+  P.vb_cap = std::min(P.sp[kElectron].vlim, v_top);
+  P.P0 = (P.ndt * P.vb_cap) * smax;
+}
+
+int check_config(slpic_ctx* c, int i) {
+  const HostInst& h = c->hi[i];
+  if (!h.gap_set) return fail(c, SLPIC_ERR_STATE, "instance %d: slpic_set_gap not called", i);
+  if (!h.gas_set) return fail(c, SLPIC_ERR_STATE, "instance %d: slpic_set_gas not called", i);
+  if (!h.xs_set)
+    return fail(c, SLPIC_ERR_STATE, "instance %d: slpic_set_cross_sections not called", i);
+  if (!h.dt_set) return fail(c, SLPIC_ERR_STATE, "instance %d: slpic_set_dt not called", i);
+  for (int s = 0; s < 2; ++s)
+    if (!h.sp[s].set)
+      return fail(c, SLPIC_ERR_STATE, "instance %d: species %d not configured", i, s);
+  return SLPIC_OK;
+}
+
+template <typename T>
+T* carve(char*& p, size_t n) {
+  T* r = reinterpret_cast<T*>(p);
+  p += (n * sizeof(T) + 255) & ~size_t(255);
+  return r;
+}
+
+size_t soa_bytes(size_t n) { return 7 * ((n * 4 + 255) & ~size_t(255)); }
+
+SoA carve_soa(char*& p, size_t n) {
+  SoA s;
+  s.cell = carve<int32_t>(p, n);
+  s.off = carve<float>(p, n);
+  s.vx = carve<float>(p, n);
+  s.vy = carve<float>(p, n);
+  s.vz = carve<float>(p, n);
+  s.wj = carve<float>(p, n);
+  s.id = carve<uint32_t>(p, n);
+  return s;
+}
+
+int dmalloc(slpic_ctx* c, void** p, size_t bytes, const char* what) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) return cuda_fail(c, e, what);
+  c->allocs.push_back(*p);
+  return SLPIC_OK;
+}
+
+// Reset the vacuum field of instance i on the device: phi linear, E = -V/d.
+int reset_field(slpic_ctx* c, int i) {
+  const InstDev& P = c->h_inst[i];
+  const int nn = P.n_cells + 1;
+  std::vector<double> phi(nn), E(nn, -P.V / P.d);
+  std::vector<float> E32(nn, (float)(-P.V / P.d));
+  for (int k = 0; k < nn; ++k) phi[k] = P.V * k / P.n_cells;
+  CK(cudaMemcpyAsync(P.phi, phi.data(), nn * 8, cudaMemcpyHostToDevice, c->stream), "field");
+  CK(cudaMemcpyAsync(P.E64, E.data(), nn * 8, cudaMemcpyHostToDevice, c->stream), "field");
+  CK(cudaMemcpyAsync(P.E32, E32.data(), nn * 4, cudaMemcpyHostToDevice, c->stream), "field");
+  CK(cudaStreamSynchronize(c->stream), "field");
+  return SLPIC_OK;
+}
+
+int upload_inst(slpic_ctx* c, int i) {
+  CK(cudaMemcpyAsync(c->d_inst + i, &c->h_inst[i], sizeof(InstDev), cudaMemcpyHostToDevice,
+                     c->stream),
+     "upload instance");
+  CK(cudaStreamSynchronize(c->stream), "upload instance");
+  return SLPIC_OK;
+}
+
+int zero_counters(slpic_ctx* c, int i) {
+  const InstDev& P = c->h_inst[i];
+  CK(cudaMemsetAsync(P.acc, 0, ACC_COUNT * 8, c->stream), "reset");
+  CK(cudaMemsetAsync(P.total, 0, sizeof(TallyRec), c->stream), "reset");
+  CK(cudaMemsetAsync(P.ring, 0, sizeof(TallyRec) * P.ring_len, c->stream), "reset");
+  CK(cudaMemsetAsync(c->d_istate + i, 0, sizeof(InstState), c->stream), "reset");
+  for (int s = 0; s < 2; ++s) {
+    CK(cudaMemsetAsync(P.rho_acc[s], 0, (P.n_cells + 1) * 8, c->stream), "reset");
+    CK(cudaMemsetAsync(P.rho_last[s], 0, (P.n_cells + 1) * 8, c->stream), "reset");
+  }
+  CK(cudaStreamSynchronize(c->stream), "reset");
+  return SLPIC_OK;
+}
+
+int commit(slpic_ctx* c) {
+  if (c->committed) return SLPIC_OK;
+  for (int i = 0; i < c->n_inst; ++i)
+    if (int rc = check_config(c, i)) return rc;
+  if (int rc = set_device(c)) return rc;
+  c->h_inst.assign(c->n_inst, InstDev{});
+  unsigned long long max_tiles = 0;
+  int max_nodes = 0;
+  for (int i = 0; i < c->n_inst; ++i) {
+    HostInst& h = c->hi[i];
+    InstDev& P = c->h_inst[i];
+    std::memset(&P, 0, sizeof P);
+    fill_constants(c, i, P);
+    const int nn = h.n_cells + 1;
+    max_nodes = std::max(max_nodes, nn);
+    // per-instance arrays
+    const size_t tab_n = h.el.size() + 1;
+    size_t bytes = 0;
+    bytes += (tab_n * 16 + 255) & ~size_t(255);
+    bytes += ((nn * 4 + 255) & ~size_t(255));
+    bytes += 2 * ((nn * 8 + 255) & ~size_t(255));
+    bytes += 4 * ((nn * 8 + 255) & ~size_t(255));
+    bytes += 256 + ((sizeof(TallyRec) * kRingLen + 255) & ~size_t(255)) + 256;
+    void* blk;
+    if (int rc = dmalloc(c, &blk, bytes, "instance arrays")) return rc;
+    char* p = (char*)blk;
+    float4* tab = carve<float4>(p, tab_n);
+    P.table = tab;
+    P.E32 = carve<float>(p, nn);
+    P.phi = carve<double>(p, nn);
+    P.E64 = carve<double>(p, nn);
+    P.rho_acc[0] = carve<unsigned long long>(p, nn);
+    P.rho_acc[1] = carve<unsigned long long>(p, nn);
+    P.rho_last[0] = carve<long long>(p, nn);
+    P.rho_last[1] = carve<long long>(p, nn);
+    P.acc = carve<unsigned long long>(p, ACC_COUNT);
+    P.ring = carve<TallyRec>(p, kRingLen);
+    P.total = carve<TallyRec>(p, 1);
+    P.ring_len = kRingLen;
+    // cumulative table (S1, S2, S3) in FP32 plus one padding node
+    std::vector<float4> ht(tab_n);
+    for (size_t j = 0; j + 1 < tab_n; ++j) {
+      const float s1 = h.el[j];
+      const float s2 = s1 + h.ex[j];
+      const float s3 = s2 + h.io[j];
+      ht[j] = make_float4(s1, s2, s3, 0.0f);
+    }
+    ht[tab_n - 1] = ht[tab_n - 2];
+    CK(cudaMemcpy(tab, ht.data(), tab_n * 16, cudaMemcpyHostToDevice), "table");
+    // species
+    for (int s = 0; s < 2; ++s) {
+      SpeciesDev& S = P.sp[s];
+      const size_t cap = (size_t)h.sp[s].cap;
+      size_t stage = std::min(cap, std::max<size_t>(65536, cap / 4));
+      stage = (stage + 3) & ~size_t(3);
+      S.cap = (uint32_t)cap;
+      S.stage_cap = (uint32_t)stage;
+      const size_t capr = (cap + kTile - 1) / kTile * kTile;  // tile-rounded
+      size_t b = 2 * soa_bytes(capr) + soa_bytes(stage) + (s == kElectron ? soa_bytes(stage) : 0);
+      void* sb;
+      if (int rc = dmalloc(c, &sb, b, "marker buffers")) return rc;
+      char* q = (char*)sb;
+      S.buf[0] = carve_soa(q, capr);
+      S.buf[1] = carve_soa(q, capr);
+      S.stage_a = carve_soa(q, stage);
+      if (s == kElectron) S.stage_b = carve_soa(q, stage);
+      else std::memset(&S.stage_b, 0, sizeof(SoA));
+      max_tiles += (cap + kTile - 1) / kTile;
+    }
+  }
+  if (max_tiles > 0x3FFFFFFFull) return fail(c, SLPIC_ERR_CAPACITY, "too many tiles");
+  void* blk;
+  const size_t nseg = 2 * (size_t)c->n_inst;
+  size_t bytes = ((sizeof(InstDev) * c->n_inst + 255) & ~size_t(255)) +
+                 ((sizeof(InstState) * c->n_inst + 255) & ~size_t(255)) +
+                 ((sizeof(SpeciesState) * nseg + 255) & ~size_t(255)) + 256 +
+                 ((sizeof(TileStatus) * (max_tiles + 1) + 255) & ~size_t(255)) +
+                 ((4 * (nseg + 1) + 255) & ~size_t(255)) + 256;
+  if (int rc = dmalloc(c, &blk, bytes, "control")) return rc;
+  CK(cudaMemset(blk, 0, bytes), "control");
+  char* p = (char*)blk;
+  c->d_inst = carve<InstDev>(p, c->n_inst);
+  c->d_istate = carve<InstState>(p, c->n_inst);
+  c->d_sstate = carve<SpeciesState>(p, nseg);
+  c->d_ctrl = carve<Control>(p, 1);
+  c->d_tiles = carve<TileStatus>(p, max_tiles + 1);
+  c->d_seg = carve<unsigned int>(p, nseg + 1);
+  c->d_scratch = carve<unsigned int>(p, 4);
+  c->refs.inst = c->d_inst;
+  c->refs.istate = c->d_istate;
+  c->refs.sstate = c->d_sstate;
+  c->refs.ctrl = c->d_ctrl;
+  c->refs.tiles = c->d_tiles;
+  c->refs.seg_start = c->d_seg;
+  c->refs.n_inst = c->n_inst;
+  c->refs.max_tiles = (unsigned int)max_tiles;
+  // the whole charge grid of the largest instance goes to shared memory when
+  // it fits next to the marker staging; otherwise deposits use global atomics
+  int smem_nodes = max_nodes <= 16385 ? max_nodes : 0;
+  int bps = 0;
+  size_t sbytes = 0;
+  int e = push_occupancy(smem_nodes, &bps, &sbytes);
+  if (e != 0 || bps == 0) {
+    smem_nodes = 0;
+    e = push_occupancy(0, &bps, &sbytes);
+    if (e != 0 || bps == 0) return fail(c, SLPIC_ERR_CUDA, "particle kernel cannot be launched");
+  }
+  c->refs.smem_nodes = smem_nodes;
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device), "attributes");
+  c->blocks_per_sm = bps;
+  c->push_grid = sms * bps;
+  for (int i = 0; i < c->n_inst; ++i) {
+    if (int rc = upload_inst(c, i)) return rc;
+    if (int rc = reset_field(c, i)) return rc;
+    if (int rc = zero_counters(c, i)) return rc;
+  }
+  CK(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking), "stream");
+  c->committed = true;
+  launch_finish(c->refs, 1, c->stream);
+  CK(cudaGetLastError(), "plan");
+  CK(cudaStreamSynchronize(c->stream), "plan");
+  return SLPIC_OK;
+}
+
+int read_state(slpic_ctx* c, int inst, int sp, SpeciesState* out) {
+  CK(cudaMemcpy(out, c->d_sstate + inst * 2 + sp, sizeof *out, cudaMemcpyDeviceToHost),
+     "read state");
+  return SLPIC_OK;
+}
+
+int write_state(slpic_ctx* c, int inst, int sp, const SpeciesState& st) {
+  CK(cudaMemcpy(c->d_sstate + inst * 2 + sp, &st, sizeof st, cudaMemcpyHostToDevice),
+     "write state");
+  return SLPIC_OK;
+}
+
+int replan(slpic_ctx* c) {
+  launch_finish(c->refs, 1, c->stream);
+  CK(cudaGetLastError(), "plan");
+  return SLPIC_OK;
+}
+
+int prepare(slpic_ctx* c) {
+  if (int rc = commit(c)) return rc;
+  if (int rc = set_device(c)) return rc;
+  return SLPIC_OK;
+}
+
+void drop_graph(slpic_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+}
+
+int build_graph(slpic_ctx* c) {
+  if (c->graph) return SLPIC_OK;
+  cudaGraph_t g;
+  CK(cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal), "capture");
+  for (int k = 0; k < kGraphSteps; ++k) {
+    launch_push(c->refs, c->push_grid, c->capture_stream);
+    launch_finish(c->refs, 0, c->capture_stream);
+  }
+  CK(cudaStreamEndCapture(c->capture_stream, &g), "capture");
+  cudaError_t e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->graph = nullptr;
+    return cuda_fail(c, e, "graph instantiate");
+  }
+  return SLPIC_OK;
+}
+
+int host_soa_check(slpic_ctx* c, const slpic_soa_f32* s) {
+  if (!s || !s->cell || !s->off || !s->vx || !s->vy || !s->vz || !s->wj || !s->id)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "null marker array");
+  return SLPIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int slpic_version(void) { return 100; }
+
+const char* slpic_last_error(const slpic_ctx* c) {
+  return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+int slpic_create(slpic_ctx** out, int device, int n_instances) {
+  if (!out) return fail(nullptr, SLPIC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_instances < 1 || n_instances > (1 << 20))
+    return fail(nullptr, SLPIC_ERR_INVALID_ARG, "n_instances must be in [1, 2^20]");
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) return fail(nullptr, SLPIC_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+  if (device < 0 || device >= n) return fail(nullptr, SLPIC_ERR_INVALID_ARG, "bad device %d", device);
+  slpic_ctx* c = new slpic_ctx;
+  c->device = device;
+  c->n_inst = n_instances;
+  c->hi.resize(n_instances);
+  *out = c;
+  return SLPIC_OK;
+}
+
+int slpic_destroy(slpic_ctx* c) {
+  if (!c) return SLPIC_OK;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graph(c);
+  for (auto& e : c->ev) cudaEventDestroy(e);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  delete c;
+  return SLPIC_OK;
+}
+
+int slpic_set_stream(slpic_ctx* c, void* stream) {
+  if (!c) return SLPIC_ERR_INVALID_ARG;
+  c->stream = (cudaStream_t)stream;
+  return SLPIC_OK;
+}
+
+int slpic_set_gap(slpic_ctx* c, int inst, double d, int n_cells, double V, int field_mode,
+                  double area) {
+  if (!valid_inst(c, inst)) return fail(c, SLPIC_ERR_INVALID_ARG, "bad instance");
+  if (!(d > 0) || n_cells < 2 || n_cells > (1 << 24) || !std::isfinite(V) ||
+      (field_mode != SLPIC_FIELD_FROZEN && field_mode != SLPIC_FIELD_POISSON) || !(area > 0))
+    return fail(c, SLPIC_ERR_INVALID_ARG, "bad gap parameters");
+  HostInst& h = c->hi[inst];
+  if (c->committed && (n_cells != h.n_cells))
+    return fail(c, SLPIC_ERR_STATE, "the cell count cannot change after the first use");
+  h.d = d;
+  h.n_cells = n_cells;
+  h.V = V;
+  h.field_mode = field_mode;
+  h.area = area;
+  h.gap_set = true;
+  if (c->committed) {
+    fill_constants(c, inst, c->h_inst[inst]);
+    if (int rc = upload_inst(c, inst)) return rc;
+    return reset_field(c, inst);
+  }
+  return SLPIC_OK;
+}
+
+int slpic_set_voltage(slpic_ctx* c, int inst, double V) {
+  if (!valid_inst(c, inst) || !std::isfinite(V)) return fail(c, SLPIC_ERR_INVALID_ARG, "bad voltage");
+  HostInst& h = c->hi[inst];
+  if (!h.gap_set) return fail(c, SLPIC_ERR_STATE, "slpic_set_gap first");
+  return slpic_set_gap(c, inst, h.d, h.n_cells, V, h.field_mode, h.area);
+}
+
+int slpic_set_gas(slpic_ctx* c, int inst, double p_Pa, double T_K) {
+  if (!valid_inst(c, inst)) return fail(c, SLPIC_ERR_INVALID_ARG, "bad instance");
+  if (!(p_Pa >= 0) || !std::isfinite(p_Pa) || !(T_K > 0))
+    return fail(c, SLPIC_ERR_INVALID_ARG, "bad gas parameters");
+  c->hi[inst].p_Pa = p_Pa;
+  c->hi[inst].T_K = T_K;
+  c->hi[inst].gas_set = true;
+  if (c->committed) {
+    fill_constants(c, inst, c->h_inst[inst]);
+    return upload_inst(c, inst);
+  }
+  return SLPIC_OK;
+}
+
+int slpic_set_cross_sections(slpic_ctx* c, int inst, int lo_exp2, int log2_sub, int octaves,
+                             const float* el, const float* ex, double e_ex, const float* io,
+                             double e_io) {
+  if (!c) return SLPIC_ERR_INVALID_ARG;
+  if (inst < -1 || inst >= c->n_inst) return fail(c, SLPIC_ERR_INVALID_ARG, "bad instance");
+  if (!el || !ex || !io || log2_sub < 0 || log2_sub > 16 || octaves < 1 || octaves > 64 ||
+      lo_exp2 < -100 || lo_exp2 + octaves > 100 || !(e_ex >= 0) || !(e_io >= 0))
+    return fail(c, SLPIC_ERR_INVALID_ARG, "bad cross-section table");
+  const size_t n = ((size_t)octaves << log2_sub) + 1;
+  for (size_t j = 0; j < n; ++j)
+    if (!(el[j] >= 0) || !(ex[j] >= 0) || !(io[j] >= 0) || !std::isfinite(el[j]) ||
+        !std::isfinite(ex[j]) || !std::isfinite(io[j]))
+      return fail(c, SLPIC_ERR_INVALID_ARG, "cross sections must be finite and >= 0");
+  if (c->committed) return fail(c, SLPIC_ERR_STATE, "tables cannot change after the first use");
+  const int lo = inst < 0 ? 0 : inst, hi = inst < 0 ? c->n_inst : inst + 1;
+  for (int i = lo; i < hi; ++i) {
+    HostInst& h = c->hi[i];
+    h.lo_exp2 = lo_exp2;
+    h.log2_sub = log2_sub;
+    h.octaves = octaves;
+    h.el.assign(el, el + n);
+    h.ex.assign(ex, ex + n);
+    h.io.assign(io, io + n);
+    h.e_ex = e_ex;
+    h.e_io = e_io;
+    h.xs_set = true;
+  }
+  return SLPIC_OK;
+}
+
+int slpic_set_species(slpic_ctx* c, int inst, int species, double mass, double charge,
+                      double v_lim, int64_t capacity) {
+  if (!valid_inst(c, inst) || (species != 0 && species != 1))
+    return fail(c, SLPIC_ERR_INVALID_ARG, "bad instance or species");
+  if (!(mass > 0) || !std::isfinite(charge) || std::isnan(v_lim) || capacity < 1 ||
+      capacity > (int64_t)0x7FFFFFFF - kTile)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "bad species parameters");
+  HostSpecies& S = c->hi[inst].sp[species];
+  if (c->committed && capacity != S.cap)
+    return fail(c, SLPIC_ERR_STATE, "capacity cannot change after the first use");
+  S.mass = mass;
+  S.charge = charge;
+  S.vlim = v_lim;
+  S.cap = capacity;
+  S.set = true;
+  if (c->committed) {
+    fill_constants(c, inst, c->h_inst[inst]);
+    return upload_inst(c, inst);
+  }
+  return SLPIC_OK;
+}
+
+int slpic_set_emission(slpic_ctx* c, int inst, double g) {
+  if (!valid_inst(c, inst) || !(g >= 0 && g <= 1)) return fail(c, SLPIC_ERR_INVALID_ARG, "gamma must be in [0, 1]");
+  c->hi[inst].gamma = g;
+  if (c->committed) {
+    fill_constants(c, inst, c->h_inst[inst]);
+    return upload_inst(c, inst);
+  }
+  return SLPIC_OK;
+}
+
+int slpic_set_dt(slpic_ctx* c, int inst, double dt) {
+  if (!valid_inst(c, inst) || !(dt >= 0) || !std::isfinite(dt))
+    return fail(c, SLPIC_ERR_INVALID_ARG, "dt must be finite and >= 0");
+  c->hi[inst].dt = dt;
+  c->hi[inst].dt_set = true;
+  if (c->committed) {
+    fill_constants(c, inst, c->h_inst[inst]);
+    return upload_inst(c, inst);
+  }
+  return SLPIC_OK;
+}
+
+int slpic_set_seed(slpic_ctx* c, int inst, uint64_t seed) {
+  if (!valid_inst(c, inst)) return fail(c, SLPIC_ERR_INVALID_ARG, "bad instance");
+  c->hi[inst].seed = seed;
+  if (c->committed) {
+    fill_constants(c, inst, c->h_inst[inst]);
+    return upload_inst(c, inst);
+  }
+  return SLPIC_OK;
+}
+
+int slpic_set_charge_shift(slpic_ctx* c, int inst, int shift) {
+  if (!valid_inst(c, inst) || shift < 0 || shift > 40)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "shift must be in [0, 40]");
+  if (c->committed) return fail(c, SLPIC_ERR_STATE, "shift cannot change after the first use");
+  c->hi[inst].shift = shift;
+  return SLPIC_OK;
+}
+
+int slpic_suggest_dt(double d, int n_cells, double V, double m_ion, int mode, double* dt) {
+  if (!dt || !(d > 0) || n_cells < 1 || !(V > 0) || !(m_ion > 0) || (mode != 0 && mode != 1))
+    return SLPIC_ERR_INVALID_ARG;
+  const double me = 9.1093837015e-31;
+  const double m = mode == 0 ? m_ion : me;
+  *dt = (d / n_cells) / std::sqrt(2.0 * kQe * V / m);
+  return SLPIC_OK;
+}
+
+int slpic_seed(slpic_ctx* c, int inst, int species, int64_t n, int mode, double e0,
+               double e_lo, double e_hi, double wj) {
+  if (!valid_inst(c, inst) || (species != 0 && species != 1) || n < 0 || mode < 0 || mode > 3)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "bad seed arguments");
+  if (!(wj >= 0) || !std::isfinite(wj) || !(e0 >= 0) || (mode == 2 && !(e_lo > 0 && e_hi >= e_lo)))
+    return fail(c, SLPIC_ERR_INVALID_ARG, "bad seed energies or weight");
+  if (int rc = prepare(c)) return rc;
+  if (int rc = sync(c)) return rc;
+  SpeciesState st;
+  if (int rc = read_state(c, inst, species, &st)) return rc;
+  const InstDev& P = c->h_inst[inst];
+  if ((uint64_t)st.n_live + (uint64_t)n > P.sp[species].cap)
+    return fail(c, SLPIC_ERR_CAPACITY, "seeding %lld markers exceeds the capacity", (long long)n);
+  if ((uint64_t)st.next_id + (uint64_t)n > kSerialMask)
+    return fail(c, SLPIC_ERR_CAPACITY, "marker serial numbers exhausted");
+  const HostInst& h = c->hi[inst];
+  float e0f = (float)e0;
+  if (mode == 3) e0f = (float)std::sqrt(kKB * h.T_K / h.sp[species].mass);
+  const float lr = mode == 2 ? (float)std::log(e_hi / e_lo) : 0.0f;
+  launch_seed(c->refs, inst, species, st.n_live, st.next_id, (uint32_t)n, mode, e0f,
+              (float)e_lo, lr, (float)wj, c->stream);
+  CK(cudaGetLastError(), "seed");
+  st.n_live += (uint32_t)n;
+  st.next_id += (uint32_t)n;
+  CK(cudaStreamSynchronize(c->stream), "seed");
+  if (int rc = write_state(c, inst, species, st)) return rc;
+  if (species == kElectron) {
+    InstState is;
+    CK(cudaMemcpy(&is, c->d_istate + inst, sizeof is, cudaMemcpyDeviceToHost), "seed");
+    is.w_seed += (unsigned long long)n * (unsigned long long)std::llrint((float)wj * P.wscale);
+    CK(cudaMemcpy(c->d_istate + inst, &is, sizeof is, cudaMemcpyHostToDevice), "seed");
+  }
+  if (int rc = replan(c)) return rc;
+  return sync(c);
+}
+
+static int load_common(slpic_ctx* c, int inst, int species, const slpic_soa_f32* src, int64_t n,
+                       uint32_t next_id, cudaMemcpyKind kind) {
+  if (!valid_inst(c, inst) || (species != 0 && species != 1) || n < 0)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "bad load arguments");
+  if (n > 0)
+    if (int rc = host_soa_check(c, src)) return rc;
+  if (next_id > kSerialMask) return fail(c, SLPIC_ERR_INVALID_ARG, "next_id beyond 2^31 - 1");
+  if (int rc = prepare(c)) return rc;
+  if (int rc = sync(c)) return rc;
+  const InstDev& P = c->h_inst[inst];
+  if ((uint64_t)n > P.sp[species].cap)
+    return fail(c, SLPIC_ERR_CAPACITY, "%lld markers exceed the capacity", (long long)n);
+  SpeciesState st;
+  if (int rc = read_state(c, inst, species, &st)) return rc;
+  const SoA& d = P.sp[species].buf[st.cur];
+  if (n > 0) {
+    const size_t b = (size_t)n * 4;
+    CK(cudaMemcpyAsync(d.cell, src->cell, b, kind, c->stream), "load");
+    CK(cudaMemcpyAsync(d.off, src->off, b, kind, c->stream), "load");
+    CK(cudaMemcpyAsync(d.vx, src->vx, b, kind, c->stream), "load");
+    CK(cudaMemcpyAsync(d.vy, src->vy, b, kind, c->stream), "load");
+    CK(cudaMemcpyAsync(d.vz, src->vz, b, kind, c->stream), "load");
+    CK(cudaMemcpyAsync(d.wj, src->wj, b, kind, c->stream), "load");
+    CK(cudaMemcpyAsync(d.id, src->id, b, kind, c->stream), "load");
+  }
+  // validate on the device: a marker outside the gap would make the step
+  // read and write outside the field and charge arrays
+  unsigned int* scratch = c->d_scratch;
+  unsigned int bad_init[4] = {0xFFFFFFFFu, 0u, 0u, 0u};
+  CK(cudaMemcpyAsync(scratch, bad_init, 16, cudaMemcpyHostToDevice, c->stream), "load");
+  launch_validate(d, (uint32_t)n, P.n_cells, P.wscale, scratch,
+                  reinterpret_cast<unsigned long long*>(scratch + 2), c->stream);
+  CK(cudaGetLastError(), "validate");
+  unsigned int res[4];
+  CK(cudaMemcpyAsync(res, scratch, 16, cudaMemcpyDeviceToHost, c->stream), "load");
+  CK(cudaStreamSynchronize(c->stream), "load");
+  if (res[0] != 0xFFFFFFFFu) {
+    st.n_live = 0;
+    write_state(c, inst, species, st);
+    replan(c);
+    return fail(c, SLPIC_ERR_INVALID_ARG,
+                "marker %u outside the gap or not finite; the species was emptied", res[0]);
+  }
+  st.n_live = (uint32_t)n;
+  st.next_id = next_id;
+  if (int rc = write_state(c, inst, species, st)) return rc;
+  if (species == kElectron) {
+    InstState is;
+    CK(cudaMemcpy(&is, c->d_istate + inst, sizeof is, cudaMemcpyDeviceToHost), "load");
+    unsigned long long wsum;
+    std::memcpy(&wsum, res + 2, 8);
+    is.w_seed = wsum;
+    CK(cudaMemcpy(c->d_istate + inst, &is, sizeof is, cudaMemcpyHostToDevice), "load");
+  }
+  if (int rc = replan(c)) return rc;
+  return sync(c);
+}
+
+int slpic_load_particles(slpic_ctx* c, int inst, int species, const slpic_soa_f32* host,
+                         int64_t n, uint32_t next_id) {
+  return load_common(c, inst, species, host, n, next_id, cudaMemcpyHostToDevice);
+}
+
+int slpic_load_particles_device(slpic_ctx* c, int inst, int species, const slpic_soa_f32* dev,
+                                int64_t n, uint32_t next_id) {
+  return load_common(c, inst, species, dev, n, next_id, cudaMemcpyDeviceToDevice);
+}
+
+int slpic_reset_counters(slpic_ctx* c, int inst) {
+  if (!valid_inst(c, inst)) return fail(c, SLPIC_ERR_INVALID_ARG, "bad instance");
+  if (int rc = prepare(c)) return rc;
+  if (int rc = sync(c)) return rc;
+  return zero_counters(c, inst);
+}
+
+int slpic_step(slpic_ctx* c, int64_t n) {
+  if (!c || n < 0) return fail(c, SLPIC_ERR_INVALID_ARG, "bad step count");
+  if (int rc = prepare(c)) return rc;
+  c->last_launches = 0;
+  if (c->profiling) {
+    for (int64_t k = 0; k < n; ++k) {
+      if (c->ev_used + 2 > c->ev.size()) {
+        for (int j = 0; j < 64; ++j) {
+          cudaEvent_t e;
+          CK(cudaEventCreate(&e), "event");
+          c->ev.push_back(e);
+        }
+      }
+      cudaEvent_t a = c->ev[c->ev_used], b = c->ev[c->ev_used + 1];
+      c->ev_used += 2;
+      CK(cudaEventRecord(a, c->stream), "event");
+      launch_push(c->refs, c->push_grid, c->stream);
+      CK(cudaEventRecord(b, c->stream), "event");
+      launch_finish(c->refs, 0, c->stream);
+      c->last_launches += 2;
+    }
+    CK(cudaGetLastError(), "step");
+    return SLPIC_OK;
+  }
+  int64_t left = n;
+  if (left >= kGraphSteps) {
+    if (int rc = build_graph(c)) return rc;
+    while (left >= kGraphSteps) {
+      CK(cudaGraphLaunch(c->graph, c->stream), "graph launch");
+      left -= kGraphSteps;
+      c->last_launches += 2 * kGraphSteps;
+    }
+  }
+  for (int64_t k = 0; k < left; ++k) {
+    launch_push(c->refs, c->push_grid, c->stream);
+    launch_finish(c->refs, 0, c->stream);
+    c->last_launches += 2;
+  }
+  CK(cudaGetLastError(), "step");
+  return SLPIC_OK;
+}
+
+int slpic_synchronize(slpic_ctx* c) {
+  if (!c) return SLPIC_ERR_INVALID_ARG;
+  return sync(c);
+}
+
+int slpic_clear_error(slpic_ctx* c) {
+  if (!c) return SLPIC_ERR_INVALID_ARG;
+  if (!c->committed) return SLPIC_OK;
+  if (int rc = set_device(c)) return rc;
+  CK(cudaStreamSynchronize(c->stream), "clear");
+  CK(cudaMemset(&c->d_ctrl->error, 0, sizeof(int)), "clear");
+  for (int i = 0; i < c->n_inst; ++i) {
+    const InstDev& P = c->h_inst[i];
+    CK(cudaMemset(P.acc, 0, ACC_COUNT * 8), "clear");
+    for (int s = 0; s < 2; ++s) CK(cudaMemset(P.rho_acc[s], 0, (P.n_cells + 1) * 8), "clear");
+  }
+  if (int rc = replan(c)) return rc;
+  CK(cudaStreamSynchronize(c->stream), "clear");
+  return SLPIC_OK;
+}
+
+int slpic_count(slpic_ctx* c, int inst, int species, int64_t* n) {
+  if (!valid_inst(c, inst) || (species != 0 && species != 1) || !n)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "bad arguments");
+  if (int rc = prepare(c)) return rc;
+  int rc = sync(c);
+  SpeciesState st;
+  if (int r2 = read_state(c, inst, species, &st)) return r2;
+  *n = st.n_live;
+  return rc;
+}
+
+int slpic_read_particles(slpic_ctx* c, int inst, int species, const slpic_soa_f32* host,
+                         int64_t capacity, int64_t* n_out) {
+  if (!valid_inst(c, inst) || (species != 0 && species != 1) || !n_out || capacity < 0)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "bad arguments");
+  if (int rc = prepare(c)) return rc;
+  int rc = sync(c);
+  SpeciesState st;
+  if (int r2 = read_state(c, inst, species, &st)) return r2;
+  *n_out = st.n_live;
+  if ((int64_t)st.n_live > capacity)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "host buffers hold %lld markers, %u live",
+                (long long)capacity, st.n_live);
+  if (st.n_live > 0) {
+    if (int r3 = host_soa_check(c, host)) return r3;
+    const SoA& d = c->h_inst[inst].sp[species].buf[st.cur];
+    const size_t b = (size_t)st.n_live * 4;
+    CK(cudaMemcpy(host->cell, d.cell, b, cudaMemcpyDeviceToHost), "read");
+    CK(cudaMemcpy(host->off, d.off, b, cudaMemcpyDeviceToHost), "read");
+    CK(cudaMemcpy(host->vx, d.vx, b, cudaMemcpyDeviceToHost), "read");
+    CK(cudaMemcpy(host->vy, d.vy, b, cudaMemcpyDeviceToHost), "read");
+    CK(cudaMemcpy(host->vz, d.vz, b, cudaMemcpyDeviceToHost), "read");
+    CK(cudaMemcpy(host->wj, d.wj, b, cudaMemcpyDeviceToHost), "read");
+    CK(cudaMemcpy(host->id, d.id, b, cudaMemcpyDeviceToHost), "read");
+  }
+  return rc;
+}
+
+int slpic_read_charge(slpic_ctx* c, int inst, int species, int64_t* host, int64_t n) {
+  if (!valid_inst(c, inst) || (species != 0 && species != 1) || !host)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "bad arguments");
+  if (int rc = prepare(c)) return rc;
+  int rc = sync(c);
+  const InstDev& P = c->h_inst[inst];
+  if (n != P.n_cells + 1) return fail(c, SLPIC_ERR_INVALID_ARG, "need n_cells + 1 values");
+  CK(cudaMemcpy(host, P.rho_last[species], n * 8, cudaMemcpyDeviceToHost), "read charge");
+  return rc;
+}
+
+int slpic_read_density(slpic_ctx* c, int inst, int species, double* host, int64_t n) {
+  if (!valid_inst(c, inst) || (species != 0 && species != 1) || !host)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "bad arguments");
+  if (int rc = prepare(c)) return rc;
+  const InstDev& P = c->h_inst[inst];
+  if (n != P.n_cells + 1) return fail(c, SLPIC_ERR_INVALID_ARG, "need n_cells + 1 values");
+  std::vector<int64_t> q(n);
+  int rc = slpic_read_charge(c, inst, species, q.data(), n);
+  if (rc && rc != SLPIC_ERR_CAPACITY && rc != SLPIC_ERR_TIMEOUT) return rc;
+  const double unit = std::ldexp(1.0, -P.charge_shift);
+  for (int64_t k = 0; k < n; ++k) {
+    const double vol = P.area * P.dx * ((k == 0 || k == n - 1) ? 0.5 : 1.0);
+    host[k] = (double)q[k] * unit / vol;
+  }
+  return rc;
+}
+
+int slpic_read_field(slpic_ctx* c, int inst, double* phi, double* E, int64_t n) {
+  if (!valid_inst(c, inst) || !phi || !E) return fail(c, SLPIC_ERR_INVALID_ARG, "bad arguments");
+  if (int rc = prepare(c)) return rc;
+  int rc = sync(c);
+  const InstDev& P = c->h_inst[inst];
+  if (n != P.n_cells + 1) return fail(c, SLPIC_ERR_INVALID_ARG, "need n_cells + 1 values");
+  CK(cudaMemcpy(phi, P.phi, n * 8, cudaMemcpyDeviceToHost), "read field");
+  CK(cudaMemcpy(E, P.E64, n * 8, cudaMemcpyDeviceToHost), "read field");
+  return rc;
+}
+
+int slpic_read_tallies(slpic_ctx* c, int inst, slpic_tallies* out) {
+  static_assert(sizeof(slpic_tallies) == sizeof(TallyRec), "tally layout");
+  if (!valid_inst(c, inst) || !out) return fail(c, SLPIC_ERR_INVALID_ARG, "bad arguments");
+  if (int rc = prepare(c)) return rc;
+  int rc = sync(c);
+  CK(cudaMemcpy(out, c->h_inst[inst].total, sizeof *out, cudaMemcpyDeviceToHost), "read tallies");
+  return rc;
+}
+
+int slpic_read_history(slpic_ctx* c, int inst, slpic_tallies* out, int64_t capacity,
+                       int64_t* n_out) {
+  if (!valid_inst(c, inst) || !out || !n_out || capacity < 0)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "bad arguments");
+  if (int rc = prepare(c)) return rc;
+  int rc = sync(c);
+  InstState is;
+  CK(cudaMemcpy(&is, c->d_istate + inst, sizeof is, cudaMemcpyDeviceToHost), "history");
+  const InstDev& P = c->h_inst[inst];
+  const long long have = std::min<long long>(is.n_steps_done, P.ring_len);
+  const long long m = std::min<long long>(have, capacity);
+  std::vector<TallyRec> ring(P.ring_len);
+  CK(cudaMemcpy(ring.data(), P.ring, sizeof(TallyRec) * P.ring_len, cudaMemcpyDeviceToHost),
+     "history");
+  for (long long k = 0; k < m; ++k) {
+    const long long s = is.n_steps_done - m + k;
+    std::memcpy(out + k, &ring[s % P.ring_len], sizeof(TallyRec));
+  }
+  *n_out = m;
+  return rc;
+}
+
+int slpic_read_current(slpic_ctx* c, int inst, double* Ia, double* Ic) {
+  if (!valid_inst(c, inst) || !Ia || !Ic) return fail(c, SLPIC_ERR_INVALID_ARG, "bad arguments");
+  slpic_tallies t;
+  int64_t n = 0;
+  int rc = slpic_read_history(c, inst, &t, 1, &n);
+  if (n == 0) {
+    *Ia = *Ic = 0;
+    return rc;
+  }
+  const double dt = c->h_inst[inst].dt;
+  // electrons leaving through the anode and ions leaving through the cathode
+  // both carry conventional current in the +x direction through the gap
+  *Ia = kQe * (t.w_abs[kElectron][1] - t.w_abs[kIon][1]) / dt;
+  *Ic = kQe * (t.w_abs[kIon][0] - t.w_abs[kElectron][0] + t.w_see) / dt;
+  return rc;
+}
+
+int slpic_read_gain(slpic_ctx* c, int inst, double* G) {
+  if (!valid_inst(c, inst) || !G) return fail(c, SLPIC_ERR_INVALID_ARG, "bad arguments");
+  slpic_tallies t;
+  int rc = slpic_read_tallies(c, inst, &t);
+  InstState is;
+  CK(cudaMemcpy(&is, c->d_istate + inst, sizeof is, cudaMemcpyDeviceToHost), "gain");
+  const InstDev& P = c->h_inst[inst];
+  const double seed = (double)is.w_seed / (double)P.wscale;
+  *G = seed > 0 ? c->hi[inst].gamma * t.w_cath_ion_gen0 / seed : 0.0;
+  return rc;
+}
+
+int slpic_set_profiling(slpic_ctx* c, int on) {
+  if (!c) return SLPIC_ERR_INVALID_ARG;
+  c->profiling = on != 0;
+  c->ev_used = 0;
+  c->prof_ms = 0;
+  c->prof_launches = 0;
+  return SLPIC_OK;
+}
+
+int slpic_read_profile(slpic_ctx* c, double* ms, int64_t* launches) {
+  if (!c || !ms || !launches) return SLPIC_ERR_INVALID_ARG;
+  if (int rc = prepare(c)) return rc;
+  int rc = sync(c);
+  for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, c->ev[k], c->ev[k + 1]), "profile");
+    c->prof_ms += t;
+    c->prof_launches += 1;
+  }
+  c->ev_used = 0;
+  *ms = c->prof_ms;
+  *launches = c->prof_launches;
+  return rc;
+}
+
+int slpic_launch_count(slpic_ctx* c, int64_t* launches) {
+  if (!c || !launches) return SLPIC_ERR_INVALID_ARG;
+  *launches = c->last_launches;
+  return SLPIC_OK;
+}
+
+int slpic_philox(int device, uint64_t seed, const uint32_t* ctr, int64_t n, uint32_t* out) {
+  if (!ctr || !out || n < 0) return SLPIC_ERR_INVALID_ARG;
+  if (n == 0) return SLPIC_OK;
+  if (cudaSetDevice(device) != cudaSuccess) return SLPIC_ERR_CUDA;
+  uint32_t *dc = nullptr, *dout = nullptr;
+  const size_t b = (size_t)n * 16;
+  if (cudaMalloc(&dc, b) != cudaSuccess) return SLPIC_ERR_CUDA;
+  if (cudaMalloc(&dout, b) != cudaSuccess) {
+    cudaFree(dc);
+    return SLPIC_ERR_CUDA;
+  }
+  int rc = SLPIC_OK;
+  if (cudaMemcpy(dc, ctr, b, cudaMemcpyHostToDevice) != cudaSuccess) rc = SLPIC_ERR_CUDA;
+  if (!rc) {
+    launch_philox((uint32_t)seed, (uint32_t)(seed >> 32), dc, dout, n, 0);
+    if (cudaGetLastError() != cudaSuccess) rc = SLPIC_ERR_CUDA;
+  }
+  if (!rc && cudaMemcpy(out, dout, b, cudaMemcpyDeviceToHost) != cudaSuccess) rc = SLPIC_ERR_CUDA;
+  cudaFree(dc);
+  cudaFree(dout);
+  return rc;
+}
+
+}  // extern "C"

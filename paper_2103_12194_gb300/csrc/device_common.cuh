@@ -1,0 +1,98 @@
+// Device helpers shared by the kernels of libslpic: Philox4x32-10, the
+// uniform map, the speed limiter and the kinematic building blocks.
+//
+// The whole library is compiled with -fmad=false and IEEE division and square
+// root, so every expression below is evaluated with one rounding per
+// operation, in the order written.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "slpic_internal.h"
+
+namespace slpic {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each two
+// 32x32 -> 64-bit products of counter words 0 and 2 with the round
+// multipliers, the high halves mixed with the other words and the round key;
+// the key advances by the Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// 32 random bits -> (floor(x / 2^9) + 1/2) 2^-23, exactly representable.
+__device__ __forceinline__ float uniform01(uint32_t x) {
+  return (__uint2float_rn(x >> 9) + 0.5f) * 1.1920928955078125e-07f;
+}
+
+__device__ __forceinline__ void uniform4(uint4 r, float u[4]) {
+  u[0] = uniform01(r.x);
+  u[1] = uniform01(r.y);
+  u[2] = uniform01(r.z);
+  u[3] = uniform01(r.w);
+}
+
+// beta(v) = min(1, v_lim / v), Eq. betaAbrupt; v_lim = +inf gives 1.
+__device__ __forceinline__ float beta_of(float v, float vlim) {
+  return v > vlim ? vlim / v : 1.0f;
+}
+
+// Direction with cos(theta) = 1 - 2 ua about x and azimuth 2 pi ub.
+__device__ __forceinline__ void isotropic(float speed, float ua, float ub, float two_pi,
+                                          float& vx, float& vy, float& vz) {
+  const float ct = 1.0f - 2.0f * ua;
+  const float st = sqrtf(fmaxf(0.0f, (1.0f - ct) * (1.0f + ct)));
+  const float ph = two_pi * ub;
+  vx = speed * ct;
+  vy = speed * (st * cosf(ph));
+  vz = speed * (st * sinf(ph));
+}
+
+// Turn the unit vector u by polar angle chi (cos cc, sin sc) and azimuth
+// (cos cp, sin sp) about itself; perpendicular frame from the x axis, or the
+// z axis when |ux| > 0.99.
+__device__ __forceinline__ void rotate(float& ux, float& uy, float& uz, float cc, float sc,
+                                       float cp, float sp) {
+  float nx, ny, nz;
+  if (fabsf(ux) <= 0.99f) {
+    const float w = sqrtf((1.0f - ux) * (1.0f + ux));
+    nx = ux * cc + sc * (cp * w);
+    ny = uy * cc + sc * ((uz * sp - ux * (uy * cp)) / w);
+    nz = uz * cc - sc * ((uy * sp + ux * (uz * cp)) / w);
+  } else {
+    const float w = sqrtf((1.0f - uz) * (1.0f + uz));
+    nx = ux * cc + sc * ((uy * sp - uz * (ux * cp)) / w);
+    ny = uy * cc - sc * ((ux * sp + uz * (uy * cp)) / w);
+    nz = uz * cc + sc * (cp * w);
+  }
+  ux = nx;
+  uy = ny;
+  uz = nz;
+}
+
+// Fixed-point charge of a marker: round(w_p 2^shift), w_p = beta w_j.
+__device__ __forceinline__ long long fixed_charge(float wp, float wscale) {
+  return __float2ll_rn(wp * wscale);
+}
+
+// Split a fixed-point charge between the two nodes of the marker's cell with
+// 24-bit linear weights: the right node gets floor(Q f / 2^24).
+__device__ __forceinline__ long long right_share(long long Q, float off) {
+  const long long f = __float2ll_rz(off * 16777216.0f);
+  return (Q * f) >> 24;
+}
+
+}  // namespace slpic

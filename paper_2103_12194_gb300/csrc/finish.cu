@@ -1,0 +1,369 @@
+// End of a step, one CTA per instance: append the staged births after the
+// compacted survivors, publish the step's deposit, solve the 1D Poisson
+// equation for the next step's field, and commit the step's tallies.  The
+// last CTA to finish plans the next step's tiles.  Also: seeding and the
+// Philox self-check kernel.
+#include "device_common.cuh"
+#include "slpic_internal.h"
+
+namespace slpic {
+
+namespace {
+
+constexpr int kFinThreads = 1024;
+
+__device__ __forceinline__ void set_error(Control* ctrl, int code, int inst) {
+  if (atomicCAS(&ctrl->error, 0, code) == 0) ctrl->error_inst = inst;
+}
+
+// Inclusive block scan (Hillis-Steele over the per-thread chunk sums).
+template <typename T>
+__device__ T block_incl_scan(T v, T* buf) {
+  buf[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 1; o < kFinThreads; o <<= 1) {
+    T add = threadIdx.x >= (unsigned)o ? buf[threadIdx.x - o] : T(0);
+    __syncthreads();
+    buf[threadIdx.x] += add;
+    __syncthreads();
+  }
+  T r = buf[threadIdx.x];
+  __syncthreads();
+  return r;
+}
+
+__device__ void copy_births(const SoA& src, const SoA& dst, unsigned int n, unsigned int at,
+                            bool assign_id, uint32_t first_serial) {
+  for (unsigned int i = threadIdx.x; i < n; i += kFinThreads) {
+    const unsigned int o = at + i;
+    dst.cell[o] = src.cell[i];
+    dst.off[o] = src.off[i];
+    dst.vx[o] = src.vx[i];
+    dst.vy[o] = src.vy[i];
+    dst.vz[o] = src.vz[i];
+    dst.wj[o] = src.wj[i];
+    dst.id[o] = assign_id ? (src.id[i] & kGenBit) | ((first_serial + i) & kSerialMask)
+                          : src.id[i];
+  }
+}
+
+// Plan the tiles of the next step from the live counts (one thread).
+__device__ void plan_next(const DeviceRefs& r) {
+  const int n_seg = r.n_inst * 2;
+  unsigned int start = 0;
+  for (int s = 0; s < n_seg; ++s) {
+    r.seg_start[s] = start;
+    const unsigned int n = r.sstate[s].n_live;
+    start += (n + kTile - 1) / kTile;
+    r.sstate[s].n_surv = 0;
+    r.sstate[s].n_ba = 0;
+    r.sstate[s].n_bb = 0;
+  }
+  r.seg_start[n_seg] = start;
+  r.ctrl->n_tiles = start;
+  r.ctrl->n_seg = n_seg;
+  r.ctrl->tile_counter = 0;
+  r.ctrl->epoch = (r.ctrl->epoch + 1u) & 0x3FFFFFFFu;
+  r.ctrl->finish_done = 0;
+}
+
+}  // namespace
+
+// mode 0: finish a step and plan the next; mode 1: plan only (one CTA).
+__global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode) {
+  __shared__ long long s_i64[kFinThreads];
+  __shared__ __int128 s_i128[kFinThreads];
+  __shared__ int s_flag;
+  Control* ctrl = r.ctrl;
+  if (mode == 1) {
+    if (threadIdx.x == 0) plan_next(r);
+    return;
+  }
+  if (*((volatile int*)&ctrl->error)) return;
+  const int inst = blockIdx.x;
+  const InstDev& P = r.inst[inst];
+  InstState& is = r.istate[inst];
+  SpeciesState& se = r.sstate[inst * 2 + kElectron];
+  SpeciesState& si = r.sstate[inst * 2 + kIon];
+
+  // ---- append births -----------------------------------------------------
+  const unsigned int n_ionz = se.n_ba;  // equals si.n_ba
+  const unsigned int n_see = se.n_bb;
+  const unsigned int ne = se.n_surv + n_ionz + n_see;
+  const unsigned int ni = si.n_surv + n_ionz;
+  if (threadIdx.x == 0) {
+    int err = 0;
+    if (ne > P.sp[kElectron].cap || ni > P.sp[kIon].cap) err = kErrCapacity;
+    if (n_ionz > P.sp[kElectron].stage_cap || n_see > P.sp[kElectron].stage_cap ||
+        n_ionz > P.sp[kIon].stage_cap)
+      err = kErrCapacity;
+    if ((unsigned long long)se.next_id + n_ionz + n_see > kSerialMask ||
+        (unsigned long long)si.next_id + n_ionz > kSerialMask)
+      err = kErrIdWrap;
+    if (err) set_error(ctrl, err, inst);
+    s_flag = err;
+  }
+  __syncthreads();
+  if (s_flag) return;
+  {
+    const SpeciesDev& E = P.sp[kElectron];
+    const SoA dst = E.buf[se.cur ^ 1u];
+    copy_births(E.stage_a, dst, n_ionz, se.n_surv, false, 0);
+    copy_births(E.stage_b, dst, n_see, se.n_surv + n_ionz, true, se.next_id + n_ionz);
+    const SpeciesDev& I = P.sp[kIon];
+    copy_births(I.stage_a, I.buf[si.cur ^ 1u], n_ionz, si.n_surv, false, 0);
+  }
+
+  // ---- deposit of the step -> rho_last; clear the accumulators -------------
+  const int nn = P.n_cells + 1;
+  for (int s = 0; s < 2; ++s) {
+    for (int k = threadIdx.x; k < nn; k += kFinThreads) {
+      P.rho_last[s][k] = (long long)P.rho_acc[s][k];
+      P.rho_acc[s][k] = 0ull;
+    }
+  }
+  __syncthreads();
+
+  // ---- Poisson: (phi[k+1] - 2 phi[k] + phi[k-1]) = -C net_k, k = 1..N-1 ----
+  // With D_k = phi[k] - phi[k-1]: D_k = D_1 - C I_k, I_k = sum_{j<k} net_j,
+  // phi[k] = k D_1 - C J_k, J_k = sum_{i<=k} I_i, and phi[N] = V fixes D_1.
+  // I and J are exact integers (64- and 128-bit), so the solution is
+  // independent of the summation order.
+  if (P.field_mode == 1) {
+    const int N = P.n_cells;
+    const int chunk = (N + kFinThreads - 1) / kFinThreads;  // over k = 1..N
+    const int k0 = 1 + threadIdx.x * chunk;
+    // local sums of net over j in [k0, k0 + chunk) restricted to 1..N-1
+    long long loc = 0;
+    for (int k = k0; k < k0 + chunk && k <= N; ++k)
+      if (k <= N - 1) loc += P.rho_last[kIon][k] - P.rho_last[kElectron][k];
+    const long long inc = block_incl_scan<long long>(loc, s_i64);
+    // I_k for k in this chunk: exclusive of net_k
+    long long I = inc - loc;
+    __int128 locJ = 0;
+    for (int k = k0; k < k0 + chunk && k <= N; ++k) {
+      locJ += (__int128)I;
+      if (k <= N - 1) I += P.rho_last[kIon][k] - P.rho_last[kElectron][k];
+    }
+    const __int128 incJ = block_incl_scan<__int128>(locJ, s_i128);
+    __shared__ __int128 s_JN;
+    if (threadIdx.x == kFinThreads - 1) s_JN = incJ;
+    __syncthreads();
+    const double C = P.pois_C;
+    const double D1 = (P.V + C * (double)s_JN) / (double)N;
+    __int128 J = incJ - locJ;
+    I = inc - loc;
+    for (int k = k0; k < k0 + chunk && k <= N; ++k) {
+      J += (__int128)I;
+      if (k <= N - 1) I += P.rho_last[kIon][k] - P.rho_last[kElectron][k];
+      P.phi[k] = (double)k * D1 - C * (double)J;
+    }
+    if (threadIdx.x == 0) P.phi[0] = 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) P.phi[N] = P.V;
+    __syncthreads();
+    const double inv2dx = 1.0 / (2.0 * P.dx);
+    for (int k = threadIdx.x; k <= N; k += kFinThreads) {
+      double e;
+      if (k == 0) e = -(P.phi[1] - P.phi[0]) / P.dx;
+      else if (k == N) e = -(P.phi[N] - P.phi[N - 1]) / P.dx;
+      else e = -(P.phi[k + 1] - P.phi[k - 1]) * inv2dx;
+      P.E64[k] = e;
+      P.E32[k] = (float)e;
+    }
+  }
+  __syncthreads();
+
+  // ---- tallies -------------------------------------------------------------
+  if (threadIdx.x == 0) {
+    const double unit = 1.0 / (double)P.wscale;
+    unsigned long long* a = P.acc;
+    TallyRec t;
+    t.step = is.step;
+    t.n_live[0] = ne;
+    t.n_live[1] = ni;
+    t.w_live[0] = (double)(long long)(a[ACC_WSURV] + a[ACC_WIONZ] + a[ACC_WSEE]) * unit;
+    t.w_live[1] = (double)(long long)(a[ACC_WSURV + 1] + a[ACC_WIONZ]) * unit;
+    for (int k = 0; k < 3; ++k) t.n_coll[k] = (long long)a[ACC_COLL0 + k];
+    t.n_candidates = (long long)a[ACC_CAND];
+    for (int s = 0; s < 2; ++s)
+      for (int e = 0; e < 2; ++e) {
+        t.n_abs[s][e] = (long long)a[ACC_NABS + 2 * s + e];
+        t.w_abs[s][e] = (double)(long long)a[ACC_WABS + 2 * s + e] * unit;
+      }
+    t.n_see = (long long)a[ACC_SEE];
+    t.w_see = (double)(long long)a[ACC_WSEE] * unit;
+    t.w_ionz = (double)(long long)a[ACC_WIONZ] * unit;
+    t.w_cath_ion = (double)(long long)a[ACC_WCATH] * unit;
+    t.w_cath_ion_gen0 = (double)(long long)a[ACC_WCATH0] * unit;
+    t.n_clamp = (long long)a[ACC_CLAMP];
+    t.n_majorant = (long long)a[ACC_MAJ];
+    t.marker_steps = (long long)a[ACC_MSTEPS];
+    P.ring[is.n_steps_done % P.ring_len] = t;
+    TallyRec& T = *P.total;
+    T.step = t.step;
+    T.n_live[0] = t.n_live[0];
+    T.n_live[1] = t.n_live[1];
+    T.w_live[0] = t.w_live[0];
+    T.w_live[1] = t.w_live[1];
+    for (int k = 0; k < 3; ++k) T.n_coll[k] += t.n_coll[k];
+    T.n_candidates += t.n_candidates;
+    for (int s = 0; s < 2; ++s)
+      for (int e = 0; e < 2; ++e) {
+        T.n_abs[s][e] += t.n_abs[s][e];
+        T.w_abs[s][e] += t.w_abs[s][e];
+      }
+    T.n_see += t.n_see;
+    T.w_see += t.w_see;
+    T.w_ionz += t.w_ionz;
+    T.w_cath_ion += t.w_cath_ion;
+    T.w_cath_ion_gen0 += t.w_cath_ion_gen0;
+    T.n_clamp += t.n_clamp;
+    T.n_majorant += t.n_majorant;
+    T.marker_steps += t.marker_steps;
+    for (int k = 0; k < ACC_COUNT; ++k) a[k] = 0ull;
+    // commit the marker state
+    se.cur ^= 1u;
+    se.n_live = ne;
+    se.next_id += n_ionz + n_see;
+    si.cur ^= 1u;
+    si.n_live = ni;
+    si.next_id += n_ionz;
+    is.step += 1u;
+    is.n_steps_done += 1;
+  }
+
+  // ---- the last CTA plans the next step --------------------------------------
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int ticket = atomicAdd(&ctrl->finish_done, 1u);
+    s_flag = ticket == gridDim.x - 1 ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_flag && threadIdx.x == 0) {
+    __threadfence();
+    plan_next(r);
+  }
+}
+
+void launch_finish(const DeviceRefs& r, int mode, cudaStream_t s) {
+  const int grid = mode == 1 ? 1 : r.n_inst;
+  k_finish<<<grid, kFinThreads, 0, s>>>(r, mode);
+}
+
+// ---------------------------------------------------------------------------
+// Seeding: n markers appended at index base = n_live of the species, drawn
+// from Philox with counter (id, 0xFFFFFFFF, inst * 2 + species, block).
+// ---------------------------------------------------------------------------
+__global__ void k_seed(DeviceRefs r, int inst, int sp, uint32_t base, uint32_t first_id,
+                       uint32_t n, int mode, float ekin, float elo, float lr, float wj) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const InstDev& P = r.inst[inst];
+  const SpeciesDev& S = P.sp[sp];
+  const SoA d = S.buf[r.sstate[inst * 2 + sp].cur];
+  const uint32_t id = first_id + i;
+  float u[4];
+  uniform4(philox4x32_10(make_uint4(id, kSeedStep, P.ctr_inst * 2u + (uint32_t)sp, 0u),
+                         P.key0, P.key1),
+           u);
+  int cell = 0;
+  float off = 0.0f, vx = 0.0f, vy = 0.0f, vz = 0.0f;
+  const int N = P.n_cells;
+  if (mode == 0) {
+    off = u[0];
+    const float v = sqrtf(ekin * S.K_V);
+    const float ct = u[1];
+    const float st = sqrtf(fmaxf(0.0f, (1.0f - ct) * (1.0f + ct)));
+    const float ph = P.two_pi * u[2];
+    vx = v * ct;
+    vy = v * (st * cosf(ph));
+    vz = v * (st * sinf(ph));
+  } else if (mode == 2 || mode == 3) {
+    const float p = u[0] * (float)N;
+    const float fl = floorf(p);
+    cell = (int)fl;
+    off = p - fl;
+    if (cell >= N) {
+      cell = N - 1;
+      off = __int_as_float(0x3F7FFFFF);  // largest float below 1
+    }
+    if (mode == 2) {
+      const float e = elo * expf(u[1] * lr);
+      isotropic(sqrtf(e * S.K_V), u[2], u[3], P.two_pi, vx, vy, vz);
+    } else {
+      float g[4];
+      uniform4(philox4x32_10(make_uint4(id, kSeedStep, P.ctr_inst * 2u + (uint32_t)sp, 1u),
+                             P.key0, P.key1),
+               g);
+      // gas-temperature Maxwellian of this species
+      const float sig = ekin;  // sqrt(k T / m), passed in ekin for this mode
+      const float r1 = sqrtf(-2.0f * logf(u[1]));
+      const float r2 = sqrtf(-2.0f * logf(u[3]));
+      const float a1 = P.two_pi * u[2], a2 = P.two_pi * g[0];
+      vx = sig * (r1 * cosf(a1));
+      vy = sig * (r1 * sinf(a1));
+      vz = sig * (r2 * cosf(a2));
+    }
+  }
+  const uint32_t o = base + i;
+  d.cell[o] = cell;
+  d.off[o] = off;
+  d.vx[o] = vx;
+  d.vy[o] = vy;
+  d.vz[o] = vz;
+  d.wj[o] = wj;
+  d.id[o] = id & kSerialMask;
+}
+
+void launch_seed(const DeviceRefs& r, int inst, int species, uint32_t base, uint32_t first_id,
+                 uint32_t n, int mode, float e0, float e_lo, float lr, float wj,
+                 cudaStream_t s) {
+  if (n == 0) return;
+  const int threads = 256;
+  const unsigned int grid = (n + threads - 1) / threads;
+  k_seed<<<grid, threads, 0, s>>>(r, inst, species, base, first_id, n, mode, e0, e_lo, lr, wj);
+}
+
+// Check loaded markers (cell in [0, N), offset in [0, 1), finite velocities,
+// finite non-negative weight); records the smallest bad index in *bad and the
+// fixed-point sum of the weights in *wsum.
+__global__ void k_validate(SoA d, uint32_t n, int N, float wscale, unsigned int* bad,
+                           unsigned long long* wsum) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long w = 0;
+  if (i < n) {
+    const float o = d.off[i], x = d.vx[i], y = d.vy[i], z = d.vz[i], wj = d.wj[i];
+    const int c = d.cell[i];
+    const bool ok = c >= 0 && c < N && o >= 0.0f && o < 1.0f && isfinite(x) && isfinite(y) &&
+                    isfinite(z) && wj >= 0.0f && isfinite(wj);
+    if (!ok) atomicMin(bad, i);
+    else w = (unsigned long long)fixed_charge(wj, wscale);
+  }
+  for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xFFFFFFFFu, w, o);
+  if ((threadIdx.x & 31) == 0 && w) atomicAdd(wsum, w);
+}
+
+void launch_validate(const SoA& d, uint32_t n, int N, float wscale, unsigned int* bad,
+                     unsigned long long* wsum, cudaStream_t s) {
+  if (n == 0) return;
+  const int threads = 256;
+  k_validate<<<(n + threads - 1) / threads, threads, 0, s>>>(d, n, N, wscale, bad, wsum);
+}
+
+__global__ void k_philox(uint32_t k0, uint32_t k1, const uint4* ctr, uint4* out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = philox4x32_10(ctr[i], k0, k1);
+}
+
+void launch_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, uint32_t* out, long long n,
+                   cudaStream_t s) {
+  if (n <= 0) return;
+  const int threads = 256;
+  const long long grid = (n + threads - 1) / threads;
+  k_philox<<<(unsigned int)grid, threads, 0, s>>>(k0, k1, reinterpret_cast<const uint4*>(ctr),
+                                                  reinterpret_cast<uint4*>(out), n);
+}
+
+}  // namespace slpic

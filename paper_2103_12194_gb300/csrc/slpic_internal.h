@@ -1,0 +1,196 @@
+// Internal device-side layout shared by the kernels and the host driver of
+// libslpic.  Nothing here is part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace slpic {
+
+constexpr int kElectron = 0;
+constexpr int kIon = 1;
+constexpr uint32_t kGenBit = 0x80000000u;
+constexpr uint32_t kSerialMask = 0x7FFFFFFFu;
+constexpr uint32_t kSeedStep = 0xFFFFFFFFu;
+
+// Particle kernel shape: kThreads threads, kPerThread consecutive markers per
+// thread (one 16-byte vector per field), one tile = kTile markers.
+constexpr int kThreads = 256;
+constexpr int kPerThread = 4;
+constexpr int kTile = kThreads * kPerThread;
+
+// Device error word values (copied to the host status codes).
+constexpr int kErrNone = 0;
+constexpr int kErrCapacity = 1;
+constexpr int kErrTimeout = 2;
+constexpr int kErrIdWrap = 3;
+
+// Bounded waits: spins of ~100 ns before a wait gives up with kErrTimeout.
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+// Per-step accumulators of one instance (integer; weights in fixed point).
+enum Acc : int {
+  ACC_CAND = 0,
+  ACC_COLL0,  // elastic
+  ACC_COLL1,  // excitation
+  ACC_COLL2,  // ionization
+  ACC_SEE,
+  ACC_NABS,        // 4 entries: [species][electrode]
+  ACC_WABS = ACC_NABS + 4,
+  ACC_WSEE = ACC_WABS + 4,
+  ACC_WIONZ,
+  ACC_WCATH,
+  ACC_WCATH0,
+  ACC_CLAMP,
+  ACC_MAJ,
+  ACC_MSTEPS,
+  ACC_WSURV,       // 2 entries: survivors' weight per species
+  ACC_COUNT = ACC_WSURV + 2
+};
+
+// Record of one step, converted (same layout as slpic_tallies).
+struct TallyRec {
+  long long step;
+  long long n_live[2];
+  double w_live[2];
+  long long n_coll[3];
+  long long n_candidates;
+  long long n_abs[2][2];
+  double w_abs[2][2];
+  long long n_see;
+  double w_see;
+  double w_ionz;
+  double w_cath_ion;
+  double w_cath_ion_gen0;
+  long long n_clamp;
+  long long n_majorant;
+  long long marker_steps;
+};
+
+struct SoA {
+  int32_t* cell;
+  float* off;
+  float* vx;
+  float* vy;
+  float* vz;
+  float* wj;
+  uint32_t* id;
+};
+
+// Mutable per-(instance, species) state, resident on the device.
+struct SpeciesState {
+  uint32_t cur;      // ping-pong buffer holding the live markers
+  uint32_t n_live;   // live markers
+  uint32_t next_id;  // next serial number
+  uint32_t n_surv;   // survivors of the current step (set by the push)
+  uint32_t n_ba;     // births staged in region A (ionization) this step
+  uint32_t n_bb;     // births staged in region B (secondary emission) this step
+  uint32_t pad[2];
+};
+
+// Configuration of one species of one instance (constant during a run).
+struct SpeciesDev {
+  SoA buf[2];       // ping-pong marker arrays
+  SoA stage_a;      // births from ionization
+  SoA stage_b;      // electrons only: births from secondary emission
+  uint32_t cap;     // capacity of each ping-pong buffer
+  uint32_t stage_cap;
+  float qmdt;       // (q / m) dt
+  float vlim;       // speed limit (+inf: beta = 1)
+  float K_V;        // 2 e / m: speed^2 per eV
+  float pad;
+};
+
+// Configuration of one instance (constant during a run).
+struct InstDev {
+  int n_cells;
+  int field_mode;
+  int charge_shift;
+  int tab_lo_exp2;
+  int tab_log2_sub;
+  int tab_nodes;      // real nodes (a padding node follows)
+  uint32_t key0, key1;
+  uint32_t ctr_inst;  // counter word 2 = ctr_inst * 2 + species
+  float dtdx;         // dt / dx
+  float K_E;          // m_e / (2 e): eV per (m/s)^2
+  float ndt;          // n_g dt
+  float P0;           // null-collision majorant probability
+  float vb_cap;       // cap of beta v in the majorant
+  float R2;           // 2 m_e / M
+  float e_ex, e_io;   // thresholds [eV]
+  float sigT_ion;     // sqrt(k T / M)
+  float gamma;        // secondary-emission yield
+  float wscale;       // 2^charge_shift
+  float two_pi;
+  float e_lo, e_hi;   // table range [eV]
+  double dx, d, V, area, dt;
+  double pois_C;      // e dx 2^-shift / (area eps0)
+  const float4* table;          // cumulative (S1, S2, S3, 0) per node
+  float* E32;                   // node field used by the push
+  double* phi;                  // node potential
+  double* E64;                  // node field
+  unsigned long long* rho_acc[2];  // fixed-point deposit of the current step
+  long long* rho_last[2];          // deposit of the last finished step
+  unsigned long long* acc;         // ACC_COUNT per-step accumulators
+  TallyRec* ring;                  // per-step records
+  TallyRec* total;                 // sums since the last reset
+  int ring_len;
+  int pad;
+  SpeciesDev sp[2];
+};
+
+// Mutable per-instance counters.
+struct InstState {
+  uint32_t step;        // step index (Philox counter word 1)
+  uint32_t pad;
+  long long n_steps_done;
+  unsigned long long w_seed;  // fixed-point sum of seeded electron weights
+};
+
+// Look-back record of one tile.
+struct TileStatus {
+  unsigned int flag;   // (epoch << 2) | state, state 1 = aggregate, 2 = inclusive
+  unsigned int agg[3];
+  unsigned int incl[3];
+  unsigned int pad;
+};
+
+// Global state of the batched step.
+struct Control {
+  unsigned int epoch;        // step epoch for look-back flags
+  unsigned int tile_counter; // next tile to hand out
+  unsigned int n_tiles;      // tiles this step
+  unsigned int n_seg;        // segments = instances * 2
+  unsigned int finish_done;  // CTAs of the finish kernel that completed
+  int error;                 // first device error (kErr*)
+  int error_inst;
+  int pad;
+};
+
+struct DeviceRefs {
+  InstDev* inst;          // [n_inst]
+  InstState* istate;      // [n_inst]
+  SpeciesState* sstate;   // [n_inst * 2]
+  Control* ctrl;
+  TileStatus* tiles;      // [max tiles]
+  unsigned int* seg_start;  // [n_seg + 1] first global tile of each segment
+  int n_inst;
+  int smem_nodes;         // deposit tile nodes in shared memory (0: global atomics)
+  unsigned int max_tiles;
+};
+
+// Launchers (defined in the .cu files).
+void launch_push(const DeviceRefs& r, int grid, cudaStream_t s);
+int push_occupancy(int smem_nodes, int* blocks_per_sm, size_t* smem_bytes);
+void launch_finish(const DeviceRefs& r, int mode, cudaStream_t s);
+// Seeding: mode 0/1/2 as SLPIC_SEED_*; for mode 3 (thermal) e0 carries the
+// thermal speed sqrt(k T / m).
+void launch_seed(const DeviceRefs& r, int inst, int species, uint32_t base, uint32_t first_id,
+                 uint32_t n, int mode, float e0, float e_lo, float lr, float wj,
+                 cudaStream_t s);
+void launch_validate(const SoA& d, uint32_t n, int N, float wscale, unsigned int* bad,
+                     unsigned long long* wsum, cudaStream_t s);
+void launch_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, uint32_t* out,
+                   long long n, cudaStream_t s);
+
+}  // namespace slpic
