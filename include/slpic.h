@@ -134,7 +134,8 @@ int slpic_set_cross_sections(slpic_ctx* ctx, int inst, int lo_exp2,
                              const float* sig_io, double e_io);
 /* Species: mass [kg], charge [C], speed limit v_lim [m/s] of Eq. betaAbrupt
  * (beta = min(1, v_lim/|v|); v_lim <= 0 or +inf gives beta = 1, i.e. PIC),
- * capacity = maximum live markers.  Only electrons collide (Sec. IV). */
+ * capacity = maximum live markers (rounded up to whole tiles of 1024 markers,
+ * plus one tile).  Only electrons collide (Sec. IV). */
 int slpic_set_species(slpic_ctx* ctx, int inst, int species, double mass,
                       double charge, double v_lim, int64_t capacity);
 /* Ion-induced secondary-electron yield gamma at the cathode (constant; the
@@ -221,6 +222,10 @@ int slpic_set_profiling(slpic_ctx* ctx, int on);
 /* Total device time [ms] and number of particle-kernel launches timed since
  * profiling was switched on (synchronises). */
 int slpic_read_profile(slpic_ctx* ctx, double* push_ms, int64_t* launches);
+/* Look-back statistics of the particle kernel since the last call: how many
+ * times a tile found its predecessor's count not yet published, and the
+ * longest such wait in polls (about 0.1 us each).  Synchronises; resets. */
+int slpic_read_wait_stats(slpic_ctx* ctx, int64_t* waits, int64_t* longest);
 /* Device-side kernel launches made by the last slpic_step call. */
 int slpic_launch_count(slpic_ctx* ctx, int64_t* launches);
 

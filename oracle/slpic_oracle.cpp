@@ -456,15 +456,25 @@ struct Sim {
     t.n_coll[proc]++;
     const R kv = K_V[ELECTRON];
     if (proc == 0) {
-      // Elastic, Vahedi-Surendra: cos chi = (2 + eps - 2 (1 + eps)^u) / eps,
-      // written as 1 - 2 expm1(u log1p(eps)) / eps; recoil energy loss.
-      R em = std::expm1(u[2] * std::log1p(eps));
-      R cc = (R)1 - (em + em) / eps;
-      cc = std::min((R)1, std::max((R)-1, cc));
-      R sc = std::sqrt(std::max((R)0, ((R)1 - cc) * ((R)1 + cc)));
+      // Elastic, Vahedi-Surendra: cos chi = (2 + eps - 2 (1 + eps)^u) / eps.
+      // Both 1 - cos chi = 2 ((1 + eps)^u - 1) / eps and
+      // 1 + cos chi = 2 (1 + eps) (1 - (1 + eps)^(u - 1)) / eps are formed
+      // without cancellation (expm1 of u log1p(eps) and of -(1 - u) log1p(eps)),
+      // so sin chi = sqrt((1 - cos chi)(1 + cos chi)) keeps its relative
+      // precision for forward and backward scattering; recoil energy loss
+      // eps 2 m/M (1 - cos chi).
+      R L = std::log1p(eps);
+      R em = std::expm1(u[2] * L);
+      R ep = -std::expm1(-((R)1 - u[2]) * L);
+      R omc = (em + em) / eps;
+      R opc = (((R)1 + eps) * (ep + ep)) / eps;
+      omc = std::min((R)2, std::max((R)0, omc));
+      opc = std::min((R)2, std::max((R)0, opc));
+      R cc = omc <= (R)1 ? (R)1 - omc : opc - (R)1;
+      R sc = std::sqrt(omc * opc);
       R ph = two_pi * u[3];
       R cp = std::cos(ph), spn = std::sin(ph);
-      R e_new = eps * ((R)1 - R2 * ((R)1 - cc));
+      R e_new = eps * ((R)1 - R2 * omc);
       R ux = m.vx / v1, uy = m.vy / v1, uz = m.vz / v1;
       rotate(ux, uy, uz, cc, sc, cp, spn);
       R v_new = std::sqrt(e_new * kv);

@@ -71,12 +71,13 @@ struct slpic_ctx {
   InstState* d_istate = nullptr;
   SpeciesState* d_sstate = nullptr;
   Control* d_ctrl = nullptr;
-  TileStatus* d_tiles = nullptr;
+  Transfer* d_xfer = nullptr;
   unsigned int* d_seg = nullptr;
   unsigned int* d_scratch = nullptr;  // 16 bytes for small device results
   std::vector<InstDev> h_inst;  // host copies of the device configuration
   DeviceRefs refs{};
   int push_grid = 0;
+  int move_grid = 0;
   int blocks_per_sm = 0;
   // graph of kGraphSteps steps
   cudaGraphExec_t graph = nullptr;
@@ -282,7 +283,6 @@ int commit(slpic_ctx* c) {
     if (int rc = check_config(c, i)) return rc;
   if (int rc = set_device(c)) return rc;
   c->h_inst.assign(c->n_inst, InstDev{});
-  unsigned long long max_tiles = 0;
   int max_nodes = 0;
   for (int i = 0; i < c->n_inst; ++i) {
     HostInst& h = c->hi[i];
@@ -325,34 +325,40 @@ int commit(slpic_ctx* c) {
     }
     ht[tab_n - 1] = ht[tab_n - 2];
     CK(cudaMemcpy(tab, ht.data(), tab_n * 16, cudaMemcpyHostToDevice), "table");
-    // species
+    // marker stores: tiles of kTile slots; births are staged in slots of the
+    // tile that created them (ionization: electron tiles, emission: ion tiles)
+    uint32_t cap_tiles[2];
+    for (int s = 0; s < 2; ++s)
+      cap_tiles[s] = (uint32_t)(((size_t)h.sp[s].cap + kTile - 1) / kTile + 1);
     for (int s = 0; s < 2; ++s) {
       SpeciesDev& S = P.sp[s];
-      const size_t cap = (size_t)h.sp[s].cap;
-      size_t stage = std::min(cap, std::max<size_t>(65536, cap / 4));
-      stage = (stage + 3) & ~size_t(3);
-      S.cap = (uint32_t)cap;
-      S.stage_cap = (uint32_t)stage;
-      const size_t capr = (cap + kTile - 1) / kTile * kTile;  // tile-rounded
-      size_t b = 2 * soa_bytes(capr) + soa_bytes(stage) + (s == kElectron ? soa_bytes(stage) : 0);
+      S.cap_tiles = cap_tiles[s];
+      const size_t slots = (size_t)cap_tiles[s] * kTile;
+      const size_t stage_a = (size_t)cap_tiles[kElectron] * kTile;
+      const size_t stage_b = s == kElectron ? (size_t)cap_tiles[kIon] * kTile : 0;
+      size_t b = 2 * soa_bytes(slots) + soa_bytes(stage_a) + soa_bytes(stage_b) +
+                 4 * (((size_t)cap_tiles[s] + 1) * 4 + 256);
       void* sb;
       if (int rc = dmalloc(c, &sb, b, "marker buffers")) return rc;
       char* q = (char*)sb;
-      S.buf[0] = carve_soa(q, capr);
-      S.buf[1] = carve_soa(q, capr);
-      S.stage_a = carve_soa(q, stage);
-      if (s == kElectron) S.stage_b = carve_soa(q, stage);
+      S.buf[0] = carve_soa(q, slots);
+      S.buf[1] = carve_soa(q, slots);
+      S.stage_a = carve_soa(q, stage_a);
+      if (stage_b) S.stage_b = carve_soa(q, stage_b);
       else std::memset(&S.stage_b, 0, sizeof(SoA));
-      max_tiles += (cap + kTile - 1) / kTile;
+      S.fill = carve<uint32_t>(q, cap_tiles[s] + 1);
+      S.births = carve<uint32_t>(q, cap_tiles[s] + 1);
+      S.boff = carve<uint32_t>(q, cap_tiles[s] + 1);
+      S.coff = carve<uint32_t>(q, cap_tiles[s] + 1);
+      CK(cudaMemset(S.fill, 0, ((size_t)cap_tiles[s] + 1) * 4), "fills");
     }
   }
-  if (max_tiles > 0x3FFFFFFFull) return fail(c, SLPIC_ERR_CAPACITY, "too many tiles");
   void* blk;
   const size_t nseg = 2 * (size_t)c->n_inst;
   size_t bytes = ((sizeof(InstDev) * c->n_inst + 255) & ~size_t(255)) +
                  ((sizeof(InstState) * c->n_inst + 255) & ~size_t(255)) +
-                 ((sizeof(SpeciesState) * nseg + 255) & ~size_t(255)) + 256 +
-                 ((sizeof(TileStatus) * (max_tiles + 1) + 255) & ~size_t(255)) +
+                 ((sizeof(SpeciesState) * nseg + 255) & ~size_t(255)) +
+                 ((sizeof(Transfer) * nseg + 255) & ~size_t(255)) + 256 +
                  ((4 * (nseg + 1) + 255) & ~size_t(255)) + 256;
   if (int rc = dmalloc(c, &blk, bytes, "control")) return rc;
   CK(cudaMemset(blk, 0, bytes), "control");
@@ -360,20 +366,19 @@ int commit(slpic_ctx* c) {
   c->d_inst = carve<InstDev>(p, c->n_inst);
   c->d_istate = carve<InstState>(p, c->n_inst);
   c->d_sstate = carve<SpeciesState>(p, nseg);
+  c->d_xfer = carve<Transfer>(p, nseg);
   c->d_ctrl = carve<Control>(p, 1);
-  c->d_tiles = carve<TileStatus>(p, max_tiles + 1);
   c->d_seg = carve<unsigned int>(p, nseg + 1);
   c->d_scratch = carve<unsigned int>(p, 4);
   c->refs.inst = c->d_inst;
   c->refs.istate = c->d_istate;
   c->refs.sstate = c->d_sstate;
+  c->refs.xfer = c->d_xfer;
   c->refs.ctrl = c->d_ctrl;
-  c->refs.tiles = c->d_tiles;
   c->refs.seg_start = c->d_seg;
   c->refs.n_inst = c->n_inst;
-  c->refs.max_tiles = (unsigned int)max_tiles;
   // the whole charge grid of the largest instance goes to shared memory when
-  // it fits next to the marker staging; otherwise deposits use global atomics
+  // it fits next to the two marker stages; otherwise deposits use global atomics
   int smem_nodes = max_nodes <= 16385 ? max_nodes : 0;
   int bps = 0;
   size_t sbytes = 0;
@@ -388,6 +393,7 @@ int commit(slpic_ctx* c) {
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device), "attributes");
   c->blocks_per_sm = bps;
   c->push_grid = sms * bps;
+  c->move_grid = sms * 2;
   for (int i = 0; i < c->n_inst; ++i) {
     if (int rc = upload_inst(c, i)) return rc;
     if (int rc = reset_field(c, i)) return rc;
@@ -437,6 +443,7 @@ int build_graph(slpic_ctx* c) {
   for (int k = 0; k < kGraphSteps; ++k) {
     launch_push(c->refs, c->push_grid, c->capture_stream);
     launch_finish(c->refs, 0, c->capture_stream);
+    launch_move(c->refs, c->move_grid, c->capture_stream);
   }
   CK(cudaStreamEndCapture(c->capture_stream, &g), "capture");
   cudaError_t e = cudaGraphInstantiate(&c->graph, g, 0);
@@ -644,8 +651,38 @@ int slpic_suggest_dt(double d, int n_cells, double V, double m_ion, int mode, do
   return SLPIC_OK;
 }
 
-int slpic_seed(slpic_ctx* c, int inst, int species, int64_t n, int mode, double e0,
-               double e_lo, double e_hi, double wj) {
+}  // extern "C"
+
+namespace {
+
+// Set the fills of tiles [first, ceil(end / kTile)) of a store whose slots
+// [first * kTile, end) are all live.
+int write_fills(slpic_ctx* c, const SpeciesDev& S, uint32_t first, uint32_t end) {
+  const uint32_t last = (end + kTile - 1) / kTile;
+  if (last <= first) return SLPIC_OK;
+  std::vector<uint32_t> f(last - first);
+  for (uint32_t k = first; k < last; ++k)
+    f[k - first] = std::min<uint32_t>(end - k * (uint32_t)kTile, (uint32_t)kTile);
+  CK(cudaMemcpy(S.fill + first, f.data(), f.size() * 4, cudaMemcpyHostToDevice), "fills");
+  return SLPIC_OK;
+}
+
+// First free slot after the last live marker of a store.
+int tail_slot(slpic_ctx* c, const SpeciesDev& S, const SpeciesState& st, uint32_t* out) {
+  if (st.n_tiles == 0) {
+    *out = 0;
+    return SLPIC_OK;
+  }
+  uint32_t f = 0;
+  CK(cudaMemcpy(&f, S.fill + st.n_tiles - 1, 4, cudaMemcpyDeviceToHost), "fills");
+  *out = (st.n_tiles - 1) * (uint32_t)kTile + f;
+  return SLPIC_OK;
+}
+
+}  // namespace
+
+extern "C" int slpic_seed(slpic_ctx* c, int inst, int species, int64_t n, int mode, double e0,
+                          double e_lo, double e_hi, double wj) {
   if (!valid_inst(c, inst) || (species != 0 && species != 1) || n < 0 || mode < 0 || mode > 3)
     return fail(c, SLPIC_ERR_INVALID_ARG, "bad seed arguments");
   if (!(wj >= 0) || !std::isfinite(wj) || !(e0 >= 0) || (mode == 2 && !(e_lo > 0 && e_hi >= e_lo)))
@@ -655,20 +692,29 @@ int slpic_seed(slpic_ctx* c, int inst, int species, int64_t n, int mode, double 
   SpeciesState st;
   if (int rc = read_state(c, inst, species, &st)) return rc;
   const InstDev& P = c->h_inst[inst];
-  if ((uint64_t)st.n_live + (uint64_t)n > P.sp[species].cap)
+  const SpeciesDev& S = P.sp[species];
+  uint32_t app = 0;
+  if (int rc = tail_slot(c, S, st, &app)) return rc;
+  if ((uint64_t)app + (uint64_t)n > (uint64_t)S.cap_tiles * kTile)
     return fail(c, SLPIC_ERR_CAPACITY, "seeding %lld markers exceeds the capacity", (long long)n);
   if ((uint64_t)st.next_id + (uint64_t)n > kSerialMask)
     return fail(c, SLPIC_ERR_CAPACITY, "marker serial numbers exhausted");
+  if (!((float)wj * P.wscale < 549755813888.0f))
+    return fail(c, SLPIC_ERR_INVALID_ARG,
+                "weight %g is too large for charge shift %d (w 2^shift must stay below 2^39)", wj,
+                P.charge_shift);
   const HostInst& h = c->hi[inst];
   float e0f = (float)e0;
   if (mode == 3) e0f = (float)std::sqrt(kKB * h.T_K / h.sp[species].mass);
   const float lr = mode == 2 ? (float)std::log(e_hi / e_lo) : 0.0f;
-  launch_seed(c->refs, inst, species, st.n_live, st.next_id, (uint32_t)n, mode, e0f,
-              (float)e_lo, lr, (float)wj, c->stream);
+  launch_seed(c->refs, inst, species, app, st.next_id, (uint32_t)n, mode, e0f, (float)e_lo, lr,
+              (float)wj, c->stream);
   CK(cudaGetLastError(), "seed");
+  CK(cudaStreamSynchronize(c->stream), "seed");
+  if (int rc = write_fills(c, S, app / kTile, app + (uint32_t)n)) return rc;
   st.n_live += (uint32_t)n;
   st.next_id += (uint32_t)n;
-  CK(cudaStreamSynchronize(c->stream), "seed");
+  st.n_tiles = std::max(st.n_tiles, (app + (uint32_t)n + kTile - 1) / (uint32_t)kTile);
   if (int rc = write_state(c, inst, species, st)) return rc;
   if (species == kElectron) {
     InstState is;
@@ -680,8 +726,10 @@ int slpic_seed(slpic_ctx* c, int inst, int species, int64_t n, int mode, double 
   return sync(c);
 }
 
-static int load_common(slpic_ctx* c, int inst, int species, const slpic_soa_f32* src, int64_t n,
-                       uint32_t next_id, cudaMemcpyKind kind) {
+namespace {
+
+int load_common(slpic_ctx* c, int inst, int species, const slpic_soa_f32* src, int64_t n,
+                uint32_t next_id, cudaMemcpyKind kind) {
   if (!valid_inst(c, inst) || (species != 0 && species != 1) || n < 0)
     return fail(c, SLPIC_ERR_INVALID_ARG, "bad load arguments");
   if (n > 0)
@@ -690,11 +738,12 @@ static int load_common(slpic_ctx* c, int inst, int species, const slpic_soa_f32*
   if (int rc = prepare(c)) return rc;
   if (int rc = sync(c)) return rc;
   const InstDev& P = c->h_inst[inst];
-  if ((uint64_t)n > P.sp[species].cap)
+  const SpeciesDev& S = P.sp[species];
+  if ((uint64_t)n > (uint64_t)S.cap_tiles * kTile)
     return fail(c, SLPIC_ERR_CAPACITY, "%lld markers exceed the capacity", (long long)n);
   SpeciesState st;
   if (int rc = read_state(c, inst, species, &st)) return rc;
-  const SoA& d = P.sp[species].buf[st.cur];
+  const SoA& d = S.buf[st.cur];
   if (n > 0) {
     const size_t b = (size_t)n * 4;
     CK(cudaMemcpyAsync(d.cell, src->cell, b, kind, c->stream), "load");
@@ -716,14 +765,18 @@ static int load_common(slpic_ctx* c, int inst, int species, const slpic_soa_f32*
   unsigned int res[4];
   CK(cudaMemcpyAsync(res, scratch, 16, cudaMemcpyDeviceToHost, c->stream), "load");
   CK(cudaStreamSynchronize(c->stream), "load");
+  st.n_live = 0;
+  st.n_tiles = 0;
   if (res[0] != 0xFFFFFFFFu) {
-    st.n_live = 0;
     write_state(c, inst, species, st);
     replan(c);
     return fail(c, SLPIC_ERR_INVALID_ARG,
-                "marker %u outside the gap or not finite; the species was emptied", res[0]);
+                "marker %u outside the gap, not finite, or with a weight of 2^39 charge "
+                "units or more; the species was emptied", res[0]);
   }
+  if (int rc = write_fills(c, S, 0, (uint32_t)n)) return rc;
   st.n_live = (uint32_t)n;
+  st.n_tiles = (uint32_t)(((uint64_t)n + kTile - 1) / kTile);
   st.next_id = next_id;
   if (int rc = write_state(c, inst, species, st)) return rc;
   if (species == kElectron) {
@@ -737,6 +790,10 @@ static int load_common(slpic_ctx* c, int inst, int species, const slpic_soa_f32*
   if (int rc = replan(c)) return rc;
   return sync(c);
 }
+
+}  // namespace
+
+extern "C" {
 
 int slpic_load_particles(slpic_ctx* c, int inst, int species, const slpic_soa_f32* host,
                          int64_t n, uint32_t next_id) {
@@ -774,7 +831,8 @@ int slpic_step(slpic_ctx* c, int64_t n) {
       launch_push(c->refs, c->push_grid, c->stream);
       CK(cudaEventRecord(b, c->stream), "event");
       launch_finish(c->refs, 0, c->stream);
-      c->last_launches += 2;
+      launch_move(c->refs, c->move_grid, c->stream);
+      c->last_launches += 3;
     }
     CK(cudaGetLastError(), "step");
     return SLPIC_OK;
@@ -785,13 +843,14 @@ int slpic_step(slpic_ctx* c, int64_t n) {
     while (left >= kGraphSteps) {
       CK(cudaGraphLaunch(c->graph, c->stream), "graph launch");
       left -= kGraphSteps;
-      c->last_launches += 2 * kGraphSteps;
+      c->last_launches += 3 * kGraphSteps;
     }
   }
   for (int64_t k = 0; k < left; ++k) {
     launch_push(c->refs, c->push_grid, c->stream);
     launch_finish(c->refs, 0, c->stream);
-    c->last_launches += 2;
+    launch_move(c->refs, c->move_grid, c->stream);
+    c->last_launches += 3;
   }
   CK(cudaGetLastError(), "step");
   return SLPIC_OK;
@@ -843,15 +902,23 @@ int slpic_read_particles(slpic_ctx* c, int inst, int species, const slpic_soa_f3
                 (long long)capacity, st.n_live);
   if (st.n_live > 0) {
     if (int r3 = host_soa_check(c, host)) return r3;
-    const SoA& d = c->h_inst[inst].sp[species].buf[st.cur];
-    const size_t b = (size_t)st.n_live * 4;
-    CK(cudaMemcpy(host->cell, d.cell, b, cudaMemcpyDeviceToHost), "read");
-    CK(cudaMemcpy(host->off, d.off, b, cudaMemcpyDeviceToHost), "read");
-    CK(cudaMemcpy(host->vx, d.vx, b, cudaMemcpyDeviceToHost), "read");
-    CK(cudaMemcpy(host->vy, d.vy, b, cudaMemcpyDeviceToHost), "read");
-    CK(cudaMemcpy(host->vz, d.vz, b, cudaMemcpyDeviceToHost), "read");
-    CK(cudaMemcpy(host->wj, d.wj, b, cudaMemcpyDeviceToHost), "read");
-    CK(cudaMemcpy(host->id, d.id, b, cudaMemcpyDeviceToHost), "read");
+    const SpeciesDev& S = c->h_inst[inst].sp[species];
+    const SoA& d = S.buf[st.cur];
+    std::vector<uint32_t> fill(st.n_tiles);
+    CK(cudaMemcpy(fill.data(), S.fill, st.n_tiles * 4, cudaMemcpyDeviceToHost), "read");
+    const size_t slots = (size_t)st.n_tiles * kTile;
+    std::vector<uint32_t> tmp(slots);
+    void* dst[7] = {host->cell, host->off, host->vx, host->vy, host->vz, host->wj, host->id};
+    const void* srcs[7] = {d.cell, d.off, d.vx, d.vy, d.vz, d.wj, d.id};
+    for (int f = 0; f < 7; ++f) {
+      CK(cudaMemcpy(tmp.data(), srcs[f], slots * 4, cudaMemcpyDeviceToHost), "read");
+      uint32_t* out = static_cast<uint32_t*>(dst[f]);
+      size_t o = 0;
+      for (uint32_t k = 0; k < st.n_tiles; ++k) {
+        std::memcpy(out + o, tmp.data() + (size_t)k * kTile, (size_t)fill[k] * 4);
+        o += fill[k];
+      }
+    }
   }
   return rc;
 }
@@ -977,6 +1044,19 @@ int slpic_read_profile(slpic_ctx* c, double* ms, int64_t* launches) {
   c->ev_used = 0;
   *ms = c->prof_ms;
   *launches = c->prof_launches;
+  return rc;
+}
+
+int slpic_read_wait_stats(slpic_ctx* c, int64_t* waits, int64_t* longest) {
+  if (!c || !waits || !longest) return SLPIC_ERR_INVALID_ARG;
+  if (int rc = prepare(c)) return rc;
+  int rc = sync(c);
+  Control h;
+  CK(cudaMemcpy(&h, c->d_ctrl, sizeof h, cudaMemcpyDeviceToHost), "wait stats");
+  *waits = h.spin_waits;
+  *longest = h.spin_max;
+  unsigned int z[2] = {0u, 0u};
+  CK(cudaMemcpy(&c->d_ctrl->spin_waits, z, sizeof z, cudaMemcpyHostToDevice), "wait stats");
   return rc;
 }
 

@@ -1,8 +1,9 @@
-// End of a step, one CTA per instance: append the staged births after the
-// compacted survivors, publish the step's deposit, solve the 1D Poisson
-// equation for the next step's field, and commit the step's tallies.  The
-// last CTA to finish plans the next step's tiles.  Also: seeding and the
-// Philox self-check kernel.
+// End of a step.  k_finish (one CTA per instance) ranks the births each tile
+// staged, decides where they are appended (and whether the tiles are
+// repacked), publishes the step's deposit, solves the 1D Poisson equation for
+// the next step's field and commits the step's tallies; the last CTA plans
+// the next step's tiles.  k_move then repacks and appends (many CTAs).  Also:
+// seeding, load validation and the Philox self-check kernel.
 #include "device_common.cuh"
 #include "slpic_internal.h"
 
@@ -11,6 +12,7 @@ namespace slpic {
 namespace {
 
 constexpr int kFinThreads = 1024;
+constexpr int kMoveThreads = 256;
 
 __device__ __forceinline__ void set_error(Control* ctrl, int code, int inst) {
   if (atomicCAS(&ctrl->error, 0, code) == 0) ctrl->error_inst = inst;
@@ -32,38 +34,43 @@ __device__ T block_incl_scan(T v, T* buf) {
   return r;
 }
 
-__device__ void copy_births(const SoA& src, const SoA& dst, unsigned int n, unsigned int at,
-                            bool assign_id, uint32_t first_serial) {
-  for (unsigned int i = threadIdx.x; i < n; i += kFinThreads) {
-    const unsigned int o = at + i;
-    dst.cell[o] = src.cell[i];
-    dst.off[o] = src.off[i];
-    dst.vx[o] = src.vx[i];
-    dst.vy[o] = src.vy[i];
-    dst.vz[o] = src.vz[i];
-    dst.wj[o] = src.wj[i];
-    dst.id[o] = assign_id ? (src.id[i] & kGenBit) | ((first_serial + i) & kSerialMask)
-                          : src.id[i];
+// Exclusive prefix of a[0..n) into out[0..n] (out[n] = total), block-wide;
+// returns the total.
+__device__ unsigned long long block_prefix(const uint32_t* a, uint32_t* out, uint32_t n,
+                                           unsigned long long* buf,
+                                           unsigned long long* s_total) {
+  const uint32_t chunk = (n + kFinThreads - 1) / kFinThreads;
+  const uint32_t k0 = threadIdx.x * chunk;
+  unsigned long long loc = 0;
+  for (uint32_t k = k0; k < k0 + chunk && k < n; ++k) loc += a[k];
+  const unsigned long long inc = block_incl_scan<unsigned long long>(loc, buf);
+  unsigned long long run = inc - loc;
+  for (uint32_t k = k0; k < k0 + chunk && k < n; ++k) {
+    out[k] = (uint32_t)run;
+    run += a[k];
   }
+  if (threadIdx.x == kFinThreads - 1) {
+    *s_total = inc;
+    out[n] = (uint32_t)inc;
+  }
+  __syncthreads();
+  const unsigned long long t = *s_total;
+  __syncthreads();
+  return t;
 }
 
-// Plan the tiles of the next step from the live counts (one thread).
+// Plan the tiles of the next step from the tiles in use (one thread).
 __device__ void plan_next(const DeviceRefs& r) {
   const int n_seg = r.n_inst * 2;
   unsigned int start = 0;
   for (int s = 0; s < n_seg; ++s) {
     r.seg_start[s] = start;
-    const unsigned int n = r.sstate[s].n_live;
-    start += (n + kTile - 1) / kTile;
-    r.sstate[s].n_surv = 0;
-    r.sstate[s].n_ba = 0;
-    r.sstate[s].n_bb = 0;
+    start += r.sstate[s].n_tiles;
   }
   r.seg_start[n_seg] = start;
   r.ctrl->n_tiles = start;
   r.ctrl->n_seg = n_seg;
   r.ctrl->tile_counter = 0;
-  r.ctrl->epoch = (r.ctrl->epoch + 1u) & 0x3FFFFFFFu;
   r.ctrl->finish_done = 0;
 }
 
@@ -71,8 +78,9 @@ __device__ void plan_next(const DeviceRefs& r) {
 
 // mode 0: finish a step and plan the next; mode 1: plan only (one CTA).
 __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode) {
-  __shared__ long long s_i64[kFinThreads];
+  __shared__ unsigned long long s_u64[kFinThreads];
   __shared__ __int128 s_i128[kFinThreads];
+  __shared__ unsigned long long s_total;
   __shared__ int s_flag;
   Control* ctrl = r.ctrl;
   if (mode == 1) {
@@ -85,33 +93,75 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode) 
   InstState& is = r.istate[inst];
   SpeciesState& se = r.sstate[inst * 2 + kElectron];
   SpeciesState& si = r.sstate[inst * 2 + kIon];
+  const SpeciesDev& E = P.sp[kElectron];
+  const SpeciesDev& I = P.sp[kIon];
 
-  // ---- append births -----------------------------------------------------
-  const unsigned int n_ionz = se.n_ba;  // equals si.n_ba
-  const unsigned int n_see = se.n_bb;
-  const unsigned int ne = se.n_surv + n_ionz + n_see;
-  const unsigned int ni = si.n_surv + n_ionz;
+  // ---- rank the staged births and count the survivors ----------------------
+  // ionization births were staged by electron tiles, emission births by ion
+  // tiles; their order is (tile, rank inside the tile)
+  const uint32_t nt_e = se.n_tiles, nt_i = si.n_tiles;
+  const uint32_t n_ionz = (uint32_t)block_prefix(E.births, E.boff, nt_e, s_u64, &s_total);
+  const uint32_t n_see = (uint32_t)block_prefix(I.births, I.boff, nt_i, s_u64, &s_total);
+  const uint32_t surv_e = (uint32_t)block_prefix(E.fill, E.coff, nt_e, s_u64, &s_total);
+  const uint32_t surv_i = (uint32_t)block_prefix(I.fill, I.coff, nt_i, s_u64, &s_total);
+
   if (threadIdx.x == 0) {
     int err = 0;
-    if (ne > P.sp[kElectron].cap || ni > P.sp[kIon].cap) err = kErrCapacity;
-    if (n_ionz > P.sp[kElectron].stage_cap || n_see > P.sp[kElectron].stage_cap ||
-        n_ionz > P.sp[kIon].stage_cap)
+    const unsigned long long ne = (unsigned long long)surv_e + n_ionz + n_see;
+    const unsigned long long ni = (unsigned long long)surv_i + n_ionz;
+    if (ne > (unsigned long long)E.cap_tiles * kTile || ni > (unsigned long long)I.cap_tiles * kTile)
       err = kErrCapacity;
     if ((unsigned long long)se.next_id + n_ionz + n_see > kSerialMask ||
         (unsigned long long)si.next_id + n_ionz > kSerialMask)
       err = kErrIdWrap;
     if (err) set_error(ctrl, err, inst);
     s_flag = err;
+    if (!err) {
+      // births go after the last live marker, or after the repacked survivors
+      // when the tiles are sparse or the store would overflow
+      for (int sp = 0; sp < 2; ++sp) {
+        SpeciesState& st = sp ? si : se;
+        const SpeciesDev& S = sp ? I : E;
+        Transfer& x = r.xfer[inst * 2 + sp];
+        const uint32_t nt = st.n_tiles;
+        const uint32_t surv = sp ? surv_i : surv_e;
+        const uint32_t nb = sp ? n_ionz : n_ionz + n_see;
+        const uint32_t tail = nt ? (nt - 1) * (uint32_t)kTile + S.fill[nt - 1] : 0u;
+        const unsigned long long end_nc = (unsigned long long)tail + nb;
+        const bool sparse =
+            nt > 2 && (unsigned long long)surv * 4 < (unsigned long long)nt * kTile * 3;
+        const bool overflow = end_nc > (unsigned long long)S.cap_tiles * kTile;
+        x.compact = (sparse || overflow) ? 1u : 0u;
+        x.src = st.cur;
+        x.dst = x.compact ? st.cur ^ 1u : st.cur;
+        x.n_tiles_old = nt;
+        x.app_pos = x.compact ? surv : tail;
+        x.n_a = n_ionz;
+        x.n_b = sp ? 0u : n_see;
+        x.serial_a = st.next_id;
+        x.serial_b = st.next_id + n_ionz;
+        x.nt_a = nt_e;
+        x.nt_b = nt_i;
+        const uint32_t end = x.app_pos + nb;
+        st.cur = x.dst;
+        st.n_live = surv + nb;
+        st.next_id += nb;
+        st.n_tiles = (end + kTile - 1) / kTile;
+      }
+    }
   }
   __syncthreads();
   if (s_flag) return;
-  {
-    const SpeciesDev& E = P.sp[kElectron];
-    const SoA dst = E.buf[se.cur ^ 1u];
-    copy_births(E.stage_a, dst, n_ionz, se.n_surv, false, 0);
-    copy_births(E.stage_b, dst, n_see, se.n_surv + n_ionz, true, se.next_id + n_ionz);
-    const SpeciesDev& I = P.sp[kIon];
-    copy_births(I.stage_a, I.buf[si.cur ^ 1u], n_ionz, si.n_surv, false, 0);
+  // new fills: a repacked store is full tiles but the last; otherwise only the
+  // tail tile and the new tiles change (their slots up to `end` are live)
+  for (int sp = 0; sp < 2; ++sp) {
+    const SpeciesState& st = sp ? si : se;
+    const SpeciesDev& S = sp ? I : E;
+    const Transfer& x = r.xfer[inst * 2 + sp];
+    const uint32_t end = x.app_pos + x.n_a + x.n_b;
+    const uint32_t first = x.compact ? 0u : x.app_pos / kTile;
+    for (uint32_t k = first + threadIdx.x; k < st.n_tiles; k += kFinThreads)
+      S.fill[k] = min(end - k * (uint32_t)kTile, (uint32_t)kTile);
   }
 
   // ---- deposit of the step -> rho_last; clear the accumulators -------------
@@ -133,17 +183,16 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode) 
     const int N = P.n_cells;
     const int chunk = (N + kFinThreads - 1) / kFinThreads;  // over k = 1..N
     const int k0 = 1 + threadIdx.x * chunk;
-    // local sums of net over j in [k0, k0 + chunk) restricted to 1..N-1
     long long loc = 0;
     for (int k = k0; k < k0 + chunk && k <= N; ++k)
       if (k <= N - 1) loc += P.rho_last[kIon][k] - P.rho_last[kElectron][k];
+    long long* s_i64 = reinterpret_cast<long long*>(s_u64);
     const long long inc = block_incl_scan<long long>(loc, s_i64);
-    // I_k for k in this chunk: exclusive of net_k
-    long long I = inc - loc;
+    long long Ik = inc - loc;  // I_k at the chunk start (exclusive of net_k)
     __int128 locJ = 0;
     for (int k = k0; k < k0 + chunk && k <= N; ++k) {
-      locJ += (__int128)I;
-      if (k <= N - 1) I += P.rho_last[kIon][k] - P.rho_last[kElectron][k];
+      locJ += (__int128)Ik;
+      if (k <= N - 1) Ik += P.rho_last[kIon][k] - P.rho_last[kElectron][k];
     }
     const __int128 incJ = block_incl_scan<__int128>(locJ, s_i128);
     __shared__ __int128 s_JN;
@@ -152,10 +201,10 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode) 
     const double C = P.pois_C;
     const double D1 = (P.V + C * (double)s_JN) / (double)N;
     __int128 J = incJ - locJ;
-    I = inc - loc;
+    Ik = inc - loc;
     for (int k = k0; k < k0 + chunk && k <= N; ++k) {
-      J += (__int128)I;
-      if (k <= N - 1) I += P.rho_last[kIon][k] - P.rho_last[kElectron][k];
+      J += (__int128)Ik;
+      if (k <= N - 1) Ik += P.rho_last[kIon][k] - P.rho_last[kElectron][k];
       P.phi[k] = (double)k * D1 - C * (double)J;
     }
     if (threadIdx.x == 0) P.phi[0] = 0.0;
@@ -180,8 +229,8 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode) 
     unsigned long long* a = P.acc;
     TallyRec t;
     t.step = is.step;
-    t.n_live[0] = ne;
-    t.n_live[1] = ni;
+    t.n_live[0] = se.n_live;
+    t.n_live[1] = si.n_live;
     t.w_live[0] = (double)(long long)(a[ACC_WSURV] + a[ACC_WIONZ] + a[ACC_WSEE]) * unit;
     t.w_live[1] = (double)(long long)(a[ACC_WSURV + 1] + a[ACC_WIONZ]) * unit;
     for (int k = 0; k < 3; ++k) t.n_coll[k] = (long long)a[ACC_COLL0 + k];
@@ -222,13 +271,6 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode) 
     T.n_majorant += t.n_majorant;
     T.marker_steps += t.marker_steps;
     for (int k = 0; k < ACC_COUNT; ++k) a[k] = 0ull;
-    // commit the marker state
-    se.cur ^= 1u;
-    se.n_live = ne;
-    se.next_id += n_ionz + n_see;
-    si.cur ^= 1u;
-    si.n_live = ni;
-    si.next_id += n_ionz;
     is.step += 1u;
     is.n_steps_done += 1;
   }
@@ -250,6 +292,79 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode) 
 void launch_finish(const DeviceRefs& r, int mode, cudaStream_t s) {
   const int grid = mode == 1 ? 1 : r.n_inst;
   k_finish<<<grid, kFinThreads, 0, s>>>(r, mode);
+}
+
+// ---------------------------------------------------------------------------
+// Repack and append, as decided by k_finish.  One tile per CTA iteration:
+// repacked tiles are copied from buffer src to their packed slots in dst;
+// births are copied from their tile-local staging slots to the append slots,
+// ionization births first then emission births, each in (tile, rank) order,
+// and receive their serial numbers.
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ void copy_marker(const SoA& s, size_t i, const SoA& d, size_t o,
+                                            uint32_t id) {
+  d.cell[o] = s.cell[i];
+  d.off[o] = s.off[i];
+  d.vx[o] = s.vx[i];
+  d.vy[o] = s.vy[i];
+  d.vz[o] = s.vz[i];
+  d.wj[o] = s.wj[i];
+  d.id[o] = id;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kMoveThreads) k_move(DeviceRefs r) {
+  if (*((volatile int*)&r.ctrl->error)) return;
+  const int n_seg = r.n_inst * 2;
+  for (int seg = 0; seg < n_seg; ++seg) {
+    const Transfer x = r.xfer[seg];
+    const InstDev& P = r.inst[seg >> 1];
+    const SpeciesDev& S = P.sp[seg & 1];
+    const SpeciesDev& E = P.sp[kElectron];
+    const SpeciesDev& I = P.sp[kIon];
+    const SoA dst = S.buf[x.dst];
+    if (x.compact) {
+      const SoA src = S.buf[x.src];
+      for (uint32_t k = blockIdx.x; k < x.n_tiles_old; k += gridDim.x) {
+        const uint32_t o = S.coff[k], n = S.coff[k + 1] - o;
+        const size_t base = (size_t)k * kTile;
+        for (uint32_t i = threadIdx.x; i < n; i += kMoveThreads)
+          copy_marker(src, base + i, dst, (size_t)o + i, src.id[base + i]);
+      }
+    }
+    if (x.n_a) {
+      for (uint32_t k = blockIdx.x; k < x.nt_a; k += gridDim.x) {
+        const uint32_t n = E.births[k];
+        if (!n) continue;
+        const uint32_t o = E.boff[k];
+        const size_t base = (size_t)k * kTile;
+        for (uint32_t i = threadIdx.x; i < n; i += kMoveThreads) {
+          const uint32_t id = (S.stage_a.id[base + i] & kGenBit) |
+                              ((x.serial_a + o + i) & kSerialMask);
+          copy_marker(S.stage_a, base + i, dst, (size_t)x.app_pos + o + i, id);
+        }
+      }
+    }
+    if (x.n_b) {
+      for (uint32_t k = blockIdx.x; k < x.nt_b; k += gridDim.x) {
+        const uint32_t n = I.births[k];
+        if (!n) continue;
+        const uint32_t o = I.boff[k];
+        const size_t base = (size_t)k * kTile;
+        for (uint32_t i = threadIdx.x; i < n; i += kMoveThreads) {
+          const uint32_t id = kGenBit | ((x.serial_b + o + i) & kSerialMask);
+          copy_marker(S.stage_b, base + i, dst, (size_t)x.app_pos + x.n_a + o + i, id);
+        }
+      }
+    }
+  }
+}
+
+void launch_move(const DeviceRefs& r, int grid, cudaStream_t s) {
+  k_move<<<grid, kMoveThreads, 0, s>>>(r);
 }
 
 // ---------------------------------------------------------------------------
@@ -327,7 +442,7 @@ void launch_seed(const DeviceRefs& r, int inst, int species, uint32_t base, uint
 }
 
 // Check loaded markers (cell in [0, N), offset in [0, 1), finite velocities,
-// finite non-negative weight); records the smallest bad index in *bad and the
+// non-negative weight below 2^39 charge units); records the smallest bad index in *bad and the
 // fixed-point sum of the weights in *wsum.
 __global__ void k_validate(SoA d, uint32_t n, int N, float wscale, unsigned int* bad,
                            unsigned long long* wsum) {
@@ -336,8 +451,10 @@ __global__ void k_validate(SoA d, uint32_t n, int N, float wscale, unsigned int*
   if (i < n) {
     const float o = d.off[i], x = d.vx[i], y = d.vy[i], z = d.vz[i], wj = d.wj[i];
     const int c = d.cell[i];
+    // the fixed-point weight must stay below 2^39 units so that the 24-bit
+    // linear split of the deposit cannot overflow 64 bits
     const bool ok = c >= 0 && c < N && o >= 0.0f && o < 1.0f && isfinite(x) && isfinite(y) &&
-                    isfinite(z) && wj >= 0.0f && isfinite(wj);
+                    isfinite(z) && wj >= 0.0f && wj * wscale < 549755813888.0f;
     if (!ok) atomicMin(bad, i);
     else w = (unsigned long long)fixed_charge(wj, wscale);
   }

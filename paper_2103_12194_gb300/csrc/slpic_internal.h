@@ -25,8 +25,9 @@ constexpr int kErrCapacity = 1;
 constexpr int kErrTimeout = 2;
 constexpr int kErrIdWrap = 3;
 
-// Bounded waits: spins of ~100 ns before a wait gives up with kErrTimeout.
-constexpr uint32_t kSpinLimit = 1u << 24;
+// Bounded waits: polls before a wait gives up with kErrTimeout (each poll of
+// an mbarrier suspends the thread for up to about a microsecond).
+constexpr uint32_t kSpinLimit = 1u << 22;
 
 // Per-step accumulators of one instance (integer; weights in fixed point).
 enum Acc : int {
@@ -77,28 +78,46 @@ struct SoA {
   uint32_t* id;
 };
 
+// Marker store of one (instance, species): a sequence of tiles of kTile
+// slots; tile k holds fill[k] live markers in its first slots, in order.  The
+// particle kernel compacts each tile in place (no dependence between tiles);
+// births are appended after the last live marker; when the tiles become
+// sparse the whole store is repacked into the other buffer.
+//
 // Mutable per-(instance, species) state, resident on the device.
 struct SpeciesState {
-  uint32_t cur;      // ping-pong buffer holding the live markers
-  uint32_t n_live;   // live markers
-  uint32_t next_id;  // next serial number
-  uint32_t n_surv;   // survivors of the current step (set by the push)
-  uint32_t n_ba;     // births staged in region A (ionization) this step
-  uint32_t n_bb;     // births staged in region B (secondary emission) this step
-  uint32_t pad[2];
+  uint32_t cur;       // buffer holding the markers
+  uint32_t n_tiles;   // tiles in use
+  uint32_t n_live;    // live markers (sum of the fills)
+  uint32_t next_id;   // next serial number
+};
+
+// What the move kernel does for one segment at the end of a step (written by
+// the finish kernel).
+struct Transfer {
+  uint32_t compact;       // repack the tiles into buffer dst
+  uint32_t src, dst;      // buffers
+  uint32_t n_tiles_old;   // tiles processed in the step
+  uint32_t app_pos;       // slot of the first appended birth in dst
+  uint32_t n_a, n_b;      // births from stage_a (ionization) and stage_b (emission)
+  uint32_t serial_a, serial_b;  // serial numbers of the first births of each kind
+  uint32_t nt_a, nt_b;    // source tiles of stage_a (electron tiles) and stage_b (ion tiles)
+  uint32_t pad;
 };
 
 // Configuration of one species of one instance (constant during a run).
 struct SpeciesDev {
-  SoA buf[2];       // ping-pong marker arrays
-  SoA stage_a;      // births from ionization
-  SoA stage_b;      // electrons only: births from secondary emission
-  uint32_t cap;     // capacity of each ping-pong buffer
-  uint32_t stage_cap;
-  float qmdt;       // (q / m) dt
-  float vlim;       // speed limit (+inf: beta = 1)
-  float K_V;        // 2 e / m: speed^2 per eV
-  float pad;
+  SoA buf[2];         // tiled marker store (cap_tiles * kTile slots each)
+  SoA stage_a;        // ionization births, slot = electron tile * kTile + rank
+  SoA stage_b;        // electrons only: emission births, slot = ion tile * kTile + rank
+  uint32_t* fill;     // [cap_tiles] live markers per tile
+  uint32_t* births;   // [cap_tiles] births created by each tile in the step
+  uint32_t* boff;     // [cap_tiles + 1] exclusive prefix of births
+  uint32_t* coff;     // [cap_tiles + 1] exclusive prefix of fills (repacking)
+  uint32_t cap_tiles;
+  float qmdt;         // (q / m) dt
+  float vlim;         // speed limit (+inf: beta = 1)
+  float K_V;          // 2 e / m: speed^2 per eV
 };
 
 // Configuration of one instance (constant during a run).
@@ -147,43 +166,37 @@ struct InstState {
   unsigned long long w_seed;  // fixed-point sum of seeded electron weights
 };
 
-// Look-back record of one tile.
-struct TileStatus {
-  unsigned int flag;   // (epoch << 2) | state, state 1 = aggregate, 2 = inclusive
-  unsigned int agg[3];
-  unsigned int incl[3];
-  unsigned int pad;
-};
-
 // Global state of the batched step.
 struct Control {
-  unsigned int epoch;        // step epoch for look-back flags
   unsigned int tile_counter; // next tile to hand out
   unsigned int n_tiles;      // tiles this step
   unsigned int n_seg;        // segments = instances * 2
   unsigned int finish_done;  // CTAs of the finish kernel that completed
   int error;                 // first device error (kErr*)
   int error_inst;
-  int pad;
+  unsigned int spin_waits;   // barrier polls that found the data not yet there
+  unsigned int spin_max;     // longest single wait, in polls
 };
 
 struct DeviceRefs {
   InstDev* inst;          // [n_inst]
   InstState* istate;      // [n_inst]
   SpeciesState* sstate;   // [n_inst * 2]
+  Transfer* xfer;         // [n_inst * 2]
   Control* ctrl;
-  TileStatus* tiles;      // [max tiles]
   unsigned int* seg_start;  // [n_seg + 1] first global tile of each segment
   int n_inst;
-  int smem_nodes;         // deposit tile nodes in shared memory (0: global atomics)
-  unsigned int max_tiles;
+  int smem_nodes;         // deposit grid nodes in shared memory (0: global atomics)
 };
 
 // Launchers (defined in the .cu files).
 void launch_push(const DeviceRefs& r, int grid, cudaStream_t s);
 int push_occupancy(int smem_nodes, int* blocks_per_sm, size_t* smem_bytes);
+// mode 0: finish a step and plan the next; mode 1: plan only (one CTA).
 void launch_finish(const DeviceRefs& r, int mode, cudaStream_t s);
-// Seeding: mode 0/1/2 as SLPIC_SEED_*; for mode 3 (thermal) e0 carries the
+void launch_move(const DeviceRefs& r, int grid, cudaStream_t s);
+// Seeding: n markers written contiguously from slot `base` of the current
+// buffer; mode 0/1/2 as SLPIC_SEED_*; for mode 3 (thermal) e0 carries the
 // thermal speed sqrt(k T / m).
 void launch_seed(const DeviceRefs& r, int inst, int species, uint32_t base, uint32_t first_id,
                  uint32_t n, int mode, float e0, float e_lo, float lr, float wj,

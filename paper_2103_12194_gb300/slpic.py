@@ -94,6 +94,7 @@ def lib():
         "slpic_set_profiling": ([vp, i32], i32),
         "slpic_read_profile": ([vp, ctypes.POINTER(f64), ctypes.POINTER(i64)], i32),
         "slpic_launch_count": ([vp, ctypes.POINTER(i64)], i32),
+        "slpic_read_wait_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
         "slpic_philox": ([i32, u64, vp, i64, vp], i32),
     }
     for name, (args, res) in sig.items():
@@ -294,6 +295,11 @@ class Simulation:
         ms, n = ctypes.c_double(), ctypes.c_int64()
         self._ck(self._L.slpic_read_profile(self._h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+    def wait_stats(self):
+        w, m = ctypes.c_int64(), ctypes.c_int64()
+        self._ck(self._L.slpic_read_wait_stats(self._h, ctypes.byref(w), ctypes.byref(m)))
+        return w.value, m.value
 
     def launch_count(self):
         n = ctypes.c_int64()
