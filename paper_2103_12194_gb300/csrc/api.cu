@@ -268,7 +268,15 @@ int zero_counters(slpic_ctx* c, int i) {
   CK(cudaMemsetAsync(P.acc, 0, ACC_COUNT * 8, c->stream), "reset");
   CK(cudaMemsetAsync(P.total, 0, sizeof(TallyRec), c->stream), "reset");
   CK(cudaMemsetAsync(P.ring, 0, sizeof(TallyRec) * P.ring_len, c->stream), "reset");
-  CK(cudaMemsetAsync(c->d_istate + i, 0, sizeof(InstState), c->stream), "reset");
+  // step counter, step count and seeded weight restart; the live weight
+  // describes the markers, which stay
+  InstState is;
+  CK(cudaMemcpyAsync(&is, c->d_istate + i, sizeof is, cudaMemcpyDeviceToHost, c->stream), "reset");
+  CK(cudaStreamSynchronize(c->stream), "reset");
+  is.step = 0;
+  is.n_steps_done = 0;
+  is.w_seed = 0;
+  CK(cudaMemcpyAsync(c->d_istate + i, &is, sizeof is, cudaMemcpyHostToDevice, c->stream), "reset");
   for (int s = 0; s < 2; ++s) {
     CK(cudaMemsetAsync(P.rho_acc[s], 0, (P.n_cells + 1) * 8, c->stream), "reset");
     CK(cudaMemsetAsync(P.rho_last[s], 0, (P.n_cells + 1) * 8, c->stream), "reset");
@@ -716,10 +724,13 @@ extern "C" int slpic_seed(slpic_ctx* c, int inst, int species, int64_t n, int mo
   st.next_id += (uint32_t)n;
   st.n_tiles = std::max(st.n_tiles, (app + (uint32_t)n + kTile - 1) / (uint32_t)kTile);
   if (int rc = write_state(c, inst, species, st)) return rc;
-  if (species == kElectron) {
+  {
     InstState is;
     CK(cudaMemcpy(&is, c->d_istate + inst, sizeof is, cudaMemcpyDeviceToHost), "seed");
-    is.w_seed += (unsigned long long)n * (unsigned long long)std::llrint((float)wj * P.wscale);
+    const unsigned long long q =
+        (unsigned long long)n * (unsigned long long)std::llrint((float)wj * P.wscale);
+    if (species == kElectron) is.w_seed += q;
+    is.w_live[species] += q;
     CK(cudaMemcpy(c->d_istate + inst, &is, sizeof is, cudaMemcpyHostToDevice), "seed");
   }
   if (int rc = replan(c)) return rc;
@@ -759,7 +770,7 @@ int load_common(slpic_ctx* c, int inst, int species, const slpic_soa_f32* src, i
   unsigned int* scratch = c->d_scratch;
   unsigned int bad_init[4] = {0xFFFFFFFFu, 0u, 0u, 0u};
   CK(cudaMemcpyAsync(scratch, bad_init, 16, cudaMemcpyHostToDevice, c->stream), "load");
-  launch_validate(d, (uint32_t)n, P.n_cells, P.wscale, scratch,
+  launch_validate(d, (uint32_t)n, P.n_cells, P.charge_shift, scratch,
                   reinterpret_cast<unsigned long long*>(scratch + 2), c->stream);
   CK(cudaGetLastError(), "validate");
   unsigned int res[4];
@@ -779,12 +790,13 @@ int load_common(slpic_ctx* c, int inst, int species, const slpic_soa_f32* src, i
   st.n_tiles = (uint32_t)(((uint64_t)n + kTile - 1) / kTile);
   st.next_id = next_id;
   if (int rc = write_state(c, inst, species, st)) return rc;
-  if (species == kElectron) {
+  {
     InstState is;
     CK(cudaMemcpy(&is, c->d_istate + inst, sizeof is, cudaMemcpyDeviceToHost), "load");
     unsigned long long wsum;
     std::memcpy(&wsum, res + 2, 8);
-    is.w_seed = wsum;
+    if (species == kElectron) is.w_seed = wsum;
+    is.w_live[species] = wsum;
     CK(cudaMemcpy(c->d_istate + inst, &is, sizeof is, cudaMemcpyHostToDevice), "load");
   }
   if (int rc = replan(c)) return rc;

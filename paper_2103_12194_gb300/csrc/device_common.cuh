@@ -83,15 +83,35 @@ __device__ __forceinline__ void rotate(float& ux, float& uy, float& uz, float cc
   uz = nz;
 }
 
-// Fixed-point charge of a marker: round(w_p 2^shift), w_p = beta w_j.
-__device__ __forceinline__ long long fixed_charge(float wp, float wscale) {
-  return __float2ll_rn(wp * wscale);
+// Fixed-point charge of a marker: round(w 2^shift) to nearest, ties to even
+// (the value llrint gives for w * 2^shift), for a finite w >= 0 whose result
+// stays below 2^39.  Integer operations only: the float is split into its
+// significand and exponent and shifted.
+__device__ __forceinline__ long long fixed_charge(float w, int shift) {
+  const uint32_t b = __float_as_uint(w);
+  const int e = (int)(b >> 23);
+  uint32_t m = b & 0x7FFFFFu;
+  int s;
+  if (e == 0) {
+    s = shift - 149;  // subnormal: w = m 2^-149
+  } else {
+    m |= 0x800000u;   // w = m 2^(e - 150)
+    s = e - 150 + shift;
+  }
+  if (s >= 0) return (long long)m << s;
+  const int t = -s;
+  if (t >= 25) return 0;  // m 2^-t < 1/2
+  const uint32_t q = m >> t;
+  const uint32_t rem = m & ((1u << t) - 1u);
+  const uint32_t half = 1u << (t - 1);
+  return (long long)(q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u));
 }
 
 // Split a fixed-point charge between the two nodes of the marker's cell with
-// 24-bit linear weights: the right node gets floor(Q f / 2^24).
+// 24-bit linear weights: the right node gets floor(Q f / 2^24),
+// f = trunc(offset 2^24).
 __device__ __forceinline__ long long right_share(long long Q, float off) {
-  const long long f = __float2ll_rz(off * 16777216.0f);
+  const long long f = (long long)__float2int_rz(off * 16777216.0f);
   return (Q * f) >> 24;
 }
 

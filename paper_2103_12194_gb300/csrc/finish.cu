@@ -231,8 +231,12 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode) 
     t.step = is.step;
     t.n_live[0] = se.n_live;
     t.n_live[1] = si.n_live;
-    t.w_live[0] = (double)(long long)(a[ACC_WSURV] + a[ACC_WIONZ] + a[ACC_WSEE]) * unit;
-    t.w_live[1] = (double)(long long)(a[ACC_WSURV + 1] + a[ACC_WIONZ]) * unit;
+    // live weight by its changes: minus what left through the electrodes,
+    // plus the births (ionization pairs, emitted electrons)
+    is.w_live[0] = is.w_live[0] - a[ACC_WABS + 0] - a[ACC_WABS + 1] + a[ACC_WIONZ] + a[ACC_WSEE];
+    is.w_live[1] = is.w_live[1] - a[ACC_WABS + 2] - a[ACC_WABS + 3] + a[ACC_WIONZ];
+    t.w_live[0] = (double)(long long)is.w_live[0] * unit;
+    t.w_live[1] = (double)(long long)is.w_live[1] * unit;
     for (int k = 0; k < 3; ++k) t.n_coll[k] = (long long)a[ACC_COLL0 + k];
     t.n_candidates = (long long)a[ACC_CAND];
     for (int s = 0; s < 2; ++s)
@@ -444,8 +448,9 @@ void launch_seed(const DeviceRefs& r, int inst, int species, uint32_t base, uint
 // Check loaded markers (cell in [0, N), offset in [0, 1), finite velocities,
 // non-negative weight below 2^39 charge units); records the smallest bad index in *bad and the
 // fixed-point sum of the weights in *wsum.
-__global__ void k_validate(SoA d, uint32_t n, int N, float wscale, unsigned int* bad,
+__global__ void k_validate(SoA d, uint32_t n, int N, int shift, unsigned int* bad,
                            unsigned long long* wsum) {
+  const float wscale = __int_as_float((127 + shift) << 23);  // 2^shift
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long w = 0;
   if (i < n) {
@@ -456,17 +461,17 @@ __global__ void k_validate(SoA d, uint32_t n, int N, float wscale, unsigned int*
     const bool ok = c >= 0 && c < N && o >= 0.0f && o < 1.0f && isfinite(x) && isfinite(y) &&
                     isfinite(z) && wj >= 0.0f && wj * wscale < 549755813888.0f;
     if (!ok) atomicMin(bad, i);
-    else w = (unsigned long long)fixed_charge(wj, wscale);
+    else w = (unsigned long long)fixed_charge(wj, shift);
   }
   for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xFFFFFFFFu, w, o);
   if ((threadIdx.x & 31) == 0 && w) atomicAdd(wsum, w);
 }
 
-void launch_validate(const SoA& d, uint32_t n, int N, float wscale, unsigned int* bad,
+void launch_validate(const SoA& d, uint32_t n, int N, int shift, unsigned int* bad,
                      unsigned long long* wsum, cudaStream_t s) {
   if (n == 0) return;
   const int threads = 256;
-  k_validate<<<(n + threads - 1) / threads, threads, 0, s>>>(d, n, N, wscale, bad, wsum);
+  k_validate<<<(n + threads - 1) / threads, threads, 0, s>>>(d, n, N, shift, bad, wsum);
 }
 
 __global__ void k_philox(uint32_t k0, uint32_t k1, const uint4* ctr, uint4* out, long long n) {

@@ -13,10 +13,10 @@ constexpr uint32_t kGenBit = 0x80000000u;
 constexpr uint32_t kSerialMask = 0x7FFFFFFFu;
 constexpr uint32_t kSeedStep = 0xFFFFFFFFu;
 
-// Particle kernel shape: kThreads threads, kPerThread consecutive markers per
-// thread (one 16-byte vector per field), one tile = kTile markers.
-constexpr int kThreads = 256;
-constexpr int kPerThread = 4;
+// Particle kernel shape: kThreads threads, kPerThread markers per thread (slots
+// t and t + kThreads of the tile), one tile = kTile markers.
+constexpr int kThreads = 512;
+constexpr int kPerThread = 2;
 constexpr int kTile = kThreads * kPerThread;
 
 // Device error word values (copied to the host status codes).
@@ -45,8 +45,7 @@ enum Acc : int {
   ACC_CLAMP,
   ACC_MAJ,
   ACC_MSTEPS,
-  ACC_WSURV,       // 2 entries: survivors' weight per species
-  ACC_COUNT = ACC_WSURV + 2
+  ACC_COUNT
 };
 
 // Record of one step, converted (same layout as slpic_tallies).
@@ -163,7 +162,8 @@ struct InstState {
   uint32_t step;        // step index (Philox counter word 1)
   uint32_t pad;
   long long n_steps_done;
-  unsigned long long w_seed;  // fixed-point sum of seeded electron weights
+  unsigned long long w_seed;     // fixed-point sum of seeded electron weights
+  unsigned long long w_live[2];  // fixed-point sum of live weights per species
 };
 
 // Global state of the batched step.
@@ -201,7 +201,7 @@ void launch_move(const DeviceRefs& r, int grid, cudaStream_t s);
 void launch_seed(const DeviceRefs& r, int inst, int species, uint32_t base, uint32_t first_id,
                  uint32_t n, int mode, float e0, float e_lo, float lr, float wj,
                  cudaStream_t s);
-void launch_validate(const SoA& d, uint32_t n, int N, float wscale, unsigned int* bad,
+void launch_validate(const SoA& d, uint32_t n, int N, int shift, unsigned int* bad,
                      unsigned long long* wsum, cudaStream_t s);
 void launch_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, uint32_t* out,
                    long long n, cudaStream_t s);
