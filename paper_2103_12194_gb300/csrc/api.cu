@@ -13,7 +13,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/slpic.h"
+#include "slpic.h"
 #include "slpic_internal.h"
 
 using namespace slpic;
@@ -78,6 +78,7 @@ struct slpic_ctx {
   DeviceRefs refs{};
   int push_grid = 0;
   int move_grid = 0;
+  int collide_grid = 0;
   int blocks_per_sm = 0;
   // graph of kGraphSteps steps
   cudaGraphExec_t graph = nullptr;
@@ -344,8 +345,9 @@ int commit(slpic_ctx* c) {
       const size_t slots = (size_t)cap_tiles[s] * kTile;
       const size_t stage_a = (size_t)cap_tiles[kElectron] * kTile;
       const size_t stage_b = s == kElectron ? (size_t)cap_tiles[kIon] * kTile : 0;
+      const size_t cand_slots = s == kElectron ? slots : 0;
       size_t b = 2 * soa_bytes(slots) + soa_bytes(stage_a) + soa_bytes(stage_b) +
-                 4 * (((size_t)cap_tiles[s] + 1) * 4 + 256);
+                 5 * (((size_t)cap_tiles[s] + 1) * 4 + 256) + cand_slots * 2 + 256;
       void* sb;
       if (int rc = dmalloc(c, &sb, b, "marker buffers")) return rc;
       char* q = (char*)sb;
@@ -358,6 +360,8 @@ int commit(slpic_ctx* c) {
       S.births = carve<uint32_t>(q, cap_tiles[s] + 1);
       S.boff = carve<uint32_t>(q, cap_tiles[s] + 1);
       S.coff = carve<uint32_t>(q, cap_tiles[s] + 1);
+      S.n_cand = carve<uint32_t>(q, cap_tiles[s] + 1);
+      S.cand = cand_slots ? carve<uint16_t>(q, cand_slots) : nullptr;
       CK(cudaMemset(S.fill, 0, ((size_t)cap_tiles[s] + 1) * 4), "fills");
     }
   }
@@ -402,6 +406,7 @@ int commit(slpic_ctx* c) {
   c->blocks_per_sm = bps;
   c->push_grid = sms * bps;
   c->move_grid = sms * 2;
+  c->collide_grid = sms * 4;
   for (int i = 0; i < c->n_inst; ++i) {
     if (int rc = upload_inst(c, i)) return rc;
     if (int rc = reset_field(c, i)) return rc;
@@ -450,6 +455,7 @@ int build_graph(slpic_ctx* c) {
   CK(cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal), "capture");
   for (int k = 0; k < kGraphSteps; ++k) {
     launch_push(c->refs, c->push_grid, c->capture_stream);
+    launch_collide(c->refs, c->collide_grid, c->capture_stream);
     launch_finish(c->refs, 0, c->capture_stream);
     launch_move(c->refs, c->move_grid, c->capture_stream);
   }
@@ -842,9 +848,10 @@ int slpic_step(slpic_ctx* c, int64_t n) {
       CK(cudaEventRecord(a, c->stream), "event");
       launch_push(c->refs, c->push_grid, c->stream);
       CK(cudaEventRecord(b, c->stream), "event");
+      launch_collide(c->refs, c->collide_grid, c->stream);
       launch_finish(c->refs, 0, c->stream);
       launch_move(c->refs, c->move_grid, c->stream);
-      c->last_launches += 3;
+      c->last_launches += 4;
     }
     CK(cudaGetLastError(), "step");
     return SLPIC_OK;
@@ -855,14 +862,15 @@ int slpic_step(slpic_ctx* c, int64_t n) {
     while (left >= kGraphSteps) {
       CK(cudaGraphLaunch(c->graph, c->stream), "graph launch");
       left -= kGraphSteps;
-      c->last_launches += 3 * kGraphSteps;
+      c->last_launches += 4 * kGraphSteps;
     }
   }
   for (int64_t k = 0; k < left; ++k) {
     launch_push(c->refs, c->push_grid, c->stream);
+    launch_collide(c->refs, c->collide_grid, c->stream);
     launch_finish(c->refs, 0, c->stream);
     launch_move(c->refs, c->move_grid, c->stream);
-    c->last_launches += 3;
+    c->last_launches += 4;
   }
   CK(cudaGetLastError(), "step");
   return SLPIC_OK;

@@ -24,10 +24,11 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
       k0 += 0x9E3779B9u;
       k1 += 0xBB67AE85u;
     }
-    const uint32_t lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    // one 32x32 -> 64-bit product each (a single wide multiply instruction)
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+    const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
     c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
   }
   return c;
@@ -45,9 +46,11 @@ __device__ __forceinline__ void uniform4(uint4 r, float u[4]) {
   u[3] = uniform01(r.w);
 }
 
-// beta(v) = min(1, v_lim / v), Eq. betaAbrupt; v_lim = +inf gives 1.
+// beta(v) = min(1, v_lim / v), Eq. betaAbrupt; v_lim = +inf gives 1.  Equal,
+// bit for bit, to (v > v_lim ? v_lim / v : 1): when v <= v_lim the rounded
+// quotient is >= 1 (rounding is monotone), and v = 0 gives +inf.
 __device__ __forceinline__ float beta_of(float v, float vlim) {
-  return v > vlim ? vlim / v : 1.0f;
+  return fminf(1.0f, vlim / v);
 }
 
 // Direction with cos(theta) = 1 - 2 ua about x and azimuth 2 pi ub.

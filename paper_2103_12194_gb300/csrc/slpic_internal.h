@@ -111,6 +111,9 @@ struct SpeciesDev {
   SoA stage_b;        // electrons only: emission births, slot = ion tile * kTile + rank
   uint32_t* fill;     // [cap_tiles] live markers per tile
   uint32_t* births;   // [cap_tiles] births created by each tile in the step
+  uint16_t* cand;     // electrons: [cap_tiles * kTile] slots of the tile's
+                      // null-collision candidates, in slot order
+  uint32_t* n_cand;   // electrons: [cap_tiles] candidates per tile
   uint32_t* boff;     // [cap_tiles + 1] exclusive prefix of births
   uint32_t* coff;     // [cap_tiles + 1] exclusive prefix of fills (repacking)
   uint32_t cap_tiles;
@@ -195,6 +198,8 @@ int push_occupancy(int smem_nodes, int* blocks_per_sm, size_t* smem_bytes);
 // mode 0: finish a step and plan the next; mode 1: plan only (one CTA).
 void launch_finish(const DeviceRefs& r, int mode, cudaStream_t s);
 void launch_move(const DeviceRefs& r, int grid, cudaStream_t s);
+// Scatter the null-collision candidates queued by the particle kernel.
+void launch_collide(const DeviceRefs& r, int grid, cudaStream_t s);
 // Seeding: n markers written contiguously from slot `base` of the current
 // buffer; mode 0/1/2 as SLPIC_SEED_*; for mode 3 (thermal) e0 carries the
 // thermal speed sqrt(k T / m).
