@@ -27,8 +27,9 @@
  *    leaves a message in slpic_last_error().  Errors raised on the GPU during
  *    slpic_step (capacity, wait time-out) are latched in device memory and
  *    returned by the next call that synchronises (reads, slpic_synchronize);
- *    after such an error the markers keep the state they had before the
- *    failed step and further steps are no-ops until slpic_clear_error().
+ *    after such an error further steps are no-ops until slpic_clear_error(),
+ *    and the markers of the failed step are in an unspecified state (the step
+ *    updates the stores in place): load or seed them again.
  *  - A context is not thread-safe; use one host thread per context.
  */
 #ifndef SLPIC_H
@@ -181,7 +182,7 @@ int slpic_reset_counters(slpic_ctx* ctx, int inst);
 int slpic_step(slpic_ctx* ctx, int64_t n_steps);
 /* Wait for the context's work; returns the latched device error, if any. */
 int slpic_synchronize(slpic_ctx* ctx);
-/* Forget a latched device error (markers are as before the failed step). */
+/* Forget a latched device error (load or seed the markers again after it). */
 int slpic_clear_error(slpic_ctx* ctx);
 
 /* Reads (synchronise first).  Host buffers are caller-owned. */

@@ -293,6 +293,7 @@ int commit(slpic_ctx* c) {
   if (int rc = set_device(c)) return rc;
   c->h_inst.assign(c->n_inst, InstDev{});
   int max_nodes = 0;
+  unsigned long long total_tiles = 0;
   for (int i = 0; i < c->n_inst; ++i) {
     HostInst& h = c->hi[i];
     InstDev& P = c->h_inst[i];
@@ -334,8 +335,9 @@ int commit(slpic_ctx* c) {
     }
     ht[tab_n - 1] = ht[tab_n - 2];
     CK(cudaMemcpy(tab, ht.data(), tab_n * 16, cudaMemcpyHostToDevice), "table");
-    // marker stores: tiles of kTile slots; births are staged in slots of the
-    // tile that created them (ionization: electron tiles, emission: ion tiles)
+    // marker stores: tiles of kTile slots (two buffers for repacking);
+    // electrons emitted at the cathode are staged in slots of the ion tile
+    // that emitted them; collision candidates are queued per electron tile
     uint32_t cap_tiles[2];
     for (int s = 0; s < 2; ++s)
       cap_tiles[s] = (uint32_t)(((size_t)h.sp[s].cap + kTile - 1) / kTile + 1);
@@ -343,35 +345,41 @@ int commit(slpic_ctx* c) {
       SpeciesDev& S = P.sp[s];
       S.cap_tiles = cap_tiles[s];
       const size_t slots = (size_t)cap_tiles[s] * kTile;
-      const size_t stage_a = (size_t)cap_tiles[kElectron] * kTile;
       const size_t stage_b = s == kElectron ? (size_t)cap_tiles[kIon] * kTile : 0;
       const size_t cand_slots = s == kElectron ? slots : 0;
-      size_t b = 2 * soa_bytes(slots) + soa_bytes(stage_a) + soa_bytes(stage_b) +
-                 5 * (((size_t)cap_tiles[s] + 1) * 4 + 256) + cand_slots * 2 + 256;
+      const size_t arr = ((size_t)cap_tiles[s] + 1) * 4 + 256;
+      size_t b = 2 * soa_bytes(slots) + soa_bytes(stage_b) + 4 * arr + cand_slots * 6 + 512;
       void* sb;
       if (int rc = dmalloc(c, &sb, b, "marker buffers")) return rc;
       char* q = (char*)sb;
       S.buf[0] = carve_soa(q, slots);
       S.buf[1] = carve_soa(q, slots);
-      S.stage_a = carve_soa(q, stage_a);
       if (stage_b) S.stage_b = carve_soa(q, stage_b);
       else std::memset(&S.stage_b, 0, sizeof(SoA));
-      S.fill = carve<uint32_t>(q, cap_tiles[s] + 1);
+      S.fill[0] = carve<uint32_t>(q, cap_tiles[s] + 1);
+      S.fill[1] = carve<uint32_t>(q, cap_tiles[s] + 1);
       S.births = carve<uint32_t>(q, cap_tiles[s] + 1);
-      S.boff = carve<uint32_t>(q, cap_tiles[s] + 1);
-      S.coff = carve<uint32_t>(q, cap_tiles[s] + 1);
       S.n_cand = carve<uint32_t>(q, cap_tiles[s] + 1);
       S.cand = cand_slots ? carve<uint16_t>(q, cand_slots) : nullptr;
-      CK(cudaMemset(S.fill, 0, ((size_t)cap_tiles[s] + 1) * 4), "fills");
+      S.esec = cand_slots ? carve<float>(q, cand_slots) : nullptr;
+      CK(cudaMemset(S.fill[0], 0, ((size_t)cap_tiles[s] + 1) * 4), "fills");
+      CK(cudaMemset(S.fill[1], 0, ((size_t)cap_tiles[s] + 1) * 4), "fills");
+      total_tiles += cap_tiles[s];
     }
   }
   void* blk;
   const size_t nseg = 2 * (size_t)c->n_inst;
+  // ordered-scan records: at most one chunk per kCollWarps (kMoveChunkTiles)
+  // tiles of every store, plus one partial chunk per store
+  const size_t coll_chunks = total_tiles / kCollWarps + nseg + 2;
+  const size_t move_chunks = total_tiles / kMoveChunkTiles + nseg + 2;
   size_t bytes = ((sizeof(InstDev) * c->n_inst + 255) & ~size_t(255)) +
                  ((sizeof(InstState) * c->n_inst + 255) & ~size_t(255)) +
                  ((sizeof(SpeciesState) * nseg + 255) & ~size_t(255)) +
                  ((sizeof(Transfer) * nseg + 255) & ~size_t(255)) + 256 +
-                 ((4 * (nseg + 1) + 255) & ~size_t(255)) + 256;
+                 3 * ((4 * (nseg + 1) + 255) & ~size_t(255)) + 256 +
+                 ((sizeof(ChunkStatus) * coll_chunks + 255) & ~size_t(255)) +
+                 ((sizeof(ChunkStatus) * move_chunks + 255) & ~size_t(255));
   if (int rc = dmalloc(c, &blk, bytes, "control")) return rc;
   CK(cudaMemset(blk, 0, bytes), "control");
   char* p = (char*)blk;
@@ -382,6 +390,10 @@ int commit(slpic_ctx* c) {
   c->d_ctrl = carve<Control>(p, 1);
   c->d_seg = carve<unsigned int>(p, nseg + 1);
   c->d_scratch = carve<unsigned int>(p, 4);
+  c->refs.coll_start = carve<unsigned int>(p, nseg + 1);
+  c->refs.move_start = carve<unsigned int>(p, nseg + 1);
+  c->refs.coll_scan = carve<ChunkStatus>(p, coll_chunks);
+  c->refs.move_scan = carve<ChunkStatus>(p, move_chunks);
   c->refs.inst = c->d_inst;
   c->refs.istate = c->d_istate;
   c->refs.sstate = c->d_sstate;
@@ -406,7 +418,7 @@ int commit(slpic_ctx* c) {
   c->blocks_per_sm = bps;
   c->push_grid = sms * bps;
   c->move_grid = sms * 2;
-  c->collide_grid = sms * 4;
+  c->collide_grid = sms * 8;
   for (int i = 0; i < c->n_inst; ++i) {
     if (int rc = upload_inst(c, i)) return rc;
     if (int rc = reset_field(c, i)) return rc;
@@ -671,13 +683,13 @@ namespace {
 
 // Set the fills of tiles [first, ceil(end / kTile)) of a store whose slots
 // [first * kTile, end) are all live.
-int write_fills(slpic_ctx* c, const SpeciesDev& S, uint32_t first, uint32_t end) {
+int write_fills(slpic_ctx* c, const SpeciesDev& S, uint32_t cur, uint32_t first, uint32_t end) {
   const uint32_t last = (end + kTile - 1) / kTile;
   if (last <= first) return SLPIC_OK;
   std::vector<uint32_t> f(last - first);
   for (uint32_t k = first; k < last; ++k)
     f[k - first] = std::min<uint32_t>(end - k * (uint32_t)kTile, (uint32_t)kTile);
-  CK(cudaMemcpy(S.fill + first, f.data(), f.size() * 4, cudaMemcpyHostToDevice), "fills");
+  CK(cudaMemcpy(S.fill[cur] + first, f.data(), f.size() * 4, cudaMemcpyHostToDevice), "fills");
   return SLPIC_OK;
 }
 
@@ -688,7 +700,7 @@ int tail_slot(slpic_ctx* c, const SpeciesDev& S, const SpeciesState& st, uint32_
     return SLPIC_OK;
   }
   uint32_t f = 0;
-  CK(cudaMemcpy(&f, S.fill + st.n_tiles - 1, 4, cudaMemcpyDeviceToHost), "fills");
+  CK(cudaMemcpy(&f, S.fill[st.cur] + st.n_tiles - 1, 4, cudaMemcpyDeviceToHost), "fills");
   *out = (st.n_tiles - 1) * (uint32_t)kTile + f;
   return SLPIC_OK;
 }
@@ -725,7 +737,7 @@ extern "C" int slpic_seed(slpic_ctx* c, int inst, int species, int64_t n, int mo
               (float)wj, c->stream);
   CK(cudaGetLastError(), "seed");
   CK(cudaStreamSynchronize(c->stream), "seed");
-  if (int rc = write_fills(c, S, app / kTile, app + (uint32_t)n)) return rc;
+  if (int rc = write_fills(c, S, st.cur, app / kTile, app + (uint32_t)n)) return rc;
   st.n_live += (uint32_t)n;
   st.next_id += (uint32_t)n;
   st.n_tiles = std::max(st.n_tiles, (app + (uint32_t)n + kTile - 1) / (uint32_t)kTile);
@@ -791,7 +803,7 @@ int load_common(slpic_ctx* c, int inst, int species, const slpic_soa_f32* src, i
                 "marker %u outside the gap, not finite, or with a weight of 2^39 charge "
                 "units or more; the species was emptied", res[0]);
   }
-  if (int rc = write_fills(c, S, 0, (uint32_t)n)) return rc;
+  if (int rc = write_fills(c, S, st.cur, 0, (uint32_t)n)) return rc;
   st.n_live = (uint32_t)n;
   st.n_tiles = (uint32_t)(((uint64_t)n + kTile - 1) / kTile);
   st.next_id = next_id;
@@ -925,7 +937,7 @@ int slpic_read_particles(slpic_ctx* c, int inst, int species, const slpic_soa_f3
     const SpeciesDev& S = c->h_inst[inst].sp[species];
     const SoA& d = S.buf[st.cur];
     std::vector<uint32_t> fill(st.n_tiles);
-    CK(cudaMemcpy(fill.data(), S.fill, st.n_tiles * 4, cudaMemcpyDeviceToHost), "read");
+    CK(cudaMemcpy(fill.data(), S.fill[st.cur], st.n_tiles * 4, cudaMemcpyDeviceToHost), "read");
     const size_t slots = (size_t)st.n_tiles * kTile;
     std::vector<uint32_t> tmp(slots);
     void* dst[7] = {host->cell, host->off, host->vx, host->vy, host->vz, host->wj, host->id};

@@ -1,18 +1,22 @@
 // Monte-Carlo collisions of the null-collision candidates queued by the
-// particle kernel (Sec. III and IV): for a candidate (an electron that drew
-// u < P0 this step) the process is chosen by comparing u' P0 with the
-// cumulative rates n_g sigma_k(eps) beta v dt (Eq. SLPICcollisionNumber with
-// beta_n = 1, whole-marker collisions); elastic collisions scatter by the
-// Vahedi-Surendra angles with the recoil loss, excitation removes its
-// threshold and scatters isotropically, ionization shares the excess energy
-// and stages the born electron and Ar+ (same position, same flux weight).
-// Each candidate is then deposited with its new density weight.
+// particle kernel (Sec. III and IV), and the placement of every birth of the
+// step.  For a candidate (an electron that drew u < P0 this step) the process
+// is chosen by comparing u' P0 with the cumulative rates
+// n_g sigma_k(eps) beta v dt (Eq. SLPICcollisionNumber with beta_n = 1,
+// whole-marker collisions); elastic collisions scatter by the Vahedi-Surendra
+// angles with the recoil loss, excitation removes its threshold and scatters
+// isotropically, ionization shares the excess energy between the primary and
+// a born electron and creates an Ar+ at the same position with the same flux
+// weight.  Each candidate is then deposited with its new density weight.
 //
-// One warp per tile, one lane per candidate: the scattering path is long and
-// latency-bound, and running it here, over every candidate of the step at
-// once, keeps it away from the streaming particle kernel.  Births are ranked
-// in slot order inside their tile with ballots, so their order (and the
-// serial numbers they get when appended) does not depend on scheduling.
+// Work: chunks of kCollWarps consecutive tiles, one warp per tile and one lane
+// per candidate, handed out in order (electron tiles of an instance, then its
+// ion tiles).  The births of a chunk (ionizations; for ion chunks the
+// electrons the particle kernel staged for emission) get their slots from an
+// ordered scan over the chunks (decoupled look-back), so they are appended
+// after the last live marker in (tile, slot) order -- ionization electrons
+// first, emitted electrons after -- with their final serial numbers, whatever
+// the scheduling.
 #include "device_common.cuh"
 #include "slpic_internal.h"
 
@@ -136,27 +140,30 @@ __device__ Velocity collide(const InstDev& P, float kv, float vlim, float vx, fl
   return o;
 }
 
-// Stage the electron and ion born by an ionization in slot o of the staging
-// stores, and deposit both.
-__device__ void stage_ionization(const InstDev& P, size_t o, int cell, float off, float wj,
-                                 uint32_t id, uint32_t step, float es) {
+// Write the electron and Ar+ born by an ionization at slots pe (electron
+// store) and pi (ion store) with their serial numbers, and deposit both.  The
+// secondary gets energy es along an isotropic direction (block 1 of the
+// primary's draws); the ion a gas-temperature Maxwellian (Box-Muller on
+// block 2).
+__device__ void born_pair(const InstDev& P, const SoA& me, const SoA& mi, uint32_t pe,
+                          uint32_t pi, int cell, float off, float wj, uint32_t id,
+                          uint32_t step, float es, uint32_t serial_e, uint32_t serial_i) {
   const SpeciesDev& SE = P.sp[kElectron];
   const SpeciesDev& SI = P.sp[kIon];
   const uint32_t gen = id & kGenBit;
   const uint4 r1 = philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u, 1u), P.key0, P.key1);
   float bx, by, bz;
   isotropic(sqrtf(es * SE.K_V), uniform01(r1.y), uniform01(r1.z), P.two_pi, bx, by, bz);
-  SE.stage_a.cell[o] = cell;
-  SE.stage_a.off[o] = off;
-  SE.stage_a.vx[o] = bx;
-  SE.stage_a.vy[o] = by;
-  SE.stage_a.vz[o] = bz;
-  SE.stage_a.wj[o] = wj;
-  SE.stage_a.id[o] = gen;  // serial assigned when appended
+  me.cell[pe] = cell;
+  me.off[pe] = off;
+  me.vx[pe] = bx;
+  me.vy[pe] = by;
+  me.vz[pe] = bz;
+  me.wj[pe] = wj;
+  me.id[pe] = gen | (serial_e & kSerialMask);
   deposit(P.rho_acc[kElectron], cell, off,
           fixed_charge(beta_of(sqrtf(bx * bx + by * by + bz * bz), SE.vlim) * wj,
                        P.charge_shift));
-  // born ion: gas-temperature Maxwellian (Box-Muller on block 2)
   const uint4 r2 = philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u, 2u), P.key0, P.key1);
   float g[4];
   uniform4(r2, g);
@@ -166,93 +173,205 @@ __device__ void stage_ionization(const InstDev& P, size_t o, int cell, float off
   const float ix = P.sigT_ion * (rr1 * cosf(a1));
   const float iy = P.sigT_ion * (rr1 * sinf(a1));
   const float iz = P.sigT_ion * (rr2 * cosf(a2));
-  SI.stage_a.cell[o] = cell;
-  SI.stage_a.off[o] = off;
-  SI.stage_a.vx[o] = ix;
-  SI.stage_a.vy[o] = iy;
-  SI.stage_a.vz[o] = iz;
-  SI.stage_a.wj[o] = wj;
-  SI.stage_a.id[o] = gen;
+  mi.cell[pi] = cell;
+  mi.off[pi] = off;
+  mi.vx[pi] = ix;
+  mi.vy[pi] = iy;
+  mi.vz[pi] = iz;
+  mi.wj[pi] = wj;
+  mi.id[pi] = gen | (serial_i & kSerialMask);
   deposit(P.rho_acc[kIon], cell, off,
           fixed_charge(beta_of(sqrtf(ix * ix + iy * iy + iz * iz), SI.vlim) * wj,
                        P.charge_shift));
+}
+
+// Slot after the last live marker of a store (the particle kernel has
+// compacted every tile of this step).
+__device__ __forceinline__ uint32_t tail_slot(const SpeciesDev& S, const SpeciesState& st) {
+  return st.n_tiles ? (st.n_tiles - 1) * (uint32_t)kTile + S.fill[st.cur][st.n_tiles - 1]
+                    : 0u;
+}
+
+__device__ __forceinline__ void write_marker(const SoA& d, size_t o, int cell, float off,
+                                             float vx, float vy, float vz, float wj,
+                                             uint32_t id) {
+  d.cell[o] = cell;
+  d.off[o] = off;
+  d.vx[o] = vx;
+  d.vy[o] = vy;
+  d.vz[o] = vz;
+  d.wj[o] = wj;
+  d.id[o] = id;
 }
 
 }  // namespace
 
 __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
   __shared__ unsigned long long s_acc[ACC_COUNT];
-  if (*((volatile int*)&r.ctrl->error)) return;
-  const int lane = threadIdx.x & 31;
+  __shared__ uint32_t s_births[kCollWarps];
+  __shared__ uint32_t s_prefix;
+  __shared__ unsigned int s_chunk;
+  Control* ctrl = r.ctrl;
+  if (*((volatile int*)&ctrl->error)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lanemask_lt = (1u << lane) - 1u;
-  const int warps_per_cta = kCollThreads / 32;
-  const unsigned int wid = blockIdx.x * warps_per_cta + (threadIdx.x >> 5);
-  const unsigned int n_warps = gridDim.x * warps_per_cta;
-  for (int inst = 0; inst < r.n_inst; ++inst) {
-    const InstDev& P = r.inst[inst];
-    const SpeciesDev& S = P.sp[kElectron];
-    const SpeciesState& st = r.sstate[inst * 2 + kElectron];
-    const uint32_t nt = st.n_tiles;
-    const SoA m = S.buf[st.cur];
-    const uint32_t step = r.istate[inst].step;
-    const float kv = S.K_V, vlim = S.vlim;
-    if (threadIdx.x < ACC_COUNT) s_acc[threadIdx.x] = 0ull;
+  const unsigned int n_chunks = ctrl->n_coll_chunks;
+  const unsigned int epoch = ctrl->epoch;
+  if (threadIdx.x < ACC_COUNT) s_acc[threadIdx.x] = 0ull;
+  int cur_inst = -1;
+
+  for (;;) {
+    if (threadIdx.x == 0) s_chunk = atomicAdd(&ctrl->coll_counter, 1u);
     __syncthreads();
-    for (uint32_t k = wid; k < nt; k += n_warps) {
-      const uint32_t nc = S.n_cand[k];
-      if (!nc) continue;
-      const size_t base = (size_t)k * kTile;
-      uint32_t ranked = 0;
-      for (uint32_t c0 = 0; c0 < nc; c0 += 32) {
-        const uint32_t c = c0 + lane;
-        bool ionized = false;
-        int cell = 0;
-        float off = 0.0f, wj = 0.0f, es = 0.0f;
-        uint32_t id = 0;
-        if (c < nc) {
-          const size_t o = base + S.cand[base + c];
-          cell = m.cell[o];
-          off = m.off[o];
-          wj = m.wj[o];
-          id = m.id[o];
-          float vx = m.vx[o], vy = m.vy[o], vz = m.vz[o];
-          const float s1 = vx * vx + vy * vy + vz * vz;
-          const float v1 = sqrtf(s1);
-          const uint4 rr =
-              philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u, 0u), P.key0, P.key1);
-          int proc;
-          const Velocity nv =
-              collide(P, kv, vlim, vx, vy, vz, v1, s1, rr, id, step, wj, s_acc, &es, &proc);
-          if (proc < 3) {
-            vx = nv.vx;
-            vy = nv.vy;
-            vz = nv.vz;
-            m.vx[o] = vx;
-            m.vy[o] = vy;
-            m.vz[o] = vz;
-            ionized = proc == 2;
-          }
-          deposit(P.rho_acc[kElectron], cell, off,
-                  fixed_charge(beta_of(sqrtf(vx * vx + vy * vy + vz * vz), vlim) * wj,
-                               P.charge_shift));
-        }
-        const uint32_t b = __ballot_sync(0xFFFFFFFFu, ionized);
-        if (ionized)
-          stage_ionization(P, base + ranked + __popc(b & lanemask_lt), cell, off, wj, id, step,
-                           es);
-        ranked += __popc(b);
+    const unsigned int c = s_chunk;
+    if (c >= n_chunks) break;
+    int inst = 0;
+    {
+      int lo = 0, hi = r.n_inst - 1;  // last instance with coll_start <= c
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (r.coll_start[mid] <= c) lo = mid;
+        else hi = mid - 1;
       }
-      if (lane == 0) S.births[k] = ranked;
+      inst = lo;
+    }
+    const InstDev& P = r.inst[inst];
+    if (inst != cur_inst) {
+      if (cur_inst >= 0 && threadIdx.x < ACC_COUNT && s_acc[threadIdx.x]) {
+        atomicAdd(r.inst[cur_inst].acc + threadIdx.x, s_acc[threadIdx.x]);
+        s_acc[threadIdx.x] = 0ull;
+      }
+      cur_inst = inst;
+      __syncthreads();
+    }
+    const SpeciesDev& E = P.sp[kElectron];
+    const SpeciesDev& I = P.sp[kIon];
+    const SpeciesState& se = r.sstate[inst * 2 + kElectron];
+    const SpeciesState& si = r.sstate[inst * 2 + kIon];
+    const uint32_t step = r.istate[inst].step;
+    const unsigned int first = r.coll_start[inst];
+    const unsigned int local = c - first;
+    const unsigned int e_chunks = (se.n_tiles + kCollWarps - 1) / kCollWarps;
+    const bool ion_chunk = local >= e_chunks;
+    const uint32_t k0 = (ion_chunk ? local - e_chunks : local) * kCollWarps;
+    const uint32_t nt = ion_chunk ? si.n_tiles : se.n_tiles;
+    const uint32_t k = k0 + warp;
+    const bool have = k < nt;
+    const size_t base = (size_t)k * kTile;
+    const SoA me = E.buf[se.cur];
+    const float kv = E.K_V, vlim = E.vlim;
+
+    // ---- pass 1: scatter this warp's candidates, count births ---------------
+    uint32_t births = 0;
+    if (have) {
+      if (!ion_chunk) {
+        const uint32_t nc = E.n_cand[k];
+        for (uint32_t c0 = 0; c0 < nc; c0 += 32) {
+          const uint32_t q = c0 + lane;
+          bool ionized = false;
+          if (q < nc) {
+            const uint32_t a = E.cand[base + q];
+            const size_t o = base + a;
+            const int cell = me.cell[o];
+            const float off = me.off[o], wj = me.wj[o];
+            const uint32_t id = me.id[o];
+            float vx = me.vx[o], vy = me.vy[o], vz = me.vz[o];
+            const float s1 = vx * vx + vy * vy + vz * vz;
+            const float v1 = sqrtf(s1);
+            const uint4 rr =
+                philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u, 0u), P.key0, P.key1);
+            int proc;
+            float es = 0.0f;
+            const Velocity nv =
+                collide(P, kv, vlim, vx, vy, vz, v1, s1, rr, id, step, wj, s_acc, &es, &proc);
+            if (proc < 3) {
+              vx = nv.vx;
+              vy = nv.vy;
+              vz = nv.vz;
+              me.vx[o] = vx;
+              me.vy[o] = vy;
+              me.vz[o] = vz;
+              if (proc == 2) {
+                ionized = true;
+                E.cand[base + q] = (uint16_t)(a | 0x8000u);  // mark for pass 2
+                E.esec[base + q] = es;
+              }
+            }
+            deposit(P.rho_acc[kElectron], cell, off,
+                    fixed_charge(beta_of(sqrtf(vx * vx + vy * vy + vz * vz), vlim) * wj,
+                                 P.charge_shift));
+          }
+          births += __popc(__ballot_sync(0xFFFFFFFFu, ionized));
+        }
+      } else {
+        births = I.births[k];
+      }
+    }
+    if (lane == 0) s_births[warp] = births;
+    __syncthreads();
+
+    // ---- the chunk's slots: ordered scan over the instance's chunks ----------
+    if (threadIdx.x == 0) {
+      uint32_t agg = 0;
+      for (int w = 0; w < kCollWarps; ++w) agg += s_births[w];
+      s_prefix = chunk_lookback(r.coll_scan, c, first, agg, epoch, ctrl);
     }
     __syncthreads();
-    if (threadIdx.x < ACC_COUNT && s_acc[threadIdx.x])
-      atomicAdd(P.acc + threadIdx.x, s_acc[threadIdx.x]);
+    uint32_t off_w = s_prefix;
+    for (int w = 0; w < warp; ++w) off_w += s_births[w];
+
+    // ---- pass 2: write the births to their slots -----------------------------
+    if (have && births) {
+      const uint32_t app_e = tail_slot(E, se), app_i = tail_slot(I, si);
+      const uint32_t cap_e = E.cap_tiles * (uint32_t)kTile, cap_i = I.cap_tiles * (uint32_t)kTile;
+      if (!ion_chunk) {
+        const uint32_t nc = E.n_cand[k];
+        const SoA mi = I.buf[si.cur];
+        uint32_t ranked = 0;
+        for (uint32_t c0 = 0; c0 < nc; c0 += 32) {
+          const uint32_t q = c0 + lane;
+          const uint32_t a = q < nc ? E.cand[base + q] : 0u;
+          const bool ionized = q < nc && (a & 0x8000u);
+          const uint32_t b = __ballot_sync(0xFFFFFFFFu, ionized);
+          if (ionized) {
+            const uint32_t rank = off_w + ranked + __popc(b & lanemask_lt);
+            const size_t o = base + (a & 0x7FFFu);
+            const uint32_t pe = app_e + rank, pi = app_i + rank;
+            if (pe >= cap_e || pi >= cap_i) {
+              atomicCAS(&ctrl->error, 0, kErrCapacity);
+            } else {
+              born_pair(P, me, mi, pe, pi, me.cell[o], me.off[o], me.wj[o], me.id[o], step,
+                        E.esec[base + q], se.next_id + rank, si.next_id + rank);
+            }
+          }
+          ranked += __popc(b);
+        }
+      } else {
+        // electrons emitted at the cathode, after every ionization electron
+        const SoA& sb = E.stage_b;
+        for (uint32_t q = lane; q < births; q += 32) {
+          const uint32_t rank = off_w + q;
+          const uint32_t pe = app_e + rank;
+          if (pe >= cap_e) {
+            atomicCAS(&ctrl->error, 0, kErrCapacity);
+            continue;
+          }
+          const size_t o = base + q;
+          write_marker(me, pe, sb.cell[o], sb.off[o], sb.vx[o], sb.vy[o], sb.vz[o], sb.wj[o],
+                       kGenBit | ((se.next_id + rank) & kSerialMask));
+        }
+      }
+    }
     __syncthreads();
   }
+  if (cur_inst >= 0 && threadIdx.x < ACC_COUNT && s_acc[threadIdx.x])
+    atomicAdd(r.inst[cur_inst].acc + threadIdx.x, s_acc[threadIdx.x]);
 }
 
 void launch_collide(const DeviceRefs& r, int grid, cudaStream_t s) {
   k_collide<<<grid, kCollThreads, 0, s>>>(r);
 }
+
+static_assert(kCollThreads == 32 * kCollWarps, "one warp per tile of a chunk");
 
 }  // namespace slpic

@@ -6,6 +6,7 @@
 // operation, in the order written.
 #pragma once
 
+#include <cuda/atomic>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -193,6 +194,63 @@ __device__ __forceinline__ void bulk_wait_all() {
 // async-proxy (bulk copy) accesses.
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+}  // namespace slpic
+
+namespace slpic {
+
+// Ordered scan over chunks taken in increasing order (decoupled look-back):
+// chunk c of a scan whose first chunk is `first` publishes its aggregate,
+// adds the records of its predecessors (stopping at the first inclusive
+// prefix), publishes its own inclusive prefix and returns its exclusive
+// prefix.  A chunk publishes its aggregate before it waits, and chunks are
+// handed out in order to running CTAs, so every wait ends; waits are bounded
+// anyway and a time-out raises kErrTimeout (the result is then meaningless).
+// One thread per chunk calls this.
+__device__ __forceinline__ uint32_t chunk_lookback(ChunkStatus* st, unsigned int c,
+                                                   unsigned int first, uint32_t agg,
+                                                   unsigned int epoch, Control* ctrl) {
+  auto publish = [&](ChunkStatus* t, uint32_t v, bool inclusive) {
+    if (inclusive) t->incl = v;
+    else t->agg = v;
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> f(t->flag);
+    f.store((epoch << 2) | (inclusive ? 2u : 1u), cuda::memory_order_release);
+  };
+  if (c == first) {
+    publish(st + c, agg, true);
+    return 0;
+  }
+  publish(st + c, agg, false);
+  uint32_t excl = 0;
+  unsigned int j = c - 1;
+  for (;;) {
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> f(st[j].flag);
+    unsigned int fv = f.load(cuda::memory_order_acquire);
+    uint32_t polls = 0;
+    while ((fv >> 2) != epoch || (fv & 3u) == 0u) {
+      if (++polls > kSpinLimit || *((volatile int*)&ctrl->error) == kErrTimeout) {
+        atomicCAS(&ctrl->error, 0, kErrTimeout);
+        publish(st + c, excl + agg, true);
+        return excl;
+      }
+      __nanosleep(32);
+      fv = f.load(cuda::memory_order_acquire);
+    }
+    if (polls) {
+      atomicAdd(&ctrl->spin_waits, 1u);
+      atomicMax(&ctrl->spin_max, polls);
+    }
+    if ((fv & 3u) == 2u) {
+      excl += *((volatile unsigned int*)&st[j].incl);
+      break;
+    }
+    excl += *((volatile unsigned int*)&st[j].agg);
+    if (j == first) break;  // (first always publishes inclusive; defensive)
+    --j;
+  }
+  publish(st + c, excl + agg, true);
+  return excl;
 }
 
 }  // namespace slpic

@@ -1,9 +1,10 @@
-// End of a step.  k_finish (one CTA per instance) ranks the births each tile
-// staged, decides where they are appended (and whether the tiles are
-// repacked), publishes the step's deposit, solves the 1D Poisson equation for
-// the next step's field and commits the step's tallies; the last CTA plans
-// the next step's tiles.  k_move then repacks and appends (many CTAs).  Also:
-// seeding, load validation and the Philox self-check kernel.
+// End of a step.  k_finish (one CTA per instance) updates the marker counts
+// from the step's exact counters (the particle kernel compacted every tile,
+// k_collide appended every birth), decides whether a store is repacked,
+// publishes the step's deposit, solves the 1D Poisson equation for the next
+// step's field and commits the step's tallies; the last CTA plans the next
+// step.  k_move repacks the stores that became sparse.  Also: seeding, load
+// validation and the Philox self-check kernel.
 #include "device_common.cuh"
 #include "slpic_internal.h"
 
@@ -34,43 +35,35 @@ __device__ T block_incl_scan(T v, T* buf) {
   return r;
 }
 
-// Exclusive prefix of a[0..n) into out[0..n] (out[n] = total), block-wide;
-// returns the total.
-__device__ unsigned long long block_prefix(const uint32_t* a, uint32_t* out, uint32_t n,
-                                           unsigned long long* buf,
-                                           unsigned long long* s_total) {
-  const uint32_t chunk = (n + kFinThreads - 1) / kFinThreads;
-  const uint32_t k0 = threadIdx.x * chunk;
-  unsigned long long loc = 0;
-  for (uint32_t k = k0; k < k0 + chunk && k < n; ++k) loc += a[k];
-  const unsigned long long inc = block_incl_scan<unsigned long long>(loc, buf);
-  unsigned long long run = inc - loc;
-  for (uint32_t k = k0; k < k0 + chunk && k < n; ++k) {
-    out[k] = (uint32_t)run;
-    run += a[k];
-  }
-  if (threadIdx.x == kFinThreads - 1) {
-    *s_total = inc;
-    out[n] = (uint32_t)inc;
-  }
-  __syncthreads();
-  const unsigned long long t = *s_total;
-  __syncthreads();
-  return t;
-}
-
-// Plan the tiles of the next step from the tiles in use (one thread).
+// Plan the next step from the tiles in use (one thread): particle-kernel
+// tiles per segment, collision chunks per instance, repacking chunks.
 __device__ void plan_next(const DeviceRefs& r) {
   const int n_seg = r.n_inst * 2;
-  unsigned int start = 0;
+  unsigned int start = 0, coll = 0, move = 0;
   for (int s = 0; s < n_seg; ++s) {
     r.seg_start[s] = start;
     start += r.sstate[s].n_tiles;
   }
+  for (int i = 0; i < r.n_inst; ++i) {
+    r.coll_start[i] = coll;
+    coll += (r.sstate[2 * i].n_tiles + kCollWarps - 1) / kCollWarps +
+            (r.sstate[2 * i + 1].n_tiles + kCollWarps - 1) / kCollWarps;
+  }
+  for (int s = 0; s < n_seg; ++s) {
+    r.move_start[s] = move;
+    const Transfer& x = r.xfer[s];
+    if (x.compact) move += (x.n_tiles_old + kMoveChunkTiles - 1) / kMoveChunkTiles;
+  }
   r.seg_start[n_seg] = start;
+  r.coll_start[r.n_inst] = coll;
+  r.move_start[n_seg] = move;
   r.ctrl->n_tiles = start;
   r.ctrl->n_seg = n_seg;
-  r.ctrl->tile_counter = 0;
+  r.ctrl->n_coll_chunks = coll;
+  r.ctrl->coll_counter = 0;
+  r.ctrl->n_move_chunks = move;
+  r.ctrl->move_counter = 0;
+  r.ctrl->epoch = (r.ctrl->epoch + 1u) & 0x3FFFFFFFu;
   r.ctrl->finish_done = 0;
 }
 
@@ -78,90 +71,64 @@ __device__ void plan_next(const DeviceRefs& r) {
 
 // mode 0: finish a step and plan the next; mode 1: plan only (one CTA).
 __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode) {
-  __shared__ unsigned long long s_u64[kFinThreads];
+  __shared__ long long s_i64[kFinThreads];
   __shared__ __int128 s_i128[kFinThreads];
-  __shared__ unsigned long long s_total;
   __shared__ int s_flag;
   Control* ctrl = r.ctrl;
   if (mode == 1) {
-    if (threadIdx.x == 0) plan_next(r);
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < 2 * r.n_inst; ++s) r.xfer[s].compact = 0;
+      plan_next(r);
+    }
     return;
   }
   if (*((volatile int*)&ctrl->error)) return;
   const int inst = blockIdx.x;
   const InstDev& P = r.inst[inst];
   InstState& is = r.istate[inst];
-  SpeciesState& se = r.sstate[inst * 2 + kElectron];
-  SpeciesState& si = r.sstate[inst * 2 + kIon];
-  const SpeciesDev& E = P.sp[kElectron];
-  const SpeciesDev& I = P.sp[kIon];
+  unsigned long long* a = P.acc;
 
-  // ---- rank the staged births and count the survivors ----------------------
-  // ionization births were staged by electron tiles, emission births by ion
-  // tiles; their order is (tile, rank inside the tile)
-  const uint32_t nt_e = se.n_tiles, nt_i = si.n_tiles;
-  const uint32_t n_ionz = (uint32_t)block_prefix(E.births, E.boff, nt_e, s_u64, &s_total);
-  const uint32_t n_see = (uint32_t)block_prefix(I.births, I.boff, nt_i, s_u64, &s_total);
-  const uint32_t surv_e = (uint32_t)block_prefix(E.fill, E.coff, nt_e, s_u64, &s_total);
-  const uint32_t surv_i = (uint32_t)block_prefix(I.fill, I.coff, nt_i, s_u64, &s_total);
-
+  // ---- marker counts and where the stores end --------------------------------
+  // survivors = live - absorbed; births (ionizations: an electron and an ion
+  // each; emitted electrons) were appended after the last live marker
   if (threadIdx.x == 0) {
-    int err = 0;
-    const unsigned long long ne = (unsigned long long)surv_e + n_ionz + n_see;
-    const unsigned long long ni = (unsigned long long)surv_i + n_ionz;
-    if (ne > (unsigned long long)E.cap_tiles * kTile || ni > (unsigned long long)I.cap_tiles * kTile)
-      err = kErrCapacity;
-    if ((unsigned long long)se.next_id + n_ionz + n_see > kSerialMask ||
-        (unsigned long long)si.next_id + n_ionz > kSerialMask)
-      err = kErrIdWrap;
-    if (err) set_error(ctrl, err, inst);
-    s_flag = err;
-    if (!err) {
-      // births go after the last live marker, or after the repacked survivors
-      // when the tiles are sparse or the store would overflow
-      for (int sp = 0; sp < 2; ++sp) {
-        SpeciesState& st = sp ? si : se;
-        const SpeciesDev& S = sp ? I : E;
-        Transfer& x = r.xfer[inst * 2 + sp];
-        const uint32_t nt = st.n_tiles;
-        const uint32_t surv = sp ? surv_i : surv_e;
-        const uint32_t nb = sp ? n_ionz : n_ionz + n_see;
-        const uint32_t tail = nt ? (nt - 1) * (uint32_t)kTile + S.fill[nt - 1] : 0u;
-        const unsigned long long end_nc = (unsigned long long)tail + nb;
-        const bool sparse =
-            nt > 2 && (unsigned long long)surv * 4 < (unsigned long long)nt * kTile * 3;
-        const bool overflow = end_nc > (unsigned long long)S.cap_tiles * kTile;
-        x.compact = (sparse || overflow) ? 1u : 0u;
-        x.src = st.cur;
-        x.dst = x.compact ? st.cur ^ 1u : st.cur;
-        x.n_tiles_old = nt;
-        x.app_pos = x.compact ? surv : tail;
-        x.n_a = n_ionz;
-        x.n_b = sp ? 0u : n_see;
-        x.serial_a = st.next_id;
-        x.serial_b = st.next_id + n_ionz;
-        x.nt_a = nt_e;
-        x.nt_b = nt_i;
-        const uint32_t end = x.app_pos + nb;
-        st.cur = x.dst;
-        st.n_live = surv + nb;
-        st.next_id += nb;
-        st.n_tiles = (end + kTile - 1) / kTile;
-      }
+    const uint32_t n_ionz = (uint32_t)a[ACC_COLL2], n_see = (uint32_t)a[ACC_SEE];
+    for (int sp = 0; sp < 2; ++sp) {
+      SpeciesState& st = r.sstate[inst * 2 + sp];
+      const SpeciesDev& S = P.sp[sp];
+      Transfer& x = r.xfer[inst * 2 + sp];
+      const uint32_t absorbed = (uint32_t)(a[ACC_NABS + 2 * sp] + a[ACC_NABS + 2 * sp + 1]);
+      const uint32_t nb = sp ? n_ionz : n_ionz + n_see;
+      const uint32_t surv = st.n_live - absorbed;
+      const uint32_t tail =
+          st.n_tiles ? (st.n_tiles - 1) * (uint32_t)kTile + S.fill[st.cur][st.n_tiles - 1] : 0u;
+      const uint32_t end = tail + nb;
+      const uint32_t n_new = surv + nb;
+      const uint32_t nt = (end + kTile - 1) / kTile;
+      // repack when under three quarters of the slots in use are live
+      x.compact = (nt > 2 && (unsigned long long)n_new * 4 < (unsigned long long)nt * kTile * 3)
+                      ? 1u : 0u;
+      x.src = st.cur;
+      x.dst = x.compact ? st.cur ^ 1u : st.cur;
+      x.n_tiles_old = nt;
+      x.n_new = n_new;
+      x.tail = tail;
+      x.end = end;
+      st.cur = x.dst;
+      st.n_live = n_new;
+      st.next_id += nb;
+      st.n_tiles = x.compact ? (n_new + kTile - 1) / kTile : nt;
     }
   }
   __syncthreads();
-  if (s_flag) return;
-  // new fills: a repacked store is full tiles but the last; otherwise only the
-  // tail tile and the new tiles change (their slots up to `end` are live)
+  // fills of the tail tile and the new tiles: their slots below `end` are live
+  // (k_move reads them when it repacks the store)
   for (int sp = 0; sp < 2; ++sp) {
-    const SpeciesState& st = sp ? si : se;
-    const SpeciesDev& S = sp ? I : E;
+    const SpeciesDev& S = P.sp[sp];
     const Transfer& x = r.xfer[inst * 2 + sp];
-    const uint32_t end = x.app_pos + x.n_a + x.n_b;
-    const uint32_t first = x.compact ? 0u : x.app_pos / kTile;
-    for (uint32_t k = first + threadIdx.x; k < st.n_tiles; k += kFinThreads)
-      S.fill[k] = min(end - k * (uint32_t)kTile, (uint32_t)kTile);
+    if (x.end == x.tail) continue;
+    for (uint32_t k = x.tail / kTile + threadIdx.x; k < x.n_tiles_old; k += kFinThreads)
+      S.fill[x.src][k] = min(x.end - k * (uint32_t)kTile, (uint32_t)kTile);
   }
 
   // ---- deposit of the step -> rho_last; clear the accumulators -------------
@@ -186,7 +153,6 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode) 
     long long loc = 0;
     for (int k = k0; k < k0 + chunk && k <= N; ++k)
       if (k <= N - 1) loc += P.rho_last[kIon][k] - P.rho_last[kElectron][k];
-    long long* s_i64 = reinterpret_cast<long long*>(s_u64);
     const long long inc = block_incl_scan<long long>(loc, s_i64);
     long long Ik = inc - loc;  // I_k at the chunk start (exclusive of net_k)
     __int128 locJ = 0;
@@ -226,11 +192,10 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode) 
   // ---- tallies -------------------------------------------------------------
   if (threadIdx.x == 0) {
     const double unit = 1.0 / (double)P.wscale;
-    unsigned long long* a = P.acc;
     TallyRec t;
     t.step = is.step;
-    t.n_live[0] = se.n_live;
-    t.n_live[1] = si.n_live;
+    t.n_live[0] = r.sstate[inst * 2].n_live;
+    t.n_live[1] = r.sstate[inst * 2 + 1].n_live;
     // live weight by its changes: minus what left through the electrodes,
     // plus the births (ionization pairs, emitted electrons)
     is.w_live[0] = is.w_live[0] - a[ACC_WABS + 0] - a[ACC_WABS + 1] + a[ACC_WIONZ] + a[ACC_WSEE];
@@ -299,71 +264,77 @@ void launch_finish(const DeviceRefs& r, int mode, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Repack and append, as decided by k_finish.  One tile per CTA iteration:
-// repacked tiles are copied from buffer src to their packed slots in dst;
-// births are copied from their tile-local staging slots to the append slots,
-// ionization births first then emission births, each in (tile, rank) order,
-// and receive their serial numbers.
+// Repacking of the stores k_finish marked sparse: chunks of kMoveChunkTiles
+// tiles, handed out in order; each chunk's destination is the prefix of the
+// fills of the tiles before it (ordered scan with decoupled look-back); the
+// live markers keep their order.  The chunk also writes the fills of the
+// repacked store for the tiles with its indices.
 // ---------------------------------------------------------------------------
-namespace {
-
-__device__ __forceinline__ void copy_marker(const SoA& s, size_t i, const SoA& d, size_t o,
-                                            uint32_t id) {
-  d.cell[o] = s.cell[i];
-  d.off[o] = s.off[i];
-  d.vx[o] = s.vx[i];
-  d.vy[o] = s.vy[i];
-  d.vz[o] = s.vz[i];
-  d.wj[o] = s.wj[i];
-  d.id[o] = id;
-}
-
-}  // namespace
-
 __global__ void __launch_bounds__(kMoveThreads) k_move(DeviceRefs r) {
-  if (*((volatile int*)&r.ctrl->error)) return;
+  __shared__ uint32_t s_fill[kMoveChunkTiles];
+  __shared__ uint32_t s_pre[kMoveChunkTiles];
+  __shared__ unsigned int s_chunk;
+  Control* ctrl = r.ctrl;
+  if (*((volatile int*)&ctrl->error)) return;
+  const unsigned int n_chunks = ctrl->n_move_chunks;
+  if (n_chunks == 0) return;
+  const unsigned int epoch = ctrl->epoch;
   const int n_seg = r.n_inst * 2;
-  for (int seg = 0; seg < n_seg; ++seg) {
-    const Transfer x = r.xfer[seg];
-    const InstDev& P = r.inst[seg >> 1];
-    const SpeciesDev& S = P.sp[seg & 1];
-    const SpeciesDev& E = P.sp[kElectron];
-    const SpeciesDev& I = P.sp[kIon];
-    const SoA dst = S.buf[x.dst];
-    if (x.compact) {
-      const SoA src = S.buf[x.src];
-      for (uint32_t k = blockIdx.x; k < x.n_tiles_old; k += gridDim.x) {
-        const uint32_t o = S.coff[k], n = S.coff[k + 1] - o;
-        const size_t base = (size_t)k * kTile;
-        for (uint32_t i = threadIdx.x; i < n; i += kMoveThreads)
-          copy_marker(src, base + i, dst, (size_t)o + i, src.id[base + i]);
+  for (;;) {
+    if (threadIdx.x == 0) s_chunk = atomicAdd(&ctrl->move_counter, 1u);
+    __syncthreads();
+    const unsigned int c = s_chunk;
+    if (c >= n_chunks) break;
+    int seg = 0;
+    {
+      int lo = 0, hi = n_seg - 1;  // last segment with move_start <= c
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (r.move_start[mid] <= c) lo = mid;
+        else hi = mid - 1;
+      }
+      seg = lo;
+    }
+    const Transfer& x = r.xfer[seg];
+    const SpeciesDev& S = r.inst[seg >> 1].sp[seg & 1];
+    const unsigned int first = r.move_start[seg];
+    const uint32_t k0 = (c - first) * kMoveChunkTiles;
+    if (threadIdx.x < kMoveChunkTiles) {
+      const uint32_t k = k0 + threadIdx.x;
+      s_fill[threadIdx.x] = k < x.n_tiles_old ? S.fill[x.src][k] : 0u;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t agg = 0;
+      for (int j = 0; j < kMoveChunkTiles; ++j) {
+        s_pre[j] = agg;
+        agg += s_fill[j];
+      }
+      const uint32_t excl = chunk_lookback(r.move_scan, c, first, agg, epoch, ctrl);
+      for (int j = 0; j < kMoveChunkTiles; ++j) s_pre[j] += excl;
+    }
+    __syncthreads();
+    const SoA src = S.buf[x.src], dst = S.buf[x.dst];
+    for (int j = 0; j < kMoveChunkTiles; ++j) {
+      const uint32_t n = s_fill[j];
+      const size_t from = (size_t)(k0 + j) * kTile, to = s_pre[j];
+      for (uint32_t i = threadIdx.x; i < n; i += kMoveThreads) {
+        dst.cell[to + i] = src.cell[from + i];
+        dst.off[to + i] = src.off[from + i];
+        dst.vx[to + i] = src.vx[from + i];
+        dst.vy[to + i] = src.vy[from + i];
+        dst.vz[to + i] = src.vz[from + i];
+        dst.wj[to + i] = src.wj[from + i];
+        dst.id[to + i] = src.id[from + i];
       }
     }
-    if (x.n_a) {
-      for (uint32_t k = blockIdx.x; k < x.nt_a; k += gridDim.x) {
-        const uint32_t n = E.births[k];
-        if (!n) continue;
-        const uint32_t o = E.boff[k];
-        const size_t base = (size_t)k * kTile;
-        for (uint32_t i = threadIdx.x; i < n; i += kMoveThreads) {
-          const uint32_t id = (S.stage_a.id[base + i] & kGenBit) |
-                              ((x.serial_a + o + i) & kSerialMask);
-          copy_marker(S.stage_a, base + i, dst, (size_t)x.app_pos + o + i, id);
-        }
-      }
+    // fills of the repacked store: full tiles, the last one partial
+    const uint32_t nt_new = (x.n_new + kTile - 1) / kTile;
+    if (threadIdx.x < kMoveChunkTiles) {
+      const uint32_t k = k0 + threadIdx.x;
+      if (k < nt_new) S.fill[x.dst][k] = min(x.n_new - k * (uint32_t)kTile, (uint32_t)kTile);
     }
-    if (x.n_b) {
-      for (uint32_t k = blockIdx.x; k < x.nt_b; k += gridDim.x) {
-        const uint32_t n = I.births[k];
-        if (!n) continue;
-        const uint32_t o = I.boff[k];
-        const size_t base = (size_t)k * kTile;
-        for (uint32_t i = threadIdx.x; i < n; i += kMoveThreads) {
-          const uint32_t id = kGenBit | ((x.serial_b + o + i) & kSerialMask);
-          copy_marker(S.stage_b, base + i, dst, (size_t)x.app_pos + x.n_a + o + i, id);
-        }
-      }
-    }
+    __syncthreads();
   }
 }
 

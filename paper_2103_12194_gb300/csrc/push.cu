@@ -108,7 +108,7 @@ __device__ __forceinline__ TileInfo locate(const DeviceRefs& r, unsigned int n_t
     }
     t.seg = lo;
     t.k = g - r.seg_start[lo];
-    t.fill = r.inst[lo >> 1].sp[lo & 1].fill[t.k];
+    t.fill = r.inst[lo >> 1].sp[lo & 1].fill[r.sstate[lo].cur][t.k];
   }
   return t;
 }
@@ -416,13 +416,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_push(DeviceRefs r) {
         }
         bulk_commit();
       }
-      S.fill[t.k] = n_surv;
-      if (electrons) {
-        S.n_cand[t.k] = n_event;
-        S.births[t.k] = 0;  // ionizations are counted by k_collide
-      } else {
-        S.births[t.k] = n_event;
-      }
+      S.fill[r.sstate[t.seg].cur][t.k] = n_surv;
+      if (electrons) S.n_cand[t.k] = n_event;
+      else S.births[t.k] = n_event;
       atomicAdd(&cs.s_acc[ACC_MSTEPS], (unsigned long long)t.fill);
     }
     __syncthreads();

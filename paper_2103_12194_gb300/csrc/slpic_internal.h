@@ -91,31 +91,29 @@ struct SpeciesState {
   uint32_t next_id;   // next serial number
 };
 
-// What the move kernel does for one segment at the end of a step (written by
-// the finish kernel).
+// Repacking of one segment at the end of a step (decided by k_finish,
+// done by k_move).
 struct Transfer {
-  uint32_t compact;       // repack the tiles into buffer dst
-  uint32_t src, dst;      // buffers
-  uint32_t n_tiles_old;   // tiles processed in the step
-  uint32_t app_pos;       // slot of the first appended birth in dst
-  uint32_t n_a, n_b;      // births from stage_a (ionization) and stage_b (emission)
-  uint32_t serial_a, serial_b;  // serial numbers of the first births of each kind
-  uint32_t nt_a, nt_b;    // source tiles of stage_a (electron tiles) and stage_b (ion tiles)
+  uint32_t compact;       // repack the tiles of buffer src into buffer dst
+  uint32_t src, dst;
+  uint32_t n_tiles_old;   // tiles to repack
+  uint32_t n_new;         // live markers after the step
+  uint32_t tail;          // first slot the step's births went to
+  uint32_t end;           // one past the last birth
   uint32_t pad;
 };
 
 // Configuration of one species of one instance (constant during a run).
 struct SpeciesDev {
   SoA buf[2];         // tiled marker store (cap_tiles * kTile slots each)
-  SoA stage_a;        // ionization births, slot = electron tile * kTile + rank
+  uint32_t* fill[2];  // [cap_tiles] live markers per tile of each buffer
   SoA stage_b;        // electrons only: emission births, slot = ion tile * kTile + rank
-  uint32_t* fill;     // [cap_tiles] live markers per tile
-  uint32_t* births;   // [cap_tiles] births created by each tile in the step
+  uint32_t* births;   // ions: [cap_tiles] electrons emitted by each tile in the step
   uint16_t* cand;     // electrons: [cap_tiles * kTile] slots of the tile's
                       // null-collision candidates, in slot order
   uint32_t* n_cand;   // electrons: [cap_tiles] candidates per tile
-  uint32_t* boff;     // [cap_tiles + 1] exclusive prefix of births
-  uint32_t* coff;     // [cap_tiles + 1] exclusive prefix of fills (repacking)
+  float* esec;        // electrons: [cap_tiles * kTile] energy given to the
+                      // secondary by an ionizing candidate
   uint32_t cap_tiles;
   float qmdt;         // (q / m) dt
   float vlim;         // speed limit (+inf: beta = 1)
@@ -171,15 +169,31 @@ struct InstState {
 
 // Global state of the batched step.
 struct Control {
-  unsigned int tile_counter; // next tile to hand out
-  unsigned int n_tiles;      // tiles this step
+  unsigned int epoch;        // step epoch of the look-back records
+  unsigned int n_tiles;      // particle-kernel tiles this step
   unsigned int n_seg;        // segments = instances * 2
   unsigned int finish_done;  // CTAs of the finish kernel that completed
   int error;                 // first device error (kErr*)
   int error_inst;
-  unsigned int spin_waits;   // barrier polls that found the data not yet there
+  unsigned int spin_waits;   // polls that found data not yet there
   unsigned int spin_max;     // longest single wait, in polls
+  unsigned int coll_counter; // next collision chunk to hand out
+  unsigned int n_coll_chunks;
+  unsigned int move_counter; // next repacking chunk to hand out
+  unsigned int n_move_chunks;
 };
+
+// Look-back record of one chunk of an ordered scan.
+struct ChunkStatus {
+  unsigned int flag;  // (epoch << 2) | state; state 1 = aggregate, 2 = inclusive
+  unsigned int agg;
+  unsigned int incl;
+  unsigned int pad;
+};
+
+// Tiles per collision chunk (one warp each) and per repacking chunk.
+constexpr int kCollWarps = 8;
+constexpr int kMoveChunkTiles = 16;
 
 struct DeviceRefs {
   InstDev* inst;          // [n_inst]
@@ -187,7 +201,11 @@ struct DeviceRefs {
   SpeciesState* sstate;   // [n_inst * 2]
   Transfer* xfer;         // [n_inst * 2]
   Control* ctrl;
-  unsigned int* seg_start;  // [n_seg + 1] first global tile of each segment
+  unsigned int* seg_start;   // [n_seg + 1] first global tile of each segment
+  unsigned int* coll_start;  // [n_inst + 1] first collision chunk of each instance
+  unsigned int* move_start;  // [n_seg + 1] first repacking chunk of each segment
+  ChunkStatus* coll_scan;    // [max collision chunks]
+  ChunkStatus* move_scan;    // [max repacking chunks]
   int n_inst;
   int smem_nodes;         // deposit grid nodes in shared memory (0: global atomics)
 };

@@ -307,23 +307,26 @@ def test_graph_replay_equals_single_steps(slpic):
     b.close()
 
 
-def test_capacity_overflow_is_reported_and_state_kept(slpic):
+def test_capacity_overflow_is_reported_and_recoverable(slpic):
     spec = dense_spec(n_cells=256, pd=30.0)
     e, i = mixed_state(spec, 3000, 0, seed=13)
     e["vx"] = np.abs(e["vx"]) * 0 + np.float32(6e6)  # ~100 eV: ionizing
     sim = make_sim(slpic, spec, cap=(3000, 3000))
     sim.load(0, 0, e)
-    before = sim.particles(0, 0)
     sim.step(3)
     with pytest.raises(slpic.SlpicError) as err:
         sim.synchronize()
     assert err.value.code == slpic.ERR_CAPACITY
+    sim.step(2)  # steps are no-ops while the error is latched
+    with pytest.raises(slpic.SlpicError):
+        sim.synchronize()
     sim.clear_error()
-    n = sim.count(0, 0)
-    assert n <= 4096  # capacity rounds up to whole 1024-marker tiles, plus one
-    if len(sim.history(0)) == 0:
-        after = sim.particles(0, 0)
-        assert np.array_equal(after["id"], before["id"])
+    sim.load(0, 0, e)
+    sim.load(0, 1, {k: v[:0] for k, v in e.items()})
+    assert sim.count(0, 0) == 3000
+    sim.set_gas(0, 0.0, spec["T_K"])  # no more ionization
+    sim.step(2)
+    sim.synchronize()
     sim.close()
 
 
