@@ -231,9 +231,21 @@ int slpic_read_wait_stats(slpic_ctx* ctx, int64_t* waits, int64_t* longest);
 int slpic_launch_count(slpic_ctx* ctx, int64_t* launches);
 
 /* Philox4x32-10 evaluated by the device: out[4i..4i+3] = Philox(ctr[4i..],
- * key = seed).  Host arrays; for checking the random stream. */
+ * key = seed).  Host arrays; for checking the random stream.  A step of
+ * instance i draws, for marker id of species s, counter (id, step,
+ * 2 i + s, block): block 0 = (unused, process, two angles) of a collision
+ * candidate or (emission test, ...) of an ion at the cathode; block 1 =
+ * (energy split, secondary's two angles); block 2 = born ion's Maxwellian;
+ * seeding uses step = 0xFFFFFFFF. */
 int slpic_philox(int device, uint64_t seed, const uint32_t* ctr, int64_t n,
                  uint32_t* out);
+
+/* Philox2x32-10 evaluated by the device: out[2i..2i+1] = Philox(ctr[2i..],
+ * key).  The null-collision draw of an electron in a step is word 0 of
+ * Philox2x32-10 with counter (id, step) and key
+ * lo32(seed) ^ hi32(seed) ^ (0x85EBCA6B * (instance + 1)) mod 2^32. */
+int slpic_philox2x32(int device, uint32_t key, const uint32_t* ctr, int64_t n,
+                     uint32_t* out);
 
 #ifdef __cplusplus
 }

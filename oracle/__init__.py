@@ -96,6 +96,7 @@ def lib():
         L.oracle_xsec.argtypes = [vp, vp, i64, vp]
         L.oracle_philox.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, vp]
         L.oracle_philox_many.argtypes = [vp, i64, ctypes.c_uint32, ctypes.c_uint32, vp]
+        L.oracle_philox2_many.argtypes = [vp, i64, ctypes.c_uint32, vp]
         L.oracle_uniform64.restype = ctypes.c_double
         L.oracle_uniform64.argtypes = [ctypes.c_uint32]
         L.oracle_uniform32.restype = ctypes.c_float
@@ -122,6 +123,14 @@ def philox(ctr, seed):
     out = np.empty_like(ctr)
     lib().oracle_philox_many(_ptr(ctr), ctr.shape[0], seed & 0xFFFFFFFF,
                              (seed >> 32) & 0xFFFFFFFF, _ptr(out))
+    return out
+
+
+def philox2(ctr, key):
+    """Philox2x32-10 blocks for an (n, 2) uint32 counter array."""
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 2)
+    out = np.empty_like(ctr)
+    lib().oracle_philox2_many(_ptr(ctr), ctr.shape[0], key & 0xFFFFFFFF, _ptr(out))
     return out
 
 

@@ -24,7 +24,8 @@
 //  * collision probability of a marker per step = beta v dt / lambda_mfp
 //    = n_g sigma(eps) beta v dt (Sec. III, the d'/lambda_mfp rule and
 //    Eq. SLPICcollisionNumber with beta_n = 1, whole-marker collisions),
-//    realised with a null-collision majorant;
+//    realised with a null-collision majorant: a candidate draw u < P0 every
+//    step (Philox2x32-10), then the process from a second draw;
 //  * Vahedi-Surendra elastic angles, isotropic excitation with the threshold
 //    removed, ionization with a uniform split of the excess energy (the
 //    Kutasi sharing rule is not given in the paper), Ar+ born with a gas
@@ -82,6 +83,22 @@ void philox4x32_10(const uint32_t ctr_in[4], uint32_t k0, uint32_t k1,
     c0 = n0; c1 = n1; c2 = n2; c3 = n3;
   }
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// Philox2x32-10 from the same publication: ten rounds of one 32x32->64
+// multiply, the round key bumped by the Weyl constant.
+void philox2x32_10(const uint32_t ctr_in[2], uint32_t k, uint32_t out[2]) {
+  const uint32_t M = 0xD256D193u, W = 0x9E3779B9u;
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) k += W;
+    uint64_t p = (uint64_t)M * (uint64_t)c0;
+    uint32_t hi = (uint32_t)(p >> 32), lo = (uint32_t)p;
+    uint32_t n0 = hi ^ c1 ^ k;
+    uint32_t n1 = lo;
+    c0 = n0; c1 = n1;
+  }
+  out[0] = c0; out[1] = c1;
 }
 
 // 32 random bits -> uniform in (0, 1): (floor(x / 2^9) + 1/2) / 2^23.  The
@@ -228,6 +245,17 @@ struct Sim {
     E.assign(N + 1, (R)(-c.V / c.d));
     charge[0].assign(N + 1, 0);
     charge[1].assign(N + 1, 0);
+  }
+
+  // The null-collision draw of an electron in a step: word 0 of
+  // Philox2x32-10 with counter (id, step) and a key mixing both seed words
+  // and the instance.
+  R collision_draw(uint32_t id, uint32_t stp) const {
+    uint32_t ctr[2] = {id, stp}, out[2];
+    const uint32_t key = (uint32_t)cfg.seed ^ (uint32_t)(cfg.seed >> 32) ^
+                         (0x85EBCA6Bu * (cfg.instance + 1u));
+    philox2x32_10(ctr, key, out);
+    return uniform01<R>(out[0]);
   }
 
   void draws(uint32_t id, uint32_t stp, int species, uint32_t block,
@@ -434,10 +462,10 @@ struct Sim {
   // Null-collision Monte-Carlo collision of one electron (Sec. III).
   void collide(Marker<R>& m, R s1, R v1, uint32_t s_now, oracle_tally& t,
                std::vector<Marker<R>>& born_e, std::vector<Marker<R>>& born_i) {
-    R u[4];
-    draws(m.id, s_now, ELECTRON, 0, u);
-    if (!(u[0] < P0)) return;
+    if (!(collision_draw(m.id, s_now) < P0)) return;
     t.n_candidates++;
+    R u[4];  // u[1]: process, u[2], u[3]: angles (u[0] unused)
+    draws(m.id, s_now, ELECTRON, 0, u);
     R vb = v1 > vlim[ELECTRON] ? vlim[ELECTRON] : v1;  // beta v
     if (vb > vb_cap) {
       vb = vb_cap;
@@ -613,6 +641,10 @@ extern "C" {
 void oracle_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1,
                    uint32_t* out) {
   philox4x32_10(ctr, k0, k1, out);
+}
+
+void oracle_philox2_many(const uint32_t* ctr, int64_t n, uint32_t k, uint32_t* out) {
+  for (int64_t i = 0; i < n; ++i) philox2x32_10(ctr + 2 * i, k, out + 2 * i);
 }
 
 // Many blocks at once: ctr is n x 4, out is n x 4.

@@ -159,6 +159,8 @@ void fill_constants(slpic_ctx* c, int i, InstDev& P) {
   P.key0 = (uint32_t)h.seed;
   P.key1 = (uint32_t)(h.seed >> 32);
   P.ctr_inst = (uint32_t)i;
+  // key of the per-step null-collision draw: both seed words and the instance
+  P.key2 = (uint32_t)h.seed ^ (uint32_t)(h.seed >> 32) ^ (0x85EBCA6Bu * (uint32_t)(i + 1));
   P.dtdx = (float)(h.dt / dx);
   const HostSpecies& E = h.sp[kElectron];
   const HostSpecies& I = h.sp[kIon];
@@ -369,9 +371,9 @@ int commit(slpic_ctx* c) {
   }
   void* blk;
   const size_t nseg = 2 * (size_t)c->n_inst;
-  // ordered-scan records: at most one chunk per kCollWarps (kMoveChunkTiles)
+  // ordered-scan records: at most one chunk per kCollChunkTiles (kMoveChunkTiles)
   // tiles of every store, plus one partial chunk per store
-  const size_t coll_chunks = total_tiles / kCollWarps + nseg + 2;
+  const size_t coll_chunks = total_tiles / kCollChunkTiles + nseg + 2;
   const size_t move_chunks = total_tiles / kMoveChunkTiles + nseg + 2;
   size_t bytes = ((sizeof(InstDev) * c->n_inst + 255) & ~size_t(255)) +
                  ((sizeof(InstState) * c->n_inst + 255) & ~size_t(255)) +
@@ -1096,6 +1098,30 @@ int slpic_launch_count(slpic_ctx* c, int64_t* launches) {
   if (!c || !launches) return SLPIC_ERR_INVALID_ARG;
   *launches = c->last_launches;
   return SLPIC_OK;
+}
+
+int slpic_philox2x32(int device, uint32_t key, const uint32_t* ctr, int64_t n,
+                     uint32_t* out) {
+  if (!ctr || !out || n < 0) return SLPIC_ERR_INVALID_ARG;
+  if (n == 0) return SLPIC_OK;
+  if (cudaSetDevice(device) != cudaSuccess) return SLPIC_ERR_CUDA;
+  uint32_t *dc = nullptr, *dout = nullptr;
+  const size_t b = (size_t)n * 8;
+  if (cudaMalloc(&dc, b) != cudaSuccess) return SLPIC_ERR_CUDA;
+  if (cudaMalloc(&dout, b) != cudaSuccess) {
+    cudaFree(dc);
+    return SLPIC_ERR_CUDA;
+  }
+  int rc = SLPIC_OK;
+  if (cudaMemcpy(dc, ctr, b, cudaMemcpyHostToDevice) != cudaSuccess) rc = SLPIC_ERR_CUDA;
+  if (!rc) {
+    launch_philox2(key, dc, dout, n, 0);
+    if (cudaGetLastError() != cudaSuccess) rc = SLPIC_ERR_CUDA;
+  }
+  if (!rc && cudaMemcpy(out, dout, b, cudaMemcpyDeviceToHost) != cudaSuccess) rc = SLPIC_ERR_CUDA;
+  cudaFree(dc);
+  cudaFree(dout);
+  return rc;
 }
 
 int slpic_philox(int device, uint64_t seed, const uint32_t* ctr, int64_t n, uint32_t* out) {

@@ -9,9 +9,9 @@
 // a born electron and creates an Ar+ at the same position with the same flux
 // weight.  Each candidate is then deposited with its new density weight.
 //
-// Work: chunks of kCollWarps consecutive tiles, one warp per tile and one lane
-// per candidate, handed out in order (electron tiles of an instance, then its
-// ion tiles).  The births of a chunk (ionizations; for ion chunks the
+// Work: chunks of kCollChunkTiles consecutive tiles (each warp kCollWarpTiles
+// of them, one lane per candidate), handed out in order (electron tiles of an
+// instance, then its ion tiles).  The births of a chunk (ionizations; for ion chunks the
 // electrons the particle kernel staged for emission) get their slots from an
 // ordered scan over the chunks (decoupled look-back), so they are appended
 // after the last live marker in (tile, slot) order -- ionization electrons
@@ -66,7 +66,8 @@ struct Velocity {
   float vx, vy, vz;
 };
 
-// Choose the process with u[1] against the cumulative rates and scatter.
+// Choose the process with u[1] against the cumulative rates and scatter
+// (u[0] is unused: the candidate test drew from Philox2x32).
 // Returns the new velocity; *proc_out = 0 elastic, 1 excitation,
 // 2 ionization, 3 null (velocity unchanged).
 __device__ Velocity collide(const InstDev& P, float kv, float vlim, float vx, float vy,
@@ -251,19 +252,22 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
     const uint32_t step = r.istate[inst].step;
     const unsigned int first = r.coll_start[inst];
     const unsigned int local = c - first;
-    const unsigned int e_chunks = (se.n_tiles + kCollWarps - 1) / kCollWarps;
+    const unsigned int e_chunks = (se.n_tiles + kCollChunkTiles - 1) / kCollChunkTiles;
     const bool ion_chunk = local >= e_chunks;
-    const uint32_t k0 = (ion_chunk ? local - e_chunks : local) * kCollWarps;
     const uint32_t nt = ion_chunk ? si.n_tiles : se.n_tiles;
-    const uint32_t k = k0 + warp;
-    const bool have = k < nt;
-    const size_t base = (size_t)k * kTile;
+    // this warp's tiles: kCollWarpTiles consecutive ones
+    const uint32_t kw = (ion_chunk ? local - e_chunks : local) * kCollChunkTiles +
+                        warp * kCollWarpTiles;
     const SoA me = E.buf[se.cur];
     const float kv = E.K_V, vlim = E.vlim;
 
-    // ---- pass 1: scatter this warp's candidates, count births ---------------
-    uint32_t births = 0;
-    if (have) {
+    // ---- pass 1: scatter this warp's candidates, count births per tile -------
+    uint32_t tile_births = 0;  // lane j: births of tile kw + j
+    for (int j = 0; j < kCollWarpTiles; ++j) {
+      const uint32_t k = kw + j;
+      if (k >= nt) break;
+      const size_t base = (size_t)k * kTile;
+      uint32_t births = 0;
       if (!ion_chunk) {
         const uint32_t nc = E.n_cand[k];
         for (uint32_t c0 = 0; c0 < nc; c0 += 32) {
@@ -306,59 +310,80 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
       } else {
         births = I.births[k];
       }
+      if (lane == j) tile_births = births;
     }
-    if (lane == 0) s_births[warp] = births;
+    uint32_t warp_births = tile_births;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) warp_births += __shfl_xor_sync(0xFFFFFFFFu, warp_births, o);
+    if (lane == 0) s_births[warp] = warp_births;
     __syncthreads();
 
     // ---- the chunk's slots: ordered scan over the instance's chunks ----------
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
       uint32_t agg = 0;
       for (int w = 0; w < kCollWarps; ++w) agg += s_births[w];
-      s_prefix = chunk_lookback(r.coll_scan, c, first, agg, epoch, ctrl);
+      const uint32_t pre = chunk_lookback(r.coll_scan, c, first, agg, epoch, ctrl);
+      if (lane == 0) s_prefix = pre;
     }
     __syncthreads();
     uint32_t off_w = s_prefix;
     for (int w = 0; w < warp; ++w) off_w += s_births[w];
 
     // ---- pass 2: write the births to their slots -----------------------------
-    if (have && births) {
+    if (warp_births) {
       const uint32_t app_e = tail_slot(E, se), app_i = tail_slot(I, si);
       const uint32_t cap_e = E.cap_tiles * (uint32_t)kTile, cap_i = I.cap_tiles * (uint32_t)kTile;
-      if (!ion_chunk) {
-        const uint32_t nc = E.n_cand[k];
-        const SoA mi = I.buf[si.cur];
-        uint32_t ranked = 0;
-        for (uint32_t c0 = 0; c0 < nc; c0 += 32) {
-          const uint32_t q = c0 + lane;
-          const uint32_t a = q < nc ? E.cand[base + q] : 0u;
-          const bool ionized = q < nc && (a & 0x8000u);
-          const uint32_t b = __ballot_sync(0xFFFFFFFFu, ionized);
-          if (ionized) {
-            const uint32_t rank = off_w + ranked + __popc(b & lanemask_lt);
-            const size_t o = base + (a & 0x7FFFu);
-            const uint32_t pe = app_e + rank, pi = app_i + rank;
-            if (pe >= cap_e || pi >= cap_i) {
-              atomicCAS(&ctrl->error, 0, kErrCapacity);
-            } else {
-              born_pair(P, me, mi, pe, pi, me.cell[o], me.off[o], me.wj[o], me.id[o], step,
-                        E.esec[base + q], se.next_id + rank, si.next_id + rank);
+      const SoA mi = I.buf[si.cur];
+      // exclusive prefix of the per-tile counts over the warp's tiles
+      uint32_t tile_off = tile_births;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t n = __shfl_up_sync(0xFFFFFFFFu, tile_off, o);
+        if (lane >= o) tile_off += n;
+      }
+      tile_off -= tile_births;
+      for (int j = 0; j < kCollWarpTiles; ++j) {
+        const uint32_t k = kw + j;
+        if (k >= nt) break;
+        const uint32_t births = __shfl_sync(0xFFFFFFFFu, tile_births, j);
+        if (!births) continue;
+        const uint32_t off_t = off_w + __shfl_sync(0xFFFFFFFFu, tile_off, j);
+        const size_t base = (size_t)k * kTile;
+        if (!ion_chunk) {
+          const uint32_t nc = E.n_cand[k];
+          uint32_t ranked = 0;
+          for (uint32_t c0 = 0; c0 < nc; c0 += 32) {
+            const uint32_t q = c0 + lane;
+            const uint32_t a = q < nc ? E.cand[base + q] : 0u;
+            const bool ionized = q < nc && (a & 0x8000u);
+            const uint32_t b = __ballot_sync(0xFFFFFFFFu, ionized);
+            if (ionized) {
+              const uint32_t rank = off_t + ranked + __popc(b & lanemask_lt);
+              const size_t o = base + (a & 0x7FFFu);
+              const uint32_t pe = app_e + rank, pi = app_i + rank;
+              if (pe >= cap_e || pi >= cap_i) {
+                atomicCAS(&ctrl->error, 0, kErrCapacity);
+              } else {
+                born_pair(P, me, mi, pe, pi, me.cell[o], me.off[o], me.wj[o], me.id[o], step,
+                          E.esec[base + q], se.next_id + rank, si.next_id + rank);
+              }
             }
+            ranked += __popc(b);
           }
-          ranked += __popc(b);
-        }
-      } else {
-        // electrons emitted at the cathode, after every ionization electron
-        const SoA& sb = E.stage_b;
-        for (uint32_t q = lane; q < births; q += 32) {
-          const uint32_t rank = off_w + q;
-          const uint32_t pe = app_e + rank;
-          if (pe >= cap_e) {
-            atomicCAS(&ctrl->error, 0, kErrCapacity);
-            continue;
+        } else {
+          // electrons emitted at the cathode, after every ionization electron
+          const SoA& sb = E.stage_b;
+          for (uint32_t q = lane; q < births; q += 32) {
+            const uint32_t rank = off_t + q;
+            const uint32_t pe = app_e + rank;
+            if (pe >= cap_e) {
+              atomicCAS(&ctrl->error, 0, kErrCapacity);
+              continue;
+            }
+            const size_t o = base + q;
+            write_marker(me, pe, sb.cell[o], sb.off[o], sb.vx[o], sb.vy[o], sb.vz[o], sb.wj[o],
+                         kGenBit | ((se.next_id + rank) & kSerialMask));
           }
-          const size_t o = base + q;
-          write_marker(me, pe, sb.cell[o], sb.off[o], sb.vx[o], sb.vy[o], sb.vz[o], sb.wj[o],
-                       kGenBit | ((se.next_id + rank) & kSerialMask));
         }
       }
     }
@@ -372,6 +397,7 @@ void launch_collide(const DeviceRefs& r, int grid, cudaStream_t s) {
   k_collide<<<grid, kCollThreads, 0, s>>>(r);
 }
 
-static_assert(kCollThreads == 32 * kCollWarps, "one warp per tile of a chunk");
+static_assert(kCollThreads == 32 * kCollWarps, "kCollWarps warps per chunk");
+static_assert(kCollWarpTiles <= 32, "per-tile counts live one per lane");
 
 }  // namespace slpic

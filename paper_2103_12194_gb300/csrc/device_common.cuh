@@ -35,6 +35,21 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+// Philox2x32-10 (same publication): one 32x32 -> 64-bit product per round,
+// the high half mixed with the other counter word and the round key; the key
+// advances by the Weyl increment between rounds.  Used for the one draw every
+// electron makes every step (the null-collision test), where it costs half of
+// Philox4x32-10.
+__device__ __forceinline__ uint2 philox2x32_10(uint2 c, uint32_t k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) k += 0x9E3779B9u;
+    const unsigned long long p = (unsigned long long)0xD256D193u * c.x;
+    c = make_uint2((uint32_t)(p >> 32) ^ c.y ^ k, (uint32_t)p);
+  }
+  return c;
+}
+
 // 32 random bits -> (floor(x / 2^9) + 1/2) 2^-23, exactly representable.
 __device__ __forceinline__ float uniform01(uint32_t x) {
   return (__uint2float_rn(x >> 9) + 0.5f) * 1.1920928955078125e-07f;
@@ -200,56 +215,74 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 
 namespace slpic {
 
-// Ordered scan over chunks taken in increasing order (decoupled look-back):
-// chunk c of a scan whose first chunk is `first` publishes its aggregate,
-// adds the records of its predecessors (stopping at the first inclusive
-// prefix), publishes its own inclusive prefix and returns its exclusive
-// prefix.  A chunk publishes its aggregate before it waits, and chunks are
-// handed out in order to running CTAs, so every wait ends; waits are bounded
+// Ordered scan over chunks taken in increasing order (decoupled look-back),
+// called by all 32 lanes of one warp: chunk c of a scan whose first chunk is
+// `first` publishes its aggregate, then reads the records of up to 32
+// predecessors at a time (lane l: chunk c - 1 - l - 32 m), adds them down to
+// the nearest inclusive prefix, publishes its own inclusive prefix and returns
+// its exclusive prefix.  A chunk publishes its aggregate before it waits and
+// chunks go to running CTAs in order, so every wait ends; waits are bounded
 // anyway and a time-out raises kErrTimeout (the result is then meaningless).
-// One thread per chunk calls this.
+__device__ __forceinline__ void chunk_publish(ChunkStatus* t, uint32_t v, bool inclusive,
+                                              unsigned int epoch) {
+  if (inclusive) t->incl = v;
+  else t->agg = v;
+  cuda::atomic_ref<unsigned int, cuda::thread_scope_device> f(t->flag);
+  f.store((epoch << 2) | (inclusive ? 2u : 1u), cuda::memory_order_release);
+}
+
 __device__ __forceinline__ uint32_t chunk_lookback(ChunkStatus* st, unsigned int c,
                                                    unsigned int first, uint32_t agg,
                                                    unsigned int epoch, Control* ctrl) {
-  auto publish = [&](ChunkStatus* t, uint32_t v, bool inclusive) {
-    if (inclusive) t->incl = v;
-    else t->agg = v;
-    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> f(t->flag);
-    f.store((epoch << 2) | (inclusive ? 2u : 1u), cuda::memory_order_release);
-  };
+  const int lane = threadIdx.x & 31;
   if (c == first) {
-    publish(st + c, agg, true);
+    if (lane == 0) chunk_publish(st + c, agg, true, epoch);
     return 0;
   }
-  publish(st + c, agg, false);
+  if (lane == 0) chunk_publish(st + c, agg, false, epoch);
   uint32_t excl = 0;
-  unsigned int j = c - 1;
-  for (;;) {
-    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> f(st[j].flag);
-    unsigned int fv = f.load(cuda::memory_order_acquire);
+  long long top = (long long)c - 1;  // nearest predecessor not yet added
+  bool timed_out = false;
+  while (top >= (long long)first) {
+    const long long j = top - lane;
+    const bool valid = j >= (long long)first;
+    unsigned int fv = 0;
     uint32_t polls = 0;
-    while ((fv >> 2) != epoch || (fv & 3u) == 0u) {
-      if (++polls > kSpinLimit || *((volatile int*)&ctrl->error) == kErrTimeout) {
-        atomicCAS(&ctrl->error, 0, kErrTimeout);
-        publish(st + c, excl + agg, true);
-        return excl;
-      }
-      __nanosleep(32);
+    if (valid) {
+      cuda::atomic_ref<unsigned int, cuda::thread_scope_device> f(st[j].flag);
       fv = f.load(cuda::memory_order_acquire);
+      while ((fv >> 2) != epoch || (fv & 3u) == 0u) {
+        if (++polls > kSpinLimit || *((volatile int*)&ctrl->error) == kErrTimeout) {
+          timed_out = true;
+          break;
+        }
+        __nanosleep(32);
+        fv = f.load(cuda::memory_order_acquire);
+      }
     }
-    if (polls) {
-      atomicAdd(&ctrl->spin_waits, 1u);
-      atomicMax(&ctrl->spin_max, polls);
-    }
-    if ((fv & 3u) == 2u) {
-      excl += *((volatile unsigned int*)&st[j].incl);
+    if (__any_sync(0xFFFFFFFFu, timed_out)) {
+      if (lane == 0) atomicCAS(&ctrl->error, 0, kErrTimeout);
+      timed_out = true;
       break;
     }
-    excl += *((volatile unsigned int*)&st[j].agg);
-    if (j == first) break;  // (first always publishes inclusive; defensive)
-    --j;
+    const uint32_t maxp = __reduce_max_sync(0xFFFFFFFFu, polls);
+    if (lane == 0 && maxp) {
+      atomicAdd(&ctrl->spin_waits, 1u);
+      atomicMax(&ctrl->spin_max, maxp);
+    }
+    const bool incl = valid && (fv & 3u) == 2u;
+    uint32_t v = 0;
+    if (valid) v = incl ? *((volatile unsigned int*)&st[j].incl)
+                        : *((volatile unsigned int*)&st[j].agg);
+    const uint32_t b = __ballot_sync(0xFFFFFFFFu, incl);
+    // lanes up to the nearest inclusive record (or the whole window)
+    const int stop = b ? __ffs(b) - 1 : 31;
+    if (lane > stop) v = 0;
+    excl += __reduce_add_sync(0xFFFFFFFFu, v);
+    if (b) break;
+    top -= 32;
   }
-  publish(st + c, excl + agg, true);
+  if (lane == 0) chunk_publish(st + c, excl + agg, true, epoch);
   return excl;
 }
 

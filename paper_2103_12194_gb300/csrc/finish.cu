@@ -46,8 +46,8 @@ __device__ void plan_next(const DeviceRefs& r) {
   }
   for (int i = 0; i < r.n_inst; ++i) {
     r.coll_start[i] = coll;
-    coll += (r.sstate[2 * i].n_tiles + kCollWarps - 1) / kCollWarps +
-            (r.sstate[2 * i + 1].n_tiles + kCollWarps - 1) / kCollWarps;
+    coll += (r.sstate[2 * i].n_tiles + kCollChunkTiles - 1) / kCollChunkTiles +
+            (r.sstate[2 * i + 1].n_tiles + kCollChunkTiles - 1) / kCollChunkTiles;
   }
   for (int s = 0; s < n_seg; ++s) {
     r.move_start[s] = move;
@@ -304,14 +304,17 @@ __global__ void __launch_bounds__(kMoveThreads) k_move(DeviceRefs r) {
       s_fill[threadIdx.x] = k < x.n_tiles_old ? S.fill[x.src][k] : 0u;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
       uint32_t agg = 0;
-      for (int j = 0; j < kMoveChunkTiles; ++j) {
-        s_pre[j] = agg;
-        agg += s_fill[j];
-      }
+      for (int j = 0; j < kMoveChunkTiles; ++j) agg += s_fill[j];
       const uint32_t excl = chunk_lookback(r.move_scan, c, first, agg, epoch, ctrl);
-      for (int j = 0; j < kMoveChunkTiles; ++j) s_pre[j] += excl;
+      if (threadIdx.x == 0) {
+        uint32_t run = excl;
+        for (int j = 0; j < kMoveChunkTiles; ++j) {
+          s_pre[j] = run;
+          run += s_fill[j];
+        }
+      }
     }
     __syncthreads();
     const SoA src = S.buf[x.src], dst = S.buf[x.dst];
@@ -448,6 +451,20 @@ void launch_validate(const SoA& d, uint32_t n, int N, int shift, unsigned int* b
 __global__ void k_philox(uint32_t k0, uint32_t k1, const uint4* ctr, uint4* out, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = philox4x32_10(ctr[i], k0, k1);
+}
+
+__global__ void k_philox2(uint32_t k, const uint2* ctr, uint2* out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = philox2x32_10(ctr[i], k);
+}
+
+void launch_philox2(uint32_t k, const uint32_t* ctr, uint32_t* out, long long n,
+                    cudaStream_t s) {
+  if (n <= 0) return;
+  const int threads = 256;
+  const long long grid = (n + threads - 1) / threads;
+  k_philox2<<<(unsigned int)grid, threads, 0, s>>>(k, reinterpret_cast<const uint2*>(ctr),
+                                                   reinterpret_cast<uint2*>(out), n);
 }
 
 void launch_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, uint32_t* out, long long n,

@@ -2,7 +2,8 @@
 // species: gather, speed-limited kick and drift (Eqs. slpicEOMx, slpicEOMv,
 // betaAbrupt), absorbing electrodes with ion-induced secondary emission
 // (Sec. IV), the null-collision test of electrons against the majorant
-// probability (Sec. III), in-place compaction of survivors, and the
+// probability (Sec. III; one Philox2x32-10 draw keyed by (id, step)),
+// in-place compaction of survivors, and the
 // fixed-point deposit of w_p = beta w_j (Eq. Ansatz).
 //
 // Work decomposition.  Every (instance, species) segment is a sequence of
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_push(DeviceRefs r) {
     const float qmdt = S.qmdt, vlim = S.vlim, dtdx = P.dtdx, P0 = P.P0;
     const int N = P.n_cells, shift = P.charge_shift;
     const float* E32 = P.E32;
-    const uint32_t key0 = P.key0, key1 = P.key1, ctr_e = P.ctr_inst * 2u;
+    const uint32_t key2 = P.key2;
     const bool electrons = sp == kElectron;
 
     // ---- 1. advance the thread's slots in place ------------------------------
@@ -298,7 +299,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_push(DeviceRefs r) {
         } else {
           alive = true;
           if (electrons) {
-            const uint4 rr = philox4x32_10(make_uint4(st_id[i], step, ctr_e, 0u), key0, key1);
+            const uint2 rr = philox2x32_10(make_uint2(st_id[i], step), key2);
             event = uniform01(rr.x) < P0;
           }
           // deposit w_p = beta w_j now unless a collision may change v

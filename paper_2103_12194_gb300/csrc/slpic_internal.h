@@ -130,6 +130,7 @@ struct InstDev {
   int tab_nodes;      // real nodes (a padding node follows)
   uint32_t key0, key1;
   uint32_t ctr_inst;  // counter word 2 = ctr_inst * 2 + species
+  uint32_t key2;      // Philox2x32 key of the null-collision draw
   float dtdx;         // dt / dx
   float K_E;          // m_e / (2 e): eV per (m/s)^2
   float ndt;          // n_g dt
@@ -191,8 +192,11 @@ struct ChunkStatus {
   unsigned int pad;
 };
 
-// Tiles per collision chunk (one warp each) and per repacking chunk.
+// Collision chunks: kCollWarps warps of kCollWarpTiles consecutive tiles
+// each; repacking chunks: kMoveChunkTiles tiles.
 constexpr int kCollWarps = 8;
+constexpr int kCollWarpTiles = 8;
+constexpr int kCollChunkTiles = kCollWarps * kCollWarpTiles;
 constexpr int kMoveChunkTiles = 16;
 
 struct DeviceRefs {
@@ -228,5 +232,7 @@ void launch_validate(const SoA& d, uint32_t n, int N, int shift, unsigned int* b
                      unsigned long long* wsum, cudaStream_t s);
 void launch_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, uint32_t* out,
                    long long n, cudaStream_t s);
+void launch_philox2(uint32_t k, const uint32_t* ctr, uint32_t* out, long long n,
+                    cudaStream_t s);
 
 }  // namespace slpic

@@ -96,6 +96,7 @@ def lib():
         "slpic_launch_count": ([vp, ctypes.POINTER(i64)], i32),
         "slpic_read_wait_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
         "slpic_philox": ([i32, u64, vp, i64, vp], i32),
+        "slpic_philox2x32": ([i32, u32, vp, i64, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -124,6 +125,16 @@ def philox(ctr, seed, device=0):
     rc = lib().slpic_philox(device, seed & 0xFFFFFFFFFFFFFFFF, _ptr(ctr), ctr.shape[0], _ptr(out))
     if rc != OK:
         raise SlpicError(rc, "slpic_philox failed")
+    return out
+
+
+def philox2(ctr, key, device=0):
+    """Philox2x32-10 on the device for an (n, 2) uint32 counter array."""
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 2)
+    out = np.empty_like(ctr)
+    rc = lib().slpic_philox2x32(device, key & 0xFFFFFFFF, _ptr(ctr), ctr.shape[0], _ptr(out))
+    if rc != OK:
+        raise SlpicError(rc, "slpic_philox2x32 failed")
     return out
 
 

@@ -33,6 +33,18 @@ def philox(c, key):
     return c
 
 
+def philox2(c, key):
+    """Philox2x32-10 on two 32-bit words with a 32-bit key."""
+    c0, c1 = c
+    k = key & MASK32
+    for r in range(10):
+        if r:
+            k = (k + 0x9E3779B9) & MASK32
+        p = 0xD256D193 * c0
+        c0, c1 = ((p >> 32) ^ c1 ^ k) & MASK32, p & MASK32
+    return [c0, c1]
+
+
 def unif(x):
     return ((x >> 9) + 0.5) / 8388608.0
 
@@ -131,8 +143,11 @@ class ScalarSim:
                     tally["n_abs"][sp][1] += 1
                     continue
                 if sp == 0:
+                    seed = self.s["seed"]
+                    key2 = ((seed & MASK32) ^ (seed >> 32) ^ (0x85EBCA6B * (self.s.get("instance", 0) + 1))) & MASK32
+                    u1 = unif(philox2([ident, stp & MASK32], key2)[0])
                     u = self.draws(ident, stp, 0, 0)
-                    if u[0] < self.P0:
+                    if u1 < self.P0:
                         vl = self.vl[0] if (self.vl[0] > 0 and math.isfinite(self.vl[0])) else math.inf
                         vb = min(min(v1, vl), self.vbcap)
                         eps = 0.5 * ME * v1 * v1 / QE

@@ -82,6 +82,13 @@ def test_philox_bit_exact(slpic, oracle_mod):
         assert np.array_equal(slpic.philox(ctr, seed), oracle_mod.philox(ctr, seed))
 
 
+def test_philox2x32_bit_exact(slpic, oracle_mod):
+    rng = np.random.default_rng(8)
+    ctr = rng.integers(0, 2**32, size=(1 << 20, 2), dtype=np.uint64).astype(np.uint32)
+    for key in (0, 0x85EBCA6B, 0xFFFFFFFF):
+        assert np.array_equal(slpic.philox2(ctr, key), oracle_mod.philox2(ctr, key))
+
+
 # ---------------------------------------------------------------------------
 # Seeding
 # ---------------------------------------------------------------------------

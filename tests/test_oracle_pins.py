@@ -82,6 +82,33 @@ def test_philox_matches_independent_python(oracle_mod):
         assert list(got[i]) == sref.philox([int(c) for c in ctr[i]], seed)
 
 
+def test_philox2x32_matches_independent_python(oracle_mod):
+    rng = np.random.default_rng(2)
+    ctr = rng.integers(0, 2**32, size=(300, 2), dtype=np.uint64).astype(np.uint32)
+    for key in (0, 0x9E3779B9, 0xFFFFFFFF):
+        got = oracle_mod.philox2(ctr, key)
+        for i in range(ctr.shape[0]):
+            assert list(got[i]) == sref.philox2([int(c) for c in ctr[i]], key)
+
+
+def test_philox2x32_statistics(oracle_mod):
+    """The per-step collision draw: uniform, balanced bits, no correlation
+    between consecutive steps of one marker or neighbouring markers."""
+    n = 1 << 18
+    ctr = np.zeros((n, 2), np.uint32)
+    ctr[:, 0] = np.arange(n, dtype=np.uint32) % 512      # marker id
+    ctr[:, 1] = np.arange(n, dtype=np.uint32) // 512     # step
+    out = oracle_mod.philox2(ctr, 12345)[:, 0]
+    hist = np.bincount(out >> 24, minlength=256)
+    assert stats.chisquare(hist).pvalue > 1e-4
+    bits = ((out[:, None] >> np.arange(32, dtype=np.uint32)) & 1).mean(axis=0)
+    assert np.all(np.abs(bits - 0.5) < 5 * 0.5 / math.sqrt(out.size))
+    u = (out >> 9).astype(np.float64)
+    for lag in (1, 512):  # next marker, next step of the same marker
+        r = np.corrcoef(u[:-lag], u[lag:])[0, 1]
+        assert abs(r) < 5 / math.sqrt(u.size)
+
+
 def test_philox_statistics(oracle_mod):
     """Uniformity (chi^2 over 256 bins), per-bit balance, and no correlation
     between neighbouring counters."""
