@@ -15,22 +15,37 @@ namespace {
 constexpr int kFinThreads = 1024;
 constexpr int kMoveThreads = 256;
 
-__device__ __forceinline__ void set_error(Control* ctrl, int code, int inst) {
-  if (atomicCAS(&ctrl->error, 0, code) == 0) ctrl->error_inst = inst;
+__device__ __forceinline__ long long shfl_up(long long v, int o) {
+  return __shfl_up_sync(0xFFFFFFFFu, v, o);
+}
+__device__ __forceinline__ __int128 shfl_up(__int128 v, int o) {
+  const unsigned long long lo = __shfl_up_sync(0xFFFFFFFFu, (unsigned long long)v, o);
+  const long long hi = __shfl_up_sync(0xFFFFFFFFu, (long long)(v >> 64), o);
+  return (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | lo);
 }
 
-// Inclusive block scan (Hillis-Steele over the per-thread chunk sums).
+// Inclusive block scan: shuffle scans within the warps, then one warp scans
+// the 32 warp totals (buf holds 32 entries).  Integer sums, so exact.
 template <typename T>
 __device__ T block_incl_scan(T v, T* buf) {
-  buf[threadIdx.x] = v;
-  __syncthreads();
-  for (int o = 1; o < kFinThreads; o <<= 1) {
-    T add = threadIdx.x >= (unsigned)o ? buf[threadIdx.x - o] : T(0);
-    __syncthreads();
-    buf[threadIdx.x] += add;
-    __syncthreads();
+  static_assert(kFinThreads == 1024, "one warp scans the 32 warp totals");
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    const T y = shfl_up(v, o);
+    if (lane >= o) v += y;
   }
-  T r = buf[threadIdx.x];
+  if (lane == 31) buf[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    T t = buf[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const T y = shfl_up(t, o);
+      if (lane >= o) t += y;
+    }
+    buf[lane] = t;
+  }
+  __syncthreads();
+  const T r = v + (w ? buf[w - 1] : T(0));
   __syncthreads();
   return r;
 }
@@ -71,8 +86,8 @@ __device__ void plan_next(const DeviceRefs& r) {
 
 // mode 0: finish a step and plan the next; mode 1: plan only (one CTA).
 __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode) {
-  __shared__ long long s_i64[kFinThreads];
-  __shared__ __int128 s_i128[kFinThreads];
+  __shared__ long long s_i64[32];
+  __shared__ __int128 s_i128[32];
   __shared__ int s_flag;
   Control* ctrl = r.ctrl;
   if (mode == 1) {
@@ -190,59 +205,71 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode) 
   __syncthreads();
 
   // ---- tallies -------------------------------------------------------------
+  // the accumulators are read by ACC_COUNT threads at once; the record is
+  // assembled in shared memory and added to the totals slot by slot
+  __shared__ unsigned long long s_acc[ACC_COUNT];
+  __shared__ TallyRec s_rec;
+  if (threadIdx.x < ACC_COUNT) {
+    s_acc[threadIdx.x] = a[threadIdx.x];
+    a[threadIdx.x] = 0ull;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
+    const unsigned long long* q = s_acc;
     const double unit = 1.0 / (double)P.wscale;
-    TallyRec t;
+    TallyRec& t = s_rec;
     t.step = is.step;
     t.n_live[0] = r.sstate[inst * 2].n_live;
     t.n_live[1] = r.sstate[inst * 2 + 1].n_live;
     // live weight by its changes: minus what left through the electrodes,
     // plus the births (ionization pairs, emitted electrons)
-    is.w_live[0] = is.w_live[0] - a[ACC_WABS + 0] - a[ACC_WABS + 1] + a[ACC_WIONZ] + a[ACC_WSEE];
-    is.w_live[1] = is.w_live[1] - a[ACC_WABS + 2] - a[ACC_WABS + 3] + a[ACC_WIONZ];
+    is.w_live[0] = is.w_live[0] - q[ACC_WABS + 0] - q[ACC_WABS + 1] + q[ACC_WIONZ] + q[ACC_WSEE];
+    is.w_live[1] = is.w_live[1] - q[ACC_WABS + 2] - q[ACC_WABS + 3] + q[ACC_WIONZ];
     t.w_live[0] = (double)(long long)is.w_live[0] * unit;
     t.w_live[1] = (double)(long long)is.w_live[1] * unit;
-    for (int k = 0; k < 3; ++k) t.n_coll[k] = (long long)a[ACC_COLL0 + k];
-    t.n_candidates = (long long)a[ACC_CAND];
+    for (int k = 0; k < 3; ++k) t.n_coll[k] = (long long)q[ACC_COLL0 + k];
+    t.n_candidates = (long long)q[ACC_CAND];
     for (int s = 0; s < 2; ++s)
       for (int e = 0; e < 2; ++e) {
-        t.n_abs[s][e] = (long long)a[ACC_NABS + 2 * s + e];
-        t.w_abs[s][e] = (double)(long long)a[ACC_WABS + 2 * s + e] * unit;
+        t.n_abs[s][e] = (long long)q[ACC_NABS + 2 * s + e];
+        t.w_abs[s][e] = (double)(long long)q[ACC_WABS + 2 * s + e] * unit;
       }
-    t.n_see = (long long)a[ACC_SEE];
-    t.w_see = (double)(long long)a[ACC_WSEE] * unit;
-    t.w_ionz = (double)(long long)a[ACC_WIONZ] * unit;
-    t.w_cath_ion = (double)(long long)a[ACC_WCATH] * unit;
-    t.w_cath_ion_gen0 = (double)(long long)a[ACC_WCATH0] * unit;
-    t.n_clamp = (long long)a[ACC_CLAMP];
-    t.n_majorant = (long long)a[ACC_MAJ];
-    t.marker_steps = (long long)a[ACC_MSTEPS];
-    P.ring[is.n_steps_done % P.ring_len] = t;
-    TallyRec& T = *P.total;
-    T.step = t.step;
-    T.n_live[0] = t.n_live[0];
-    T.n_live[1] = t.n_live[1];
-    T.w_live[0] = t.w_live[0];
-    T.w_live[1] = t.w_live[1];
-    for (int k = 0; k < 3; ++k) T.n_coll[k] += t.n_coll[k];
-    T.n_candidates += t.n_candidates;
-    for (int s = 0; s < 2; ++s)
-      for (int e = 0; e < 2; ++e) {
-        T.n_abs[s][e] += t.n_abs[s][e];
-        T.w_abs[s][e] += t.w_abs[s][e];
-      }
-    T.n_see += t.n_see;
-    T.w_see += t.w_see;
-    T.w_ionz += t.w_ionz;
-    T.w_cath_ion += t.w_cath_ion;
-    T.w_cath_ion_gen0 += t.w_cath_ion_gen0;
-    T.n_clamp += t.n_clamp;
-    T.n_majorant += t.n_majorant;
-    T.marker_steps += t.marker_steps;
-    for (int k = 0; k < ACC_COUNT; ++k) a[k] = 0ull;
+    t.n_see = (long long)q[ACC_SEE];
+    t.w_see = (double)(long long)q[ACC_WSEE] * unit;
+    t.w_ionz = (double)(long long)q[ACC_WIONZ] * unit;
+    t.w_cath_ion = (double)(long long)q[ACC_WCATH] * unit;
+    t.w_cath_ion_gen0 = (double)(long long)q[ACC_WCATH0] * unit;
+    t.n_clamp = (long long)q[ACC_CLAMP];
+    t.n_majorant = (long long)q[ACC_MAJ];
+    t.marker_steps = (long long)q[ACC_MSTEPS];
     is.step += 1u;
-    is.n_steps_done += 1;
   }
+  __syncthreads();
+  // slot layout of TallyRec (8 bytes each): 0 step, 1-2 n_live, 3-4 w_live,
+  // 5-7 n_coll, 8 n_candidates, 9-12 n_abs, 13-16 w_abs, 17 n_see, 18 w_see,
+  // 19 w_ionz, 20 w_cath_ion, 21 w_cath_ion_gen0, 22 n_clamp, 23 n_majorant,
+  // 24 marker_steps; slots 0-4 are states (replaced), the others sums
+  constexpr int kSlots = (int)(sizeof(TallyRec) / 8);
+  static_assert(kSlots == 25, "TallyRec layout");
+  if (threadIdx.x < kSlots) {
+    const int j = threadIdx.x;
+    const long long* src = reinterpret_cast<const long long*>(&s_rec);
+    long long* ring = reinterpret_cast<long long*>(P.ring + is.n_steps_done % P.ring_len);
+    long long* tot = reinterpret_cast<long long*>(P.total);
+    ring[j] = src[j];
+    const bool is_double = (j >= 3 && j <= 4) || (j >= 13 && j <= 16) || (j >= 18 && j <= 21);
+    if (j <= 4) {
+      tot[j] = src[j];
+    } else if (is_double) {
+      double* td = reinterpret_cast<double*>(tot);
+      const double* sd = reinterpret_cast<const double*>(src);
+      td[j] += sd[j];
+    } else {
+      tot[j] += src[j];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) is.n_steps_done += 1;
 
   // ---- the last CTA plans the next step --------------------------------------
   __threadfence();
