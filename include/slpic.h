@@ -100,7 +100,8 @@ typedef struct {
 int slpic_version(void);
 
 /* Message of the last failed call on ctx (owned by ctx; valid until the next
- * call).  With ctx = NULL: the last failure of slpic_create. */
+ * call).  With ctx = NULL: the last failure of slpic_create or
+ * slpic_philox_static. */
 const char* slpic_last_error(const slpic_ctx* ctx);
 
 /* Create a context on CUDA device `device` with `n_instances` >= 1 instances.
@@ -246,6 +247,39 @@ int slpic_philox(int device, uint64_t seed, const uint32_t* ctr, int64_t n,
  * lo32(seed) ^ hi32(seed) ^ (0x85EBCA6B * (instance + 1)) mod 2^32. */
 int slpic_philox2x32(int device, uint32_t key, const uint32_t* ctr, int64_t n,
                      uint32_t* out);
+
+/* Largest n that slpic_philox_static accepts: its device scratch holds this
+ * many 16-byte counters and as many 16-byte outputs (1 MiB in all). */
+#define SLPIC_PHILOX_STATIC_MAX 32768
+
+/* slpic_philox without any device allocation.  A library utility; the method
+ * has no counterpart.  Same arguments and results as slpic_philox, but the
+ * counters and outputs are staged in one fixed device array that the library
+ * owns (SLPIC_PHILOX_STATIC_MAX counters, reserved when the library is
+ * loaded), so the call makes no cudaMalloc or cudaFree.  It is for callers
+ * that must not allocate device memory at the time of the call: a process
+ * whose memory pool already holds all of the device, or one that checks the
+ * random stream while a simulation runs on another stream of the same device
+ * (the cudaFree in slpic_philox synchronises the whole device and would stall
+ * that stream).
+ *  - n > SLPIC_PHILOX_STATIC_MAX, n < 0 or a NULL array: SLPIC_ERR_INVALID_ARG
+ *    before anything runs; the message is in slpic_last_error(NULL).  CUDA
+ *    failures return SLPIC_ERR_CUDA with the message there too.
+ *  - Nothing in the scratch has to start at zero: each call copies its n
+ *    counters in before the kernel reads them, and copies back only the n
+ *    outputs the kernel has written.
+ *  - There is one scratch array per device in a process: calls that overlap
+ *    on one device (made from several host threads) race on it and return
+ *    wrong words; serialise them.
+ *  - The first call on each device looks up the scratch address
+ *    (cudaGetSymbolAddress, with that device current) and caches it.  As this
+ *    setup happens lazily, make the first call on a device before any stream
+ *    capture begins on it.
+ *  - Like slpic_philox, the call makes `device` current for the calling
+ *    thread and runs on the legacy default stream; it returns when out is
+ *    written. */
+int slpic_philox_static(int device, uint64_t seed, const uint32_t* ctr, int64_t n,
+                        uint32_t* out);
 
 #ifdef __cplusplus
 }

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1148,3 +1149,60 @@ int slpic_philox(int device, uint64_t seed, const uint32_t* ctr, int64_t n, uint
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// slpic_philox_static: the Philox self-check without device allocation.  The
+// counters (first half) and the outputs (second half) live in one file-scope
+// device array of the module, whose address is looked up once per device.
+// Callers that cannot allocate: a process whose memory pool already holds the
+// whole device, or one checking the random stream while a simulation runs on
+// another stream (cudaFree would synchronise the device under it).
+
+static __device__ __align__(256) uint32_t g_philox_scratch[2 * 4 * SLPIC_PHILOX_STATIC_MAX];
+
+namespace {
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_scratch_mu;
+uint32_t* g_scratch_ptr[kStaticMaxDevices];
+}  // namespace
+
+extern "C" int slpic_philox_static(int device, uint64_t seed, const uint32_t* ctr, int64_t n,
+                                   uint32_t* out) {
+  if (!ctr || !out || n < 0)
+    return fail(nullptr, SLPIC_ERR_INVALID_ARG, "slpic_philox_static: NULL array or n < 0");
+  if (n > SLPIC_PHILOX_STATIC_MAX)
+    return fail(nullptr, SLPIC_ERR_INVALID_ARG,
+                "slpic_philox_static: n = %lld counters exceeds SLPIC_PHILOX_STATIC_MAX = %d "
+                "(the size of its fixed scratch); use slpic_philox or split the call",
+                (long long)n, SLPIC_PHILOX_STATIC_MAX);
+  if (device < 0 || device >= kStaticMaxDevices)
+    return fail(nullptr, SLPIC_ERR_INVALID_ARG, "slpic_philox_static: device %d out of range",
+                device);
+  if (n == 0) return SLPIC_OK;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "slpic_philox_static: cudaSetDevice");
+  uint32_t* scratch = nullptr;
+  {
+    // once per device, with that device current; later calls reuse it
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[device]) {
+      uint32_t* p = nullptr;
+      e = cudaGetSymbolAddress((void**)&p, g_philox_scratch);
+      if (e != cudaSuccess)
+        return cuda_fail(nullptr, e, "slpic_philox_static: cudaGetSymbolAddress");
+      g_scratch_ptr[device] = p;
+    }
+    scratch = g_scratch_ptr[device];
+  }
+  uint32_t* dctr = scratch;
+  uint32_t* dout = scratch + 4 * (size_t)SLPIC_PHILOX_STATIC_MAX;
+  const size_t b = (size_t)n * 16;
+  e = cudaMemcpy(dctr, ctr, b, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "slpic_philox_static: counters to device");
+  launch_philox((uint32_t)seed, (uint32_t)(seed >> 32), dctr, dout, n, 0);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "slpic_philox_static: launch");
+  e = cudaMemcpy(out, dout, b, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "slpic_philox_static: outputs to host");
+  return SLPIC_OK;
+}

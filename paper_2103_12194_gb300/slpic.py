@@ -16,6 +16,7 @@ OK = 0
 ERR_INVALID_ARG, ERR_STATE, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERIC = -1, -2, -3, -4, -5, -6
 ELECTRON, ION = 0, 1
 FIELD_FROZEN, FIELD_POISSON = 0, 1
+PHILOX_STATIC_MAX = 32768  # SLPIC_PHILOX_STATIC_MAX
 SEED_CATHODE, SEED_REST, SEED_GAP, SEED_THERMAL = 0, 1, 2, 3
 
 _ERRNAMES = {ERR_INVALID_ARG: "INVALID_ARG", ERR_STATE: "STATE", ERR_CAPACITY: "CAPACITY",
@@ -97,6 +98,7 @@ def lib():
         "slpic_read_wait_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
         "slpic_philox": ([i32, u64, vp, i64, vp], i32),
         "slpic_philox2x32": ([i32, u32, vp, i64, vp], i32),
+        "slpic_philox_static": ([i32, u64, vp, i64, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -125,6 +127,19 @@ def philox(ctr, seed, device=0):
     rc = lib().slpic_philox(device, seed & 0xFFFFFFFFFFFFFFFF, _ptr(ctr), ctr.shape[0], _ptr(out))
     if rc != OK:
         raise SlpicError(rc, "slpic_philox failed")
+    return out
+
+
+def philox_static(ctr, seed, device=0):
+    """slpic_philox_static: Philox4x32-10 on the device for an (n, 4) uint32
+    counter array, staged in the library's fixed device scratch (no device
+    allocation; n <= PHILOX_STATIC_MAX; calls on one device must not overlap)."""
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    out = np.empty_like(ctr)
+    L = lib()
+    rc = L.slpic_philox_static(device, seed & 0xFFFFFFFFFFFFFFFF, _ptr(ctr), ctr.shape[0], _ptr(out))
+    if rc != OK:
+        raise SlpicError(rc, L.slpic_last_error(None).decode())
     return out
 
 
