@@ -33,7 +33,7 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--markers", type=int, default=32_000_000)
@@ -65,16 +65,23 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def push_source_hash():
+    """Hash of the particle kernel's sources (the kernel and its headers)."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2103_12194_gb300", "csrc")
+    for name in ("push.cu", "device_common.cuh", "slpic_internal.h"):
+        h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def push_traffic():
     """DRAM bytes per marker of the particle kernel from the committed ncu
     summary, if it was taken on the current kernel source."""
-    src = os.path.join(ROOT, "paper_2103_12194_gb300", "csrc", "push.cu")
     path = os.path.join(ROOT, "profiles", "push_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if d.get("push_cu_sha256_16") == h:
+        if d.get("push_source_sha256_16") == push_source_hash():
             return float(d["dram_bytes_per_marker"])
     except Exception:
         pass
@@ -94,7 +101,7 @@ class ClockSampler:
                  "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -146,7 +153,7 @@ def cpu_baseline(spec, n_markers, seconds):
     o.step(1)
     t1 = time.perf_counter()
     per_step = max(t1 - t0, 1e-6)
-    k = max(1, min(200, int(seconds / per_step)))
+    k = max(1, min(5000, int(seconds / per_step)))
     t0 = time.perf_counter()
     o.step(k)
     dt = time.perf_counter() - t0
@@ -193,8 +200,8 @@ def run_ours(args):
     spec, run = inputs.microbench_config(n_markers=args.markers, seed=rank)
     spec["instance"] = 0
     n = args.markers
-    cap_e = int(n * 1.25)
-    cap_i = max(1 << 20, n // 4)
+    cap_e = 4 * n  # the avalanche grows the electrons over 1000 steps
+    cap_i = 3 * n
 
     def barrier():
         if world > 1:
@@ -303,6 +310,7 @@ def run_ours(args):
             "config": {"workload": "push+MCC microbenchmark gap: 3.2e7 electrons log-uniform "
                                    "0.1-200 eV, 4096 cells, 1 Torr, 300 V, Poisson on",
                        "markers": n, "cells": spec["n_cells"], "instances_per_gpu": 1,
+                       "live_at_end": [int(x) for x in t_after["n_live"]],
                        "parallelism": "independent instance per GPU" if world > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (%.2f GB of markers > %.0f MB)"
                              % (state_bytes / 1e9, L2_BYTES / 2**20)},
