@@ -136,7 +136,7 @@ int slpic_set_cross_sections(slpic_ctx* ctx, int inst, int lo_exp2,
                              const float* sig_io, double e_io);
 /* Species: mass [kg], charge [C], speed limit v_lim [m/s] of Eq. betaAbrupt
  * (beta = min(1, v_lim/|v|); v_lim <= 0 or +inf gives beta = 1, i.e. PIC),
- * capacity = maximum live markers (rounded up to whole tiles of 1024 markers,
+ * capacity = maximum live markers (rounded up to whole tiles of 128 markers,
  * plus one tile).  Only electrons collide (Sec. IV). */
 int slpic_set_species(slpic_ctx* ctx, int inst, int species, double mass,
                       double charge, double v_lim, int64_t capacity);

@@ -380,7 +380,7 @@ int commit(slpic_ctx* c) {
                  ((sizeof(InstState) * c->n_inst + 255) & ~size_t(255)) +
                  ((sizeof(SpeciesState) * nseg + 255) & ~size_t(255)) +
                  ((sizeof(Transfer) * nseg + 255) & ~size_t(255)) + 256 +
-                 3 * ((4 * (nseg + 1) + 255) & ~size_t(255)) + 256 +
+                 4 * ((4 * (nseg + 1) + 255) & ~size_t(255)) + 256 +
                  ((sizeof(ChunkStatus) * coll_chunks + 255) & ~size_t(255)) +
                  ((sizeof(ChunkStatus) * move_chunks + 255) & ~size_t(255));
   if (int rc = dmalloc(c, &blk, bytes, "control")) return rc;
@@ -393,6 +393,7 @@ int commit(slpic_ctx* c) {
   c->d_ctrl = carve<Control>(p, 1);
   c->d_seg = carve<unsigned int>(p, nseg + 1);
   c->d_scratch = carve<unsigned int>(p, 4);
+  c->refs.seg_wstart = carve<unsigned int>(p, nseg + 1);
   c->refs.coll_start = carve<unsigned int>(p, nseg + 1);
   c->refs.move_start = carve<unsigned int>(p, nseg + 1);
   c->refs.coll_scan = carve<ChunkStatus>(p, coll_chunks);
@@ -405,17 +406,19 @@ int commit(slpic_ctx* c) {
   c->refs.seg_start = c->d_seg;
   c->refs.n_inst = c->n_inst;
   // the whole charge grid of the largest instance goes to shared memory when
-  // it fits next to the two marker stages; otherwise deposits use global atomics
+  // it fits next to the warps' marker stages (with at least 4 warps per CTA);
+  // otherwise deposits use global atomics
   int smem_nodes = max_nodes <= 16385 ? max_nodes : 0;
-  int bps = 0;
+  int bps = 0, warps = 0;
   size_t sbytes = 0;
-  int e = push_occupancy(smem_nodes, &bps, &sbytes);
+  int e = push_config(smem_nodes, &warps, &bps, &sbytes);
   if (e != 0 || bps == 0) {
     smem_nodes = 0;
-    e = push_occupancy(0, &bps, &sbytes);
+    e = push_config(0, &warps, &bps, &sbytes);
     if (e != 0 || bps == 0) return fail(c, SLPIC_ERR_CUDA, "particle kernel cannot be launched");
   }
   c->refs.smem_nodes = smem_nodes;
+  c->refs.push_warps = warps;
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device), "attributes");
   c->blocks_per_sm = bps;

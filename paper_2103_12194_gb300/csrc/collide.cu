@@ -10,8 +10,9 @@
 // weight.  Each candidate is then deposited with its new density weight.
 //
 // Work: chunks of kCollChunkTiles consecutive tiles (each warp kCollWarpTiles
-// of them, one lane per candidate), handed out in order (electron tiles of an
-// instance, then its ion tiles).  The births of a chunk (ionizations; for ion chunks the
+// of them; the warp numbers the candidates of its tiles in (tile, slot) order
+// and takes them 32 at a time, one lane each), handed out in order (electron
+// tiles of an instance, then its ion tiles).  The births of a chunk (ionizations; for ion chunks the
 // electrons the particle kernel staged for emission) get their slots from an
 // ordered scan over the chunks (decoupled look-back), so they are appended
 // after the last live marker in (tile, slot) order -- ionization electrons
@@ -255,66 +256,83 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
     const unsigned int e_chunks = (se.n_tiles + kCollChunkTiles - 1) / kCollChunkTiles;
     const bool ion_chunk = local >= e_chunks;
     const uint32_t nt = ion_chunk ? si.n_tiles : se.n_tiles;
-    // this warp's tiles: kCollWarpTiles consecutive ones
+    // this warp's tiles: kCollWarpTiles consecutive ones, tile kw + j at lane j
     const uint32_t kw = (ion_chunk ? local - e_chunks : local) * kCollChunkTiles +
                         warp * kCollWarpTiles;
     const SoA me = E.buf[se.cur];
     const float kv = E.K_V, vlim = E.vlim;
-
-    // ---- pass 1: scatter this warp's candidates, count births per tile -------
-    uint32_t tile_births = 0;  // lane j: births of tile kw + j
-    for (int j = 0; j < kCollWarpTiles; ++j) {
-      const uint32_t k = kw + j;
-      if (k >= nt) break;
-      const size_t base = (size_t)k * kTile;
-      uint32_t births = 0;
-      if (!ion_chunk) {
-        const uint32_t nc = E.n_cand[k];
-        for (uint32_t c0 = 0; c0 < nc; c0 += 32) {
-          const uint32_t q = c0 + lane;
-          bool ionized = false;
-          if (q < nc) {
-            const uint32_t a = E.cand[base + q];
-            const size_t o = base + a;
-            const int cell = me.cell[o];
-            const float off = me.off[o], wj = me.wj[o];
-            const uint32_t id = me.id[o];
-            float vx = me.vx[o], vy = me.vy[o], vz = me.vz[o];
-            const float s1 = vx * vx + vy * vy + vz * vz;
-            const float v1 = sqrtf(s1);
-            const uint4 rr =
-                philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u, 0u), P.key0, P.key1);
-            int proc;
-            float es = 0.0f;
-            const Velocity nv =
-                collide(P, kv, vlim, vx, vy, vz, v1, s1, rr, id, step, wj, s_acc, &es, &proc);
-            if (proc < 3) {
-              vx = nv.vx;
-              vy = nv.vy;
-              vz = nv.vz;
-              me.vx[o] = vx;
-              me.vy[o] = vy;
-              me.vz[o] = vz;
-              if (proc == 2) {
-                ionized = true;
-                E.cand[base + q] = (uint16_t)(a | 0x8000u);  // mark for pass 2
-                E.esec[base + q] = es;
-              }
-            }
-            deposit(P.rho_acc[kElectron], cell, off,
-                    fixed_charge(beta_of(sqrtf(vx * vx + vy * vy + vz * vz), vlim) * wj,
-                                 P.charge_shift));
-          }
-          births += __popc(__ballot_sync(0xFFFFFFFFu, ionized));
-        }
-      } else {
-        births = I.births[k];
-      }
-      if (lane == j) tile_births = births;
-    }
-    uint32_t warp_births = tile_births;
+    // events of the tiles (electron chunks: queued candidates; ion chunks:
+    // electrons emitted at the cathode) and their exclusive prefix: the
+    // warp's events are numbered in (tile, slot) order
+    uint32_t cnt = 0;
+    if (lane < kCollWarpTiles && kw + lane < nt) cnt = ion_chunk ? I.births[kw + lane] : E.n_cand[kw + lane];
+    uint32_t excl = cnt;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) warp_births += __shfl_xor_sync(0xFFFFFFFFu, warp_births, o);
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t n = __shfl_up_sync(0xFFFFFFFFu, excl, o);
+      if (lane >= o) excl += n;
+    }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, excl, 31);
+    excl -= cnt;
+    // tile (lane index j) and rank inside it of the warp's event number e < total:
+    // the last tile whose prefix is <= e (that tile has events)
+    auto locate_event = [&](uint32_t e, uint32_t& q) -> int {
+      int j = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t v = __shfl_sync(0xFFFFFFFFu, excl, j + step);
+        if (v <= e) j += step;
+      }
+      q = e - __shfl_sync(0xFFFFFFFFu, excl, j);
+      return j;
+    };
+
+    // ---- pass 1: scatter this warp's candidates, count the births ------------
+    uint32_t warp_births = 0;
+    if (!ion_chunk) {
+      for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+        const uint32_t ce = c0 + lane;
+        uint32_t q;
+        const int j = locate_event(ce < total ? ce : total - 1, q);
+        bool ionized = false;
+        if (ce < total) {
+          const size_t base = (size_t)(kw + j) * kTile;
+          const uint32_t a = E.cand[base + q];
+          const size_t o = base + a;
+          const int cell = me.cell[o];
+          const float off = me.off[o], wj = me.wj[o];
+          const uint32_t id = me.id[o];
+          float vx = me.vx[o], vy = me.vy[o], vz = me.vz[o];
+          const float s1 = vx * vx + vy * vy + vz * vz;
+          const float v1 = sqrtf(s1);
+          const uint4 rr =
+              philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u, 0u), P.key0, P.key1);
+          int proc;
+          float es = 0.0f;
+          const Velocity nv =
+              collide(P, kv, vlim, vx, vy, vz, v1, s1, rr, id, step, wj, s_acc, &es, &proc);
+          if (proc < 3) {
+            vx = nv.vx;
+            vy = nv.vy;
+            vz = nv.vz;
+            me.vx[o] = vx;
+            me.vy[o] = vy;
+            me.vz[o] = vz;
+            if (proc == 2) {
+              ionized = true;
+              E.cand[base + q] = (uint16_t)(a | 0x8000u);  // mark for pass 2
+              E.esec[base + q] = es;
+            }
+          }
+          deposit(P.rho_acc[kElectron], cell, off,
+                  fixed_charge(beta_of(sqrtf(vx * vx + vy * vy + vz * vz), vlim) * wj,
+                               P.charge_shift));
+        }
+        warp_births += __popc(__ballot_sync(0xFFFFFFFFu, ionized));
+      }
+    } else {
+      warp_births = total;
+    }
     if (lane == 0) s_births[warp] = warp_births;
     __syncthreads();
 
@@ -334,56 +352,46 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
       const uint32_t app_e = tail_slot(E, se), app_i = tail_slot(I, si);
       const uint32_t cap_e = E.cap_tiles * (uint32_t)kTile, cap_i = I.cap_tiles * (uint32_t)kTile;
       const SoA mi = I.buf[si.cur];
-      // exclusive prefix of the per-tile counts over the warp's tiles
-      uint32_t tile_off = tile_births;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t n = __shfl_up_sync(0xFFFFFFFFu, tile_off, o);
-        if (lane >= o) tile_off += n;
-      }
-      tile_off -= tile_births;
-      for (int j = 0; j < kCollWarpTiles; ++j) {
-        const uint32_t k = kw + j;
-        if (k >= nt) break;
-        const uint32_t births = __shfl_sync(0xFFFFFFFFu, tile_births, j);
-        if (!births) continue;
-        const uint32_t off_t = off_w + __shfl_sync(0xFFFFFFFFu, tile_off, j);
-        const size_t base = (size_t)k * kTile;
-        if (!ion_chunk) {
-          const uint32_t nc = E.n_cand[k];
-          uint32_t ranked = 0;
-          for (uint32_t c0 = 0; c0 < nc; c0 += 32) {
-            const uint32_t q = c0 + lane;
-            const uint32_t a = q < nc ? E.cand[base + q] : 0u;
-            const bool ionized = q < nc && (a & 0x8000u);
-            const uint32_t b = __ballot_sync(0xFFFFFFFFu, ionized);
-            if (ionized) {
-              const uint32_t rank = off_t + ranked + __popc(b & lanemask_lt);
-              const size_t o = base + (a & 0x7FFFu);
-              const uint32_t pe = app_e + rank, pi = app_i + rank;
-              if (pe >= cap_e || pi >= cap_i) {
-                atomicCAS(&ctrl->error, 0, kErrCapacity);
-              } else {
-                born_pair(P, me, mi, pe, pi, me.cell[o], me.off[o], me.wj[o], me.id[o], step,
-                          E.esec[base + q], se.next_id + rank, si.next_id + rank);
-              }
-            }
-            ranked += __popc(b);
-          }
-        } else {
-          // electrons emitted at the cathode, after every ionization electron
-          const SoA& sb = E.stage_b;
-          for (uint32_t q = lane; q < births; q += 32) {
-            const uint32_t rank = off_t + q;
-            const uint32_t pe = app_e + rank;
-            if (pe >= cap_e) {
+      if (!ion_chunk) {
+        uint32_t ranked = 0;
+        for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+          const uint32_t ce = c0 + lane;
+          uint32_t q;
+          const int j = locate_event(ce < total ? ce : total - 1, q);
+          const size_t base = (size_t)(kw + j) * kTile;
+          const uint32_t a = ce < total ? E.cand[base + q] : 0u;
+          const bool ionized = ce < total && (a & 0x8000u);
+          const uint32_t b = __ballot_sync(0xFFFFFFFFu, ionized);
+          if (ionized) {
+            const uint32_t rank = off_w + ranked + __popc(b & lanemask_lt);
+            const size_t o = base + (a & 0x7FFFu);
+            const uint32_t pe = app_e + rank, pi = app_i + rank;
+            if (pe >= cap_e || pi >= cap_i) {
               atomicCAS(&ctrl->error, 0, kErrCapacity);
-              continue;
+            } else {
+              born_pair(P, me, mi, pe, pi, me.cell[o], me.off[o], me.wj[o], me.id[o], step,
+                        E.esec[base + q], se.next_id + rank, si.next_id + rank);
             }
-            const size_t o = base + q;
-            write_marker(me, pe, sb.cell[o], sb.off[o], sb.vx[o], sb.vy[o], sb.vz[o], sb.wj[o],
-                         kGenBit | ((se.next_id + rank) & kSerialMask));
           }
+          ranked += __popc(b);
+        }
+      } else {
+        // electrons emitted at the cathode, after every ionization electron
+        const SoA& sb = E.stage_b;
+        for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+          const uint32_t ce = c0 + lane;
+          uint32_t q;
+          const int j = locate_event(ce < total ? ce : total - 1, q);
+          if (ce >= total) continue;
+          const uint32_t rank = off_w + ce;
+          const uint32_t pe = app_e + rank;
+          if (pe >= cap_e) {
+            atomicCAS(&ctrl->error, 0, kErrCapacity);
+            continue;
+          }
+          const size_t o = (size_t)(kw + j) * kTile + q;
+          write_marker(me, pe, sb.cell[o], sb.off[o], sb.vx[o], sb.vy[o], sb.vz[o], sb.wj[o],
+                       kGenBit | ((se.next_id + rank) & kSerialMask));
         }
       }
     }
@@ -399,5 +407,6 @@ void launch_collide(const DeviceRefs& r, int grid, cudaStream_t s) {
 
 static_assert(kCollThreads == 32 * kCollWarps, "kCollWarps warps per chunk");
 static_assert(kCollWarpTiles <= 32, "per-tile counts live one per lane");
+static_assert(kTile <= 0x8000, "candidate slots leave the top bit for the ionization mark");
 
 }  // namespace slpic

@@ -126,6 +126,13 @@ __device__ __forceinline__ long long fixed_charge(float w, int shift) {
   return (long long)(q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u));
 }
 
+// The same value as fixed_charge(w, shift) from the hardware conversion, for
+// wscale = 2^shift: w * 2^shift is exact in float (a power-of-two scaling that
+// stays in range), and cvt.rni rounds it to the nearest integer, ties to even.
+__device__ __forceinline__ long long fixed_charge_scaled(float w, float wscale) {
+  return __float2ll_rn(w * wscale);
+}
+
 // Split a fixed-point charge between the two nodes of the marker's cell with
 // 24-bit linear weights: the right node gets floor(Q f / 2^24),
 // f = trunc(offset 2^24).

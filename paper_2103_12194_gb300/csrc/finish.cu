@@ -51,13 +51,18 @@ __device__ T block_incl_scan(T v, T* buf) {
 }
 
 // Plan the next step from the tiles in use (one thread): particle-kernel
-// tiles per segment, collision chunks per instance, repacking chunks.
+// super-tiles (push_warps tiles each) and their weights per segment,
+// collision chunks per instance, repacking chunks.
 __device__ void plan_next(const DeviceRefs& r) {
   const int n_seg = r.n_inst * 2;
-  unsigned int start = 0, coll = 0, move = 0;
+  const unsigned int W = (unsigned int)r.push_warps;
+  unsigned int start = 0, wstart = 0, coll = 0, move = 0;
   for (int s = 0; s < n_seg; ++s) {
     r.seg_start[s] = start;
-    start += r.sstate[s].n_tiles;
+    r.seg_wstart[s] = wstart;
+    const unsigned int ns = (r.sstate[s].n_tiles + W - 1) / W;
+    start += ns;
+    wstart += ns * ((s & 1) ? kWeightIon : kWeightElectron);
   }
   for (int i = 0; i < r.n_inst; ++i) {
     r.coll_start[i] = coll;
@@ -70,9 +75,11 @@ __device__ void plan_next(const DeviceRefs& r) {
     if (x.compact) move += (x.n_tiles_old + kMoveChunkTiles - 1) / kMoveChunkTiles;
   }
   r.seg_start[n_seg] = start;
+  r.seg_wstart[n_seg] = wstart;
   r.coll_start[r.n_inst] = coll;
   r.move_start[n_seg] = move;
-  r.ctrl->n_tiles = start;
+  r.ctrl->n_super = start;
+  r.ctrl->w_total = wstart;
   r.ctrl->n_seg = n_seg;
   r.ctrl->n_coll_chunks = coll;
   r.ctrl->coll_counter = 0;
@@ -301,12 +308,14 @@ __global__ void __launch_bounds__(kMoveThreads) k_move(DeviceRefs r) {
   __shared__ uint32_t s_fill[kMoveChunkTiles];
   __shared__ uint32_t s_pre[kMoveChunkTiles];
   __shared__ unsigned int s_chunk;
+  constexpr int kPerLaneTiles = kMoveChunkTiles / 32;
   Control* ctrl = r.ctrl;
   if (*((volatile int*)&ctrl->error)) return;
   const unsigned int n_chunks = ctrl->n_move_chunks;
   if (n_chunks == 0) return;
   const unsigned int epoch = ctrl->epoch;
   const int n_seg = r.n_inst * 2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (;;) {
     if (threadIdx.x == 0) s_chunk = atomicAdd(&ctrl->move_counter, 1u);
     __syncthreads();
@@ -326,29 +335,35 @@ __global__ void __launch_bounds__(kMoveThreads) k_move(DeviceRefs r) {
     const SpeciesDev& S = r.inst[seg >> 1].sp[seg & 1];
     const unsigned int first = r.move_start[seg];
     const uint32_t k0 = (c - first) * kMoveChunkTiles;
-    if (threadIdx.x < kMoveChunkTiles) {
-      const uint32_t k = k0 + threadIdx.x;
-      s_fill[threadIdx.x] = k < x.n_tiles_old ? S.fill[x.src][k] : 0u;
+    for (int j = threadIdx.x; j < kMoveChunkTiles; j += kMoveThreads) {
+      const uint32_t k = k0 + j;
+      s_fill[j] = k < x.n_tiles_old ? S.fill[x.src][k] : 0u;
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
-      uint32_t agg = 0;
-      for (int j = 0; j < kMoveChunkTiles; ++j) agg += s_fill[j];
+    if (warp == 0) {
+      // lane l sums tiles l * kPerLaneTiles ..; scan over the lanes
+      uint32_t loc = 0;
+      for (int j = 0; j < kPerLaneTiles; ++j) loc += s_fill[lane * kPerLaneTiles + j];
+      uint32_t inc = loc;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t n = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += n;
+      }
+      const uint32_t agg = __shfl_sync(0xFFFFFFFFu, inc, 31);
       const uint32_t excl = chunk_lookback(r.move_scan, c, first, agg, epoch, ctrl);
-      if (threadIdx.x == 0) {
-        uint32_t run = excl;
-        for (int j = 0; j < kMoveChunkTiles; ++j) {
-          s_pre[j] = run;
-          run += s_fill[j];
-        }
+      uint32_t run = excl + inc - loc;
+      for (int j = 0; j < kPerLaneTiles; ++j) {
+        s_pre[lane * kPerLaneTiles + j] = run;
+        run += s_fill[lane * kPerLaneTiles + j];
       }
     }
     __syncthreads();
+    // one warp per tile, in order of the tiles
     const SoA src = S.buf[x.src], dst = S.buf[x.dst];
-    for (int j = 0; j < kMoveChunkTiles; ++j) {
+    for (int j = warp; j < kMoveChunkTiles; j += kMoveThreads / 32) {
       const uint32_t n = s_fill[j];
       const size_t from = (size_t)(k0 + j) * kTile, to = s_pre[j];
-      for (uint32_t i = threadIdx.x; i < n; i += kMoveThreads) {
+      for (uint32_t i = lane; i < n; i += 32) {
         dst.cell[to + i] = src.cell[from + i];
         dst.off[to + i] = src.off[from + i];
         dst.vx[to + i] = src.vx[from + i];
@@ -360,8 +375,8 @@ __global__ void __launch_bounds__(kMoveThreads) k_move(DeviceRefs r) {
     }
     // fills of the repacked store: full tiles, the last one partial
     const uint32_t nt_new = (x.n_new + kTile - 1) / kTile;
-    if (threadIdx.x < kMoveChunkTiles) {
-      const uint32_t k = k0 + threadIdx.x;
+    for (int j = threadIdx.x; j < kMoveChunkTiles; j += kMoveThreads) {
+      const uint32_t k = k0 + j;
       if (k < nt_new) S.fill[x.dst][k] = min(x.n_new - k * (uint32_t)kTile, (uint32_t)kTile);
     }
     __syncthreads();

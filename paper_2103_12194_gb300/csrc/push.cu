@@ -3,30 +3,34 @@
 // betaAbrupt), absorbing electrodes with ion-induced secondary emission
 // (Sec. IV), the null-collision test of electrons against the majorant
 // probability (Sec. III; one Philox2x32-10 draw keyed by (id, step)),
-// in-place compaction of survivors, and the
-// fixed-point deposit of w_p = beta w_j (Eq. Ansatz).
+// in-place compaction of survivors, and the fixed-point deposit of
+// w_p = beta w_j (Eq. Ansatz).
 //
 // Work decomposition.  Every (instance, species) segment is a sequence of
-// tiles of kTile marker slots (tile k holds fill[k] markers).  A persistent
-// grid takes the tiles round-robin (CTA c: tiles c, c + G, c + 2G, ...);
-// tiles are independent, so no CTA ever waits for another.  Per CTA the tiles
-// go through a two-stage shared-memory pipeline:
-//   - bulk asynchronous copies (TMA, cp.async.bulk) bring the seven SoA
-//     streams of the next tile into one stage while the current tile is
-//     advanced in the other;
-//   - each thread advances the markers of slots t and t + kThreads in place
-//     in the stage and deposits the survivors into a shared-memory copy of the
-//     segment's charge grid (integer atomics);
-//   - warp ballots and one scan over the warps rank survivors and events
-//     (ion emissions, electron collision candidates); when a marker left the
-//     tile the survivors are compacted in order; the fields that changed are
-//     stored to the tile's own slots with bulk copies.
+// tiles of kTile = 128 marker slots (tile k holds fill[k] markers), and every
+// tile belongs to one warp: no block-wide barrier is needed to advance,
+// rank, compact and store it.
+//   - A CTA of W warps takes super-tiles of W consecutive tiles of one
+//     segment (warp w: tile w of each); the CTAs split the super-tiles into
+//     contiguous ranges of equal weight, so a CTA deposits into few segments.
+//   - Each warp streams its tiles through three shared-memory stages: lane 0
+//     starts the bulk asynchronous copies (TMA, cp.async.bulk) of the seven
+//     SoA streams of the tile two rounds ahead while the warp advances the
+//     current one, so two tiles per warp are in flight.
+//   - Lane l advances slots l, l + 32, l + 64, l + 96 (read into registers)
+//     and deposits the survivors into a shared-memory copy of the segment's
+//     charge grid (integer atomics).
+//   - Ballots rank survivors and events (ion emissions, electron collision
+//     candidates); the survivors go back to the stage, compacted in order
+//     when a marker left the tile, and lane 0 stores the fields that changed
+//     to the tile's own slots with bulk copies.
 // Collision candidates (the electrons that drew u < P0) are not scattered
 // here: their final slots are queued per tile and k_collide scatters them
 // all at once, so the long, rare scattering path never stalls the stream.
 // The shared charge grid is added to global memory with integer atomics when
-// the CTA moves to another segment or finishes, so the deposit is exact and
-// independent of the order of the additions.
+// the CTA moves to another segment (a CTA-wide barrier, taken by all warps at
+// the same round) or finishes, so the deposit is exact and independent of the
+// order of the additions.
 #include "device_common.cuh"
 #include "slpic_internal.h"
 
@@ -34,22 +38,17 @@ namespace slpic {
 
 namespace {
 
-constexpr int kWarps = kThreads / 32;
-
-struct TileInfo {
-  unsigned int g;     // global tile index (>= n_tiles: none)
-  int seg;            // segment = instance * 2 + species
-  unsigned int k;     // tile inside the segment
-  unsigned int fill;  // live markers in the tile
+// Tile of a warp in one round: the super-tile's segment (CTA-uniform) and,
+// when the warp has a tile there, its index and fill.
+struct WarpTile {
+  int sseg;       // segment of the super-tile
+  bool valid;     // the warp has a tile in it
+  uint32_t k;     // tile inside the segment
+  uint32_t fill;  // live markers in the tile
 };
 
-struct CtaShared {
-  unsigned long long warp_cnt[kWarps];  // packed counts per warp (16-bit fields)
-  unsigned long long warp_pre[kWarps];  // their exclusive prefix over warps
-  unsigned long long tot;               // their totals
+struct PushShared {
   unsigned long long s_acc[ACC_COUNT];
-  uint64_t bar[2];
-  TileInfo cur;
   int abort;
 };
 
@@ -57,8 +56,10 @@ __device__ __forceinline__ void set_error(Control* ctrl, int code) {
   atomicCAS(&ctrl->error, 0, code);
 }
 
+// Add the CTA's shared charge grid and accumulators of segment seg to global
+// memory and clear them (all threads; barriers before and after).
 __device__ __forceinline__ void flush_segment(const DeviceRefs& r, int seg,
-                                              unsigned long long* s_rho, CtaShared& cs,
+                                              unsigned long long* s_rho, PushShared& cs,
                                               bool use_smem) {
   const int inst = seg >> 1, sp = seg & 1;
   const InstDev& P = r.inst[inst];
@@ -66,7 +67,7 @@ __device__ __forceinline__ void flush_segment(const DeviceRefs& r, int seg,
   if (use_smem) {
     const int nn = P.n_cells + 1;
     unsigned long long* g = P.rho_acc[sp];
-    for (int k = threadIdx.x; k < nn; k += kThreads) {
+    for (int k = threadIdx.x; k < nn; k += blockDim.x) {
       const unsigned long long v = s_rho[k];
       if (v) {
         atomicAdd(g + k, v);
@@ -84,42 +85,48 @@ __device__ __forceinline__ void flush_segment(const DeviceRefs& r, int seg,
   __syncthreads();
 }
 
-__device__ __forceinline__ void deposit(unsigned long long* rho, int cell, float off,
-                                        long long Q) {
-  const long long right = right_share(Q, off);
-  const long long left = Q - right;
-  if (left) atomicAdd(rho + cell, (unsigned long long)left);
-  if (right) atomicAdd(rho + cell + 1, (unsigned long long)right);
+// Segment of super-tile q (q < n_super): the last segment starting at or
+// before q.
+__device__ __forceinline__ int segment_of(const DeviceRefs& r, unsigned int q) {
+  int lo = 0, hi = r.n_inst * 2 - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (r.seg_start[mid] <= q) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
 }
 
-// Segment and tile of global tile g (g < n_tiles) and its fill.
-__device__ __forceinline__ TileInfo locate(const DeviceRefs& r, unsigned int n_tiles,
-                                           unsigned int g) {
-  TileInfo t;
-  t.g = g;
-  t.seg = -1;
-  t.k = 0;
-  t.fill = 0;
-  if (g < n_tiles) {
-    int lo = 0, hi = r.n_inst * 2 - 1;  // last segment with seg_start <= g
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (r.seg_start[mid] <= g) lo = mid;
-      else hi = mid - 1;
-    }
-    t.seg = lo;
-    t.k = g - r.seg_start[lo];
-    t.fill = r.inst[lo >> 1].sp[lo & 1].fill[r.sstate[lo].cur][t.k];
+// First super-tile whose weighted start is at or after `target`.
+__device__ __forceinline__ unsigned int first_super(const DeviceRefs& r, unsigned int target) {
+  const int n_seg = r.n_inst * 2;
+  if (target >= r.seg_wstart[n_seg]) return r.seg_start[n_seg];
+  int lo = 0, hi = n_seg - 1;  // last segment with weighted start <= target
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (r.seg_wstart[mid] <= target) lo = mid;
+    else hi = mid - 1;
   }
+  const unsigned int w = (lo & 1) ? kWeightIon : kWeightElectron;
+  const unsigned int q = r.seg_start[lo] + (target - r.seg_wstart[lo] + w - 1) / w;
+  return min(q, r.seg_start[lo + 1]);
+}
+
+__device__ __forceinline__ WarpTile tile_of(const DeviceRefs& r, unsigned int q, int warp) {
+  WarpTile t;
+  t.sseg = segment_of(r, q);
+  t.k = (q - r.seg_start[t.sseg]) * (uint32_t)r.push_warps + (uint32_t)warp;
+  const SpeciesState& st = r.sstate[t.sseg];
+  t.valid = t.k < st.n_tiles;
+  t.fill = t.valid ? r.inst[t.sseg >> 1].sp[t.sseg & 1].fill[st.cur][t.k] : 0u;
   return t;
 }
 
-// Start the bulk loads of tile t into `stage` (thread 0).
-__device__ __forceinline__ void load_tile(const DeviceRefs& r, const TileInfo& t, float* stage,
+// Start the bulk loads of tile t into `stage` (lane 0).
+__device__ __forceinline__ void load_tile(const DeviceRefs& r, const WarpTile& t, float* stage,
                                           uint64_t* bar) {
-  if (t.seg < 0 || t.fill == 0) return;
-  const SpeciesDev& S = r.inst[t.seg >> 1].sp[t.seg & 1];
-  const SoA in = S.buf[r.sstate[t.seg].cur];
+  const SpeciesDev& S = r.inst[t.sseg >> 1].sp[t.sseg & 1];
+  const SoA in = S.buf[r.sstate[t.sseg].cur];
   const size_t base = (size_t)t.k * kTile;
   const uint32_t bytes = ((t.fill + 3u) & ~3u) * 4u;
   fence_proxy_async_smem();
@@ -166,299 +173,360 @@ __device__ __noinline__ void stage_emission(const InstDev& P, size_t o, float wj
   atomicAdd(P.rho_acc[kElectron], (unsigned long long)fixed_charge(wj, P.charge_shift));
 }
 
-// Field j (0..3) of a packed count word: 16 bits each.
-__device__ __forceinline__ uint32_t field16(unsigned long long v, int j) {
-  return (uint32_t)(v >> (16 * j)) & 0xFFFFu;
-}
-
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads, 2) k_push(DeviceRefs r) {
+__global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float* stage0 = reinterpret_cast<float*>(smem_raw);
-  float* stage1 = stage0 + 7 * kTile;
-  unsigned long long* s_rho = reinterpret_cast<unsigned long long*>(stage1 + 7 * kTile);
-  __shared__ CtaShared cs;
+  __shared__ uint64_t s_bar[kPushMaxWarps][kPushStages];
+  __shared__ PushShared cs;
+  const int W = (int)(blockDim.x >> 5);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lanemask_lt = (1u << lane) - 1u;
+  float* stages = reinterpret_cast<float*>(smem_raw) + (size_t)warp * kPushStages * kStageWords;
+  unsigned long long* s_rho = reinterpret_cast<unsigned long long*>(
+      smem_raw + (size_t)W * kPushStages * kStageWords * 4);
+  uint64_t* bars = s_bar[warp];
 
   Control* ctrl = r.ctrl;
   if (*((volatile int*)&ctrl->error)) return;
-  const unsigned int n_tiles = ctrl->n_tiles;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t lanemask_lt = (1u << lane) - 1u;
+  // this CTA's contiguous range of super-tiles (equal weight per CTA)
+  const unsigned long long wt = ctrl->w_total;
+  const unsigned int q0 =
+      first_super(r, (unsigned int)((unsigned long long)blockIdx.x * wt / gridDim.x));
+  const unsigned int q1 =
+      first_super(r, (unsigned int)((unsigned long long)(blockIdx.x + 1) * wt / gridDim.x));
+  const int n_rounds = (int)(q1 - q0);
 
-  for (int k = threadIdx.x; k < r.smem_nodes; k += kThreads) s_rho[k] = 0ull;
+  for (int k = threadIdx.x; k < r.smem_nodes; k += blockDim.x) s_rho[k] = 0ull;
   if (threadIdx.x < ACC_COUNT) cs.s_acc[threadIdx.x] = 0ull;
-  // static schedule: this CTA takes tiles blockIdx.x + n gridDim.x; thread 0
-  // keeps the next two in registers so that their fills are loaded a whole
-  // tile ahead of their bulk loads
-  TileInfo nxt, nxt2;
-  if (threadIdx.x == 0) {
-    mbar_init(&cs.bar[0], 1);
-    mbar_init(&cs.bar[1], 1);
+  if (threadIdx.x == 0) cs.abort = 0;
+  if (lane == 0) {
+    for (int s = 0; s < kPushStages; ++s) mbar_init(&bars[s], 1);
     fence_mbar_init();
-    cs.abort = 0;
-    const TileInfo first = locate(r, n_tiles, blockIdx.x);
-    load_tile(r, first, stage0, &cs.bar[0]);
-    cs.cur = first;
-    nxt = locate(r, n_tiles, blockIdx.x + gridDim.x);
-    nxt2 = locate(r, n_tiles, blockIdx.x + 2 * gridDim.x);
   }
   __syncthreads();
+  volatile int* abort_flag = &cs.abort;
 
-  uint32_t phase0 = 0, phase1 = 0;
-  int stage_idx = 0;
+  // descriptors of rounds m .. m + 3 (the fill of round m + 3 is loaded a
+  // round before the bulk loads that need it are issued)
+  WarpTile d[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    d[j].valid = false;
+    d[j].fill = 0u;
+    d[j].sseg = 0;
+    d[j].k = 0u;
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+    if (j < n_rounds) d[j] = tile_of(r, q0 + j, warp);
+  uint32_t phase = 0;    // parity bit per stage
+  uint32_t pending = 0;  // stages with a bulk load not yet waited for
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    if (d[j].valid && d[j].fill) {
+      if (lane == 0) load_tile(r, d[j], stages + j * kStageWords, &bars[j]);
+      pending |= 1u << j;
+    }
+  }
+
   int cur_seg = -1;
   bool use_smem = false;
-
-  for (;;) {
-    const TileInfo t = cs.cur;
-    if (t.g >= n_tiles) break;
-    float* st = stage_idx ? stage1 : stage0;
-    int32_t* st_cell = reinterpret_cast<int32_t*>(st);
-    float* st_off = st + 1 * kTile;
-    float* st_vx = st + 2 * kTile;
-    float* st_vy = st + 3 * kTile;
-    float* st_vz = st + 4 * kTile;
-    float* st_wj = st + 5 * kTile;
-    uint32_t* st_id = reinterpret_cast<uint32_t*>(st + 6 * kTile);
-    uint64_t* bar = &cs.bar[stage_idx];
-    // prefetch the next tile into the other stage once the bulk stores that
-    // read it (the previous tile) are done with it
-    if (threadIdx.x == 0) {
-      bulk_wait_read_all();
-      load_tile(r, nxt, stage_idx ? stage0 : stage1, &cs.bar[stage_idx ^ 1]);
+  for (int m = 0; m < n_rounds; ++m) {
+    // ---- 0. descriptors ahead; bulk loads of round m + 2 ---------------------
+    if (m + 3 < n_rounds) d[3] = tile_of(r, q0 + m + 3, warp);
+    const int sc = m % kPushStages;        // stage of round m
+    const int sn = (m + 2) % kPushStages;  // stage of round m + 2
+    const bool aborted = *abort_flag != 0;
+    if (m + 2 < n_rounds && d[2].valid && d[2].fill && !aborted) {
+      if (lane == 0) {
+        // the stage's last bulk stores (round m - 1) must have read it
+        bulk_wait_read_all();
+        load_tile(r, d[2], stages + sn * kStageWords, &bars[sn]);
+      }
+      pending |= 1u << sn;
     }
-    if (t.seg != cur_seg) {
+    // ---- 1. segment change: flush the shared grid (all warps, same round) ----
+    if (d[0].sseg != cur_seg) {
       if (cur_seg >= 0) flush_segment(r, cur_seg, s_rho, cs, use_smem);
-      cur_seg = t.seg;
-      use_smem = r.inst[t.seg >> 1].n_cells + 1 <= r.smem_nodes;
-    }
-    // wait for this tile's data (bounded)
-    if (t.fill) {
-      const uint32_t ph = stage_idx ? phase1 : phase0;
-      uint32_t polls = 0;
-      while (!mbar_try_wait(bar, ph)) {
-        if (++polls > kSpinLimit) {
-          set_error(ctrl, kErrTimeout);
-          cs.abort = 1;
-          break;
-        }
-      }
-      if (threadIdx.x == 0 && polls) {
-        atomicAdd(&ctrl->spin_waits, 1u);
-        atomicMax(&ctrl->spin_max, polls);
-      }
-      if (stage_idx) phase1 ^= 1u;
-      else phase0 ^= 1u;
+      cur_seg = d[0].sseg;
+      use_smem = r.inst[cur_seg >> 1].n_cells + 1 <= r.smem_nodes;
     }
 
-    const int inst = t.seg >> 1, sp = t.seg & 1;
-    const InstDev& P = r.inst[inst];
-    const SpeciesDev& S = P.sp[sp];
-    const uint32_t step = r.istate[inst].step;
-    unsigned long long* rho = use_smem ? s_rho : P.rho_acc[sp];
-    const float qmdt = S.qmdt, vlim = S.vlim, dtdx = P.dtdx, P0 = P.P0;
-    const int N = P.n_cells, shift = P.charge_shift;
-    const float* E32 = P.E32;
-    const uint32_t key2 = P.key2;
-    const bool electrons = sp == kElectron;
-
-    // ---- 1. advance the thread's slots in place ------------------------------
-    // event: an ion emitting an electron at the cathode, or an electron that
-    // is a null-collision candidate
-    uint32_t alive_bits = 0, event_bits = 0;
-    uint32_t b_alive[kPerThread], b_event[kPerThread];
-#pragma unroll
-    for (int j = 0; j < kPerThread; ++j) {
-      const int i = j * kThreads + threadIdx.x;
-      bool alive = false, event = false;
-      if (i < (int)t.fill && !cs.abort) {
-        int cell = st_cell[i];
-        float off = st_off[i], vx = st_vx[i];
-        const float vy = st_vy[i], vz = st_vz[i];
-        // gather (linear between the cell's nodes)
-        const float E0 = __ldg(E32 + cell), E1 = __ldg(E32 + cell + 1);
-        const float Ex = E0 + off * (E1 - E0);
-        // speed-limited kick (beta of the pre-kick speed) and drift (beta of
-        // the post-kick speed)
-        const float s0 = vx * vx + vy * vy + vz * vz;
-        const float b0 = beta_of(sqrtf(s0), vlim);
-        vx = vx + b0 * (qmdt * Ex);
-        const float s1 = vx * vx + vy * vy + vz * vz;
-        const float b1 = beta_of(sqrtf(s1), vlim);
-        off = off + b1 * (vx * dtdx);
-        const float fl = floorf(off);
-        cell += (int)fl;
-        off = off - fl;
-        if (off >= 1.0f) {
-          off = 0.0f;
-          cell += 1;
-        }
-        if (cell < 0 || cell >= N) {
-          event = absorb(P, sp, cell < 0 ? 0 : 1, st_wj[i], st_id[i], step, cs.s_acc);
-        } else {
-          alive = true;
-          if (electrons) {
-            const uint2 rr = philox2x32_10(make_uint2(st_id[i], step), key2);
-            event = uniform01(rr.x) < P0;
+    const WarpTile t = d[0];
+    if (t.valid && !aborted) {
+      const int inst = t.sseg >> 1, sp = t.sseg & 1;
+      const InstDev& P = r.inst[inst];
+      const SpeciesDev& S = P.sp[sp];
+      const uint32_t cur_buf = r.sstate[t.sseg].cur;
+      const size_t tbase = (size_t)t.k * kTile;
+      uint32_t n_surv = 0, n_event = 0;
+      bool compact = false;
+      float* st = stages + sc * kStageWords;
+      int32_t* st_cell = reinterpret_cast<int32_t*>(st);
+      float* st_off = st + 1 * kTile;
+      float* st_vx = st + 2 * kTile;
+      float* st_vy = st + 3 * kTile;
+      float* st_vz = st + 4 * kTile;
+      float* st_wj = st + 5 * kTile;
+      uint32_t* st_id = reinterpret_cast<uint32_t*>(st + 6 * kTile);
+      // ---- 2. the tile's data: wait (bounded), then read it into registers -----
+      bool ok = true;
+      if (t.fill) {
+        uint32_t polls = 0;
+        while (!mbar_try_wait(&bars[sc], (phase >> sc) & 1u)) {
+          if (++polls > kSpinLimit) {
+            set_error(ctrl, kErrTimeout);
+            *abort_flag = 1;
+            ok = false;
+            break;
           }
-          // deposit w_p = beta w_j now unless a collision may change v
-          if (!event) deposit(rho, cell, off, fixed_charge(b1 * st_wj[i], shift));
-          st_cell[i] = cell;
-          st_off[i] = off;
-          st_vx[i] = vx;
+        }
+        ok = __all_sync(0xFFFFFFFFu, ok);
+        if (ok) {
+          phase ^= 1u << sc;
+          pending &= ~(1u << sc);
+        }
+        if (lane == 0 && polls) {
+          atomicAdd(&ctrl->spin_waits, 1u);
+          atomicMax(&ctrl->spin_max, polls);
         }
       }
-      b_alive[j] = __ballot_sync(0xFFFFFFFFu, alive);
-      b_event[j] = __ballot_sync(0xFFFFFFFFu, event);
-      alive_bits |= (alive ? 1u : 0u) << j;
-      event_bits |= (event ? 1u : 0u) << j;
-    }
-
-    // ---- 2. rank survivors and events inside the tile ------------------------
-    // packed word: alive pass 0 | alive pass 1 | events pass 0 | events pass 1
-    if (lane == 0) {
-      cs.warp_cnt[warp] = (unsigned long long)__popc(b_alive[0]) |
-                          ((unsigned long long)__popc(b_alive[1]) << 16) |
-                          ((unsigned long long)__popc(b_event[0]) << 32) |
-                          ((unsigned long long)__popc(b_event[1]) << 48);
-    }
-    __syncthreads();
-    if (warp == 0) {
-      const unsigned long long v = lane < kWarps ? cs.warp_cnt[lane] : 0ull;
-      unsigned long long inc = v;
+      if (t.fill && ok) {
+        // slots past the fill are read (stage memory) but never used; their
+        // cell is taken as 0 so that the gather stays in range
+        int cell[kPerLane];
+        float off[kPerLane], vx[kPerLane], vy[kPerLane], vz[kPerLane], wj[kPerLane];
+        uint32_t id[kPerLane];
+        bool live[kPerLane];
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long n = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-        if (lane >= o) inc += n;
-      }
-      if (lane < kWarps) cs.warp_pre[lane] = inc - v;
-      if (lane == kWarps - 1) cs.tot = inc;
-    }
-    __syncthreads();
-    const unsigned long long pre = cs.warp_pre[warp], tot = cs.tot;
-    const uint32_t n_surv = field16(tot, 0) + field16(tot, 1);
-    const uint32_t n_event = field16(tot, 2) + field16(tot, 3);
-    const size_t tbase = (size_t)t.k * kTile;
+        for (int j = 0; j < kPerLane; ++j) {
+          const int i = j * 32 + lane;
+          live[j] = i < (int)t.fill;
+          cell[j] = live[j] ? st_cell[i] : 0;
+          off[j] = st_off[i];
+          vx[j] = st_vx[i];
+          vy[j] = st_vy[i];
+          vz[j] = st_vz[i];
+          wj[j] = st_wj[i];
+          id[j] = st_id[i];
+        }
+        unsigned long long* rho = use_smem ? s_rho : P.rho_acc[sp];
+        const uint32_t step = r.istate[inst].step;
+        const float qmdt = S.qmdt, vlim = S.vlim, dtdx = P.dtdx, P0 = P.P0;
+        const float wscale = P.wscale;
+        const uint32_t N = (uint32_t)P.n_cells;
+        const float* E32 = P.E32;
+        const bool electrons = sp == kElectron;
+        const bool limited = vlim < INFINITY;  // beta = 1 for an unlimited species
 
-    // ---- 3. events: emissions to staging, candidates to the queue -------------
-    if (event_bits) {
+        // ---- 4. advance the lane's slots ---------------------------------------
+        // straight-line over the kPerLane slots so that their dependency chains
+        // interleave
+        float a[kPerLane], b1[kPerLane];
 #pragma unroll
-      for (int j = 0; j < kPerThread; ++j) {
-        if (!(event_bits >> j & 1u)) continue;
-        const int i = j * kThreads + threadIdx.x;
-        const uint32_t e = (j ? field16(tot, 2) : 0u) + field16(pre, 2 + j) +
-                           (uint32_t)__popc(b_event[j] & lanemask_lt);
-        if (electrons) {
-          // the candidate's slot after compaction = its rank among survivors
-          const uint32_t a = (j ? field16(tot, 0) : 0u) + field16(pre, j) +
-                             (uint32_t)__popc(b_alive[j] & lanemask_lt);
-          S.cand[tbase + e] = (uint16_t)a;
+        for (int j = 0; j < kPerLane; ++j) {
+          // gather (linear between the cell's nodes)
+          const float E0 = __ldg(E32 + cell[j]), E1 = __ldg(E32 + cell[j] + 1);
+          a[j] = qmdt * (E0 + off[j] * (E1 - E0));
+        }
+        // speed-limited kick (beta of the pre-kick speed) and drift (beta of the
+        // post-kick speed); an unlimited species has beta = 1 exactly
+        if (limited) {
+#pragma unroll
+          for (int j = 0; j < kPerLane; ++j) {
+            const float b0 = beta_of(sqrtf(vx[j] * vx[j] + vy[j] * vy[j] + vz[j] * vz[j]), vlim);
+            vx[j] = vx[j] + b0 * a[j];
+          }
+#pragma unroll
+          for (int j = 0; j < kPerLane; ++j)
+            b1[j] = beta_of(sqrtf(vx[j] * vx[j] + vy[j] * vy[j] + vz[j] * vz[j]), vlim);
         } else {
-          stage_emission(P, tbase + e, st_wj[i]);
-        }
-      }
-    }
-
-    // ---- 4. compact the survivors in place (only if a marker left) ----------
-    const bool compact = n_surv != t.fill;
-    if (compact) {
-      int32_t c_cell[kPerThread];
-      float c_off[kPerThread], c_vx[kPerThread], c_vy[kPerThread], c_vz[kPerThread],
-          c_wj[kPerThread];
-      uint32_t c_id[kPerThread];
 #pragma unroll
-      for (int j = 0; j < kPerThread; ++j) {
-        const int i = j * kThreads + threadIdx.x;
-        if (alive_bits >> j & 1u) {
-          c_cell[j] = st_cell[i];
-          c_off[j] = st_off[i];
-          c_vx[j] = st_vx[i];
-          c_vy[j] = st_vy[i];
-          c_vz[j] = st_vz[i];
-          c_wj[j] = st_wj[i];
-          c_id[j] = st_id[i];
+          for (int j = 0; j < kPerLane; ++j) {
+            vx[j] = vx[j] + a[j];
+            b1[j] = 1.0f;
+          }
         }
-      }
-      __syncthreads();
 #pragma unroll
-      for (int j = 0; j < kPerThread; ++j) {
-        if (alive_bits >> j & 1u) {
-          const uint32_t a = (j ? field16(tot, 0) : 0u) + field16(pre, j) +
-                             (uint32_t)__popc(b_alive[j] & lanemask_lt);
-          st_cell[a] = c_cell[j];
-          st_off[a] = c_off[j];
-          st_vx[a] = c_vx[j];
-          st_vy[a] = c_vy[j];
-          st_vz[a] = c_vz[j];
-          st_wj[a] = c_wj[j];
-          st_id[a] = c_id[j];
+        for (int j = 0; j < kPerLane; ++j) {
+          float o = off[j] + b1[j] * (vx[j] * dtdx);
+          const float fl = floorf(o);
+          int c = cell[j] + (int)fl;
+          o = o - fl;
+          if (o >= 1.0f) {
+            o = 0.0f;
+            c += 1;
+          }
+          cell[j] = c;
+          off[j] = o;
         }
-      }
-    }
-    fence_proxy_async_smem();
-    __syncthreads();
+        // ---- 5. electrodes (rare, out of line), candidate draws, deposit -------
+        bool alive[kPerLane], event[kPerLane];
+#pragma unroll
+        for (int j = 0; j < kPerLane; ++j) {
+          alive[j] = live[j] && (uint32_t)cell[j] < N;
+          event[j] = false;
+        }
+#pragma unroll
+        for (int j = 0; j < kPerLane; ++j) {
+          if (live[j] && !alive[j])
+            event[j] = absorb(P, sp, cell[j] < 0 ? 0 : 1, wj[j], id[j], step, cs.s_acc);
+        }
+        if (electrons) {
+          const uint32_t key2 = P.key2;
+#pragma unroll
+          for (int j = 0; j < kPerLane; ++j) {
+            const uint2 rr = philox2x32_10(make_uint2(id[j], step), key2);
+            event[j] = alive[j] && uniform01(rr.x) < P0;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kPerLane; ++j) {
+          // deposit w_p = beta w_j now unless a collision may change v
+          if (alive[j] && !event[j]) {
+            const long long Q = fixed_charge_scaled(b1[j] * wj[j], wscale);
+            const long long right = right_share(Q, off[j]);
+            atomicAdd(rho + cell[j], (unsigned long long)(Q - right));
+            atomicAdd(rho + cell[j] + 1, (unsigned long long)right);
+          }
+        }
 
-    // ---- 5. store the tile to its own slots -----------------------------------
-    // position and vx change every step; vy, vz, w_j and the id only move here
-    // when the tile was compacted (collisions write vy, vz in k_collide)
-    if (threadIdx.x == 0) {
-      if (n_surv) {
-        const SoA out = S.buf[r.sstate[t.seg].cur];
-        const uint32_t bytes = ((n_surv + 3u) & ~3u) * 4u;
-        bulk_store(out.cell + tbase, st + 0 * kTile, bytes);
-        bulk_store(out.off + tbase, st + 1 * kTile, bytes);
-        bulk_store(out.vx + tbase, st + 2 * kTile, bytes);
-        if (compact) {
-          bulk_store(out.vy + tbase, st + 3 * kTile, bytes);
-          bulk_store(out.vz + tbase, st + 4 * kTile, bytes);
-          bulk_store(out.wj + tbase, st + 5 * kTile, bytes);
-          bulk_store(out.id + tbase, st + 6 * kTile, bytes);
+        // ---- 6. rank survivors and events ------------------------------------
+        uint32_t b_alive[kPerLane], b_event[kPerLane];
+        uint32_t pre_alive[kPerLane], pre_event[kPerLane];
+#pragma unroll
+        for (int j = 0; j < kPerLane; ++j) {
+          b_alive[j] = __ballot_sync(0xFFFFFFFFu, alive[j]);
+          b_event[j] = __ballot_sync(0xFFFFFFFFu, event[j]);
+          pre_alive[j] = n_surv;
+          pre_event[j] = n_event;
+          n_surv += __popc(b_alive[j]);
+          n_event += __popc(b_event[j]);
         }
-        bulk_commit();
+        // ---- 7. events: emissions to staging, candidates to the queue ----------
+#pragma unroll
+        for (int j = 0; j < kPerLane; ++j) {
+          if (event[j]) {
+            const uint32_t e = pre_event[j] + (uint32_t)__popc(b_event[j] & lanemask_lt);
+            if (electrons) {
+              // the candidate's slot after compaction = its rank among survivors
+              const uint32_t r_a = pre_alive[j] + (uint32_t)__popc(b_alive[j] & lanemask_lt);
+              S.cand[tbase + e] = (uint16_t)r_a;
+            } else {
+              stage_emission(P, tbase + e, wj[j]);
+            }
+          }
+        }
+        // ---- 8. write the survivors back to the stage: in place, or compacted
+        // in order when a marker left (every lane holds its slots in registers,
+        // so one warp barrier separates the reads from the writes)
+        compact = n_surv != t.fill;
+        if (!compact) {
+#pragma unroll
+          for (int j = 0; j < kPerLane; ++j) {
+            const int i = j * 32 + lane;
+            if (alive[j]) {
+              st_cell[i] = cell[j];
+              st_off[i] = off[j];
+              st_vx[i] = vx[j];
+            }
+          }
+        } else {
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < kPerLane; ++j) {
+            if (alive[j]) {
+              const uint32_t r_a = pre_alive[j] + (uint32_t)__popc(b_alive[j] & lanemask_lt);
+              st_cell[r_a] = cell[j];
+              st_off[r_a] = off[j];
+              st_vx[r_a] = vx[j];
+              st_vy[r_a] = vy[j];
+              st_vz[r_a] = vz[j];
+              st_wj[r_a] = wj[j];
+              st_id[r_a] = id[j];
+            }
+          }
+        }
       }
-      S.fill[r.sstate[t.seg].cur][t.k] = n_surv;
-      if (electrons) S.n_cand[t.k] = n_event;
-      else S.births[t.k] = n_event;
-      atomicAdd(&cs.s_acc[ACC_MSTEPS], (unsigned long long)t.fill);
+      // ---- 9. store the tile to its own slots ---------------------------------
+      // position and vx change every step; vy, vz, w_j and the id only move
+      // here when the tile was compacted (collisions write vy, vz in k_collide)
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0 && ok) {
+        if (n_surv) {
+          const SoA o = S.buf[cur_buf];
+          const uint32_t bytes = ((n_surv + 3u) & ~3u) * 4u;
+          bulk_store(o.cell + tbase, st + 0 * kTile, bytes);
+          bulk_store(o.off + tbase, st + 1 * kTile, bytes);
+          bulk_store(o.vx + tbase, st + 2 * kTile, bytes);
+          if (compact) {
+            bulk_store(o.vy + tbase, st + 3 * kTile, bytes);
+            bulk_store(o.vz + tbase, st + 4 * kTile, bytes);
+            bulk_store(o.wj + tbase, st + 5 * kTile, bytes);
+            bulk_store(o.id + tbase, st + 6 * kTile, bytes);
+          }
+          bulk_commit();
+        }
+        S.fill[cur_buf][t.k] = n_surv;
+        if (sp == kElectron) S.n_cand[t.k] = n_event;
+        else S.births[t.k] = n_event;
+        if (t.fill) atomicAdd(&cs.s_acc[ACC_MSTEPS], (unsigned long long)t.fill);
+      }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      cs.cur = nxt;
-      nxt = nxt2;
-      nxt2 = locate(r, n_tiles, nxt.g + gridDim.x);
-    }
-    stage_idx ^= 1;
-    __syncthreads();
-    if (cs.abort) break;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) d[j] = d[j + 1];
+    d[3].valid = false;
+    d[3].fill = 0u;
   }
-  if (cur_seg >= 0 && !cs.abort) flush_segment(r, cur_seg, s_rho, cs, use_smem);
-  if (threadIdx.x == 0) {
+  if (n_rounds > 0) flush_segment(r, cur_seg, s_rho, cs, use_smem);
+  if (lane == 0) {
     // no bulk copy may outlive the CTA's shared memory
     bulk_wait_all();
-    if (cs.abort) {
-      for (int s = 0; s < 2; ++s) {
-        const uint32_t ph = s ? phase1 : phase0;
-        for (uint32_t p = 0; p < kSpinLimit && !mbar_try_wait(&cs.bar[s], ph); ++p) {
-        }
+    for (int s = 0; s < kPushStages; ++s) {
+      if (!(pending >> s & 1u)) continue;
+      const uint32_t ph = (phase >> s) & 1u;
+      for (uint32_t p = 0; p < kSpinLimit && !mbar_try_wait(&bars[s], ph); ++p) {
       }
     }
   }
 }
 
-int push_occupancy(int smem_nodes, int* blocks_per_sm, size_t* smem_bytes) {
-  const size_t bytes = (size_t)2 * 7 * kTile * 4 + (size_t)smem_nodes * 8;
-  cudaError_t e = cudaFuncSetAttribute(k_push, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)bytes);
+int push_config(int smem_nodes, int* warps, int* blocks_per_sm, size_t* smem_bytes) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return (int)e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_push, kThreads, bytes);
-  *smem_bytes = bytes;
-  return (int)e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return (int)e;
+  const size_t fixed = sizeof(uint64_t) * kPushMaxWarps * kPushStages + sizeof(PushShared) + 1024;
+  *warps = 0;
+  *blocks_per_sm = 0;
+  for (int w = kPushMaxWarps; w >= 4; w -= 4) {
+    const size_t bytes = (size_t)w * kPushStages * kStageWords * 4 + (size_t)smem_nodes * 8;
+    if (bytes + fixed > (size_t)optin) continue;
+    e = cudaFuncSetAttribute(k_push, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return (int)e;
+    int bps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_push, w * 32, bytes);
+    if (e != cudaSuccess) return (int)e;
+    if (bps > 0) {
+      *warps = w;
+      *blocks_per_sm = bps;
+      *smem_bytes = bytes;
+      return 0;
+    }
+  }
+  return 0;
 }
 
 void launch_push(const DeviceRefs& r, int grid, cudaStream_t s) {
-  const size_t bytes = (size_t)2 * 7 * kTile * 4 + (size_t)r.smem_nodes * 8;
-  k_push<<<grid, kThreads, bytes, s>>>(r);
+  const size_t bytes =
+      (size_t)r.push_warps * kPushStages * kStageWords * 4 + (size_t)r.smem_nodes * 8;
+  k_push<<<grid, r.push_warps * 32, bytes, s>>>(r);
 }
+
+static_assert(kTile == 32 * kPerLane, "a tile is kPerLane slots per lane of one warp");
+static_assert((kStageWords * 4) % 128 == 0, "stages keep 128-byte alignment");
 
 }  // namespace slpic

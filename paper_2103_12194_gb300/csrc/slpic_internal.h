@@ -13,11 +13,20 @@ constexpr uint32_t kGenBit = 0x80000000u;
 constexpr uint32_t kSerialMask = 0x7FFFFFFFu;
 constexpr uint32_t kSeedStep = 0xFFFFFFFFu;
 
-// Particle kernel shape: kThreads threads, kPerThread markers per thread (slots
-// t and t + kThreads of the tile), one tile = kTile markers.
-constexpr int kThreads = 512;
-constexpr int kPerThread = 2;
-constexpr int kTile = kThreads * kPerThread;
+// Marker stores are sequences of tiles of kTile slots.  The particle kernel
+// gives every tile to one warp (kPerLane slots per lane: lane l holds slots
+// l, l + 32, ...); a CTA of up to kPushMaxWarps warps takes super-tiles of
+// one tile per warp, and each warp streams its tiles through kPushStages
+// shared-memory stages.
+constexpr int kTile = 128;
+constexpr int kPerLane = kTile / 32;
+constexpr int kPushMaxWarps = 16;
+constexpr int kPushStages = 3;
+constexpr int kStageWords = 7 * kTile;  // the seven SoA streams of one tile
+// Relative cost of a super-tile of each species in the particle kernel's
+// static split of the super-tiles over the CTAs (ions draw no collision test).
+constexpr unsigned int kWeightElectron = 3;
+constexpr unsigned int kWeightIon = 2;
 
 // Device error word values (copied to the host status codes).
 constexpr int kErrNone = 0;
@@ -171,7 +180,8 @@ struct InstState {
 // Global state of the batched step.
 struct Control {
   unsigned int epoch;        // step epoch of the look-back records
-  unsigned int n_tiles;      // particle-kernel tiles this step
+  unsigned int n_super;      // particle-kernel super-tiles this step
+  unsigned int w_total;      // their summed weights
   unsigned int n_seg;        // segments = instances * 2
   unsigned int finish_done;  // CTAs of the finish kernel that completed
   int error;                 // first device error (kErr*)
@@ -195,9 +205,9 @@ struct ChunkStatus {
 // Collision chunks: kCollWarps warps of kCollWarpTiles consecutive tiles
 // each; repacking chunks: kMoveChunkTiles tiles.
 constexpr int kCollWarps = 8;
-constexpr int kCollWarpTiles = 8;
+constexpr int kCollWarpTiles = 32;
 constexpr int kCollChunkTiles = kCollWarps * kCollWarpTiles;
-constexpr int kMoveChunkTiles = 16;
+constexpr int kMoveChunkTiles = 128;
 
 struct DeviceRefs {
   InstDev* inst;          // [n_inst]
@@ -205,18 +215,22 @@ struct DeviceRefs {
   SpeciesState* sstate;   // [n_inst * 2]
   Transfer* xfer;         // [n_inst * 2]
   Control* ctrl;
-  unsigned int* seg_start;   // [n_seg + 1] first global tile of each segment
+  unsigned int* seg_start;   // [n_seg + 1] first super-tile of each segment
+  unsigned int* seg_wstart;  // [n_seg + 1] summed super-tile weights before each segment
   unsigned int* coll_start;  // [n_inst + 1] first collision chunk of each instance
   unsigned int* move_start;  // [n_seg + 1] first repacking chunk of each segment
   ChunkStatus* coll_scan;    // [max collision chunks]
   ChunkStatus* move_scan;    // [max repacking chunks]
   int n_inst;
   int smem_nodes;         // deposit grid nodes in shared memory (0: global atomics)
+  int push_warps;         // warps per particle-kernel CTA = tiles per super-tile
 };
 
 // Launchers (defined in the .cu files).
 void launch_push(const DeviceRefs& r, int grid, cudaStream_t s);
-int push_occupancy(int smem_nodes, int* blocks_per_sm, size_t* smem_bytes);
+// Particle-kernel shape for a shared-memory deposit grid of smem_nodes nodes:
+// warps per CTA, resident CTAs per SM and dynamic shared memory per CTA.
+int push_config(int smem_nodes, int* warps, int* blocks_per_sm, size_t* smem_bytes);
 // mode 0: finish a step and plan the next; mode 1: plan only (one CTA).
 void launch_finish(const DeviceRefs& r, int mode, cudaStream_t s);
 void launch_move(const DeviceRefs& r, int grid, cudaStream_t s);
