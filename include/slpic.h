@@ -217,6 +217,49 @@ int slpic_read_current(slpic_ctx* ctx, int inst, double* I_anode,
  * breakdown criterion gamma (e^(alpha d) - 1) >= 1 (Sec. II.A). */
 int slpic_read_gain(slpic_ctx* ctx, int inst, double* G);
 
+/* Breakdown-voltage search over a batch (Sec. V, Fig. paschen): the context
+ * holds n_pd * n_v configured instances, instance p * n_v + j being voltage j
+ * of pd point p (gap, gas, cross sections, species capacities and gamma set
+ * by the caller).  Every round, each pd point's bracket [lo, hi] is cut at
+ * n_v interior voltages V_j = lo + (hi - lo)(j + 1)/(n_v + 1), one per
+ * instance, and each instance runs one avalanche:
+ *  - electron v_lim = vlim_factor sqrt(2 e V / M) and dt = dx / v_lim
+ *    (vlim_factor <= 0: standard PIC, beta = 1, dt = dx / sqrt(2 e V / m_e));
+ *  - its markers are replaced by n_seed electrons at the cathode (energy e0,
+ *    SLPIC_SEED_CATHODE, unit weight), with the instance's seed advanced by
+ *    the round;
+ *  - secondary emission is switched off during the run, and the gain
+ *    G = gamma * (flux weight of first-generation ions reaching the cathode)
+ *    / (seeded weight) is its expected value (Townsend: G >= 1 is
+ *    breakdown, Sec. II.A);
+ *  - the batch steps in chunks of chunk_steps until every instance has no
+ *    marker left, or max_steps; an instance with more than
+ *    (1 + 1/gamma) n_seed live electrons or at least n_seed/gamma live ions
+ *    is above breakdown for certain (each ionization leaves an ion that
+ *    reaches the cathode): it is emptied and counts as G = +inf.  Every
+ *    instance needs gamma > 0 and capacities of at least
+ *    16 (1 + 1/gamma) n_seed electrons and n_seed/gamma + 16 (1 + 1/gamma)
+ *    n_seed ions (growth is at most x2 per step), else SLPIC_ERR_INVALID_ARG.
+ * Then each bracket shrinks to [V_{j-1}, V_j] around the first j with
+ * G >= 1 (V_{-1} = lo, V_{n_v} = hi).  On return Vb_lo/Vb_hi [n_pd] hold the
+ * final brackets and, if not NULL, gain [n_pd * n_v] the last round's G.  The
+ * instances keep the last round's voltage, v_lim and dt; gamma is restored.
+ * Errors as the other calls (a capacity error cannot occur: see above). */
+typedef struct {
+  int n_pd;            /* pd points */
+  int n_v;             /* voltages per pd point and round */
+  int rounds;          /* section-search rounds (>= 1) */
+  int64_t n_seed;      /* electrons seeded per instance and round */
+  double e0;           /* their energy [eV] */
+  double vlim_factor;  /* see above */
+  int64_t chunk_steps; /* steps between checks of the live counts (1..4) */
+  int64_t max_steps;   /* per round */
+  const double* V_lo;  /* [n_pd] initial bracket [V] */
+  const double* V_hi;  /* [n_pd] */
+} slpic_paschen_spec;
+int slpic_paschen_bisect(slpic_ctx* ctx, const slpic_paschen_spec* spec, double* Vb_lo,
+                         double* Vb_hi, double* gain);
+
 /* Per-step timing of the particle kernel: when on, slpic_step launches each
  * step without a CUDA graph and brackets every particle-kernel launch with
  * CUDA events on the context's stream. */

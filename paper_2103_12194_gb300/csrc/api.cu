@@ -1154,6 +1154,157 @@ int slpic_philox(int device, uint64_t seed, const uint32_t* ctr, int64_t n, uint
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Breakdown-voltage search (the batched Paschen sweep).  Host orchestration of
+// the public calls: per round, set every instance's voltage, speed limit and
+// step, replace its markers by the seed electrons, step the whole batch in
+// chunks until every avalanche has left the gap, and shrink the brackets.
+// ---------------------------------------------------------------------------
+extern "C" int slpic_paschen_bisect(slpic_ctx* c, const slpic_paschen_spec* ps, double* Vb_lo,
+                                    double* Vb_hi, double* gain) {
+  if (!c) return SLPIC_ERR_INVALID_ARG;
+  if (!ps || !Vb_lo || !Vb_hi || !ps->V_lo || !ps->V_hi)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "paschen: NULL argument");
+  const int np = ps->n_pd, nv = ps->n_v;
+  if (np < 1 || nv < 1 || (long long)np * nv != c->n_inst)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "paschen: the context must hold n_pd * n_v = %d instances",
+                c->n_inst);
+  if (ps->rounds < 1 || ps->n_seed < 1 || ps->chunk_steps < 1 || ps->chunk_steps > 4 ||
+      ps->max_steps < 1 || !(ps->e0 >= 0))
+    return fail(c, SLPIC_ERR_INVALID_ARG, "paschen: bad rounds, n_seed, e0 or step counts");
+  for (int p = 0; p < np; ++p)
+    if (!(ps->V_lo[p] > 0) || !(ps->V_hi[p] > ps->V_lo[p]))
+      return fail(c, SLPIC_ERR_INVALID_ARG, "paschen: bracket %d is not 0 < lo < hi", p);
+  // An avalanche with more than T_e = (1 + 1/gamma) n_seed live electrons, or
+  // T_i = n_seed / gamma live ions, has G >= 1 for certain (every ionization
+  // leaves an ion that reaches the cathode); growth is at most x2 per step,
+  // so with chunks of <= 4 steps the stores need 16 T_e electrons and
+  // T_i + 16 T_e ions.
+  const int n = c->n_inst;
+  std::vector<int64_t> thr_e(n), thr_i(n);
+  for (int i = 0; i < n; ++i) {
+    if (int rc = check_config(c, i)) return rc;
+    const double g = c->hi[i].gamma;
+    if (!(g > 0)) return fail(c, SLPIC_ERR_INVALID_ARG, "paschen: instance %d has gamma <= 0", i);
+    thr_e[i] = (int64_t)std::ceil((1.0 + 1.0 / g) * (double)ps->n_seed);
+    thr_i[i] = (int64_t)std::ceil((double)ps->n_seed / g);
+    if (c->hi[i].sp[kElectron].cap < 16 * thr_e[i] ||
+        c->hi[i].sp[kIon].cap < thr_i[i] + 16 * thr_e[i])
+      return fail(c, SLPIC_ERR_INVALID_ARG,
+                  "paschen: instance %d needs capacities of at least %lld electrons and %lld "
+                  "ions (16 (1 + 1/gamma) n_seed and n_seed/gamma + 16 (1 + 1/gamma) n_seed)",
+                  i, (long long)(16 * thr_e[i]), (long long)(thr_i[i] + 16 * thr_e[i]));
+  }
+  if (int rc = prepare(c)) return rc;
+  std::vector<double> lo(ps->V_lo, ps->V_lo + np), hi(ps->V_hi, ps->V_hi + np);
+  std::vector<double> gam(n), G(n, 0.0), V(n);
+  std::vector<uint64_t> seed0(n);
+  for (int i = 0; i < n; ++i) {
+    gam[i] = c->hi[i].gamma;
+    seed0[i] = c->hi[i].seed;
+  }
+  std::vector<SpeciesState> st(2 * (size_t)n);
+  std::vector<char> saturated(n);
+  int rc = SLPIC_OK;
+  for (int round = 0; round < ps->rounds && !rc; ++round) {
+    // ---- configure and seed every instance --------------------------------
+    for (int p = 0; p < np && !rc; ++p) {
+      for (int j = 0; j < nv && !rc; ++j) {
+        const int i = p * nv + j;
+        const HostInst& h = c->hi[i];
+        V[i] = lo[p] + (hi[p] - lo[p]) * (j + 1) / (nv + 1);
+        const double dx = h.d / h.n_cells;
+        double vlim = 0.0, dt;
+        if (ps->vlim_factor > 0) {
+          vlim = ps->vlim_factor * std::sqrt(2.0 * kQe * V[i] / h.sp[kIon].mass);
+          dt = dx / vlim;
+        } else {
+          dt = dx / std::sqrt(2.0 * kQe * V[i] / h.sp[kElectron].mass);
+        }
+        const HostSpecies& se = h.sp[kElectron];
+        if ((rc = slpic_set_voltage(c, i, V[i]))) break;
+        if ((rc = slpic_set_species(c, i, kElectron, se.mass, se.charge, vlim, se.cap))) break;
+        if ((rc = slpic_set_dt(c, i, dt))) break;
+        if ((rc = slpic_set_emission(c, i, 0.0))) break;
+        if ((rc = slpic_set_seed(c, i, seed0[i] + 0x9E3779B97F4A7C15ull * (uint64_t)round)))
+          break;
+        if ((rc = load_common(c, i, kIon, nullptr, 0, 0, cudaMemcpyHostToDevice))) break;
+        if ((rc = load_common(c, i, kElectron, nullptr, 0, 0, cudaMemcpyHostToDevice))) break;
+        if ((rc = slpic_seed(c, i, kElectron, ps->n_seed, SLPIC_SEED_CATHODE, ps->e0, 0.0, 0.0,
+                             1.0)))
+          break;
+        saturated[i] = 0;
+      }
+    }
+    if (rc) break;
+    // ---- step the batch until every avalanche has left the gap --------------
+    for (int64_t done = 0; done < ps->max_steps && !rc;) {
+      const int64_t k = std::min<int64_t>(ps->chunk_steps, ps->max_steps - done);
+      if ((rc = slpic_step(c, k))) break;
+      done += k;
+      if ((rc = sync(c))) break;
+      if (cudaMemcpy(st.data(), c->d_sstate, sizeof(SpeciesState) * st.size(),
+                     cudaMemcpyDeviceToHost) != cudaSuccess) {
+        rc = fail(c, SLPIC_ERR_CUDA, "paschen: reading the live counts");
+        break;
+      }
+      bool live = false;
+      for (int i = 0; i < n && !rc; ++i) {
+        if (saturated[i]) continue;
+        const uint32_t ne = st[2 * i].n_live, ni = st[2 * i + 1].n_live;
+        // above breakdown for certain; stop this avalanche before it can
+        // outgrow the stores in the next chunk
+        if ((int64_t)ne > thr_e[i] || (int64_t)ni >= thr_i[i]) {
+          saturated[i] = 1;
+          rc = load_common(c, i, kIon, nullptr, 0, 0, cudaMemcpyHostToDevice);
+          if (!rc) rc = load_common(c, i, kElectron, nullptr, 0, 0, cudaMemcpyHostToDevice);
+          continue;
+        }
+        if (ne || ni) live = true;
+      }
+      if (!live) break;
+    }
+    if (rc) break;
+    // ---- gains and brackets -------------------------------------------------
+    for (int i = 0; i < n && !rc; ++i) {
+      if (saturated[i]) {
+        G[i] = std::numeric_limits<double>::infinity();
+        continue;
+      }
+      slpic_tallies t;
+      if ((rc = slpic_read_tallies(c, i, &t))) break;
+      InstState is;
+      if (cudaMemcpy(&is, c->d_istate + i, sizeof is, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        rc = fail(c, SLPIC_ERR_CUDA, "paschen: reading the seeded weight");
+        break;
+      }
+      const double w_seed = (double)is.w_seed / (double)c->h_inst[i].wscale;
+      G[i] = w_seed > 0 ? gam[i] * t.w_cath_ion_gen0 / w_seed : 0.0;
+    }
+    if (rc) break;
+    for (int p = 0; p < np; ++p) {
+      int j = 0;
+      while (j < nv && !(G[p * nv + j] >= 1.0)) ++j;
+      const double a = j == 0 ? lo[p] : V[p * nv + j - 1];
+      const double b = j == nv ? hi[p] : V[p * nv + j];
+      lo[p] = a;
+      hi[p] = b;
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    const int r2 = slpic_set_emission(c, i, gam[i]);
+    if (!rc) rc = r2;
+  }
+  if (rc) return rc;
+  for (int p = 0; p < np; ++p) {
+    Vb_lo[p] = lo[p];
+    Vb_hi[p] = hi[p];
+  }
+  if (gain)
+    for (int i = 0; i < n; ++i) gain[i] = G[i];
+  return SLPIC_OK;
+}
+
+// ---------------------------------------------------------------------------
 // slpic_philox_static: the Philox self-check without device allocation.  The
 // counters (first half) and the outputs (second half) live in one file-scope
 // device array of the module, whose address is looked up once per device.

@@ -29,6 +29,14 @@ class SlpicError(RuntimeError):
         self.code = code
 
 
+class PaschenSpec(ctypes.Structure):
+    _fields_ = [("n_pd", ctypes.c_int), ("n_v", ctypes.c_int), ("rounds", ctypes.c_int),
+                ("n_seed", ctypes.c_int64), ("e0", ctypes.c_double),
+                ("vlim_factor", ctypes.c_double), ("chunk_steps", ctypes.c_int64),
+                ("max_steps", ctypes.c_int64), ("V_lo", ctypes.c_void_p),
+                ("V_hi", ctypes.c_void_p)]
+
+
 class SoA(ctypes.Structure):
     _fields_ = [("cell", ctypes.c_void_p), ("off", ctypes.c_void_p), ("vx", ctypes.c_void_p),
                 ("vy", ctypes.c_void_p), ("vz", ctypes.c_void_p), ("wj", ctypes.c_void_p),
@@ -99,6 +107,7 @@ def lib():
         "slpic_philox": ([i32, u64, vp, i64, vp], i32),
         "slpic_philox2x32": ([i32, u32, vp, i64, vp], i32),
         "slpic_philox_static": ([i32, u64, vp, i64, vp], i32),
+        "slpic_paschen_bisect": ([vp, ctypes.POINTER(PaschenSpec), vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -313,6 +322,22 @@ class Simulation:
         g = ctypes.c_double()
         self._ck(self._L.slpic_read_gain(self._h, i, ctypes.byref(g)))
         return g.value
+
+    def paschen_bisect(self, V_lo, V_hi, n_v, rounds, n_seed, e0=1.0, vlim_factor=4.0,
+                       chunk_steps=4, max_steps=1_000_000):
+        """slpic_paschen_bisect over the context's len(V_lo) * n_v instances;
+        returns (Vb_lo, Vb_hi, gain[n_pd, n_v] of the last round)."""
+        lo = np.ascontiguousarray(V_lo, np.float64)
+        hi = np.ascontiguousarray(V_hi, np.float64)
+        n_pd = lo.shape[0]
+        spec = PaschenSpec(n_pd, int(n_v), int(rounds), int(n_seed), float(e0),
+                           float(vlim_factor), int(chunk_steps), int(max_steps),
+                           lo.ctypes.data, hi.ctypes.data)
+        out_lo, out_hi = np.empty(n_pd), np.empty(n_pd)
+        gain = np.empty(n_pd * int(n_v))
+        self._ck(self._L.slpic_paschen_bisect(self._h, ctypes.byref(spec), _ptr(out_lo),
+                                              _ptr(out_hi), _ptr(gain)))
+        return out_lo, out_hi, gain.reshape(n_pd, int(n_v))
 
     def set_profiling(self, on):
         self._ck(self._L.slpic_set_profiling(self._h, 1 if on else 0))
