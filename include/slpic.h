@@ -74,6 +74,17 @@ typedef struct {
   uint32_t* id;
 } slpic_soa_f32;
 
+/* FP64 marker arrays, for contexts whose marker path is FP64. */
+typedef struct {
+  int32_t* cell;
+  double* off;
+  double* vx;
+  double* vy;
+  double* vz;
+  double* wj;
+  uint32_t* id;
+} slpic_soa_f64;
+
 /* What happened in one step of one instance (or, from slpic_read_tallies, the
  * sums over all steps since the last seed/load).  Counts are exact; weight
  * sums are exact integer sums of w_j in units of 2^-charge_shift converted to
@@ -163,6 +174,13 @@ int slpic_suggest_dt(double d, int n_cells, double V, double m_ion, int mode,
  * every marker gets flux weight wj.  Resets the step counter and tallies. */
 int slpic_seed(slpic_ctx* ctx, int inst, int species, int64_t n, int mode,
                double e0, double e_lo, double e_hi, double wj);
+/* Arithmetic type of the marker path: 32 (default; positions, velocities and
+ * weights in float, the deposit in int64 fixed point, the field solve and
+ * tallies in double) or 64 (everything of the marker path in double, the
+ * plain FP64 form).  Set before the first use of the context; the FP32
+ * marker calls then fail with SLPIC_ERR_STATE and the _f64 ones are used. */
+int slpic_set_precision(slpic_ctx* ctx, int bits);
+
 /* Replace the markers of `species` by n markers from host arrays (FP32 SoA);
  * next_id = serial number of the next born marker.  Cells must lie in
  * [0, N) and offsets in [0, 1).  Resets the step counter and tallies. */
@@ -173,6 +191,10 @@ int slpic_load_particles(slpic_ctx* ctx, int inst, int species,
 int slpic_load_particles_device(slpic_ctx* ctx, int inst, int species,
                                 const slpic_soa_f32* dev, int64_t n,
                                 uint32_t next_id);
+/* slpic_load_particles for an FP64 context (host FP64 SoA). */
+int slpic_load_particles_f64(slpic_ctx* ctx, int inst, int species,
+                             const slpic_soa_f64* host, int64_t n,
+                             uint32_t next_id);
 /* Reset the step counter and tallies without touching the markers. */
 int slpic_reset_counters(slpic_ctx* ctx, int inst);
 
@@ -191,6 +213,10 @@ int slpic_count(slpic_ctx* ctx, int inst, int species, int64_t* n_out);
 int slpic_read_particles(slpic_ctx* ctx, int inst, int species,
                          const slpic_soa_f32* host, int64_t capacity,
                          int64_t* n_out);
+/* slpic_read_particles for an FP64 context. */
+int slpic_read_particles_f64(slpic_ctx* ctx, int inst, int species,
+                             const slpic_soa_f64* host, int64_t capacity,
+                             int64_t* n_out);
 /* Fixed-point deposit of the last step (n_cells + 1 int64 node values). */
 int slpic_read_charge(slpic_ctx* ctx, int inst, int species, int64_t* host,
                       int64_t n);

@@ -63,6 +63,7 @@ struct slpic_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t capture_stream = nullptr;
   int n_inst = 0;
+  int fp64 = 0;  // marker path in double precision
   std::vector<HostInst> hi;
   std::string err;
   bool committed = false;
@@ -146,8 +147,49 @@ int sync(slpic_ctx* c) {
   return device_error(c);
 }
 
-// Derive the single-precision constants of instance i (everything that does
-// not need reallocation) into c->h_inst[i].
+// The step's constants in the marker path's type R, each rounded once from
+// its double-precision definition; the majorant is formed in R from the R
+// table, with the same operations the step uses.
+template <typename R>
+void derive_consts(const HostInst& h, StepConsts<R>& K) {
+  const double dx = h.d / h.n_cells;
+  const HostSpecies& E = h.sp[kElectron];
+  const HostSpecies& I = h.sp[kIon];
+  for (int s = 0; s < 2; ++s) {
+    const HostSpecies& S = h.sp[s];
+    const bool limited = S.vlim > 0.0 && std::isfinite(S.vlim);
+    K.qmdt[s] = (R)((S.charge / S.mass) * h.dt);
+    K.vlim[s] = limited ? (R)S.vlim : std::numeric_limits<R>::infinity();
+    K.K_V[s] = (R)(2.0 * kQe / S.mass);
+  }
+  K.dtdx = (R)(h.dt / dx);
+  K.K_E = (R)(0.5 * E.mass / kQe);
+  const double n_g = h.p_Pa / (kKB * h.T_K);
+  K.ndt = (R)(n_g * h.dt);
+  K.R2 = (R)(2.0 * E.mass / I.mass);
+  K.e_ex = (R)h.e_ex;
+  K.e_io = (R)h.e_io;
+  K.sigT_ion = (R)std::sqrt(kKB * h.T_K / I.mass);
+  K.gamma = (R)h.gamma;
+  K.wscale = (R)std::ldexp(1.0, h.shift);
+  K.two_pi = (R)kTwoPi;
+  K.e_lo = (R)std::ldexp(1.0, h.lo_exp2);
+  K.e_hi = (R)std::ldexp(1.0, h.lo_exp2 + h.octaves);
+  // majorant of n_g sigma_tot(eps) min(v, vlim) dt over the table
+  R smax = 0;
+  for (size_t j = 0; j < h.el.size(); ++j) {
+    const R s1 = (R)h.el[j];
+    const R s2 = s1 + (R)h.ex[j];
+    const R s3 = s2 + (R)h.io[j];
+    smax = std::max(smax, s3);
+  }
+  const R v_top = std::sqrt(K.e_hi * K.K_V[kElectron]);
+  K.vb_cap = std::min(K.vlim[kElectron], v_top);
+  K.P0 = (K.ndt * K.vb_cap) * smax;
+}
+
+// Derive the constants of instance i (everything that does not need
+// reallocation) into c->h_inst[i].
 void fill_constants(slpic_ctx* c, int i, InstDev& P) {
   const HostInst& h = c->hi[i];
   const double dx = h.d / h.n_cells;
@@ -162,46 +204,14 @@ void fill_constants(slpic_ctx* c, int i, InstDev& P) {
   P.ctr_inst = (uint32_t)i;
   // key of the per-step null-collision draw: both seed words and the instance
   P.key2 = (uint32_t)h.seed ^ (uint32_t)(h.seed >> 32) ^ (0x85EBCA6Bu * (uint32_t)(i + 1));
-  P.dtdx = (float)(h.dt / dx);
-  const HostSpecies& E = h.sp[kElectron];
-  const HostSpecies& I = h.sp[kIon];
-  P.K_E = (float)(0.5 * E.mass / kQe);
-  const double n_g = h.p_Pa / (kKB * h.T_K);
-  P.ndt = (float)(n_g * h.dt);
-  P.R2 = (float)(2.0 * E.mass / I.mass);
-  P.e_ex = (float)h.e_ex;
-  P.e_io = (float)h.e_io;
-  P.sigT_ion = (float)std::sqrt(kKB * h.T_K / I.mass);
-  P.gamma = (float)h.gamma;
-  P.wscale = (float)std::ldexp(1.0, h.shift);
-  P.two_pi = (float)kTwoPi;
-  P.e_lo = (float)std::ldexp(1.0, h.lo_exp2);
-  P.e_hi = (float)std::ldexp(1.0, h.lo_exp2 + h.octaves);
+  derive_consts(h, P.c32);
+  derive_consts(h, P.c64);
   P.dx = dx;
   P.d = h.d;
   P.V = h.V;
   P.area = h.area;
   P.dt = h.dt;
   P.pois_C = kQe * dx * std::ldexp(1.0, -h.shift) / (h.area * kEps0);
-  for (int s = 0; s < 2; ++s) {
-    const HostSpecies& S = h.sp[s];
-    const bool limited = S.vlim > 0.0 && std::isfinite(S.vlim);
-    P.sp[s].qmdt = (float)((S.charge / S.mass) * h.dt);
-    P.sp[s].vlim = limited ? (float)S.vlim : std::numeric_limits<float>::infinity();
-    P.sp[s].K_V = (float)(2.0 * kQe / S.mass);
-  }
-  // majorant of n_g sigma_tot(eps) min(v, vlim) dt over the table (FP32, the
-  // same operations the step uses)
-  float smax = 0.0f;
-  const size_t nn = h.el.size();
-  for (size_t j = 0; j < nn; ++j) {
-    const float s3 = (h.el[j] + h.ex[j]) + h.io[j];
-    smax = std::max(smax, s3);
-  }
-  const float e_top = P.e_hi;
-  const float v_top = std::sqrt(e_top * P.sp[kElectron].K_V);
-  P.vb_cap = std::min(P.sp[kElectron].vlim, v_top);
-  P.P0 = (P.ndt * P.vb_cap) * smax;
 }
 
 int check_config(slpic_ctx* c, int i) {
@@ -224,16 +234,19 @@ T* carve(char*& p, size_t n) {
   return r;
 }
 
-size_t soa_bytes(size_t n) { return 7 * ((n * 4 + 255) & ~size_t(255)); }
+// Bytes of a store of n slots whose five real streams have rsz bytes each.
+size_t soa_bytes(size_t n, size_t rsz) {
+  return 2 * ((n * 4 + 255) & ~size_t(255)) + 5 * ((n * rsz + 255) & ~size_t(255));
+}
 
-SoA carve_soa(char*& p, size_t n) {
+SoA carve_soa(char*& p, size_t n, size_t rsz) {
   SoA s;
   s.cell = carve<int32_t>(p, n);
-  s.off = carve<float>(p, n);
-  s.vx = carve<float>(p, n);
-  s.vy = carve<float>(p, n);
-  s.vz = carve<float>(p, n);
-  s.wj = carve<float>(p, n);
+  s.off = reinterpret_cast<float*>(carve<char>(p, n * rsz));
+  s.vx = reinterpret_cast<float*>(carve<char>(p, n * rsz));
+  s.vy = reinterpret_cast<float*>(carve<char>(p, n * rsz));
+  s.vz = reinterpret_cast<float*>(carve<char>(p, n * rsz));
+  s.wj = reinterpret_cast<float*>(carve<char>(p, n * rsz));
   s.id = carve<uint32_t>(p, n);
   return s;
 }
@@ -308,6 +321,7 @@ int commit(slpic_ctx* c) {
     const size_t tab_n = h.el.size() + 1;
     size_t bytes = 0;
     bytes += (tab_n * 16 + 255) & ~size_t(255);
+    if (c->fp64) bytes += (tab_n * sizeof(TabNode64) + 255) & ~size_t(255);
     bytes += ((nn * 4 + 255) & ~size_t(255));
     bytes += 2 * ((nn * 8 + 255) & ~size_t(255));
     bytes += 4 * ((nn * 8 + 255) & ~size_t(255));
@@ -317,6 +331,8 @@ int commit(slpic_ctx* c) {
     char* p = (char*)blk;
     float4* tab = carve<float4>(p, tab_n);
     P.table = tab;
+    TabNode64* tab64 = c->fp64 ? carve<TabNode64>(p, tab_n) : nullptr;
+    P.table64 = tab64;
     P.E32 = carve<float>(p, nn);
     P.phi = carve<double>(p, nn);
     P.E64 = carve<double>(p, nn);
@@ -338,6 +354,19 @@ int commit(slpic_ctx* c) {
     }
     ht[tab_n - 1] = ht[tab_n - 2];
     CK(cudaMemcpy(tab, ht.data(), tab_n * 16, cudaMemcpyHostToDevice), "table");
+    if (tab64) {
+      // the same cumulative sums in double
+      std::vector<TabNode64> hd(tab_n);
+      for (size_t j = 0; j + 1 < tab_n; ++j) {
+        const double s1 = h.el[j];
+        const double s2 = s1 + (double)h.ex[j];
+        const double s3 = s2 + (double)h.io[j];
+        hd[j] = TabNode64{s1, s2, s3, 0.0};
+      }
+      hd[tab_n - 1] = hd[tab_n - 2];
+      CK(cudaMemcpy(tab64, hd.data(), tab_n * sizeof(TabNode64), cudaMemcpyHostToDevice),
+         "table");
+    }
     // marker stores: tiles of kTile slots (two buffers for repacking);
     // electrons emitted at the cathode are staged in slots of the ion tile
     // that emitted them; collision candidates are queued per electron tile
@@ -351,20 +380,22 @@ int commit(slpic_ctx* c) {
       const size_t stage_b = s == kElectron ? (size_t)cap_tiles[kIon] * kTile : 0;
       const size_t cand_slots = s == kElectron ? slots : 0;
       const size_t arr = ((size_t)cap_tiles[s] + 1) * 4 + 256;
-      size_t b = 2 * soa_bytes(slots) + soa_bytes(stage_b) + 4 * arr + cand_slots * 6 + 512;
+      const size_t rsz = c->fp64 ? 8 : 4;
+      size_t b = 2 * soa_bytes(slots, rsz) + soa_bytes(stage_b, rsz) + 4 * arr +
+                 cand_slots * (2 + rsz) + 512;
       void* sb;
       if (int rc = dmalloc(c, &sb, b, "marker buffers")) return rc;
       char* q = (char*)sb;
-      S.buf[0] = carve_soa(q, slots);
-      S.buf[1] = carve_soa(q, slots);
-      if (stage_b) S.stage_b = carve_soa(q, stage_b);
+      S.buf[0] = carve_soa(q, slots, rsz);
+      S.buf[1] = carve_soa(q, slots, rsz);
+      if (stage_b) S.stage_b = carve_soa(q, stage_b, rsz);
       else std::memset(&S.stage_b, 0, sizeof(SoA));
       S.fill[0] = carve<uint32_t>(q, cap_tiles[s] + 1);
       S.fill[1] = carve<uint32_t>(q, cap_tiles[s] + 1);
       S.births = carve<uint32_t>(q, cap_tiles[s] + 1);
       S.n_cand = carve<uint32_t>(q, cap_tiles[s] + 1);
       S.cand = cand_slots ? carve<uint16_t>(q, cand_slots) : nullptr;
-      S.esec = cand_slots ? carve<float>(q, cand_slots) : nullptr;
+      S.esec = cand_slots ? (void*)carve<char>(q, cand_slots * rsz) : nullptr;
       CK(cudaMemset(S.fill[0], 0, ((size_t)cap_tiles[s] + 1) * 4), "fills");
       CK(cudaMemset(S.fill[1], 0, ((size_t)cap_tiles[s] + 1) * 4), "fills");
       total_tiles += cap_tiles[s];
@@ -411,14 +442,15 @@ int commit(slpic_ctx* c) {
   int smem_nodes = max_nodes <= 16385 ? max_nodes : 0;
   int bps = 0, warps = 0;
   size_t sbytes = 0;
-  int e = push_config(smem_nodes, &warps, &bps, &sbytes);
+  int e = push_config(c->fp64, smem_nodes, &warps, &bps, &sbytes);
   if (e != 0 || bps == 0) {
     smem_nodes = 0;
-    e = push_config(0, &warps, &bps, &sbytes);
+    e = push_config(c->fp64, 0, &warps, &bps, &sbytes);
     if (e != 0 || bps == 0) return fail(c, SLPIC_ERR_CUDA, "particle kernel cannot be launched");
   }
   c->refs.smem_nodes = smem_nodes;
   c->refs.push_warps = warps;
+  c->refs.fp64 = c->fp64;
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device), "attributes");
   c->blocks_per_sm = bps;
@@ -487,10 +519,50 @@ int build_graph(slpic_ctx* c) {
   return SLPIC_OK;
 }
 
-int host_soa_check(slpic_ctx* c, const slpic_soa_f32* s) {
-  if (!s || !s->cell || !s->off || !s->vx || !s->vy || !s->vz || !s->wj || !s->id)
-    return fail(c, SLPIC_ERR_INVALID_ARG, "null marker array");
+// The seven marker arrays of a caller (cell, off, vx, vy, vz, w_j, id), in
+// the precision the call names.
+struct Arrays {
+  void* f[7];
+  int fp64;
+};
+
+Arrays arrays_of(const slpic_soa_f32* s) {
+  Arrays a{};
+  if (s) {
+    void* f[7] = {s->cell, s->off, s->vx, s->vy, s->vz, s->wj, s->id};
+    std::memcpy(a.f, f, sizeof f);
+  }
+  a.fp64 = 0;
+  return a;
+}
+
+Arrays arrays_of(const slpic_soa_f64* s) {
+  Arrays a{};
+  if (s) {
+    void* f[7] = {s->cell, s->off, s->vx, s->vy, s->vz, s->wj, s->id};
+    std::memcpy(a.f, f, sizeof f);
+  }
+  a.fp64 = 1;
+  return a;
+}
+
+int arrays_check(slpic_ctx* c, const Arrays& a) {
+  for (int k = 0; k < 7; ++k)
+    if (!a.f[k]) return fail(c, SLPIC_ERR_INVALID_ARG, "null marker array");
   return SLPIC_OK;
+}
+
+int precision_check(slpic_ctx* c, int fp64) {
+  if (fp64 != c->fp64)
+    return fail(c, SLPIC_ERR_STATE,
+                "the context's marker path is FP%d: use the %s marker calls", c->fp64 ? 64 : 32,
+                c->fp64 ? "_f64" : "FP32");
+  return SLPIC_OK;
+}
+
+// Bytes of field k of n markers.
+size_t field_bytes(const slpic_ctx* c, int k, size_t n) {
+  return (k == 0 || k == 6) ? n * 4 : n * (c->fp64 ? 8 : 4);
 }
 
 }  // namespace
@@ -731,16 +803,19 @@ extern "C" int slpic_seed(slpic_ctx* c, int inst, int species, int64_t n, int mo
     return fail(c, SLPIC_ERR_CAPACITY, "seeding %lld markers exceeds the capacity", (long long)n);
   if ((uint64_t)st.next_id + (uint64_t)n > kSerialMask)
     return fail(c, SLPIC_ERR_CAPACITY, "marker serial numbers exhausted");
-  if (!((float)wj * P.wscale < 549755813888.0f))
+  // the weight in the marker path's type, and its fixed-point charge
+  const double wr = c->fp64 ? wj : (double)(float)wj;
+  const double wq = wr * P.c64.wscale;  // exact: a power-of-two scaling
+  if (!(wq < 549755813888.0))
     return fail(c, SLPIC_ERR_INVALID_ARG,
                 "weight %g is too large for charge shift %d (w 2^shift must stay below 2^39)", wj,
                 P.charge_shift);
   const HostInst& h = c->hi[inst];
-  float e0f = (float)e0;
-  if (mode == 3) e0f = (float)std::sqrt(kKB * h.T_K / h.sp[species].mass);
-  const float lr = mode == 2 ? (float)std::log(e_hi / e_lo) : 0.0f;
-  launch_seed(c->refs, inst, species, app, st.next_id, (uint32_t)n, mode, e0f, (float)e_lo, lr,
-              (float)wj, c->stream);
+  // each parameter is rounded once to the marker path's type on the device
+  const double ekin = mode == 3 ? std::sqrt(kKB * h.T_K / h.sp[species].mass) : e0;
+  const double lr = mode == 2 ? std::log(e_hi / e_lo) : 0.0;
+  launch_seed(c->refs, inst, species, app, st.next_id, (uint32_t)n, mode, ekin, e_lo, lr, wj,
+              c->stream);
   CK(cudaGetLastError(), "seed");
   CK(cudaStreamSynchronize(c->stream), "seed");
   if (int rc = write_fills(c, S, st.cur, app / kTile, app + (uint32_t)n)) return rc;
@@ -751,8 +826,7 @@ extern "C" int slpic_seed(slpic_ctx* c, int inst, int species, int64_t n, int mo
   {
     InstState is;
     CK(cudaMemcpy(&is, c->d_istate + inst, sizeof is, cudaMemcpyDeviceToHost), "seed");
-    const unsigned long long q =
-        (unsigned long long)n * (unsigned long long)std::llrint((float)wj * P.wscale);
+    const unsigned long long q = (unsigned long long)n * (unsigned long long)std::llrint(wq);
     if (species == kElectron) is.w_seed += q;
     is.w_live[species] += q;
     CK(cudaMemcpy(c->d_istate + inst, &is, sizeof is, cudaMemcpyHostToDevice), "seed");
@@ -763,12 +837,13 @@ extern "C" int slpic_seed(slpic_ctx* c, int inst, int species, int64_t n, int mo
 
 namespace {
 
-int load_common(slpic_ctx* c, int inst, int species, const slpic_soa_f32* src, int64_t n,
+int load_common(slpic_ctx* c, int inst, int species, const Arrays& src, int64_t n,
                 uint32_t next_id, cudaMemcpyKind kind) {
   if (!valid_inst(c, inst) || (species != 0 && species != 1) || n < 0)
     return fail(c, SLPIC_ERR_INVALID_ARG, "bad load arguments");
+  if (int rc = precision_check(c, src.fp64)) return rc;
   if (n > 0)
-    if (int rc = host_soa_check(c, src)) return rc;
+    if (int rc = arrays_check(c, src)) return rc;
   if (next_id > kSerialMask) return fail(c, SLPIC_ERR_INVALID_ARG, "next_id beyond 2^31 - 1");
   if (int rc = prepare(c)) return rc;
   if (int rc = sync(c)) return rc;
@@ -780,21 +855,17 @@ int load_common(slpic_ctx* c, int inst, int species, const slpic_soa_f32* src, i
   if (int rc = read_state(c, inst, species, &st)) return rc;
   const SoA& d = S.buf[st.cur];
   if (n > 0) {
-    const size_t b = (size_t)n * 4;
-    CK(cudaMemcpyAsync(d.cell, src->cell, b, kind, c->stream), "load");
-    CK(cudaMemcpyAsync(d.off, src->off, b, kind, c->stream), "load");
-    CK(cudaMemcpyAsync(d.vx, src->vx, b, kind, c->stream), "load");
-    CK(cudaMemcpyAsync(d.vy, src->vy, b, kind, c->stream), "load");
-    CK(cudaMemcpyAsync(d.vz, src->vz, b, kind, c->stream), "load");
-    CK(cudaMemcpyAsync(d.wj, src->wj, b, kind, c->stream), "load");
-    CK(cudaMemcpyAsync(d.id, src->id, b, kind, c->stream), "load");
+    void* dst[7] = {d.cell, d.off, d.vx, d.vy, d.vz, d.wj, d.id};
+    for (int k = 0; k < 7; ++k)
+      CK(cudaMemcpyAsync(dst[k], src.f[k], field_bytes(c, k, (size_t)n), kind, c->stream),
+         "load");
   }
   // validate on the device: a marker outside the gap would make the step
   // read and write outside the field and charge arrays
   unsigned int* scratch = c->d_scratch;
   unsigned int bad_init[4] = {0xFFFFFFFFu, 0u, 0u, 0u};
   CK(cudaMemcpyAsync(scratch, bad_init, 16, cudaMemcpyHostToDevice, c->stream), "load");
-  launch_validate(d, (uint32_t)n, P.n_cells, P.charge_shift, scratch,
+  launch_validate(c->fp64, d, (uint32_t)n, P.n_cells, P.charge_shift, scratch,
                   reinterpret_cast<unsigned long long*>(scratch + 2), c->stream);
   CK(cudaGetLastError(), "validate");
   unsigned int res[4];
@@ -833,12 +904,26 @@ extern "C" {
 
 int slpic_load_particles(slpic_ctx* c, int inst, int species, const slpic_soa_f32* host,
                          int64_t n, uint32_t next_id) {
-  return load_common(c, inst, species, host, n, next_id, cudaMemcpyHostToDevice);
+  return load_common(c, inst, species, arrays_of(host), n, next_id, cudaMemcpyHostToDevice);
 }
 
 int slpic_load_particles_device(slpic_ctx* c, int inst, int species, const slpic_soa_f32* dev,
                                 int64_t n, uint32_t next_id) {
-  return load_common(c, inst, species, dev, n, next_id, cudaMemcpyDeviceToDevice);
+  return load_common(c, inst, species, arrays_of(dev), n, next_id, cudaMemcpyDeviceToDevice);
+}
+
+int slpic_load_particles_f64(slpic_ctx* c, int inst, int species, const slpic_soa_f64* host,
+                             int64_t n, uint32_t next_id) {
+  return load_common(c, inst, species, arrays_of(host), n, next_id, cudaMemcpyHostToDevice);
+}
+
+int slpic_set_precision(slpic_ctx* c, int bits) {
+  if (!c || (bits != 32 && bits != 64))
+    return fail(c, SLPIC_ERR_INVALID_ARG, "precision must be 32 or 64");
+  if (c->committed && (bits == 64) != (c->fp64 != 0))
+    return fail(c, SLPIC_ERR_STATE, "the precision cannot change after the first use");
+  c->fp64 = bits == 64 ? 1 : 0;
+  return SLPIC_OK;
 }
 
 int slpic_reset_counters(slpic_ctx* c, int inst) {
@@ -926,10 +1011,13 @@ int slpic_count(slpic_ctx* c, int inst, int species, int64_t* n) {
   return rc;
 }
 
-int slpic_read_particles(slpic_ctx* c, int inst, int species, const slpic_soa_f32* host,
-                         int64_t capacity, int64_t* n_out) {
+namespace {
+
+int read_common(slpic_ctx* c, int inst, int species, const Arrays& host, int64_t capacity,
+                int64_t* n_out) {
   if (!valid_inst(c, inst) || (species != 0 && species != 1) || !n_out || capacity < 0)
     return fail(c, SLPIC_ERR_INVALID_ARG, "bad arguments");
+  if (int rc = precision_check(c, host.fp64)) return rc;
   if (int rc = prepare(c)) return rc;
   int rc = sync(c);
   SpeciesState st;
@@ -939,26 +1027,38 @@ int slpic_read_particles(slpic_ctx* c, int inst, int species, const slpic_soa_f3
     return fail(c, SLPIC_ERR_INVALID_ARG, "host buffers hold %lld markers, %u live",
                 (long long)capacity, st.n_live);
   if (st.n_live > 0) {
-    if (int r3 = host_soa_check(c, host)) return r3;
+    if (int r3 = arrays_check(c, host)) return r3;
     const SpeciesDev& S = c->h_inst[inst].sp[species];
     const SoA& d = S.buf[st.cur];
     std::vector<uint32_t> fill(st.n_tiles);
     CK(cudaMemcpy(fill.data(), S.fill[st.cur], st.n_tiles * 4, cudaMemcpyDeviceToHost), "read");
     const size_t slots = (size_t)st.n_tiles * kTile;
-    std::vector<uint32_t> tmp(slots);
-    void* dst[7] = {host->cell, host->off, host->vx, host->vy, host->vz, host->wj, host->id};
+    std::vector<char> tmp(field_bytes(c, 1, slots));
     const void* srcs[7] = {d.cell, d.off, d.vx, d.vy, d.vz, d.wj, d.id};
     for (int f = 0; f < 7; ++f) {
-      CK(cudaMemcpy(tmp.data(), srcs[f], slots * 4, cudaMemcpyDeviceToHost), "read");
-      uint32_t* out = static_cast<uint32_t*>(dst[f]);
+      const size_t esz = field_bytes(c, f, 1);
+      CK(cudaMemcpy(tmp.data(), srcs[f], slots * esz, cudaMemcpyDeviceToHost), "read");
+      char* out = static_cast<char*>(host.f[f]);
       size_t o = 0;
       for (uint32_t k = 0; k < st.n_tiles; ++k) {
-        std::memcpy(out + o, tmp.data() + (size_t)k * kTile, (size_t)fill[k] * 4);
+        std::memcpy(out + o * esz, tmp.data() + (size_t)k * kTile * esz, (size_t)fill[k] * esz);
         o += fill[k];
       }
     }
   }
   return rc;
+}
+
+}  // namespace
+
+int slpic_read_particles(slpic_ctx* c, int inst, int species, const slpic_soa_f32* host,
+                         int64_t capacity, int64_t* n_out) {
+  return read_common(c, inst, species, arrays_of(host), capacity, n_out);
+}
+
+int slpic_read_particles_f64(slpic_ctx* c, int inst, int species, const slpic_soa_f64* host,
+                             int64_t capacity, int64_t* n_out) {
+  return read_common(c, inst, species, arrays_of(host), capacity, n_out);
 }
 
 int slpic_read_charge(slpic_ctx* c, int inst, int species, int64_t* host, int64_t n) {
@@ -1055,7 +1155,7 @@ int slpic_read_gain(slpic_ctx* c, int inst, double* G) {
   InstState is;
   CK(cudaMemcpy(&is, c->d_istate + inst, sizeof is, cudaMemcpyDeviceToHost), "gain");
   const InstDev& P = c->h_inst[inst];
-  const double seed = (double)is.w_seed / (double)P.wscale;
+  const double seed = (double)is.w_seed / P.c64.wscale;
   *G = seed > 0 ? c->hi[inst].gamma * t.w_cath_ion_gen0 / seed : 0.0;
   return rc;
 }
@@ -1227,8 +1327,8 @@ extern "C" int slpic_paschen_bisect(slpic_ctx* c, const slpic_paschen_spec* ps, 
         if ((rc = slpic_set_emission(c, i, 0.0))) break;
         if ((rc = slpic_set_seed(c, i, seed0[i] + 0x9E3779B97F4A7C15ull * (uint64_t)round)))
           break;
-        if ((rc = load_common(c, i, kIon, nullptr, 0, 0, cudaMemcpyHostToDevice))) break;
-        if ((rc = load_common(c, i, kElectron, nullptr, 0, 0, cudaMemcpyHostToDevice))) break;
+        if ((rc = load_common(c, i, kIon, Arrays{{}, c->fp64}, 0, 0, cudaMemcpyHostToDevice))) break;
+        if ((rc = load_common(c, i, kElectron, Arrays{{}, c->fp64}, 0, 0, cudaMemcpyHostToDevice))) break;
         if ((rc = slpic_seed(c, i, kElectron, ps->n_seed, SLPIC_SEED_CATHODE, ps->e0, 0.0, 0.0,
                              1.0)))
           break;
@@ -1255,8 +1355,8 @@ extern "C" int slpic_paschen_bisect(slpic_ctx* c, const slpic_paschen_spec* ps, 
         // outgrow the stores in the next chunk
         if ((int64_t)ne > thr_e[i] || (int64_t)ni >= thr_i[i]) {
           saturated[i] = 1;
-          rc = load_common(c, i, kIon, nullptr, 0, 0, cudaMemcpyHostToDevice);
-          if (!rc) rc = load_common(c, i, kElectron, nullptr, 0, 0, cudaMemcpyHostToDevice);
+          rc = load_common(c, i, kIon, Arrays{{}, c->fp64}, 0, 0, cudaMemcpyHostToDevice);
+          if (!rc) rc = load_common(c, i, kElectron, Arrays{{}, c->fp64}, 0, 0, cudaMemcpyHostToDevice);
           continue;
         }
         if (ne || ni) live = true;
@@ -1277,7 +1377,7 @@ extern "C" int slpic_paschen_bisect(slpic_ctx* c, const slpic_paschen_spec* ps, 
         rc = fail(c, SLPIC_ERR_CUDA, "paschen: reading the seeded weight");
         break;
       }
-      const double w_seed = (double)is.w_seed / (double)c->h_inst[i].wscale;
+      const double w_seed = (double)is.w_seed / c->h_inst[i].c64.wscale;
       G[i] = w_seed > 0 ? gam[i] * t.w_cath_ion_gen0 / w_seed : 0.0;
     }
     if (rc) break;

@@ -28,15 +28,17 @@ namespace {
 constexpr int kCollThreads = 256;
 
 // Interpolated cumulative cross sections at eps (linear between the nodes of
-// the octave-uniform grid, held constant outside it).
+// the octave-uniform grid, held constant outside it).  The node index and the
+// fraction come exactly from the exponent and mantissa bits of eps.
 __device__ __forceinline__ void xsec(const InstDev& P, float eps, float& s1, float& s2,
                                      float& s3) {
+  const StepConsts<float>& K = P.c32;
   int j;
   float t;
-  if (!(eps >= P.e_lo)) {
+  if (!(eps >= K.e_lo)) {
     j = 0;
     t = 0.0f;
-  } else if (eps >= P.e_hi) {
+  } else if (eps >= K.e_hi) {
     j = P.tab_nodes - 1;
     t = 0.0f;
   } else {
@@ -55,88 +57,117 @@ __device__ __forceinline__ void xsec(const InstDev& P, float eps, float& s1, flo
   s3 = a.z + t * (c.z - a.z);
 }
 
-__device__ __forceinline__ void deposit(unsigned long long* rho, int cell, float off,
-                                        long long Q) {
+__device__ __forceinline__ void xsec(const InstDev& P, double eps, double& s1, double& s2,
+                                     double& s3) {
+  const StepConsts<double>& K = P.c64;
+  int j;
+  double t;
+  if (!(eps >= K.e_lo)) {
+    j = 0;
+    t = 0.0;
+  } else if (eps >= K.e_hi) {
+    j = P.tab_nodes - 1;
+    t = 0.0;
+  } else {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(eps);
+    const int octave = (int)(b >> 52) - 1023 - P.tab_lo_exp2;
+    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+    const int sh = 52 - P.tab_log2_sub;
+    j = (octave << P.tab_log2_sub) + (int)(mant >> sh);
+    const double scale = __longlong_as_double((long long)(1023 - sh) << 52);  // 2^-sh
+    t = (double)(mant & ((1ull << sh) - 1ull)) * scale;
+  }
+  const TabNode64 a = P.table64[j];
+  const TabNode64 c = P.table64[j + 1];
+  s1 = a.s1 + t * (c.s1 - a.s1);
+  s2 = a.s2 + t * (c.s2 - a.s2);
+  s3 = a.s3 + t * (c.s3 - a.s3);
+}
+
+template <typename R>
+__device__ __forceinline__ void deposit(unsigned long long* rho, int cell, R off, long long Q) {
   const long long right = right_share(Q, off);
   const long long left = Q - right;
   if (left) atomicAdd(rho + cell, (unsigned long long)left);
   if (right) atomicAdd(rho + cell + 1, (unsigned long long)right);
 }
 
+template <typename R>
 struct Velocity {
-  float vx, vy, vz;
+  R vx, vy, vz;
 };
 
 // Choose the process with u[1] against the cumulative rates and scatter
 // (u[0] is unused: the candidate test drew from Philox2x32).
 // Returns the new velocity; *proc_out = 0 elastic, 1 excitation,
 // 2 ionization, 3 null (velocity unchanged).
-__device__ Velocity collide(const InstDev& P, float kv, float vlim, float vx, float vy,
-                            float vz, float v1, float s1, uint4 rr, uint32_t id, uint32_t step,
-                            float wj, unsigned long long* acc, float* e_sec_out,
-                            int* proc_out) {
-  float u[4];
-  uniform4(rr, u);
+template <typename R>
+__device__ Velocity<R> collide(const InstDev& P, R kv, R vlim, R vx, R vy, R vz, R v1, R s1,
+                               uint4 rr, uint32_t id, uint32_t step, R wj,
+                               unsigned long long* acc, R* e_sec_out, int* proc_out) {
+  const StepConsts<R>& K = consts<R>(P);
+  R u[4];
+  uniform4<R>(rr, u);
   atomicAdd(&acc[ACC_CAND], 1ull);
-  float vb = v1 > vlim ? vlim : v1;
-  if (vb > P.vb_cap) {
-    vb = P.vb_cap;
+  R vb = v1 > vlim ? vlim : v1;
+  if (vb > K.vb_cap) {
+    vb = K.vb_cap;
     atomicAdd(&acc[ACC_MAJ], 1ull);
   }
-  const float c = P.ndt * vb;
-  const float eps = s1 * P.K_E;
-  float x1, x2, x3;
+  const R c = K.ndt * vb;
+  const R eps = s1 * K.K_E;
+  R x1, x2, x3;
   xsec(P, eps, x1, x2, x3);
-  const float rsel = u[1] * P.P0;
+  const R rsel = u[1] * K.P0;
   int proc = 3;
   if (rsel < c * x1) proc = 0;
   else if (rsel < c * x2) proc = 1;
   else if (rsel < c * x3) proc = 2;
   *proc_out = proc;
-  Velocity o = {vx, vy, vz};
+  Velocity<R> o = {vx, vy, vz};
   if (proc == 3) return o;
   atomicAdd(&acc[ACC_COLL0 + proc], 1ull);
   if (proc == 0) {
     // Vahedi-Surendra: cos chi = (2 + eps - 2 (1 + eps)^u) / eps, with
     // 1 - cos chi and 1 + cos chi each formed without cancellation so that
     // sin chi keeps its relative precision at both ends
-    const float L = log1pf(eps);
-    const float em = expm1f(u[2] * L);
-    const float ep = -expm1f(-(1.0f - u[2]) * L);
-    float omc = (em + em) / eps;
-    float opc = ((1.0f + eps) * (ep + ep)) / eps;
-    omc = fminf(2.0f, fmaxf(0.0f, omc));
-    opc = fminf(2.0f, fmaxf(0.0f, opc));
-    const float cc = omc <= 1.0f ? 1.0f - omc : opc - 1.0f;
-    const float sc = sqrtf(omc * opc);
-    const float ph = P.two_pi * u[3];
-    const float cp = cosf(ph), sn = sinf(ph);
-    const float e_new = eps * (1.0f - P.R2 * omc);
-    float ux = vx / v1, uy = vy / v1, uz = vz / v1;
+    const R L = r_log1p(eps);
+    const R em = r_expm1(u[2] * L);
+    const R ep = -r_expm1(-((R)1 - u[2]) * L);
+    R omc = (em + em) / eps;
+    R opc = (((R)1 + eps) * (ep + ep)) / eps;
+    omc = r_min((R)2, r_max((R)0, omc));
+    opc = r_min((R)2, r_max((R)0, opc));
+    const R cc = omc <= (R)1 ? (R)1 - omc : opc - (R)1;
+    const R sc = r_sqrt(omc * opc);
+    const R ph = K.two_pi * u[3];
+    const R cp = r_cos(ph), sn = r_sin(ph);
+    const R e_new = eps * ((R)1 - K.R2 * omc);
+    R ux = vx / v1, uy = vy / v1, uz = vz / v1;
     rotate(ux, uy, uz, cc, sc, cp, sn);
-    const float vn = sqrtf(e_new * kv);
+    const R vn = r_sqrt(e_new * kv);
     o.vx = vn * ux;
     o.vy = vn * uy;
     o.vz = vn * uz;
   } else if (proc == 1) {
-    float e_new = eps - P.e_ex;
-    if (e_new < 0.0f) {
-      e_new = 0.0f;
+    R e_new = eps - K.e_ex;
+    if (e_new < (R)0) {
+      e_new = (R)0;
       atomicAdd(&acc[ACC_CLAMP], 1ull);
     }
-    isotropic(sqrtf(e_new * kv), u[2], u[3], P.two_pi, o.vx, o.vy, o.vz);
+    isotropic(r_sqrt(e_new * kv), u[2], u[3], K.two_pi, o.vx, o.vy, o.vz);
   } else {
-    float e_av = eps - P.e_io;
-    if (e_av < 0.0f) {
-      e_av = 0.0f;
+    R e_av = eps - K.e_io;
+    if (e_av < (R)0) {
+      e_av = (R)0;
       atomicAdd(&acc[ACC_CLAMP], 1ull);
     }
-    atomicAdd(&acc[ACC_WIONZ], (unsigned long long)fixed_charge(wj, P.charge_shift));
+    atomicAdd(&acc[ACC_WIONZ], (unsigned long long)fixed_charge(wj, K.wscale));
     const uint4 r1 =
         philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u, 1u), P.key0, P.key1);
-    const float es = uniform01(r1.x) * e_av;
-    const float ep = e_av - es;
-    isotropic(sqrtf(ep * kv), u[2], u[3], P.two_pi, o.vx, o.vy, o.vz);
+    const R es = uniform01r<R>(r1.x) * e_av;
+    const R ep = e_av - es;
+    isotropic(r_sqrt(ep * kv), u[2], u[3], K.two_pi, o.vx, o.vy, o.vz);
     *e_sec_out = es;
   }
   return o;
@@ -147,15 +178,16 @@ __device__ Velocity collide(const InstDev& P, float kv, float vlim, float vx, fl
 // secondary gets energy es along an isotropic direction (block 1 of the
 // primary's draws); the ion a gas-temperature Maxwellian (Box-Muller on
 // block 2).
-__device__ void born_pair(const InstDev& P, const SoA& me, const SoA& mi, uint32_t pe,
-                          uint32_t pi, int cell, float off, float wj, uint32_t id,
-                          uint32_t step, float es, uint32_t serial_e, uint32_t serial_i) {
-  const SpeciesDev& SE = P.sp[kElectron];
-  const SpeciesDev& SI = P.sp[kIon];
+template <typename R>
+__device__ void born_pair(const InstDev& P, const SoAT<R>& me, const SoAT<R>& mi, uint32_t pe,
+                          uint32_t pi, int cell, R off, R wj, uint32_t id, uint32_t step, R es,
+                          uint32_t serial_e, uint32_t serial_i) {
+  const StepConsts<R>& K = consts<R>(P);
   const uint32_t gen = id & kGenBit;
   const uint4 r1 = philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u, 1u), P.key0, P.key1);
-  float bx, by, bz;
-  isotropic(sqrtf(es * SE.K_V), uniform01(r1.y), uniform01(r1.z), P.two_pi, bx, by, bz);
+  R bx, by, bz;
+  isotropic(r_sqrt(es * K.K_V[kElectron]), uniform01r<R>(r1.y), uniform01r<R>(r1.z), K.two_pi,
+            bx, by, bz);
   me.cell[pe] = cell;
   me.off[pe] = off;
   me.vx[pe] = bx;
@@ -164,17 +196,17 @@ __device__ void born_pair(const InstDev& P, const SoA& me, const SoA& mi, uint32
   me.wj[pe] = wj;
   me.id[pe] = gen | (serial_e & kSerialMask);
   deposit(P.rho_acc[kElectron], cell, off,
-          fixed_charge(beta_of(sqrtf(bx * bx + by * by + bz * bz), SE.vlim) * wj,
-                       P.charge_shift));
+          fixed_charge(beta_of(r_sqrt(bx * bx + by * by + bz * bz), K.vlim[kElectron]) * wj,
+                       K.wscale));
   const uint4 r2 = philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u, 2u), P.key0, P.key1);
-  float g[4];
-  uniform4(r2, g);
-  const float rr1 = sqrtf(-2.0f * logf(g[0]));
-  const float rr2 = sqrtf(-2.0f * logf(g[2]));
-  const float a1 = P.two_pi * g[1], a2 = P.two_pi * g[3];
-  const float ix = P.sigT_ion * (rr1 * cosf(a1));
-  const float iy = P.sigT_ion * (rr1 * sinf(a1));
-  const float iz = P.sigT_ion * (rr2 * cosf(a2));
+  R g[4];
+  uniform4<R>(r2, g);
+  const R rr1 = r_sqrt((R)-2 * r_log(g[0]));
+  const R rr2 = r_sqrt((R)-2 * r_log(g[2]));
+  const R a1 = K.two_pi * g[1], a2 = K.two_pi * g[3];
+  const R ix = K.sigT_ion * (rr1 * r_cos(a1));
+  const R iy = K.sigT_ion * (rr1 * r_sin(a1));
+  const R iz = K.sigT_ion * (rr2 * r_cos(a2));
   mi.cell[pi] = cell;
   mi.off[pi] = off;
   mi.vx[pi] = ix;
@@ -183,8 +215,8 @@ __device__ void born_pair(const InstDev& P, const SoA& me, const SoA& mi, uint32
   mi.wj[pi] = wj;
   mi.id[pi] = gen | (serial_i & kSerialMask);
   deposit(P.rho_acc[kIon], cell, off,
-          fixed_charge(beta_of(sqrtf(ix * ix + iy * iy + iz * iz), SI.vlim) * wj,
-                       P.charge_shift));
+          fixed_charge(beta_of(r_sqrt(ix * ix + iy * iy + iz * iz), K.vlim[kIon]) * wj,
+                       K.wscale));
 }
 
 // Slot after the last live marker of a store (the particle kernel has
@@ -194,9 +226,9 @@ __device__ __forceinline__ uint32_t tail_slot(const SpeciesDev& S, const Species
                     : 0u;
 }
 
-__device__ __forceinline__ void write_marker(const SoA& d, size_t o, int cell, float off,
-                                             float vx, float vy, float vz, float wj,
-                                             uint32_t id) {
+template <typename R>
+__device__ __forceinline__ void write_marker(const SoAT<R>& d, size_t o, int cell, R off, R vx,
+                                             R vy, R vz, R wj, uint32_t id) {
   d.cell[o] = cell;
   d.off[o] = off;
   d.vx[o] = vx;
@@ -208,6 +240,7 @@ __device__ __forceinline__ void write_marker(const SoA& d, size_t o, int cell, f
 
 }  // namespace
 
+template <typename R>
 __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
   __shared__ unsigned long long s_acc[ACC_COUNT];
   __shared__ uint32_t s_births[kCollWarps];
@@ -259,8 +292,10 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
     // this warp's tiles: kCollWarpTiles consecutive ones, tile kw + j at lane j
     const uint32_t kw = (ion_chunk ? local - e_chunks : local) * kCollChunkTiles +
                         warp * kCollWarpTiles;
-    const SoA me = E.buf[se.cur];
-    const float kv = E.K_V, vlim = E.vlim;
+    const SoAT<R> me = soa_as<R>(E.buf[se.cur]);
+    const StepConsts<R>& K = consts<R>(P);
+    const R kv = K.K_V[kElectron], vlim = K.vlim[kElectron];
+    R* esec = reinterpret_cast<R*>(E.esec);
     // events of the tiles (electron chunks: queued candidates; ion chunks:
     // electrons emitted at the cathode) and their exclusive prefix: the
     // warp's events are numbered in (tile, slot) order
@@ -300,17 +335,17 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
           const uint32_t a = E.cand[base + q];
           const size_t o = base + a;
           const int cell = me.cell[o];
-          const float off = me.off[o], wj = me.wj[o];
+          const R off = me.off[o], wj = me.wj[o];
           const uint32_t id = me.id[o];
-          float vx = me.vx[o], vy = me.vy[o], vz = me.vz[o];
-          const float s1 = vx * vx + vy * vy + vz * vz;
-          const float v1 = sqrtf(s1);
+          R vx = me.vx[o], vy = me.vy[o], vz = me.vz[o];
+          const R s1 = vx * vx + vy * vy + vz * vz;
+          const R v1 = r_sqrt(s1);
           const uint4 rr =
               philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u, 0u), P.key0, P.key1);
           int proc;
-          float es = 0.0f;
-          const Velocity nv =
-              collide(P, kv, vlim, vx, vy, vz, v1, s1, rr, id, step, wj, s_acc, &es, &proc);
+          R es = (R)0;
+          const Velocity<R> nv =
+              collide<R>(P, kv, vlim, vx, vy, vz, v1, s1, rr, id, step, wj, s_acc, &es, &proc);
           if (proc < 3) {
             vx = nv.vx;
             vy = nv.vy;
@@ -321,12 +356,12 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
             if (proc == 2) {
               ionized = true;
               E.cand[base + q] = (uint16_t)(a | 0x8000u);  // mark for pass 2
-              E.esec[base + q] = es;
+              esec[base + q] = es;
             }
           }
           deposit(P.rho_acc[kElectron], cell, off,
-                  fixed_charge(beta_of(sqrtf(vx * vx + vy * vy + vz * vz), vlim) * wj,
-                               P.charge_shift));
+                  fixed_charge(beta_of(r_sqrt(vx * vx + vy * vy + vz * vz), vlim) * wj,
+                               K.wscale));
         }
         warp_births += __popc(__ballot_sync(0xFFFFFFFFu, ionized));
       }
@@ -351,7 +386,7 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
     if (warp_births) {
       const uint32_t app_e = tail_slot(E, se), app_i = tail_slot(I, si);
       const uint32_t cap_e = E.cap_tiles * (uint32_t)kTile, cap_i = I.cap_tiles * (uint32_t)kTile;
-      const SoA mi = I.buf[si.cur];
+      const SoAT<R> mi = soa_as<R>(I.buf[si.cur]);
       if (!ion_chunk) {
         uint32_t ranked = 0;
         for (uint32_t c0 = 0; c0 < total; c0 += 32) {
@@ -369,15 +404,15 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
             if (pe >= cap_e || pi >= cap_i) {
               atomicCAS(&ctrl->error, 0, kErrCapacity);
             } else {
-              born_pair(P, me, mi, pe, pi, me.cell[o], me.off[o], me.wj[o], me.id[o], step,
-                        E.esec[base + q], se.next_id + rank, si.next_id + rank);
+              born_pair<R>(P, me, mi, pe, pi, me.cell[o], me.off[o], me.wj[o], me.id[o], step,
+                           esec[base + q], se.next_id + rank, si.next_id + rank);
             }
           }
           ranked += __popc(b);
         }
       } else {
         // electrons emitted at the cathode, after every ionization electron
-        const SoA& sb = E.stage_b;
+        const SoAT<R> sb = soa_as<R>(E.stage_b);
         for (uint32_t c0 = 0; c0 < total; c0 += 32) {
           const uint32_t ce = c0 + lane;
           uint32_t q;
@@ -402,7 +437,8 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
 }
 
 void launch_collide(const DeviceRefs& r, int grid, cudaStream_t s) {
-  k_collide<<<grid, kCollThreads, 0, s>>>(r);
+  if (r.fp64) k_collide<double><<<grid, kCollThreads, 0, s>>>(r);
+  else k_collide<float><<<grid, kCollThreads, 0, s>>>(r);
 }
 
 static_assert(kCollThreads == 32 * kCollWarps, "kCollWarps warps per chunk");

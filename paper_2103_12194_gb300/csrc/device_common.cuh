@@ -55,44 +55,111 @@ __device__ __forceinline__ float uniform01(uint32_t x) {
   return (__uint2float_rn(x >> 9) + 0.5f) * 1.1920928955078125e-07f;
 }
 
-__device__ __forceinline__ void uniform4(uint4 r, float u[4]) {
-  u[0] = uniform01(r.x);
-  u[1] = uniform01(r.y);
-  u[2] = uniform01(r.z);
-  u[3] = uniform01(r.w);
+// The step's constants and node field in the arithmetic type R.
+template <typename R>
+__device__ __forceinline__ const StepConsts<R>& consts(const InstDev& P);
+template <>
+__device__ __forceinline__ const StepConsts<float>& consts<float>(const InstDev& P) {
+  return P.c32;
+}
+template <>
+__device__ __forceinline__ const StepConsts<double>& consts<double>(const InstDev& P) {
+  return P.c64;
+}
+template <typename R>
+__device__ __forceinline__ const R* node_field(const InstDev& P);
+template <>
+__device__ __forceinline__ const float* node_field<float>(const InstDev& P) {
+  return P.E32;
+}
+template <>
+__device__ __forceinline__ const double* node_field<double>(const InstDev& P) {
+  return P.E64;
+}
+
+// Elementary functions by precision (the library's own float and double
+// versions; nothing here is fused or approximated).
+__device__ __forceinline__ float r_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double r_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float r_floor(float x) { return floorf(x); }
+__device__ __forceinline__ double r_floor(double x) { return floor(x); }
+__device__ __forceinline__ float r_min(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double r_min(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float r_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double r_max(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float r_abs(float x) { return fabsf(x); }
+__device__ __forceinline__ double r_abs(double x) { return fabs(x); }
+__device__ __forceinline__ float r_log(float x) { return logf(x); }
+__device__ __forceinline__ double r_log(double x) { return log(x); }
+__device__ __forceinline__ float r_exp(float x) { return expf(x); }
+__device__ __forceinline__ double r_exp(double x) { return exp(x); }
+__device__ __forceinline__ float r_log1p(float x) { return log1pf(x); }
+__device__ __forceinline__ double r_log1p(double x) { return log1p(x); }
+__device__ __forceinline__ float r_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double r_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ float r_cos(float x) { return cosf(x); }
+__device__ __forceinline__ double r_cos(double x) { return cos(x); }
+__device__ __forceinline__ float r_sin(float x) { return sinf(x); }
+__device__ __forceinline__ double r_sin(double x) { return sin(x); }
+
+// Largest value of R below 1.
+template <typename R>
+__device__ __forceinline__ R nextafter_below_one();
+template <>
+__device__ __forceinline__ float nextafter_below_one<float>() {
+  return __int_as_float(0x3F7FFFFF);
+}
+template <>
+__device__ __forceinline__ double nextafter_below_one<double>() {
+  return __longlong_as_double(0x3FEFFFFFFFFFFFFFll);
+}
+
+// The same uniform in R (exact in both types).
+template <typename R>
+__device__ __forceinline__ R uniform01r(uint32_t x) {
+  return (R)uniform01(x);
+}
+
+template <typename R>
+__device__ __forceinline__ void uniform4(uint4 r, R u[4]) {
+  u[0] = uniform01r<R>(r.x);
+  u[1] = uniform01r<R>(r.y);
+  u[2] = uniform01r<R>(r.z);
+  u[3] = uniform01r<R>(r.w);
 }
 
 // beta(v) = min(1, v_lim / v), Eq. betaAbrupt; v_lim = +inf gives 1.  Equal,
 // bit for bit, to (v > v_lim ? v_lim / v : 1): when v <= v_lim the rounded
 // quotient is >= 1 (rounding is monotone), and v = 0 gives +inf.
-__device__ __forceinline__ float beta_of(float v, float vlim) {
-  return fminf(1.0f, vlim / v);
+template <typename R>
+__device__ __forceinline__ R beta_of(R v, R vlim) {
+  return r_min((R)1, vlim / v);
 }
 
 // Direction with cos(theta) = 1 - 2 ua about x and azimuth 2 pi ub.
-__device__ __forceinline__ void isotropic(float speed, float ua, float ub, float two_pi,
-                                          float& vx, float& vy, float& vz) {
-  const float ct = 1.0f - 2.0f * ua;
-  const float st = sqrtf(fmaxf(0.0f, (1.0f - ct) * (1.0f + ct)));
-  const float ph = two_pi * ub;
+template <typename R>
+__device__ __forceinline__ void isotropic(R speed, R ua, R ub, R two_pi, R& vx, R& vy, R& vz) {
+  const R ct = (R)1 - (R)2 * ua;
+  const R st = r_sqrt(r_max((R)0, ((R)1 - ct) * ((R)1 + ct)));
+  const R ph = two_pi * ub;
   vx = speed * ct;
-  vy = speed * (st * cosf(ph));
-  vz = speed * (st * sinf(ph));
+  vy = speed * (st * r_cos(ph));
+  vz = speed * (st * r_sin(ph));
 }
 
 // Turn the unit vector u by polar angle chi (cos cc, sin sc) and azimuth
 // (cos cp, sin sp) about itself; perpendicular frame from the x axis, or the
 // z axis when |ux| > 0.99.
-__device__ __forceinline__ void rotate(float& ux, float& uy, float& uz, float cc, float sc,
-                                       float cp, float sp) {
-  float nx, ny, nz;
-  if (fabsf(ux) <= 0.99f) {
-    const float w = sqrtf((1.0f - ux) * (1.0f + ux));
+template <typename R>
+__device__ __forceinline__ void rotate(R& ux, R& uy, R& uz, R cc, R sc, R cp, R sp) {
+  R nx, ny, nz;
+  if (r_abs(ux) <= (R)0.99) {
+    const R w = r_sqrt(((R)1 - ux) * ((R)1 + ux));
     nx = ux * cc + sc * (cp * w);
     ny = uy * cc + sc * ((uz * sp - ux * (uy * cp)) / w);
     nz = uz * cc - sc * ((uy * sp + ux * (uz * cp)) / w);
   } else {
-    const float w = sqrtf((1.0f - uz) * (1.0f + uz));
+    const R w = r_sqrt(((R)1 - uz) * ((R)1 + uz));
     nx = ux * cc + sc * ((uy * sp - uz * (ux * cp)) / w);
     ny = uy * cc - sc * ((ux * sp + uz * (uy * cp)) / w);
     nz = uz * cc + sc * (cp * w);
@@ -102,35 +169,15 @@ __device__ __forceinline__ void rotate(float& ux, float& uy, float& uz, float cc
   uz = nz;
 }
 
-// Fixed-point charge of a marker: round(w 2^shift) to nearest, ties to even
-// (the value llrint gives for w * 2^shift), for a finite w >= 0 whose result
-// stays below 2^39.  Integer operations only: the float is split into its
-// significand and exponent and shifted.
-__device__ __forceinline__ long long fixed_charge(float w, int shift) {
-  const uint32_t b = __float_as_uint(w);
-  const int e = (int)(b >> 23);
-  uint32_t m = b & 0x7FFFFFu;
-  int s;
-  if (e == 0) {
-    s = shift - 149;  // subnormal: w = m 2^-149
-  } else {
-    m |= 0x800000u;   // w = m 2^(e - 150)
-    s = e - 150 + shift;
-  }
-  if (s >= 0) return (long long)m << s;
-  const int t = -s;
-  if (t >= 25) return 0;  // m 2^-t < 1/2
-  const uint32_t q = m >> t;
-  const uint32_t rem = m & ((1u << t) - 1u);
-  const uint32_t half = 1u << (t - 1);
-  return (long long)(q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u));
-}
-
-// The same value as fixed_charge(w, shift) from the hardware conversion, for
-// wscale = 2^shift: w * 2^shift is exact in float (a power-of-two scaling that
-// stays in range), and cvt.rni rounds it to the nearest integer, ties to even.
-__device__ __forceinline__ long long fixed_charge_scaled(float w, float wscale) {
+// Fixed-point charge of a marker: round(w 2^shift) to the nearest integer,
+// ties to even (the value llrint gives), for wscale = 2^shift: w * 2^shift is
+// exact in either type (a power-of-two scaling that stays in range) and the
+// conversion rounds it once.
+__device__ __forceinline__ long long fixed_charge(float w, float wscale) {
   return __float2ll_rn(w * wscale);
+}
+__device__ __forceinline__ long long fixed_charge(double w, double wscale) {
+  return __double2ll_rn(w * wscale);
 }
 
 // Split a fixed-point charge between the two nodes of the marker's cell with
@@ -138,6 +185,10 @@ __device__ __forceinline__ long long fixed_charge_scaled(float w, float wscale) 
 // f = trunc(offset 2^24).
 __device__ __forceinline__ long long right_share(long long Q, float off) {
   const long long f = (long long)__float2int_rz(off * 16777216.0f);
+  return (Q * f) >> 24;
+}
+__device__ __forceinline__ long long right_share(long long Q, double off) {
+  const long long f = (long long)__double2int_rz(off * 16777216.0);
   return (Q * f) >> 24;
 }
 

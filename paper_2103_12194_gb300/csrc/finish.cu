@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode) 
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned long long* q = s_acc;
-    const double unit = 1.0 / (double)P.wscale;
+    const double unit = 1.0 / P.c64.wscale;
     TallyRec& t = s_rec;
     t.step = is.step;
     t.n_live[0] = r.sstate[inst * 2].n_live;
@@ -304,6 +304,7 @@ void launch_finish(const DeviceRefs& r, int mode, cudaStream_t s) {
 // live markers keep their order.  The chunk also writes the fills of the
 // repacked store for the tiles with its indices.
 // ---------------------------------------------------------------------------
+template <typename R>
 __global__ void __launch_bounds__(kMoveThreads) k_move(DeviceRefs r) {
   __shared__ uint32_t s_fill[kMoveChunkTiles];
   __shared__ uint32_t s_pre[kMoveChunkTiles];
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(kMoveThreads) k_move(DeviceRefs r) {
     }
     __syncthreads();
     // one warp per tile, in order of the tiles
-    const SoA src = S.buf[x.src], dst = S.buf[x.dst];
+    const SoAT<R> src = soa_as<R>(S.buf[x.src]), dst = soa_as<R>(S.buf[x.dst]);
     for (int j = warp; j < kMoveChunkTiles; j += kMoveThreads / 32) {
       const uint32_t n = s_fill[j];
       const size_t from = (size_t)(k0 + j) * kTile, to = s_pre[j];
@@ -384,62 +385,67 @@ __global__ void __launch_bounds__(kMoveThreads) k_move(DeviceRefs r) {
 }
 
 void launch_move(const DeviceRefs& r, int grid, cudaStream_t s) {
-  k_move<<<grid, kMoveThreads, 0, s>>>(r);
+  if (r.fp64) k_move<double><<<grid, kMoveThreads, 0, s>>>(r);
+  else k_move<float><<<grid, kMoveThreads, 0, s>>>(r);
 }
 
 // ---------------------------------------------------------------------------
 // Seeding: n markers appended at index base = n_live of the species, drawn
 // from Philox with counter (id, 0xFFFFFFFF, inst * 2 + species, block).
 // ---------------------------------------------------------------------------
+template <typename R>
 __global__ void k_seed(DeviceRefs r, int inst, int sp, uint32_t base, uint32_t first_id,
-                       uint32_t n, int mode, float ekin, float elo, float lr, float wj) {
+                       uint32_t n, int mode, double ekin_d, double elo_d, double lr_d,
+                       double wj_d) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const InstDev& P = r.inst[inst];
   const SpeciesDev& S = P.sp[sp];
-  const SoA d = S.buf[r.sstate[inst * 2 + sp].cur];
+  const StepConsts<R>& K = consts<R>(P);
+  const SoAT<R> d = soa_as<R>(S.buf[r.sstate[inst * 2 + sp].cur]);
+  const R ekin = (R)ekin_d, elo = (R)elo_d, lr = (R)lr_d, wj = (R)wj_d;
   const uint32_t id = first_id + i;
-  float u[4];
-  uniform4(philox4x32_10(make_uint4(id, kSeedStep, P.ctr_inst * 2u + (uint32_t)sp, 0u),
-                         P.key0, P.key1),
-           u);
+  R u[4];
+  uniform4<R>(philox4x32_10(make_uint4(id, kSeedStep, P.ctr_inst * 2u + (uint32_t)sp, 0u),
+                            P.key0, P.key1),
+              u);
   int cell = 0;
-  float off = 0.0f, vx = 0.0f, vy = 0.0f, vz = 0.0f;
+  R off = (R)0, vx = (R)0, vy = (R)0, vz = (R)0;
   const int N = P.n_cells;
   if (mode == 0) {
     off = u[0];
-    const float v = sqrtf(ekin * S.K_V);
-    const float ct = u[1];
-    const float st = sqrtf(fmaxf(0.0f, (1.0f - ct) * (1.0f + ct)));
-    const float ph = P.two_pi * u[2];
+    const R v = r_sqrt(ekin * K.K_V[sp]);
+    const R ct = u[1];
+    const R st = r_sqrt(r_max((R)0, ((R)1 - ct) * ((R)1 + ct)));
+    const R ph = K.two_pi * u[2];
     vx = v * ct;
-    vy = v * (st * cosf(ph));
-    vz = v * (st * sinf(ph));
+    vy = v * (st * r_cos(ph));
+    vz = v * (st * r_sin(ph));
   } else if (mode == 2 || mode == 3) {
-    const float p = u[0] * (float)N;
-    const float fl = floorf(p);
+    const R p = u[0] * (R)N;
+    const R fl = r_floor(p);
     cell = (int)fl;
     off = p - fl;
     if (cell >= N) {
       cell = N - 1;
-      off = __int_as_float(0x3F7FFFFF);  // largest float below 1
+      off = nextafter_below_one<R>();
     }
     if (mode == 2) {
-      const float e = elo * expf(u[1] * lr);
-      isotropic(sqrtf(e * S.K_V), u[2], u[3], P.two_pi, vx, vy, vz);
+      const R e = elo * r_exp(u[1] * lr);
+      isotropic(r_sqrt(e * K.K_V[sp]), u[2], u[3], K.two_pi, vx, vy, vz);
     } else {
-      float g[4];
-      uniform4(philox4x32_10(make_uint4(id, kSeedStep, P.ctr_inst * 2u + (uint32_t)sp, 1u),
-                             P.key0, P.key1),
-               g);
+      R g[4];
+      uniform4<R>(philox4x32_10(make_uint4(id, kSeedStep, P.ctr_inst * 2u + (uint32_t)sp, 1u),
+                                P.key0, P.key1),
+                  g);
       // gas-temperature Maxwellian of this species
-      const float sig = ekin;  // sqrt(k T / m), passed in ekin for this mode
-      const float r1 = sqrtf(-2.0f * logf(u[1]));
-      const float r2 = sqrtf(-2.0f * logf(u[3]));
-      const float a1 = P.two_pi * u[2], a2 = P.two_pi * g[0];
-      vx = sig * (r1 * cosf(a1));
-      vy = sig * (r1 * sinf(a1));
-      vz = sig * (r2 * cosf(a2));
+      const R sig = ekin;  // sqrt(k T / m), passed in ekin for this mode
+      const R r1 = r_sqrt((R)-2 * r_log(u[1]));
+      const R r2 = r_sqrt((R)-2 * r_log(u[3]));
+      const R a1 = K.two_pi * u[2], a2 = K.two_pi * g[0];
+      vx = sig * (r1 * r_cos(a1));
+      vy = sig * (r1 * r_sin(a1));
+      vz = sig * (r2 * r_cos(a2));
     }
   }
   const uint32_t o = base + i;
@@ -453,41 +459,51 @@ __global__ void k_seed(DeviceRefs r, int inst, int sp, uint32_t base, uint32_t f
 }
 
 void launch_seed(const DeviceRefs& r, int inst, int species, uint32_t base, uint32_t first_id,
-                 uint32_t n, int mode, float e0, float e_lo, float lr, float wj,
+                 uint32_t n, int mode, double e0, double e_lo, double lr, double wj,
                  cudaStream_t s) {
   if (n == 0) return;
   const int threads = 256;
   const unsigned int grid = (n + threads - 1) / threads;
-  k_seed<<<grid, threads, 0, s>>>(r, inst, species, base, first_id, n, mode, e0, e_lo, lr, wj);
+  if (r.fp64)
+    k_seed<double><<<grid, threads, 0, s>>>(r, inst, species, base, first_id, n, mode, e0, e_lo,
+                                           lr, wj);
+  else
+    k_seed<float><<<grid, threads, 0, s>>>(r, inst, species, base, first_id, n, mode, e0, e_lo,
+                                          lr, wj);
 }
 
 // Check loaded markers (cell in [0, N), offset in [0, 1), finite velocities,
 // non-negative weight below 2^39 charge units); records the smallest bad index in *bad and the
 // fixed-point sum of the weights in *wsum.
-__global__ void k_validate(SoA d, uint32_t n, int N, int shift, unsigned int* bad,
+template <typename R>
+__global__ void k_validate(SoA dv, uint32_t n, int N, int shift, unsigned int* bad,
                            unsigned long long* wsum) {
-  const float wscale = __int_as_float((127 + shift) << 23);  // 2^shift
+  const SoAT<R> d = soa_as<R>(dv);
+  const R wscale = (R)ldexp(1.0, shift);  // 2^shift, exact
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long w = 0;
   if (i < n) {
-    const float o = d.off[i], x = d.vx[i], y = d.vy[i], z = d.vz[i], wj = d.wj[i];
+    const R o = d.off[i], x = d.vx[i], y = d.vy[i], z = d.vz[i], wj = d.wj[i];
     const int c = d.cell[i];
     // the fixed-point weight must stay below 2^39 units so that the 24-bit
     // linear split of the deposit cannot overflow 64 bits
-    const bool ok = c >= 0 && c < N && o >= 0.0f && o < 1.0f && isfinite(x) && isfinite(y) &&
-                    isfinite(z) && wj >= 0.0f && wj * wscale < 549755813888.0f;
+    const bool ok = c >= 0 && c < N && o >= (R)0 && o < (R)1 && isfinite(x) && isfinite(y) &&
+                    isfinite(z) && wj >= (R)0 && wj * wscale < (R)549755813888.0;
     if (!ok) atomicMin(bad, i);
-    else w = (unsigned long long)fixed_charge(wj, shift);
+    else w = (unsigned long long)fixed_charge(wj, wscale);
   }
   for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xFFFFFFFFu, w, o);
   if ((threadIdx.x & 31) == 0 && w) atomicAdd(wsum, w);
 }
 
-void launch_validate(const SoA& d, uint32_t n, int N, int shift, unsigned int* bad,
+void launch_validate(int fp64, const SoA& d, uint32_t n, int N, int shift, unsigned int* bad,
                      unsigned long long* wsum, cudaStream_t s) {
   if (n == 0) return;
   const int threads = 256;
-  k_validate<<<(n + threads - 1) / threads, threads, 0, s>>>(d, n, N, shift, bad, wsum);
+  if (fp64)
+    k_validate<double><<<(n + threads - 1) / threads, threads, 0, s>>>(d, n, N, shift, bad, wsum);
+  else
+    k_validate<float><<<(n + threads - 1) / threads, threads, 0, s>>>(d, n, N, shift, bad, wsum);
 }
 
 __global__ void k_philox(uint32_t k0, uint32_t k1, const uint4* ctr, uint4* out, long long n) {

@@ -122,30 +122,50 @@ __device__ __forceinline__ WarpTile tile_of(const DeviceRefs& r, unsigned int q,
   return t;
 }
 
+// Views of a tile's stage: cell and id, then the five real streams.
+template <typename R>
+struct Stage {
+  int32_t* cell;
+  uint32_t* id;
+  R* f[5];  // off, vx, vy, vz, w_j
+  __device__ __forceinline__ explicit Stage(unsigned char* base) {
+    cell = reinterpret_cast<int32_t*>(base);
+    id = reinterpret_cast<uint32_t*>(base + kTile * 4);
+    R* rr = reinterpret_cast<R*>(base + kTile * 8);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) f[q] = rr + q * kTile;
+  }
+};
+
 // Start the bulk loads of tile t into `stage` (lane 0).
-__device__ __forceinline__ void load_tile(const DeviceRefs& r, const WarpTile& t, float* stage,
-                                          uint64_t* bar) {
+template <typename R>
+__device__ __forceinline__ void load_tile(const DeviceRefs& r, const WarpTile& t,
+                                          unsigned char* stage, uint64_t* bar) {
   const SpeciesDev& S = r.inst[t.sseg >> 1].sp[t.sseg & 1];
-  const SoA in = S.buf[r.sstate[t.sseg].cur];
+  const SoAT<R> in = soa_as<R>(S.buf[r.sstate[t.sseg].cur]);
   const size_t base = (size_t)t.k * kTile;
-  const uint32_t bytes = ((t.fill + 3u) & ~3u) * 4u;
+  const uint32_t n4 = (t.fill + 3u) & ~3u;  // 16-byte multiples
+  const uint32_t b4 = n4 * 4u, br = n4 * (uint32_t)sizeof(R);
+  Stage<R> st(stage);
   fence_proxy_async_smem();
-  mbar_arrive_expect_tx(bar, 7u * bytes);
-  bulk_load(stage + 0 * kTile, in.cell + base, bytes, bar);
-  bulk_load(stage + 1 * kTile, in.off + base, bytes, bar);
-  bulk_load(stage + 2 * kTile, in.vx + base, bytes, bar);
-  bulk_load(stage + 3 * kTile, in.vy + base, bytes, bar);
-  bulk_load(stage + 4 * kTile, in.vz + base, bytes, bar);
-  bulk_load(stage + 5 * kTile, in.wj + base, bytes, bar);
-  bulk_load(stage + 6 * kTile, in.id + base, bytes, bar);
+  mbar_arrive_expect_tx(bar, 2u * b4 + 5u * br);
+  bulk_load(st.cell, in.cell + base, b4, bar);
+  bulk_load(st.id, in.id + base, b4, bar);
+  bulk_load(st.f[0], in.off + base, br, bar);
+  bulk_load(st.f[1], in.vx + base, br, bar);
+  bulk_load(st.f[2], in.vy + base, br, bar);
+  bulk_load(st.f[3], in.vz + base, br, bar);
+  bulk_load(st.f[4], in.wj + base, br, bar);
 }
 
 // A marker left the gap: tally the flux through the electrode (Eq. j); an ion
 // at the cathode emits an electron with probability gamma.  Returns true when
 // an electron is emitted.  Rare; kept out of line.
-__device__ __noinline__ bool absorb(const InstDev& P, int sp, int side, float wj, uint32_t id,
+template <typename R>
+__device__ __noinline__ bool absorb(const InstDev& P, int sp, int side, R wj, uint32_t id,
                                     uint32_t step, unsigned long long* acc) {
-  const long long Qw = fixed_charge(wj, P.charge_shift);
+  const StepConsts<R>& K = consts<R>(P);
+  const long long Qw = fixed_charge(wj, K.wscale);
   atomicAdd(&acc[ACC_NABS + sp * 2 + side], 1ull);
   atomicAdd(&acc[ACC_WABS + sp * 2 + side], (unsigned long long)Qw);
   if (sp != kIon || side != 0) return false;
@@ -153,28 +173,30 @@ __device__ __noinline__ bool absorb(const InstDev& P, int sp, int side, float wj
   if (!(id & kGenBit)) atomicAdd(&acc[ACC_WCATH0], (unsigned long long)Qw);
   const uint4 rr =
       philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u + 1u, 0u), P.key0, P.key1);
-  if (!(uniform01(rr.x) < P.gamma)) return false;
+  if (!(uniform01r<R>(rr.x) < K.gamma)) return false;
   atomicAdd(&acc[ACC_SEE], 1ull);
   atomicAdd(&acc[ACC_WSEE], (unsigned long long)Qw);
   return true;
 }
 
 // Stage an electron emitted at the cathode (x = 0, at rest, the ion's w_j).
-__device__ __noinline__ void stage_emission(const InstDev& P, size_t o, float wj) {
-  const SpeciesDev& SE = P.sp[kElectron];
-  SE.stage_b.cell[o] = 0;
-  SE.stage_b.off[o] = 0.0f;
-  SE.stage_b.vx[o] = 0.0f;
-  SE.stage_b.vy[o] = 0.0f;
-  SE.stage_b.vz[o] = 0.0f;
-  SE.stage_b.wj[o] = wj;
-  SE.stage_b.id[o] = kGenBit;
+template <typename R>
+__device__ __noinline__ void stage_emission(const InstDev& P, size_t o, R wj) {
+  const SoAT<R> sb = soa_as<R>(P.sp[kElectron].stage_b);
+  sb.cell[o] = 0;
+  sb.off[o] = (R)0;
+  sb.vx[o] = (R)0;
+  sb.vy[o] = (R)0;
+  sb.vz[o] = (R)0;
+  sb.wj[o] = wj;
+  sb.id[o] = kGenBit;
   // at rest: beta = 1, all the charge on node 0
-  atomicAdd(P.rho_acc[kElectron], (unsigned long long)fixed_charge(wj, P.charge_shift));
+  atomicAdd(P.rho_acc[kElectron], (unsigned long long)fixed_charge(wj, consts<R>(P).wscale));
 }
 
 }  // namespace
 
+template <typename R>
 __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ uint64_t s_bar[kPushMaxWarps][kPushStages];
@@ -182,9 +204,10 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
   const int W = (int)(blockDim.x >> 5);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lanemask_lt = (1u << lane) - 1u;
-  float* stages = reinterpret_cast<float*>(smem_raw) + (size_t)warp * kPushStages * kStageWords;
-  unsigned long long* s_rho = reinterpret_cast<unsigned long long*>(
-      smem_raw + (size_t)W * kPushStages * kStageWords * 4);
+  constexpr int kSB = stage_bytes<R>();
+  unsigned char* stages = smem_raw + (size_t)warp * kPushStages * kSB;
+  unsigned long long* s_rho =
+      reinterpret_cast<unsigned long long*>(smem_raw + (size_t)W * kPushStages * kSB);
   uint64_t* bars = s_bar[warp];
 
   Control* ctrl = r.ctrl;
@@ -225,7 +248,7 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     if (d[j].valid && d[j].fill) {
-      if (lane == 0) load_tile(r, d[j], stages + j * kStageWords, &bars[j]);
+      if (lane == 0) load_tile<R>(r, d[j], stages + j * kSB, &bars[j]);
       pending |= 1u << j;
     }
   }
@@ -242,7 +265,7 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
       if (lane == 0) {
         // the stage's last bulk stores (round m - 1) must have read it
         bulk_wait_read_all();
-        load_tile(r, d[2], stages + sn * kStageWords, &bars[sn]);
+        load_tile<R>(r, d[2], stages + sn * kSB, &bars[sn]);
       }
       pending |= 1u << sn;
     }
@@ -262,14 +285,14 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
       const size_t tbase = (size_t)t.k * kTile;
       uint32_t n_surv = 0, n_event = 0;
       bool compact = false;
-      float* st = stages + sc * kStageWords;
-      int32_t* st_cell = reinterpret_cast<int32_t*>(st);
-      float* st_off = st + 1 * kTile;
-      float* st_vx = st + 2 * kTile;
-      float* st_vy = st + 3 * kTile;
-      float* st_vz = st + 4 * kTile;
-      float* st_wj = st + 5 * kTile;
-      uint32_t* st_id = reinterpret_cast<uint32_t*>(st + 6 * kTile);
+      const Stage<R> st(stages + sc * kSB);
+      int32_t* st_cell = st.cell;
+      R* st_off = st.f[0];
+      R* st_vx = st.f[1];
+      R* st_vy = st.f[2];
+      R* st_vz = st.f[3];
+      R* st_wj = st.f[4];
+      uint32_t* st_id = st.id;
       // ---- 2. the tile's data: wait (bounded), then read it into registers -----
       bool ok = true;
       if (t.fill) {
@@ -296,7 +319,7 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
         // slots past the fill are read (stage memory) but never used; their
         // cell is taken as 0 so that the gather stays in range
         int cell[kPerLane];
-        float off[kPerLane], vx[kPerLane], vy[kPerLane], vz[kPerLane], wj[kPerLane];
+        R off[kPerLane], vx[kPerLane], vy[kPerLane], vz[kPerLane], wj[kPerLane];
         uint32_t id[kPerLane];
         bool live[kPerLane];
 #pragma unroll
@@ -313,21 +336,22 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
         }
         unsigned long long* rho = use_smem ? s_rho : P.rho_acc[sp];
         const uint32_t step = r.istate[inst].step;
-        const float qmdt = S.qmdt, vlim = S.vlim, dtdx = P.dtdx, P0 = P.P0;
-        const float wscale = P.wscale;
+        const StepConsts<R>& K = consts<R>(P);
+        const R qmdt = K.qmdt[sp], vlim = K.vlim[sp], dtdx = K.dtdx, P0 = K.P0;
+        const R wscale = K.wscale;
         const uint32_t N = (uint32_t)P.n_cells;
-        const float* E32 = P.E32;
+        const R* Enode = node_field<R>(P);
         const bool electrons = sp == kElectron;
-        const bool limited = vlim < INFINITY;  // beta = 1 for an unlimited species
+        const bool limited = vlim < (R)INFINITY;  // beta = 1 for an unlimited species
 
         // ---- 4. advance the lane's slots ---------------------------------------
         // straight-line over the kPerLane slots so that their dependency chains
         // interleave
-        float a[kPerLane], b1[kPerLane];
+        R a[kPerLane], b1[kPerLane];
 #pragma unroll
         for (int j = 0; j < kPerLane; ++j) {
           // gather (linear between the cell's nodes)
-          const float E0 = __ldg(E32 + cell[j]), E1 = __ldg(E32 + cell[j] + 1);
+          const R E0 = __ldg(Enode + cell[j]), E1 = __ldg(Enode + cell[j] + 1);
           a[j] = qmdt * (E0 + off[j] * (E1 - E0));
         }
         // speed-limited kick (beta of the pre-kick speed) and drift (beta of the
@@ -335,27 +359,27 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
         if (limited) {
 #pragma unroll
           for (int j = 0; j < kPerLane; ++j) {
-            const float b0 = beta_of(sqrtf(vx[j] * vx[j] + vy[j] * vy[j] + vz[j] * vz[j]), vlim);
+            const R b0 = beta_of(r_sqrt(vx[j] * vx[j] + vy[j] * vy[j] + vz[j] * vz[j]), vlim);
             vx[j] = vx[j] + b0 * a[j];
           }
 #pragma unroll
           for (int j = 0; j < kPerLane; ++j)
-            b1[j] = beta_of(sqrtf(vx[j] * vx[j] + vy[j] * vy[j] + vz[j] * vz[j]), vlim);
+            b1[j] = beta_of(r_sqrt(vx[j] * vx[j] + vy[j] * vy[j] + vz[j] * vz[j]), vlim);
         } else {
 #pragma unroll
           for (int j = 0; j < kPerLane; ++j) {
             vx[j] = vx[j] + a[j];
-            b1[j] = 1.0f;
+            b1[j] = (R)1;
           }
         }
 #pragma unroll
         for (int j = 0; j < kPerLane; ++j) {
-          float o = off[j] + b1[j] * (vx[j] * dtdx);
-          const float fl = floorf(o);
+          R o = off[j] + b1[j] * (vx[j] * dtdx);
+          const R fl = r_floor(o);
           int c = cell[j] + (int)fl;
           o = o - fl;
-          if (o >= 1.0f) {
-            o = 0.0f;
+          if (o >= (R)1) {
+            o = (R)0;
             c += 1;
           }
           cell[j] = c;
@@ -371,21 +395,21 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
 #pragma unroll
         for (int j = 0; j < kPerLane; ++j) {
           if (live[j] && !alive[j])
-            event[j] = absorb(P, sp, cell[j] < 0 ? 0 : 1, wj[j], id[j], step, cs.s_acc);
+            event[j] = absorb<R>(P, sp, cell[j] < 0 ? 0 : 1, wj[j], id[j], step, cs.s_acc);
         }
         if (electrons) {
           const uint32_t key2 = P.key2;
 #pragma unroll
           for (int j = 0; j < kPerLane; ++j) {
             const uint2 rr = philox2x32_10(make_uint2(id[j], step), key2);
-            event[j] = alive[j] && uniform01(rr.x) < P0;
+            event[j] = alive[j] && uniform01r<R>(rr.x) < P0;
           }
         }
 #pragma unroll
         for (int j = 0; j < kPerLane; ++j) {
           // deposit w_p = beta w_j now unless a collision may change v
           if (alive[j] && !event[j]) {
-            const long long Q = fixed_charge_scaled(b1[j] * wj[j], wscale);
+            const long long Q = fixed_charge(b1[j] * wj[j], wscale);
             const long long right = right_share(Q, off[j]);
             atomicAdd(rho + cell[j], (unsigned long long)(Q - right));
             atomicAdd(rho + cell[j] + 1, (unsigned long long)right);
@@ -414,7 +438,7 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
               const uint32_t r_a = pre_alive[j] + (uint32_t)__popc(b_alive[j] & lanemask_lt);
               S.cand[tbase + e] = (uint16_t)r_a;
             } else {
-              stage_emission(P, tbase + e, wj[j]);
+              stage_emission<R>(P, tbase + e, wj[j]);
             }
           }
         }
@@ -456,16 +480,17 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
       __syncwarp();
       if (lane == 0 && ok) {
         if (n_surv) {
-          const SoA o = S.buf[cur_buf];
-          const uint32_t bytes = ((n_surv + 3u) & ~3u) * 4u;
-          bulk_store(o.cell + tbase, st + 0 * kTile, bytes);
-          bulk_store(o.off + tbase, st + 1 * kTile, bytes);
-          bulk_store(o.vx + tbase, st + 2 * kTile, bytes);
+          const SoAT<R> o = soa_as<R>(S.buf[cur_buf]);
+          const uint32_t n4 = (n_surv + 3u) & ~3u;  // 16-byte multiples
+          const uint32_t b4 = n4 * 4u, br = n4 * (uint32_t)sizeof(R);
+          bulk_store(o.cell + tbase, st_cell, b4);
+          bulk_store(o.off + tbase, st_off, br);
+          bulk_store(o.vx + tbase, st_vx, br);
           if (compact) {
-            bulk_store(o.vy + tbase, st + 3 * kTile, bytes);
-            bulk_store(o.vz + tbase, st + 4 * kTile, bytes);
-            bulk_store(o.wj + tbase, st + 5 * kTile, bytes);
-            bulk_store(o.id + tbase, st + 6 * kTile, bytes);
+            bulk_store(o.vy + tbase, st_vy, br);
+            bulk_store(o.vz + tbase, st_vz, br);
+            bulk_store(o.wj + tbase, st_wj, br);
+            bulk_store(o.id + tbase, st_id, b4);
           }
           bulk_commit();
         }
@@ -493,7 +518,8 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
   }
 }
 
-int push_config(int smem_nodes, int* warps, int* blocks_per_sm, size_t* smem_bytes) {
+template <typename R>
+int push_config_t(int smem_nodes, int* warps, int* blocks_per_sm, size_t* smem_bytes) {
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return (int)e;
@@ -503,12 +529,12 @@ int push_config(int smem_nodes, int* warps, int* blocks_per_sm, size_t* smem_byt
   *warps = 0;
   *blocks_per_sm = 0;
   for (int w = kPushMaxWarps; w >= 4; w -= 4) {
-    const size_t bytes = (size_t)w * kPushStages * kStageWords * 4 + (size_t)smem_nodes * 8;
+    const size_t bytes = (size_t)w * kPushStages * stage_bytes<R>() + (size_t)smem_nodes * 8;
     if (bytes + fixed > (size_t)optin) continue;
-    e = cudaFuncSetAttribute(k_push, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    e = cudaFuncSetAttribute(k_push<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return (int)e;
     int bps = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_push, w * 32, bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_push<R>, w * 32, bytes);
     if (e != cudaSuccess) return (int)e;
     if (bps > 0) {
       *warps = w;
@@ -520,13 +546,25 @@ int push_config(int smem_nodes, int* warps, int* blocks_per_sm, size_t* smem_byt
   return 0;
 }
 
+int push_config(int fp64, int smem_nodes, int* warps, int* blocks_per_sm, size_t* smem_bytes) {
+  return fp64 ? push_config_t<double>(smem_nodes, warps, blocks_per_sm, smem_bytes)
+              : push_config_t<float>(smem_nodes, warps, blocks_per_sm, smem_bytes);
+}
+
 void launch_push(const DeviceRefs& r, int grid, cudaStream_t s) {
-  const size_t bytes =
-      (size_t)r.push_warps * kPushStages * kStageWords * 4 + (size_t)r.smem_nodes * 8;
-  k_push<<<grid, r.push_warps * 32, bytes, s>>>(r);
+  if (r.fp64) {
+    const size_t bytes = (size_t)r.push_warps * kPushStages * stage_bytes<double>() +
+                         (size_t)r.smem_nodes * 8;
+    k_push<double><<<grid, r.push_warps * 32, bytes, s>>>(r);
+  } else {
+    const size_t bytes = (size_t)r.push_warps * kPushStages * stage_bytes<float>() +
+                         (size_t)r.smem_nodes * 8;
+    k_push<float><<<grid, r.push_warps * 32, bytes, s>>>(r);
+  }
 }
 
 static_assert(kTile == 32 * kPerLane, "a tile is kPerLane slots per lane of one warp");
-static_assert((kStageWords * 4) % 128 == 0, "stages keep 128-byte alignment");
+static_assert(stage_bytes<float>() % 128 == 0 && stage_bytes<double>() % 128 == 0,
+              "stages keep 128-byte alignment");
 
 }  // namespace slpic

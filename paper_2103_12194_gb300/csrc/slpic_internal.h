@@ -22,7 +22,12 @@ constexpr int kTile = 128;
 constexpr int kPerLane = kTile / 32;
 constexpr int kPushMaxWarps = 16;
 constexpr int kPushStages = 3;
-constexpr int kStageWords = 7 * kTile;  // the seven SoA streams of one tile
+// Shared-memory stage of one tile: cell and id (4 bytes each), then the five
+// real streams (off, vx, vy, vz, w_j) of sizeof(R) bytes.
+template <typename R>
+__host__ __device__ constexpr int stage_bytes() {
+  return kTile * (8 + 5 * (int)sizeof(R));
+}
 // Relative cost of a super-tile of each species in the particle kernel's
 // static split of the super-tiles over the CTAs (ions draw no collision test).
 constexpr unsigned int kWeightElectron = 3;
@@ -76,14 +81,53 @@ struct TallyRec {
   long long marker_steps;
 };
 
-struct SoA {
+// Structure-of-arrays marker store in the arithmetic type R of the marker
+// path (float in FP32 contexts, double in FP64 contexts).  The device
+// descriptors hold the float view; kernels of an FP64 context take the double
+// view of the same pointers.
+template <typename R>
+struct SoAT {
   int32_t* cell;
-  float* off;
-  float* vx;
-  float* vy;
-  float* vz;
-  float* wj;
+  R* off;
+  R* vx;
+  R* vy;
+  R* vz;
+  R* wj;
   uint32_t* id;
+};
+using SoA = SoAT<float>;
+
+template <typename R>
+__host__ __device__ inline SoAT<R> soa_as(const SoA& s) {
+  return SoAT<R>{s.cell, reinterpret_cast<R*>(s.off), reinterpret_cast<R*>(s.vx),
+                 reinterpret_cast<R*>(s.vy), reinterpret_cast<R*>(s.vz),
+                 reinterpret_cast<R*>(s.wj), s.id};
+}
+
+// One node of the FP64 cross-section table: cumulative (S1, S2, S3) and a pad.
+struct alignas(32) TabNode64 {
+  double s1, s2, s3, pad;
+};
+
+// Constants of the step in the marker path's arithmetic type R; the host
+// derives both sets from the same double-precision configuration.
+template <typename R>
+struct StepConsts {
+  R qmdt[2];      // (q / m) dt per species
+  R vlim[2];      // speed limit per species (+inf: beta = 1)
+  R K_V[2];       // 2 e / m: speed^2 per eV, per species
+  R dtdx;         // dt / dx
+  R K_E;          // m_e / (2 e): eV per (m/s)^2
+  R ndt;          // n_g dt
+  R P0;           // null-collision majorant probability
+  R vb_cap;       // cap of beta v in the majorant
+  R R2;           // 2 m_e / M
+  R e_ex, e_io;   // thresholds [eV]
+  R sigT_ion;     // sqrt(k T / M)
+  R gamma;        // secondary-emission yield
+  R wscale;       // 2^charge_shift
+  R two_pi;
+  R e_lo, e_hi;   // table range [eV]
 };
 
 // Marker store of one (instance, species): a sequence of tiles of kTile
@@ -121,12 +165,10 @@ struct SpeciesDev {
   uint16_t* cand;     // electrons: [cap_tiles * kTile] slots of the tile's
                       // null-collision candidates, in slot order
   uint32_t* n_cand;   // electrons: [cap_tiles] candidates per tile
-  float* esec;        // electrons: [cap_tiles * kTile] energy given to the
-                      // secondary by an ionizing candidate
+  void* esec;         // electrons: [cap_tiles * kTile] energy (type R) given
+                      // to the secondary by an ionizing candidate
   uint32_t cap_tiles;
-  float qmdt;         // (q / m) dt
-  float vlim;         // speed limit (+inf: beta = 1)
-  float K_V;          // 2 e / m: speed^2 per eV
+  uint32_t pad;
 };
 
 // Configuration of one instance (constant during a run).
@@ -140,22 +182,13 @@ struct InstDev {
   uint32_t key0, key1;
   uint32_t ctr_inst;  // counter word 2 = ctr_inst * 2 + species
   uint32_t key2;      // Philox2x32 key of the null-collision draw
-  float dtdx;         // dt / dx
-  float K_E;          // m_e / (2 e): eV per (m/s)^2
-  float ndt;          // n_g dt
-  float P0;           // null-collision majorant probability
-  float vb_cap;       // cap of beta v in the majorant
-  float R2;           // 2 m_e / M
-  float e_ex, e_io;   // thresholds [eV]
-  float sigT_ion;     // sqrt(k T / M)
-  float gamma;        // secondary-emission yield
-  float wscale;       // 2^charge_shift
-  float two_pi;
-  float e_lo, e_hi;   // table range [eV]
+  StepConsts<float> c32;
+  StepConsts<double> c64;
   double dx, d, V, area, dt;
   double pois_C;      // e dx 2^-shift / (area eps0)
-  const float4* table;          // cumulative (S1, S2, S3, 0) per node
-  float* E32;                   // node field used by the push
+  const float4* table;          // FP32: cumulative (S1, S2, S3, 0) per node
+  const TabNode64* table64;     // FP64: the same in double
+  float* E32;                   // node field used by the FP32 push
   double* phi;                  // node potential
   double* E64;                  // node field
   unsigned long long* rho_acc[2];  // fixed-point deposit of the current step
@@ -224,13 +257,14 @@ struct DeviceRefs {
   int n_inst;
   int smem_nodes;         // deposit grid nodes in shared memory (0: global atomics)
   int push_warps;         // warps per particle-kernel CTA = tiles per super-tile
+  int fp64;               // marker path in double precision (else float)
 };
 
 // Launchers (defined in the .cu files).
 void launch_push(const DeviceRefs& r, int grid, cudaStream_t s);
 // Particle-kernel shape for a shared-memory deposit grid of smem_nodes nodes:
 // warps per CTA, resident CTAs per SM and dynamic shared memory per CTA.
-int push_config(int smem_nodes, int* warps, int* blocks_per_sm, size_t* smem_bytes);
+int push_config(int fp64, int smem_nodes, int* warps, int* blocks_per_sm, size_t* smem_bytes);
 // mode 0: finish a step and plan the next; mode 1: plan only (one CTA).
 void launch_finish(const DeviceRefs& r, int mode, cudaStream_t s);
 void launch_move(const DeviceRefs& r, int grid, cudaStream_t s);
@@ -240,9 +274,9 @@ void launch_collide(const DeviceRefs& r, int grid, cudaStream_t s);
 // buffer; mode 0/1/2 as SLPIC_SEED_*; for mode 3 (thermal) e0 carries the
 // thermal speed sqrt(k T / m).
 void launch_seed(const DeviceRefs& r, int inst, int species, uint32_t base, uint32_t first_id,
-                 uint32_t n, int mode, float e0, float e_lo, float lr, float wj,
+                 uint32_t n, int mode, double e0, double e_lo, double lr, double wj,
                  cudaStream_t s);
-void launch_validate(const SoA& d, uint32_t n, int N, int shift, unsigned int* bad,
+void launch_validate(int fp64, const SoA& d, uint32_t n, int N, int shift, unsigned int* bad,
                      unsigned long long* wsum, cudaStream_t s);
 void launch_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, uint32_t* out,
                    long long n, cudaStream_t s);

@@ -108,6 +108,10 @@ def lib():
         "slpic_philox2x32": ([i32, u32, vp, i64, vp], i32),
         "slpic_philox_static": ([i32, u64, vp, i64, vp], i32),
         "slpic_paschen_bisect": ([vp, ctypes.POINTER(PaschenSpec), vp, vp, vp], i32),
+        "slpic_set_precision": ([vp, i32], i32),
+        "slpic_load_particles_f64": ([vp, i32, i32, ctypes.POINTER(SoA), i64, u32], i32),
+        "slpic_read_particles_f64": ([vp, i32, i32, ctypes.POINTER(SoA), i64,
+                                      ctypes.POINTER(i64)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -166,7 +170,7 @@ class Simulation:
     """A context with ``n_instances`` gaps.  ``configure(i, spec)`` takes the
     mapping produced by :func:`paper_2103_12194_gb300.inputs.gap_spec`."""
 
-    def __init__(self, n_instances=1, device=0, stream=None):
+    def __init__(self, n_instances=1, device=0, stream=None, precision=32):
         self._L = lib()
         h = ctypes.c_void_p()
         rc = self._L.slpic_create(ctypes.byref(h), device, n_instances)
@@ -176,6 +180,10 @@ class Simulation:
         self.n_instances = n_instances
         self.device = device
         self.n_cells = [0] * n_instances
+        self.precision = int(precision)
+        self._real = np.float64 if self.precision == 64 else np.float32
+        if self.precision != 32:
+            self._ck(self._L.slpic_set_precision(self._h, self.precision))
         if stream is not None:
             self.set_stream(stream)
 
@@ -244,12 +252,14 @@ class Simulation:
 
     def load(self, i, species, state, next_id=None):
         n = len(state["cell"])
-        arrs = {k: np.ascontiguousarray(state[k], dtype=DTYPES.get(k, np.float32)) for k in FIELDS}
+        arrs = {k: np.ascontiguousarray(state[k], dtype=DTYPES.get(k, self._real))
+                for k in FIELDS}
         if next_id is None:
             next_id = int((arrs["id"] & 0x7FFFFFFF).max()) + 1 if n else 0
         soa = SoA(*[arrs[k].ctypes.data for k in FIELDS])
-        self._ck(self._L.slpic_load_particles(self._h, i, species, ctypes.byref(soa), n,
-                                              int(next_id)))
+        fn = (self._L.slpic_load_particles_f64 if self.precision == 64
+              else self._L.slpic_load_particles)
+        self._ck(fn(self._h, i, species, ctypes.byref(soa), n, int(next_id)))
 
     def load_device(self, i, species, tensors, next_id):
         """tensors: mapping of the seven fields to CUDA tensors (contiguous)."""
@@ -265,11 +275,12 @@ class Simulation:
 
     def particles(self, i, species):
         n = self.count(i, species)
-        out = {k: np.empty(n, dtype=DTYPES.get(k, np.float32)) for k in FIELDS}
+        out = {k: np.empty(n, dtype=DTYPES.get(k, self._real)) for k in FIELDS}
         soa = SoA(*[out[k].ctypes.data for k in FIELDS])
         got = ctypes.c_int64()
-        self._ck(self._L.slpic_read_particles(self._h, i, species, ctypes.byref(soa), n,
-                                              ctypes.byref(got)))
+        fn = (self._L.slpic_read_particles_f64 if self.precision == 64
+              else self._L.slpic_read_particles)
+        self._ck(fn(self._h, i, species, ctypes.byref(soa), n, ctypes.byref(got)))
         return out
 
     # ---- stepping -------------------------------------------------------
