@@ -26,6 +26,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_MARKER_STEP = 48  # read 28 B of state, write the 20 B that change
+BYTES_PER_MARKER_STEP_FP64 = 84  # FP64 marker: read 48 B, write the 36 B that change
 L2_BYTES = 129 * 2**20
 FALLBACK_HBM_GBS = 6800.0
 
@@ -40,6 +41,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--paschen", action="store_true",
+                    help="also time the batched FP32 breakdown-voltage sweep against the "
+                         "plain one-instance FP64 bisection")
     return ap.parse_args()
 
 
@@ -164,6 +169,56 @@ def cpu_baseline(spec, n_markers, seconds):
                       "single host thread, %.1f s" % (n, k, dt)}
 
 
+def paschen_sweep(slpic, inputs, local, stream, pds=(0.5, 1.0, 2.0, 4.0), n_v=8, rounds=3,
+                  n_seed=2000, v_lo=100.0, v_hi=900.0):
+    """Breakdown voltages at a few pd points (d = 1 cm, gamma = 0.07, cells
+    from dx = lambda_min / 4): the batched FP32 search (all pd points and n_v
+    voltages per round in one context) against the plain FP64 bisection (one
+    single-instance context per pd point, one voltage per round, as many
+    halvings as reach the same bracket width)."""
+    import numpy as np
+    import torch
+    table = inputs.make_table()
+    smax = float(np.max(table["sig_el"].astype(np.float64) + table["sig_ex"] + table["sig_io"]))
+
+    def spec_for(pd, j, inst):
+        n_g = pd / 1.0 * inputs.TORR / (inputs.KB * 300.0)
+        cells = int(min(16384, max(128, math.ceil(4 * 0.01 * n_g * smax))))
+        return inputs.gap_spec(n_cells=cells, V=300.0, pd_torr_cm=pd, gamma_se=0.07,
+                               field_mode=0, seed=11 + inst, instance=inst)
+
+    cap = (2 * 16 * n_seed, 32 * n_seed)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim = slpic.Simulation(len(pds) * n_v, device=local, stream=stream)
+    for p, pd in enumerate(pds):
+        for j in range(n_v):
+            sim.configure(p * n_v + j, spec_for(pd, j, p * n_v + j), capacity=cap)
+    lo32, hi32, _ = sim.paschen_bisect([v_lo] * len(pds), [v_hi] * len(pds), n_v=n_v,
+                                       rounds=rounds, n_seed=n_seed)
+    sim.close()
+    t32 = time.perf_counter() - t0
+    halvings = int(math.ceil(rounds * math.log2(n_v + 1)))
+    t0 = time.perf_counter()
+    lo64, hi64 = [], []
+    for p, pd in enumerate(pds):
+        sim = slpic.Simulation(1, device=local, stream=stream, precision=64)
+        sim.configure(0, spec_for(pd, 0, 0), capacity=cap)
+        lo, hi, _ = sim.paschen_bisect([v_lo], [v_hi], n_v=1, rounds=halvings, n_seed=n_seed)
+        sim.close()
+        lo64.append(float(lo[0]))
+        hi64.append(float(hi[0]))
+    t64 = time.perf_counter() - t0
+    return {"pd_torr_cm": list(pds), "n_seed": n_seed,
+            "fp32_batched": {"s": t32, "instances": len(pds) * n_v, "rounds": rounds,
+                             "Vb_lo": [float(x) for x in lo32], "Vb_hi": [float(x) for x in hi32]},
+            "fp64_plain": {"s": t64, "instances": 1, "rounds": halvings,
+                           "Vb_lo": lo64, "Vb_hi": hi64},
+            "bracket_width_V": {"fp32_batched": (v_hi - v_lo) / (n_v + 1) ** rounds,
+                                "fp64_plain": (v_hi - v_lo) / 2 ** halvings},
+            "speedup": t64 / t32}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -258,6 +313,37 @@ def run_ours(args):
     sim.close()
     del sim
 
+    # ---- the same workload on the FP64 marker path (fewer steps) ----------
+    fp64 = None
+    if not args.no_fp64:
+        k64 = max(10, args.steps // 10)
+        sim = slpic.Simulation(1, device=local, stream=stream, precision=64)
+        sim.configure(0, spec, capacity=(cap_e, cap_i))
+        sim.seed(0, slpic.ELECTRON, n, slpic.SEED_GAP, e_lo=run["e_lo"], e_hi=run["e_hi"])
+        sim.step(args.warmup)
+        sim.synchronize()
+        sim.set_profiling(True)
+        ms0 = int(sim.tallies(0)["marker_steps"])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(k64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = int(sim.tallies(0)["marker_steps"]) - ms0
+        p_ms, p_n = sim.profile()
+        t64 = e0.elapsed_time(e1) / 1e3
+        ach64 = BYTES_PER_MARKER_STEP_FP64 * (ms64 / max(1, p_n)) / (p_ms / 1e3 / max(1, p_n)) / 1e9
+        fp64 = {"value": ms64 / t64, "unit": "marker-steps/s", "steps": k64,
+                "ms_per_step": t64 * 1e3 / k64, "dtype": "f64",
+                "roofline": {"bound": "hbm", "achieved": ach64, "peak": peak, "unit": "GB/s",
+                             "frac": ach64 / peak, "bytes_per_marker_step": BYTES_PER_MARKER_STEP_FP64,
+                             "kernel": "k_push<double>"},
+                "note": "same workload and seeds on the FP64 marker path; profiled steps "
+                        "without graph replay"}
+        sim.set_profiling(False)
+        sim.close()
+        del sim
+
     # ---- end to end through the C ABI with host buffers -----------------
     e2e = None
     if not args.no_e2e:
@@ -296,6 +382,10 @@ def run_ours(args):
                        "K steps, per-step tallies and density read back"}
         sim.close()
 
+    sweep = None
+    if args.paschen and rank == 0:
+        sweep = paschen_sweep(slpic, inputs, local, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(spec, n, args.cpu_seconds)
@@ -318,6 +408,8 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
+            "variants": {"fp64": fp64},
+            "paschen_sweep": sweep,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

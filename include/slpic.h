@@ -171,7 +171,9 @@ int slpic_suggest_dt(double d, int n_cells, double V, double m_ion, int mode,
 /* Seed n markers of `species` on the device (appended to the live ones),
  * drawn from the instance's Philox stream (counter word 1 = 0xFFFFFFFF):
  * mode SLPIC_SEED_*; e0 [eV] for SEED_CATHODE; [e_lo, e_hi] eV for SEED_GAP;
- * every marker gets flux weight wj.  Resets the step counter and tallies. */
+ * every marker gets flux weight wj.  Seeded electrons add to the instance's
+ * seeded weight (the gain's denominator); the step counter and the tallies
+ * go on (slpic_reset_counters restarts them). */
 int slpic_seed(slpic_ctx* ctx, int inst, int species, int64_t n, int mode,
                double e0, double e_lo, double e_hi, double wj);
 /* Arithmetic type of the marker path: 32 (default; positions, velocities and
@@ -183,7 +185,9 @@ int slpic_set_precision(slpic_ctx* ctx, int bits);
 
 /* Replace the markers of `species` by n markers from host arrays (FP32 SoA);
  * next_id = serial number of the next born marker.  Cells must lie in
- * [0, N) and offsets in [0, 1).  Resets the step counter and tallies. */
+ * [0, N) and offsets in [0, 1).  For electrons the loaded weight becomes the
+ * seeded weight; the step counter and the tallies go on
+ * (slpic_reset_counters restarts them). */
 int slpic_load_particles(slpic_ctx* ctx, int inst, int species,
                          const slpic_soa_f32* host, int64_t n,
                          uint32_t next_id);
@@ -258,14 +262,16 @@ int slpic_read_gain(slpic_ctx* ctx, int inst, double* G);
  *    G = gamma * (flux weight of first-generation ions reaching the cathode)
  *    / (seeded weight) is its expected value (Townsend: G >= 1 is
  *    breakdown, Sec. II.A);
- *  - the batch steps in chunks of chunk_steps until every instance has no
- *    marker left, or max_steps; an instance with more than
+ *  - the batch steps until every instance has no marker left, or
+ *    max_steps, in chunks of at most chunk_steps steps between checks of the
+ *    live counts: a chunk is shortened so that no store can overflow in it
+ *    (electrons at most double per step); an instance with more than
  *    (1 + 1/gamma) n_seed live electrons or at least n_seed/gamma live ions
  *    is above breakdown for certain (each ionization leaves an ion that
  *    reaches the cathode): it is emptied and counts as G = +inf.  Every
  *    instance needs gamma > 0 and capacities of at least
- *    16 (1 + 1/gamma) n_seed electrons and n_seed/gamma + 16 (1 + 1/gamma)
- *    n_seed ions (growth is at most x2 per step), else SLPIC_ERR_INVALID_ARG.
+ *    2 (1 + 1/gamma) n_seed electrons and n_seed/gamma + (1 + 1/gamma) n_seed
+ *    ions, else SLPIC_ERR_INVALID_ARG.
  * Then each bracket shrinks to [V_{j-1}, V_j] around the first j with
  * G >= 1 (V_{-1} = lo, V_{n_v} = hi).  On return Vb_lo/Vb_hi [n_pd] hold the
  * final brackets and, if not NULL, gain [n_pd * n_v] the last round's G.  The
@@ -278,7 +284,7 @@ typedef struct {
   int64_t n_seed;      /* electrons seeded per instance and round */
   double e0;           /* their energy [eV] */
   double vlim_factor;  /* see above */
-  int64_t chunk_steps; /* steps between checks of the live counts (1..4) */
+  int64_t chunk_steps; /* most steps between checks of the live counts */
   int64_t max_steps;   /* per round */
   const double* V_lo;  /* [n_pd] initial bracket [V] */
   const double* V_hi;  /* [n_pd] */

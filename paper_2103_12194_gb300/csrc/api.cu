@@ -1268,17 +1268,17 @@ extern "C" int slpic_paschen_bisect(slpic_ctx* c, const slpic_paschen_spec* ps, 
   if (np < 1 || nv < 1 || (long long)np * nv != c->n_inst)
     return fail(c, SLPIC_ERR_INVALID_ARG, "paschen: the context must hold n_pd * n_v = %d instances",
                 c->n_inst);
-  if (ps->rounds < 1 || ps->n_seed < 1 || ps->chunk_steps < 1 || ps->chunk_steps > 4 ||
-      ps->max_steps < 1 || !(ps->e0 >= 0))
+  if (ps->rounds < 1 || ps->n_seed < 1 || ps->chunk_steps < 1 || ps->max_steps < 1 ||
+      !(ps->e0 >= 0))
     return fail(c, SLPIC_ERR_INVALID_ARG, "paschen: bad rounds, n_seed, e0 or step counts");
   for (int p = 0; p < np; ++p)
     if (!(ps->V_lo[p] > 0) || !(ps->V_hi[p] > ps->V_lo[p]))
       return fail(c, SLPIC_ERR_INVALID_ARG, "paschen: bracket %d is not 0 < lo < hi", p);
   // An avalanche with more than T_e = (1 + 1/gamma) n_seed live electrons, or
   // T_i = n_seed / gamma live ions, has G >= 1 for certain (every ionization
-  // leaves an ion that reaches the cathode); growth is at most x2 per step,
-  // so with chunks of <= 4 steps the stores need 16 T_e electrons and
-  // T_i + 16 T_e ions.
+  // leaves an ion that reaches the cathode).  Electrons at most double per
+  // step, so the next chunk is as long as the stores allow (at least one
+  // step: 2 T_e electrons and T_i + T_e ions).
   const int n = c->n_inst;
   std::vector<int64_t> thr_e(n), thr_i(n);
   for (int i = 0; i < n; ++i) {
@@ -1287,12 +1287,12 @@ extern "C" int slpic_paschen_bisect(slpic_ctx* c, const slpic_paschen_spec* ps, 
     if (!(g > 0)) return fail(c, SLPIC_ERR_INVALID_ARG, "paschen: instance %d has gamma <= 0", i);
     thr_e[i] = (int64_t)std::ceil((1.0 + 1.0 / g) * (double)ps->n_seed);
     thr_i[i] = (int64_t)std::ceil((double)ps->n_seed / g);
-    if (c->hi[i].sp[kElectron].cap < 16 * thr_e[i] ||
-        c->hi[i].sp[kIon].cap < thr_i[i] + 16 * thr_e[i])
+    if (c->hi[i].sp[kElectron].cap < 2 * thr_e[i] ||
+        c->hi[i].sp[kIon].cap < thr_i[i] + thr_e[i])
       return fail(c, SLPIC_ERR_INVALID_ARG,
                   "paschen: instance %d needs capacities of at least %lld electrons and %lld "
-                  "ions (16 (1 + 1/gamma) n_seed and n_seed/gamma + 16 (1 + 1/gamma) n_seed)",
-                  i, (long long)(16 * thr_e[i]), (long long)(thr_i[i] + 16 * thr_e[i]));
+                  "ions (2 (1 + 1/gamma) n_seed and n_seed/gamma + (1 + 1/gamma) n_seed)",
+                  i, (long long)(2 * thr_e[i]), (long long)(thr_i[i] + thr_e[i]));
   }
   if (int rc = prepare(c)) return rc;
   std::vector<double> lo(ps->V_lo, ps->V_lo + np), hi(ps->V_hi, ps->V_hi + np);
@@ -1329,6 +1329,8 @@ extern "C" int slpic_paschen_bisect(slpic_ctx* c, const slpic_paschen_spec* ps, 
           break;
         if ((rc = load_common(c, i, kIon, Arrays{{}, c->fp64}, 0, 0, cudaMemcpyHostToDevice))) break;
         if ((rc = load_common(c, i, kElectron, Arrays{{}, c->fp64}, 0, 0, cudaMemcpyHostToDevice))) break;
+        // tallies, seeded weight and step counter start from zero every round
+        if ((rc = zero_counters(c, i))) break;
         if ((rc = slpic_seed(c, i, kElectron, ps->n_seed, SLPIC_SEED_CATHODE, ps->e0, 0.0, 0.0,
                              1.0)))
           break;
@@ -1337,8 +1339,9 @@ extern "C" int slpic_paschen_bisect(slpic_ctx* c, const slpic_paschen_spec* ps, 
     }
     if (rc) break;
     // ---- step the batch until every avalanche has left the gap --------------
+    int64_t k = 1;  // next chunk: no instance can outgrow its stores in it
     for (int64_t done = 0; done < ps->max_steps && !rc;) {
-      const int64_t k = std::min<int64_t>(ps->chunk_steps, ps->max_steps - done);
+      k = std::min<int64_t>(k, ps->max_steps - done);
       if ((rc = slpic_step(c, k))) break;
       done += k;
       if ((rc = sync(c))) break;
@@ -1348,18 +1351,30 @@ extern "C" int slpic_paschen_bisect(slpic_ctx* c, const slpic_paschen_spec* ps, 
         break;
       }
       bool live = false;
+      k = ps->chunk_steps;
       for (int i = 0; i < n && !rc; ++i) {
         if (saturated[i]) continue;
-        const uint32_t ne = st[2 * i].n_live, ni = st[2 * i + 1].n_live;
+        const int64_t ne = st[2 * i].n_live, ni = st[2 * i + 1].n_live;
         // above breakdown for certain; stop this avalanche before it can
-        // outgrow the stores in the next chunk
-        if ((int64_t)ne > thr_e[i] || (int64_t)ni >= thr_i[i]) {
+        // outgrow the stores
+        if (ne > thr_e[i] || ni >= thr_i[i]) {
           saturated[i] = 1;
           rc = load_common(c, i, kIon, Arrays{{}, c->fp64}, 0, 0, cudaMemcpyHostToDevice);
-          if (!rc) rc = load_common(c, i, kElectron, Arrays{{}, c->fp64}, 0, 0, cudaMemcpyHostToDevice);
+          if (!rc)
+            rc = load_common(c, i, kElectron, Arrays{{}, c->fp64}, 0, 0, cudaMemcpyHostToDevice);
           continue;
         }
         if (ne || ni) live = true;
+        // in s steps the electrons grow at most to ne 2^s and the ions to
+        // ni + ne (2^s - 1)
+        if (ne > 0) {
+          const int64_t ce = c->hi[i].sp[kElectron].cap, ci = c->hi[i].sp[kIon].cap;
+          int64_t s = 1;  // grows while s + 1 steps stay inside both stores
+          while (s < k && s < 30 && ne * (int64_t(2) << s) <= ce &&
+                 ni + ne * ((int64_t(2) << s) - 1) <= ci)
+            ++s;
+          k = std::min(k, s);
+        }
       }
       if (!live) break;
     }

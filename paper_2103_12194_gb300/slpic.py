@@ -335,7 +335,7 @@ class Simulation:
         return g.value
 
     def paschen_bisect(self, V_lo, V_hi, n_v, rounds, n_seed, e0=1.0, vlim_factor=4.0,
-                       chunk_steps=4, max_steps=1_000_000):
+                       chunk_steps=256, max_steps=1_000_000):
         """slpic_paschen_bisect over the context's len(V_lo) * n_v instances;
         returns (Vb_lo, Vb_hi, gain[n_pd, n_v] of the last round)."""
         lo = np.ascontiguousarray(V_lo, np.float64)
