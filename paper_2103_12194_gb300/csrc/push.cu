@@ -112,13 +112,32 @@ __device__ __forceinline__ unsigned int first_super(const DeviceRefs& r, unsigne
   return min(q, r.seg_start[lo + 1]);
 }
 
-__device__ __forceinline__ WarpTile tile_of(const DeviceRefs& r, unsigned int q, int warp) {
+// A warp's look-ahead stays in one segment for many rounds: the segment of
+// the last super-tile looked up, with its super-tile range, tile count and
+// fill array, so that a round costs one load (the fill) instead of a search
+// and a chain of dependent loads.
+struct SegCursor {
+  int seg;
+  unsigned int q_begin, q_end;  // super-tiles of the segment
+  uint32_t n_tiles;
+  const uint32_t* fill;
+};
+
+__device__ __forceinline__ WarpTile tile_of(const DeviceRefs& r, SegCursor& c, unsigned int q,
+                                            int warp) {
+  if (q < c.q_begin || q >= c.q_end) {
+    c.seg = segment_of(r, q);
+    c.q_begin = r.seg_start[c.seg];
+    c.q_end = r.seg_start[c.seg + 1];
+    const SpeciesState& st = r.sstate[c.seg];
+    c.n_tiles = st.n_tiles;
+    c.fill = r.inst[c.seg >> 1].sp[c.seg & 1].fill[st.cur];
+  }
   WarpTile t;
-  t.sseg = segment_of(r, q);
-  t.k = (q - r.seg_start[t.sseg]) * (uint32_t)r.push_warps + (uint32_t)warp;
-  const SpeciesState& st = r.sstate[t.sseg];
-  t.valid = t.k < st.n_tiles;
-  t.fill = t.valid ? r.inst[t.sseg >> 1].sp[t.sseg & 1].fill[st.cur][t.k] : 0u;
+  t.sseg = c.seg;
+  t.k = (q - c.q_begin) * (uint32_t)r.push_warps + (uint32_t)warp;
+  t.valid = t.k < c.n_tiles;
+  t.fill = t.valid ? c.fill[t.k] : 0u;
   return t;
 }
 
@@ -232,6 +251,12 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
 
   // descriptors of rounds m .. m + 3 (the fill of round m + 3 is loaded a
   // round before the bulk loads that need it are issued)
+  SegCursor cursor;
+  cursor.seg = 0;
+  cursor.q_begin = 1u;  // empty range: the first look-up searches
+  cursor.q_end = 0u;
+  cursor.n_tiles = 0u;
+  cursor.fill = nullptr;
   WarpTile d[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -242,7 +267,7 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
   }
 #pragma unroll
   for (int j = 0; j < 3; ++j)
-    if (j < n_rounds) d[j] = tile_of(r, q0 + j, warp);
+    if (j < n_rounds) d[j] = tile_of(r, cursor, q0 + j, warp);
   uint32_t phase = 0;    // parity bit per stage
   uint32_t pending = 0;  // stages with a bulk load not yet waited for
 #pragma unroll
@@ -257,7 +282,7 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
   bool use_smem = false;
   for (int m = 0; m < n_rounds; ++m) {
     // ---- 0. descriptors ahead; bulk loads of round m + 2 ---------------------
-    if (m + 3 < n_rounds) d[3] = tile_of(r, q0 + m + 3, warp);
+    if (m + 3 < n_rounds) d[3] = tile_of(r, cursor, q0 + m + 3, warp);
     const int sc = m % kPushStages;        // stage of round m
     const int sn = (m + 2) % kPushStages;  // stage of round m + 2
     const bool aborted = *abort_flag != 0;
