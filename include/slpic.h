@@ -292,6 +292,23 @@ typedef struct {
 int slpic_paschen_bisect(slpic_ctx* ctx, const slpic_paschen_spec* spec, double* Vb_lo,
                          double* Vb_hi, double* gain);
 
+/* Launch shape of the step: warps per CTA of the particle kernel (a
+ * multiple of 4, at most what fits next to the largest charge grid; each
+ * warp owns a 128-slot tile) and CTAs per SM of the collision kernel
+ * (1..32).  The library's own choice is the largest warp count and 8.
+ * Results do not depend on the shape, bit for bit: tiles are independent,
+ * deposits are integer sums and births are ordered by (tile, slot). */
+int slpic_set_launch_shape(slpic_ctx* ctx, int push_warps, int collide_ctas_per_sm);
+int slpic_get_launch_shape(slpic_ctx* ctx, int* push_warps, int* collide_ctas_per_sm);
+/* Autotuner: times candidate shapes on the context's own markers and keeps
+ * the fastest per marker-step; writes it to the out arguments (may be
+ * NULL).  It tries every warp count, then collision CTAs per SM of
+ * 2, 4, 8 and 16, running steps_each steps of the simulation for each.
+ * These are real steps: the state advances by (push candidates + 4) *
+ * steps_each steps, exactly as slpic_step would have advanced it. */
+int slpic_autotune(slpic_ctx* ctx, int64_t steps_each, int* push_warps,
+                   int* collide_ctas_per_sm);
+
 /* Per-step timing of the particle kernel: when on, slpic_step launches each
  * step without a CUDA graph and brackets every particle-kernel launch with
  * CUDA events on the context's stream. */

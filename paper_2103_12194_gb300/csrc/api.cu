@@ -81,6 +81,9 @@ struct slpic_ctx {
   int push_grid = 0;
   int move_grid = 0;
   int collide_grid = 0;
+  int sms = 0;             // multiprocessors of the device
+  int max_push_warps = 0;  // most particle-kernel warps per CTA that fit
+  int collide_per_sm = 8;  // collision CTAs per SM
   int blocks_per_sm = 0;
   // graph of kGraphSteps steps
   cudaGraphExec_t graph = nullptr;
@@ -453,10 +456,12 @@ int commit(slpic_ctx* c) {
   c->refs.fp64 = c->fp64;
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device), "attributes");
+  c->sms = sms;
+  c->max_push_warps = warps;
   c->blocks_per_sm = bps;
   c->push_grid = sms * bps;
   c->move_grid = sms * 2;
-  c->collide_grid = sms * 8;
+  c->collide_grid = sms * c->collide_per_sm;
   for (int i = 0; i < c->n_inst; ++i) {
     if (int rc = upload_inst(c, i)) return rc;
     if (int rc = reset_field(c, i)) return rc;
@@ -517,6 +522,31 @@ int build_graph(slpic_ctx* c) {
     return cuda_fail(c, e, "graph instantiate");
   }
   return SLPIC_OK;
+}
+
+// Launch shape of the step: warps per particle-kernel CTA (the super-tile
+// size, so the next step is replanned) and collision CTAs per SM.  Results do
+// not depend on it: tiles are independent, deposits are integer sums and
+// births are ordered by (tile, slot).
+int apply_shape(slpic_ctx* c, int warps, int coll_per_sm) {
+  if (warps < 4 || warps > c->max_push_warps || warps % 4 || coll_per_sm < 1 || coll_per_sm > 32)
+    return fail(c, SLPIC_ERR_INVALID_ARG,
+                "launch shape: push warps must be a multiple of 4 in [4, %d], collision CTAs "
+                "per SM in [1, 32]",
+                c->max_push_warps);
+  int bps = 0;
+  if (int e = push_blocks_per_sm(c->fp64, warps, c->refs.smem_nodes, &bps))
+    return cuda_fail(c, (cudaError_t)e, "launch shape");
+  if (bps < 1) return fail(c, SLPIC_ERR_CUDA, "launch shape: particle kernel does not fit");
+  if (int rc = sync(c)) return rc;
+  drop_graph(c);
+  c->refs.push_warps = warps;
+  c->blocks_per_sm = bps;
+  c->push_grid = c->sms * bps;
+  c->collide_per_sm = coll_per_sm;
+  c->collide_grid = c->sms * coll_per_sm;
+  if (int rc = replan(c)) return rc;
+  return sync(c);
 }
 
 // The seven marker arrays of a caller (cell, off, vx, vy, vz, w_j, id), in
@@ -1252,6 +1282,97 @@ int slpic_philox(int device, uint64_t seed, const uint32_t* ctr, int64_t n, uint
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Launch shape and its autotuner.
+// ---------------------------------------------------------------------------
+extern "C" int slpic_set_launch_shape(slpic_ctx* c, int push_warps, int collide_ctas_per_sm) {
+  if (!c) return SLPIC_ERR_INVALID_ARG;
+  if (int rc = prepare(c)) return rc;
+  return apply_shape(c, push_warps, collide_ctas_per_sm);
+}
+
+extern "C" int slpic_get_launch_shape(slpic_ctx* c, int* push_warps, int* collide_ctas_per_sm) {
+  if (!c || !push_warps || !collide_ctas_per_sm)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "NULL argument");
+  if (int rc = prepare(c)) return rc;
+  *push_warps = c->refs.push_warps;
+  *collide_ctas_per_sm = c->collide_per_sm;
+  return SLPIC_OK;
+}
+
+namespace {
+
+// Device time per marker-step of `steps` steps of the current shape, on the
+// context's own markers (the graph is built before the clock starts).
+int time_shape(slpic_ctx* c, int64_t steps, double* ns_per_marker_step) {
+  if (steps >= kGraphSteps)
+    if (int rc = build_graph(c)) return rc;
+  auto marker_steps = [&](long long* out) -> int {
+    long long sum = 0;
+    for (int i = 0; i < c->n_inst; ++i) {
+      slpic_tallies t;
+      if (int rc = slpic_read_tallies(c, i, &t)) return rc;
+      sum += t.marker_steps;
+    }
+    *out = sum;
+    return SLPIC_OK;
+  };
+  long long m0 = 0, m1 = 0;
+  if (int rc = marker_steps(&m0)) return rc;
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a), "event");
+  CK(cudaEventCreate(&b), "event");
+  cudaEventRecord(a, c->stream);
+  int rc = slpic_step(c, steps);
+  cudaEventRecord(b, c->stream);
+  if (!rc) rc = sync(c);
+  float ms = 0.0f;
+  if (!rc && cudaEventElapsedTime(&ms, a, b) != cudaSuccess)
+    rc = fail(c, SLPIC_ERR_CUDA, "autotune: event timing");
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (!rc) rc = marker_steps(&m1);
+  if (rc) return rc;
+  *ns_per_marker_step = m1 > m0 ? 1e6 * ms / (double)(m1 - m0) : 1e30;
+  return SLPIC_OK;
+}
+
+}  // namespace
+
+extern "C" int slpic_autotune(slpic_ctx* c, int64_t steps_each, int* push_warps,
+                              int* collide_ctas_per_sm) {
+  if (!c) return SLPIC_ERR_INVALID_ARG;
+  if (steps_each < 1) return fail(c, SLPIC_ERR_INVALID_ARG, "autotune: steps_each < 1");
+  if (int rc = prepare(c)) return rc;
+  // coordinate search: particle-kernel warps with the current collision
+  // shape, then collision CTAs per SM with the best warps
+  int best_w = c->refs.push_warps, best_cc = c->collide_per_sm;
+  double best = 1e300;
+  for (int w = 4; w <= c->max_push_warps; w += 4) {
+    if (int rc = apply_shape(c, w, best_cc)) return rc;
+    double t = 0;
+    if (int rc = time_shape(c, steps_each, &t)) return rc;
+    if (t < best) {
+      best = t;
+      best_w = w;
+    }
+  }
+  const int cc_try[4] = {2, 4, 8, 16};
+  for (int k = 0; k < 4; ++k) {
+    if (int rc = apply_shape(c, best_w, cc_try[k])) return rc;
+    double t = 0;
+    if (int rc = time_shape(c, steps_each, &t)) return rc;
+    if (t < best) {
+      best = t;
+      best_cc = cc_try[k];
+    }
+  }
+  if (int rc = apply_shape(c, best_w, best_cc)) return rc;
+  if (push_warps) *push_warps = best_w;
+  if (collide_ctas_per_sm) *collide_ctas_per_sm = best_cc;
+  return SLPIC_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Breakdown-voltage search (the batched Paschen sweep).  Host orchestration of

@@ -571,6 +571,18 @@ int push_config_t(int smem_nodes, int* warps, int* blocks_per_sm, size_t* smem_b
   return 0;
 }
 
+template <typename R>
+int push_bps_t(int warps, int smem_nodes, int* blocks_per_sm) {
+  const size_t bytes = (size_t)warps * kPushStages * stage_bytes<R>() + (size_t)smem_nodes * 8;
+  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_push<R>, warps * 32,
+                                                            bytes);
+}
+
+int push_blocks_per_sm(int fp64, int warps, int smem_nodes, int* blocks_per_sm) {
+  return fp64 ? push_bps_t<double>(warps, smem_nodes, blocks_per_sm)
+              : push_bps_t<float>(warps, smem_nodes, blocks_per_sm);
+}
+
 int push_config(int fp64, int smem_nodes, int* warps, int* blocks_per_sm, size_t* smem_bytes) {
   return fp64 ? push_config_t<double>(smem_nodes, warps, blocks_per_sm, smem_bytes)
               : push_config_t<float>(smem_nodes, warps, blocks_per_sm, smem_bytes);

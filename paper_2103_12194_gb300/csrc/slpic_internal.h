@@ -265,6 +265,8 @@ void launch_push(const DeviceRefs& r, int grid, cudaStream_t s);
 // Particle-kernel shape for a shared-memory deposit grid of smem_nodes nodes:
 // warps per CTA, resident CTAs per SM and dynamic shared memory per CTA.
 int push_config(int fp64, int smem_nodes, int* warps, int* blocks_per_sm, size_t* smem_bytes);
+// Resident particle-kernel CTAs per SM for `warps` warps per CTA.
+int push_blocks_per_sm(int fp64, int warps, int smem_nodes, int* blocks_per_sm);
 // mode 0: finish a step and plan the next; mode 1: plan only (one CTA).
 void launch_finish(const DeviceRefs& r, int mode, cudaStream_t s);
 void launch_move(const DeviceRefs& r, int grid, cudaStream_t s);

@@ -109,6 +109,9 @@ def lib():
         "slpic_philox_static": ([i32, u64, vp, i64, vp], i32),
         "slpic_paschen_bisect": ([vp, ctypes.POINTER(PaschenSpec), vp, vp, vp], i32),
         "slpic_set_precision": ([vp, i32], i32),
+        "slpic_set_launch_shape": ([vp, i32, i32], i32),
+        "slpic_get_launch_shape": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
+        "slpic_autotune": ([vp, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
         "slpic_load_particles_f64": ([vp, i32, i32, ctypes.POINTER(SoA), i64, u32], i32),
         "slpic_read_particles_f64": ([vp, i32, i32, ctypes.POINTER(SoA), i64,
                                       ctypes.POINTER(i64)], i32),
@@ -349,6 +352,23 @@ class Simulation:
         self._ck(self._L.slpic_paschen_bisect(self._h, ctypes.byref(spec), _ptr(out_lo),
                                               _ptr(out_hi), _ptr(gain)))
         return out_lo, out_hi, gain.reshape(n_pd, int(n_v))
+
+    def set_launch_shape(self, push_warps, collide_ctas_per_sm):
+        self._ck(self._L.slpic_set_launch_shape(self._h, int(push_warps),
+                                                int(collide_ctas_per_sm)))
+
+    def launch_shape(self):
+        w, cc = ctypes.c_int32(), ctypes.c_int32()
+        self._ck(self._L.slpic_get_launch_shape(self._h, ctypes.byref(w), ctypes.byref(cc)))
+        return w.value, cc.value
+
+    def autotune(self, steps_each=32):
+        """slpic_autotune: advances the simulation while timing shapes;
+        returns the chosen (push warps, collision CTAs per SM)."""
+        w, cc = ctypes.c_int32(), ctypes.c_int32()
+        self._ck(self._L.slpic_autotune(self._h, int(steps_each), ctypes.byref(w),
+                                        ctypes.byref(cc)))
+        return w.value, cc.value
 
     def set_profiling(self, on):
         self._ck(self._L.slpic_set_profiling(self._h, 1 if on else 0))
