@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--paschen", action="store_true",
                     help="also time the batched FP32 breakdown-voltage sweep against the "
                          "plain one-instance FP64 bisection")
@@ -219,6 +220,25 @@ def paschen_sweep(slpic, inputs, local, stream, pds=(0.5, 1.0, 2.0, 4.0), n_v=8,
             "speedup": t64 / t32}
 
 
+def combine_ranks(elapsed_ms, marker_steps, world, device):
+    """Whole-job figures of a weak-scaling run: every rank advances its own
+    independent instance, so the job's time is the slowest rank's and its
+    work the sum of the ranks' marker-steps.  Returns (seconds, marker-steps).
+    With world > 1 the ranks exchange their two numbers (all-gather on
+    `device`: "cuda" under NCCL, "cpu" under gloo)."""
+    times, counts = [float(elapsed_ms)], [float(marker_steps)]
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([float(elapsed_ms), float(marker_steps)], dtype=torch.float64,
+                          device=device)
+        allt = [torch.zeros_like(tt) for _ in range(world)]
+        dist.all_gather(allt, tt)
+        times = [float(x[0]) for x in allt]
+        counts = [float(x[1]) for x in allt]
+    return max(times) / 1e3, sum(counts)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -267,6 +287,10 @@ def run_ours(args):
     sim = slpic.Simulation(1, device=local, stream=stream)
     sim.configure(0, spec, capacity=(cap_e, cap_i))
     sim.seed(0, slpic.ELECTRON, n, slpic.SEED_GAP, e_lo=run["e_lo"], e_hi=run["e_hi"])
+    shape = sim.launch_shape()
+    if not args.no_autotune:
+        # real steps of the run, before the warm-up and the timed region
+        shape = sim.autotune(steps_each=16)
     sim.step(args.warmup)
     sim.synchronize()
     sim.set_profiling(True)
@@ -288,17 +312,8 @@ def run_ours(args):
     push_ms, push_launches = sim.profile()
     t_after = sim.tallies(0)
     marker_steps = int(t_after["marker_steps"]) - ms_before
-    times = [elapsed_ms]
-    counts = [marker_steps]
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([elapsed_ms, float(marker_steps)], device="cuda")
-        allt = [torch.zeros_like(tt) for _ in range(world)]
-        dist.all_gather(allt, tt)
-        times = [float(x[0]) for x in allt]
-        counts = [float(x[1]) for x in allt]
-    t_max = max(times) / 1e3
-    value = sum(counts) / t_max
+    t_max, total = combine_ranks(elapsed_ms, marker_steps, world, "cuda")
+    value = total / t_max
     avg_push_s = push_ms / 1e3 / max(1, push_launches)
     markers_per_launch = marker_steps / max(1, push_launches)
     achieved = BYTES_PER_MARKER_STEP * markers_per_launch / avg_push_s / 1e9
@@ -359,6 +374,7 @@ def run_ours(args):
         sim = slpic.Simulation(1, device=local, stream=stream)
         sim.configure(0, spec, capacity=(cap_e, cap_i))
         sim.load(0, slpic.ELECTRON, pinned)   # build and warm the context
+        sim.set_launch_shape(*shape)
         sim.step(args.warmup)
         sim.synchronize()
         dens = np.empty(spec["n_cells"] + 1)
@@ -401,6 +417,9 @@ def run_ours(args):
                                    "0.1-200 eV, 4096 cells, 1 Torr, 300 V, Poisson on",
                        "markers": n, "cells": spec["n_cells"], "instances_per_gpu": 1,
                        "live_at_end": [int(x) for x in t_after["n_live"]],
+                       "launch_shape": {"push_warps_per_cta": shape[0],
+                                        "collide_ctas_per_sm": shape[1],
+                                        "autotuned": not args.no_autotune},
                        "parallelism": "independent instance per GPU" if world > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (%.2f GB of markers > %.0f MB)"
                              % (state_bytes / 1e9, L2_BYTES / 2**20)},
