@@ -84,6 +84,9 @@ struct slpic_ctx {
   int sms = 0;             // multiprocessors of the device
   int max_push_warps = 0;  // most particle-kernel warps per CTA that fit
   int collide_per_sm = 8;  // collision CTAs per SM
+  // per instance: stepped since its field was last reset (phi is then formed
+  // from the last deposit when read)
+  std::vector<char> stepped;
   int blocks_per_sm = 0;
   // graph of kGraphSteps steps
   cudaGraphExec_t graph = nullptr;
@@ -272,6 +275,7 @@ int reset_field(slpic_ctx* c, int i) {
   CK(cudaMemcpyAsync(P.E64, E.data(), nn * 8, cudaMemcpyHostToDevice, c->stream), "field");
   CK(cudaMemcpyAsync(P.E32, E32.data(), nn * 4, cudaMemcpyHostToDevice, c->stream), "field");
   CK(cudaStreamSynchronize(c->stream), "field");
+  if ((int)c->stepped.size() == c->n_inst) c->stepped[i] = 0;
   return SLPIC_OK;
 }
 
@@ -454,6 +458,12 @@ int commit(slpic_ctx* c) {
   c->refs.smem_nodes = smem_nodes;
   c->refs.push_warps = warps;
   c->refs.fp64 = c->fp64;
+  {
+    int net_nodes = 0;
+    if (int e2 = finish_config(max_nodes, &net_nodes))
+      return cuda_fail(c, (cudaError_t)e2, "finish kernel configuration");
+    c->refs.finish_net_nodes = net_nodes;
+  }
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device), "attributes");
   c->sms = sms;
@@ -618,6 +628,7 @@ int slpic_create(slpic_ctx** out, int device, int n_instances) {
   c->device = device;
   c->n_inst = n_instances;
   c->hi.resize(n_instances);
+  c->stepped.assign(n_instances, 0);
   *out = c;
   return SLPIC_OK;
 }
@@ -966,6 +977,7 @@ int slpic_reset_counters(slpic_ctx* c, int inst) {
 int slpic_step(slpic_ctx* c, int64_t n) {
   if (!c || n < 0) return fail(c, SLPIC_ERR_INVALID_ARG, "bad step count");
   if (int rc = prepare(c)) return rc;
+  if (n > 0) std::fill(c->stepped.begin(), c->stepped.end(), 1);
   c->last_launches = 0;
   if (c->profiling) {
     for (int64_t k = 0; k < n; ++k) {
@@ -1125,6 +1137,13 @@ int slpic_read_field(slpic_ctx* c, int inst, double* phi, double* E, int64_t n) 
   int rc = sync(c);
   const InstDev& P = c->h_inst[inst];
   if (n != P.n_cells + 1) return fail(c, SLPIC_ERR_INVALID_ARG, "need n_cells + 1 values");
+  // the step keeps only the node field; phi is formed from the last deposit
+  // (in the frozen-field mode it stays the vacuum solution)
+  if (P.field_mode == 1 && c->stepped[inst]) {
+    launch_phi(c->refs, inst, c->stream);
+    CK(cudaGetLastError(), "read field");
+    CK(cudaStreamSynchronize(c->stream), "read field");
+  }
   CK(cudaMemcpy(phi, P.phi, n * 8, cudaMemcpyDeviceToHost), "read field");
   CK(cudaMemcpy(E, P.E64, n * 8, cudaMemcpyDeviceToHost), "read field");
   return rc;

@@ -50,58 +50,121 @@ __device__ T block_incl_scan(T v, T* buf) {
   return r;
 }
 
-// Plan the next step from the tiles in use (one thread): particle-kernel
-// super-tiles (push_warps tiles each) and their weights per segment,
-// collision chunks per instance, repacking chunks.
-__device__ void plan_next(const DeviceRefs& r) {
+// Plan the next step from the tiles in use (all threads of one CTA):
+// particle-kernel super-tiles (push_warps tiles each) and their weights per
+// segment, repacking chunks per segment and collision chunks per instance,
+// as exclusive block scans in rounds of kFinThreads entries.
+__device__ void plan_next(const DeviceRefs& r, long long* s_buf) {
+  __shared__ long long s_carry[4];
   const int n_seg = r.n_inst * 2;
-  const unsigned int W = (unsigned int)r.push_warps;
-  unsigned int start = 0, wstart = 0, coll = 0, move = 0;
-  for (int s = 0; s < n_seg; ++s) {
-    r.seg_start[s] = start;
-    r.seg_wstart[s] = wstart;
-    const unsigned int ns = (r.sstate[s].n_tiles + W - 1) / W;
-    start += ns;
-    wstart += ns * ((s & 1) ? kWeightIon : kWeightElectron);
+  const long long W = r.push_warps;
+  const int t = threadIdx.x;
+  if (t < 4) s_carry[t] = 0;
+  __syncthreads();
+  for (int base = 0; base < n_seg; base += kFinThreads) {
+    const int sg = base + t;
+    long long ns = 0, w = 0, mv = 0;
+    if (sg < n_seg) {
+      ns = ((long long)r.sstate[sg].n_tiles + W - 1) / W;
+      w = ns * ((sg & 1) ? kWeightIon : kWeightElectron);
+      const Transfer& x = r.xfer[sg];
+      if (x.compact) mv = ((long long)x.n_tiles_old + kMoveChunkTiles - 1) / kMoveChunkTiles;
+    }
+    const long long i_ns = block_incl_scan<long long>(ns, s_buf);
+    const long long i_w = block_incl_scan<long long>(w, s_buf);
+    const long long i_mv = block_incl_scan<long long>(mv, s_buf);
+    if (sg < n_seg) {
+      r.seg_start[sg] = (unsigned int)(s_carry[0] + i_ns - ns);
+      r.seg_wstart[sg] = (unsigned int)(s_carry[1] + i_w - w);
+      r.move_start[sg] = (unsigned int)(s_carry[2] + i_mv - mv);
+    }
+    __syncthreads();
+    if (t == kFinThreads - 1) {
+      s_carry[0] += i_ns;
+      s_carry[1] += i_w;
+      s_carry[2] += i_mv;
+    }
+    __syncthreads();
   }
-  for (int i = 0; i < r.n_inst; ++i) {
-    r.coll_start[i] = coll;
-    coll += (r.sstate[2 * i].n_tiles + kCollChunkTiles - 1) / kCollChunkTiles +
-            (r.sstate[2 * i + 1].n_tiles + kCollChunkTiles - 1) / kCollChunkTiles;
+  for (int base = 0; base < r.n_inst; base += kFinThreads) {
+    const int i = base + t;
+    long long nc = 0;
+    if (i < r.n_inst)
+      nc = ((long long)r.sstate[2 * i].n_tiles + kCollChunkTiles - 1) / kCollChunkTiles +
+           ((long long)r.sstate[2 * i + 1].n_tiles + kCollChunkTiles - 1) / kCollChunkTiles;
+    const long long i_nc = block_incl_scan<long long>(nc, s_buf);
+    if (i < r.n_inst) r.coll_start[i] = (unsigned int)(s_carry[3] + i_nc - nc);
+    __syncthreads();
+    if (t == kFinThreads - 1) s_carry[3] += i_nc;
+    __syncthreads();
   }
-  for (int s = 0; s < n_seg; ++s) {
-    r.move_start[s] = move;
-    const Transfer& x = r.xfer[s];
-    if (x.compact) move += (x.n_tiles_old + kMoveChunkTiles - 1) / kMoveChunkTiles;
+  if (t == 0) {
+    const unsigned int start = (unsigned int)s_carry[0], wstart = (unsigned int)s_carry[1];
+    const unsigned int move = (unsigned int)s_carry[2], coll = (unsigned int)s_carry[3];
+    r.seg_start[n_seg] = start;
+    r.seg_wstart[n_seg] = wstart;
+    r.coll_start[r.n_inst] = coll;
+    r.move_start[n_seg] = move;
+    r.ctrl->n_super = start;
+    r.ctrl->w_total = wstart;
+    r.ctrl->n_seg = n_seg;
+    r.ctrl->n_coll_chunks = coll;
+    r.ctrl->coll_counter = 0;
+    r.ctrl->n_move_chunks = move;
+    r.ctrl->move_counter = 0;
+    r.ctrl->epoch = (r.ctrl->epoch + 1u) & 0x3FFFFFFFu;
+    r.ctrl->finish_done = 0;
   }
-  r.seg_start[n_seg] = start;
-  r.seg_wstart[n_seg] = wstart;
-  r.coll_start[r.n_inst] = coll;
-  r.move_start[n_seg] = move;
-  r.ctrl->n_super = start;
-  r.ctrl->w_total = wstart;
-  r.ctrl->n_seg = n_seg;
-  r.ctrl->n_coll_chunks = coll;
-  r.ctrl->coll_counter = 0;
-  r.ctrl->n_move_chunks = move;
-  r.ctrl->move_counter = 0;
-  r.ctrl->epoch = (r.ctrl->epoch + 1u) & 0x3FFFFFFFu;
-  r.ctrl->finish_done = 0;
 }
 
 }  // namespace
 
-// mode 0: finish a step and plan the next; mode 1: plan only (one CTA).
-__global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode) {
+// Net deposit (ions minus electrons) at node k of the last step: from the
+// CTA's shared copy when there is one, else from the last deposit.
+__device__ __forceinline__ long long net_at(const InstDev& P, const long long* s_net, int k) {
+  return s_net ? s_net[k] : P.rho_last[kIon][k] - P.rho_last[kElectron][k];
+}
+
+// The exact integer sums of the 1D Poisson solve over the last step's net
+// deposit (all threads of a kFinThreads CTA; thread t covers k = k0 ..
+// k0 + chunk - 1 of 1..N): returns D_1 = (V + C J_N) / N and writes I_{k0}.
+__device__ double poisson_d1(const InstDev& P, const long long* s_net, int k0, int chunk,
+                             long long* s_i64, __int128* s_i128, long long* I_k0) {
+  const int N = P.n_cells;
+  long long loc = 0;
+  for (int k = k0; k < k0 + chunk && k <= N - 1; ++k) loc += net_at(P, s_net, k);
+  const long long inc = block_incl_scan<long long>(loc, s_i64);
+  long long Ik = inc - loc;  // I_k at the chunk start (exclusive of net_k)
+  *I_k0 = Ik;
+  __int128 locJ = 0;
+  for (int k = k0; k < k0 + chunk && k <= N; ++k) {
+    locJ += (__int128)Ik;
+    if (k <= N - 1) Ik += net_at(P, s_net, k);
+  }
+  const __int128 incJ = block_incl_scan<__int128>(locJ, s_i128);
+  __shared__ __int128 s_JN;
+  if (threadIdx.x == kFinThreads - 1) s_JN = incJ;
+  __syncthreads();
+  const __int128 JN = s_JN;
+  __syncthreads();
+  return (P.V + P.pois_C * (double)JN) / (double)N;
+}
+
+// mode 0: finish a step (one CTA per instance; the last one plans the next
+// step); mode 1: plan only (one CTA).  Dynamic shared memory: net_nodes
+// int64 nodes for the net deposit (0: read it from global memory).
+__global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode, int net_nodes) {
+  extern __shared__ long long s_dyn[];
   __shared__ long long s_i64[32];
   __shared__ __int128 s_i128[32];
+  __shared__ unsigned long long s_acc[ACC_COUNT];
   __shared__ int s_flag;
   Control* ctrl = r.ctrl;
+  const int t = threadIdx.x;
   if (mode == 1) {
-    if (threadIdx.x == 0) {
-      for (int s = 0; s < 2 * r.n_inst; ++s) r.xfer[s].compact = 0;
-      plan_next(r);
-    }
+    for (int sg = t; sg < 2 * r.n_inst; sg += kFinThreads) r.xfer[sg].compact = 0;
+    __syncthreads();
+    plan_next(r, s_i64);
     return;
   }
   if (*((volatile int*)&ctrl->error)) return;
@@ -109,38 +172,60 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode) 
   const InstDev& P = r.inst[inst];
   InstState& is = r.istate[inst];
   unsigned long long* a = P.acc;
+  const int N = P.n_cells, nn = N + 1;
+  long long* s_net = nn <= net_nodes ? s_dyn : nullptr;
 
-  // ---- marker counts and where the stores end --------------------------------
+  // ---- accumulators and the step's deposit, all threads at once -------------
+  // deposit -> rho_last (and the net charge to shared memory); clear both
+  if (t < ACC_COUNT) {
+    s_acc[t] = a[t];
+    a[t] = 0ull;
+  }
+  for (int k = t; k < nn; k += kFinThreads) {
+    const long long qe = (long long)P.rho_acc[kElectron][k];
+    const long long qi = (long long)P.rho_acc[kIon][k];
+    P.rho_last[kElectron][k] = qe;
+    P.rho_last[kIon][k] = qi;
+    P.rho_acc[kElectron][k] = 0ull;
+    P.rho_acc[kIon][k] = 0ull;
+    if (s_net) s_net[k] = qi - qe;
+  }
+  __syncthreads();
+
+  // ---- marker counts and where the stores end (one thread per species) -------
   // survivors = live - absorbed; births (ionizations: an electron and an ion
   // each; emitted electrons) were appended after the last live marker
-  if (threadIdx.x == 0) {
-    const uint32_t n_ionz = (uint32_t)a[ACC_COLL2], n_see = (uint32_t)a[ACC_SEE];
-    for (int sp = 0; sp < 2; ++sp) {
-      SpeciesState& st = r.sstate[inst * 2 + sp];
-      const SpeciesDev& S = P.sp[sp];
-      Transfer& x = r.xfer[inst * 2 + sp];
-      const uint32_t absorbed = (uint32_t)(a[ACC_NABS + 2 * sp] + a[ACC_NABS + 2 * sp + 1]);
-      const uint32_t nb = sp ? n_ionz : n_ionz + n_see;
-      const uint32_t surv = st.n_live - absorbed;
-      const uint32_t tail =
-          st.n_tiles ? (st.n_tiles - 1) * (uint32_t)kTile + S.fill[st.cur][st.n_tiles - 1] : 0u;
-      const uint32_t end = tail + nb;
-      const uint32_t n_new = surv + nb;
-      const uint32_t nt = (end + kTile - 1) / kTile;
-      // repack when under three quarters of the slots in use are live
-      x.compact = (nt > 2 && (unsigned long long)n_new * 4 < (unsigned long long)nt * kTile * 3)
-                      ? 1u : 0u;
-      x.src = st.cur;
-      x.dst = x.compact ? st.cur ^ 1u : st.cur;
-      x.n_tiles_old = nt;
-      x.n_new = n_new;
-      x.tail = tail;
-      x.end = end;
-      st.cur = x.dst;
-      st.n_live = n_new;
-      st.next_id += nb;
-      st.n_tiles = x.compact ? (n_new + kTile - 1) / kTile : nt;
-    }
+  if (t < 2) {
+    const int sp = t;
+    const uint32_t n_ionz = (uint32_t)s_acc[ACC_COLL2], n_see = (uint32_t)s_acc[ACC_SEE];
+    SpeciesState& st = r.sstate[inst * 2 + sp];
+    const SpeciesDev& S = P.sp[sp];
+    Transfer& x = r.xfer[inst * 2 + sp];
+    const uint32_t absorbed = (uint32_t)(s_acc[ACC_NABS + 2 * sp] + s_acc[ACC_NABS + 2 * sp + 1]);
+    const uint32_t nb = sp ? n_ionz : n_ionz + n_see;
+    const SpeciesState s0 = st;
+    const uint32_t surv = s0.n_live - absorbed;
+    const uint32_t tail =
+        s0.n_tiles ? (s0.n_tiles - 1) * (uint32_t)kTile + S.fill[s0.cur][s0.n_tiles - 1] : 0u;
+    const uint32_t end = tail + nb;
+    const uint32_t n_new = surv + nb;
+    const uint32_t nt = (end + kTile - 1) / kTile;
+    // repack when under three quarters of the slots in use are live
+    const uint32_t compact =
+        (nt > 2 && (unsigned long long)n_new * 4 < (unsigned long long)nt * kTile * 3) ? 1u : 0u;
+    x.compact = compact;
+    x.src = s0.cur;
+    x.dst = compact ? s0.cur ^ 1u : s0.cur;
+    x.n_tiles_old = nt;
+    x.n_new = n_new;
+    x.tail = tail;
+    x.end = end;
+    SpeciesState s1;
+    s1.cur = x.dst;
+    s1.n_live = n_new;
+    s1.next_id = s0.next_id + nb;
+    s1.n_tiles = compact ? (n_new + kTile - 1) / kTile : nt;
+    st = s1;
   }
   __syncthreads();
   // fills of the tail tile and the new tiles: their slots below `end` are live
@@ -149,152 +234,180 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode) 
     const SpeciesDev& S = P.sp[sp];
     const Transfer& x = r.xfer[inst * 2 + sp];
     if (x.end == x.tail) continue;
-    for (uint32_t k = x.tail / kTile + threadIdx.x; k < x.n_tiles_old; k += kFinThreads)
+    for (uint32_t k = x.tail / kTile + t; k < x.n_tiles_old; k += kFinThreads)
       S.fill[x.src][k] = min(x.end - k * (uint32_t)kTile, (uint32_t)kTile);
   }
 
-  // ---- deposit of the step -> rho_last; clear the accumulators -------------
-  const int nn = P.n_cells + 1;
-  for (int s = 0; s < 2; ++s) {
-    for (int k = threadIdx.x; k < nn; k += kFinThreads) {
-      P.rho_last[s][k] = (long long)P.rho_acc[s][k];
-      P.rho_acc[s][k] = 0ull;
-    }
-  }
-  __syncthreads();
-
   // ---- Poisson: (phi[k+1] - 2 phi[k] + phi[k-1]) = -C net_k, k = 1..N-1 ----
-  // With D_k = phi[k] - phi[k-1]: D_k = D_1 - C I_k, I_k = sum_{j<k} net_j,
-  // phi[k] = k D_1 - C J_k, J_k = sum_{i<=k} I_i, and phi[N] = V fixes D_1.
-  // I and J are exact integers (64- and 128-bit), so the solution is
-  // independent of the summation order.
+  // With D_k = phi[k] - phi[k-1]: D_k = D_1 - C I_k, I_k = sum_{0<j<k} net_j,
+  // and phi[N] = V fixes D_1 = (V + C J_N) / N, J_N = sum_{0<i<=N} I_i.
+  // The node field is the centred difference of phi, written with the exact
+  // integer sums: E_k = -(D_k + D_{k+1}) / (2 dx) = -(2 D_1 - C (I_k + I_{k+1}))
+  // / (2 dx), one-sided at the electrodes; phi itself is formed on demand
+  // (k_phi) when it is read.
   if (P.field_mode == 1) {
-    const int N = P.n_cells;
     const int chunk = (N + kFinThreads - 1) / kFinThreads;  // over k = 1..N
-    const int k0 = 1 + threadIdx.x * chunk;
-    long long loc = 0;
-    for (int k = k0; k < k0 + chunk && k <= N; ++k)
-      if (k <= N - 1) loc += P.rho_last[kIon][k] - P.rho_last[kElectron][k];
-    const long long inc = block_incl_scan<long long>(loc, s_i64);
-    long long Ik = inc - loc;  // I_k at the chunk start (exclusive of net_k)
-    __int128 locJ = 0;
-    for (int k = k0; k < k0 + chunk && k <= N; ++k) {
-      locJ += (__int128)Ik;
-      if (k <= N - 1) Ik += P.rho_last[kIon][k] - P.rho_last[kElectron][k];
-    }
-    const __int128 incJ = block_incl_scan<__int128>(locJ, s_i128);
-    __shared__ __int128 s_JN;
-    if (threadIdx.x == kFinThreads - 1) s_JN = incJ;
-    __syncthreads();
+    const int k0 = 1 + t * chunk;
+    long long I0;
+    const double D1 = poisson_d1(P, s_net, k0, chunk, s_i64, s_i128, &I0);
     const double C = P.pois_C;
-    const double D1 = (P.V + C * (double)s_JN) / (double)N;
-    __int128 J = incJ - locJ;
-    Ik = inc - loc;
-    for (int k = k0; k < k0 + chunk && k <= N; ++k) {
-      J += (__int128)Ik;
-      if (k <= N - 1) Ik += P.rho_last[kIon][k] - P.rho_last[kElectron][k];
-      P.phi[k] = (double)k * D1 - C * (double)J;
-    }
-    if (threadIdx.x == 0) P.phi[0] = 0.0;
-    __syncthreads();
-    if (threadIdx.x == 0) P.phi[N] = P.V;
-    __syncthreads();
     const double inv2dx = 1.0 / (2.0 * P.dx);
-    for (int k = threadIdx.x; k <= N; k += kFinThreads) {
+    const double twoD1 = D1 + D1;
+    long long Ik = I0;
+    for (int k = k0; k < k0 + chunk && k <= N; ++k) {
       double e;
-      if (k == 0) e = -(P.phi[1] - P.phi[0]) / P.dx;
-      else if (k == N) e = -(P.phi[N] - P.phi[N - 1]) / P.dx;
-      else e = -(P.phi[k + 1] - P.phi[k - 1]) * inv2dx;
+      if (k <= N - 1) {
+        const long long Ik1 = Ik + net_at(P, s_net, k);
+        e = -(twoD1 - C * (double)(Ik + Ik1)) * inv2dx;
+        Ik = Ik1;
+      } else {
+        e = -(D1 - C * (double)Ik) / P.dx;  // k = N
+      }
       P.E64[k] = e;
       P.E32[k] = (float)e;
     }
+    if (t == 0) {
+      const double e0 = -D1 / P.dx;  // I_1 = 0: D_1
+      P.E64[0] = e0;
+      P.E32[0] = (float)e0;
+    }
   }
-  __syncthreads();
 
-  // ---- tallies -------------------------------------------------------------
-  // the accumulators are read by ACC_COUNT threads at once; the record is
-  // assembled in shared memory and added to the totals slot by slot
-  __shared__ unsigned long long s_acc[ACC_COUNT];
-  __shared__ TallyRec s_rec;
-  if (threadIdx.x < ACC_COUNT) {
-    s_acc[threadIdx.x] = a[threadIdx.x];
-    a[threadIdx.x] = 0ull;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned long long* q = s_acc;
-    const double unit = 1.0 / P.c64.wscale;
-    TallyRec& t = s_rec;
-    t.step = is.step;
-    t.n_live[0] = r.sstate[inst * 2].n_live;
-    t.n_live[1] = r.sstate[inst * 2 + 1].n_live;
-    // live weight by its changes: minus what left through the electrodes,
-    // plus the births (ionization pairs, emitted electrons)
-    is.w_live[0] = is.w_live[0] - q[ACC_WABS + 0] - q[ACC_WABS + 1] + q[ACC_WIONZ] + q[ACC_WSEE];
-    is.w_live[1] = is.w_live[1] - q[ACC_WABS + 2] - q[ACC_WABS + 3] + q[ACC_WIONZ];
-    t.w_live[0] = (double)(long long)is.w_live[0] * unit;
-    t.w_live[1] = (double)(long long)is.w_live[1] * unit;
-    for (int k = 0; k < 3; ++k) t.n_coll[k] = (long long)q[ACC_COLL0 + k];
-    t.n_candidates = (long long)q[ACC_CAND];
-    for (int s = 0; s < 2; ++s)
-      for (int e = 0; e < 2; ++e) {
-        t.n_abs[s][e] = (long long)q[ACC_NABS + 2 * s + e];
-        t.w_abs[s][e] = (double)(long long)q[ACC_WABS + 2 * s + e] * unit;
-      }
-    t.n_see = (long long)q[ACC_SEE];
-    t.w_see = (double)(long long)q[ACC_WSEE] * unit;
-    t.w_ionz = (double)(long long)q[ACC_WIONZ] * unit;
-    t.w_cath_ion = (double)(long long)q[ACC_WCATH] * unit;
-    t.w_cath_ion_gen0 = (double)(long long)q[ACC_WCATH0] * unit;
-    t.n_clamp = (long long)q[ACC_CLAMP];
-    t.n_majorant = (long long)q[ACC_MAJ];
-    t.marker_steps = (long long)q[ACC_MSTEPS];
-    is.step += 1u;
-  }
-  __syncthreads();
-  // slot layout of TallyRec (8 bytes each): 0 step, 1-2 n_live, 3-4 w_live,
-  // 5-7 n_coll, 8 n_candidates, 9-12 n_abs, 13-16 w_abs, 17 n_see, 18 w_see,
-  // 19 w_ionz, 20 w_cath_ion, 21 w_cath_ion_gen0, 22 n_clamp, 23 n_majorant,
-  // 24 marker_steps; slots 0-4 are states (replaced), the others sums
+  // ---- tallies: one thread per 8-byte slot of the record ---------------------
+  // slot layout of TallyRec: 0 step, 1-2 n_live, 3-4 w_live, 5-7 n_coll,
+  // 8 n_candidates, 9-12 n_abs, 13-16 w_abs, 17 n_see, 18 w_see, 19 w_ionz,
+  // 20 w_cath_ion, 21 w_cath_ion_gen0, 22 n_clamp, 23 n_majorant,
+  // 24 marker_steps; slots 0-4 are states (replaced in the totals), the
+  // others sums
   constexpr int kSlots = (int)(sizeof(TallyRec) / 8);
   static_assert(kSlots == 25, "TallyRec layout");
-  if (threadIdx.x < kSlots) {
-    const int j = threadIdx.x;
-    const long long* src = reinterpret_cast<const long long*>(&s_rec);
+  if (t < kSlots) {
+    const unsigned long long* q = s_acc;
+    const double unit = 1.0 / P.c64.wscale;
+    long long iv = 0;
+    double dv = 0.0;
+    bool is_double = false;
+    if (t == 0) {
+      iv = is.step;
+    } else if (t <= 2) {
+      iv = r.sstate[inst * 2 + t - 1].n_live;
+    } else if (t <= 4) {
+      // live weight by its changes: minus what left through the electrodes,
+      // plus the births (ionization pairs; emitted electrons)
+      const int sp = t - 3;
+      unsigned long long w = is.w_live[sp] - q[ACC_WABS + 2 * sp] - q[ACC_WABS + 2 * sp + 1] +
+                             q[ACC_WIONZ] + (sp == 0 ? q[ACC_WSEE] : 0ull);
+      is.w_live[sp] = w;
+      dv = (double)(long long)w * unit;
+      is_double = true;
+    } else if (t <= 7) {
+      iv = (long long)q[ACC_COLL0 + t - 5];
+    } else if (t == 8) {
+      iv = (long long)q[ACC_CAND];
+    } else if (t <= 12) {
+      iv = (long long)q[ACC_NABS + t - 9];
+    } else if (t <= 16) {
+      dv = (double)(long long)q[ACC_WABS + t - 13] * unit;
+      is_double = true;
+    } else if (t == 17) {
+      iv = (long long)q[ACC_SEE];
+    } else if (t <= 21) {
+      const int acc_of[4] = {ACC_WSEE, ACC_WIONZ, ACC_WCATH, ACC_WCATH0};
+      dv = (double)(long long)q[acc_of[t - 18]] * unit;
+      is_double = true;
+    } else if (t == 22) {
+      iv = (long long)q[ACC_CLAMP];
+    } else if (t == 23) {
+      iv = (long long)q[ACC_MAJ];
+    } else {
+      iv = (long long)q[ACC_MSTEPS];
+    }
     long long* ring = reinterpret_cast<long long*>(P.ring + is.n_steps_done % P.ring_len);
     long long* tot = reinterpret_cast<long long*>(P.total);
-    ring[j] = src[j];
-    const bool is_double = (j >= 3 && j <= 4) || (j >= 13 && j <= 16) || (j >= 18 && j <= 21);
-    if (j <= 4) {
-      tot[j] = src[j];
-    } else if (is_double) {
-      double* td = reinterpret_cast<double*>(tot);
-      const double* sd = reinterpret_cast<const double*>(src);
-      td[j] += sd[j];
+    if (is_double) {
+      reinterpret_cast<double*>(ring)[t] = dv;
+      if (t <= 4) reinterpret_cast<double*>(tot)[t] = dv;
+      else reinterpret_cast<double*>(tot)[t] += dv;
     } else {
-      tot[j] += src[j];
+      ring[t] = iv;
+      if (t <= 4) tot[t] = iv;
+      else tot[t] += iv;
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) is.n_steps_done += 1;
+  if (t == 0) {
+    is.step += 1u;
+    is.n_steps_done += 1;
+  }
 
   // ---- the last CTA plans the next step --------------------------------------
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (t == 0) {
     const unsigned int ticket = atomicAdd(&ctrl->finish_done, 1u);
     s_flag = ticket == gridDim.x - 1 ? 1 : 0;
   }
   __syncthreads();
-  if (s_flag && threadIdx.x == 0) {
+  if (s_flag) {
     __threadfence();
-    plan_next(r);
+    plan_next(r, s_i64);
   }
+}
+
+// phi_k = k D_1 - C J_k, J_k = sum_{0<i<=k} I_i, from the last step's deposit
+// (one CTA; read only when the field is read).
+__global__ void __launch_bounds__(kFinThreads) k_phi(DeviceRefs r, int inst) {
+  __shared__ long long s_i64[32];
+  __shared__ __int128 s_i128[32];
+  const InstDev& P = r.inst[inst];
+  const int N = P.n_cells;
+  const int chunk = (N + kFinThreads - 1) / kFinThreads;
+  const int k0 = 1 + threadIdx.x * chunk;
+  long long Ik;
+  const double D1 = poisson_d1(P, nullptr, k0, chunk, s_i64, s_i128, &Ik);
+  const double C = P.pois_C;
+  // J at the chunk start: exclusive scan of the chunks' sums of I
+  __int128 locJ = 0;
+  {
+    long long I = Ik;
+    for (int k = k0; k < k0 + chunk && k <= N; ++k) {
+      locJ += (__int128)I;
+      if (k <= N - 1) I += P.rho_last[kIon][k] - P.rho_last[kElectron][k];
+    }
+  }
+  const __int128 incJ = block_incl_scan<__int128>(locJ, s_i128);
+  __int128 J = incJ - locJ;
+  for (int k = k0; k < k0 + chunk && k <= N; ++k) {
+    J += (__int128)Ik;
+    if (k <= N - 1) Ik += P.rho_last[kIon][k] - P.rho_last[kElectron][k];
+    P.phi[k] = k == N ? P.V : (double)k * D1 - C * (double)J;
+  }
+  if (threadIdx.x == 0) P.phi[0] = 0.0;
+}
+
+void launch_phi(const DeviceRefs& r, int inst, cudaStream_t s) {
+  k_phi<<<1, kFinThreads, 0, s>>>(r, inst);
+}
+
+// Dynamic shared memory of k_finish: the net deposit of the largest grid,
+// when it fits (DeviceRefs::finish_net_nodes, from finish_config).
+int finish_config(int max_nodes, int* net_nodes) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return (int)e;
+  const int room = (optin - 8 * 1024) / 8;  // static shared memory stays below 8 KB
+  *net_nodes = max_nodes <= room ? max_nodes : 0;
+  e = cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           *net_nodes * 8);
+  return (int)e;
 }
 
 void launch_finish(const DeviceRefs& r, int mode, cudaStream_t s) {
   const int grid = mode == 1 ? 1 : r.n_inst;
-  k_finish<<<grid, kFinThreads, 0, s>>>(r, mode);
+  const int nodes = mode == 1 ? 0 : r.finish_net_nodes;
+  k_finish<<<grid, kFinThreads, (size_t)nodes * 8, s>>>(r, mode, nodes);
 }
 
 // ---------------------------------------------------------------------------

@@ -258,6 +258,7 @@ struct DeviceRefs {
   int smem_nodes;         // deposit grid nodes in shared memory (0: global atomics)
   int push_warps;         // warps per particle-kernel CTA = tiles per super-tile
   int fp64;               // marker path in double precision (else float)
+  int finish_net_nodes;   // k_finish keeps the net deposit of up to this many nodes in shared memory
 };
 
 // Launchers (defined in the .cu files).
@@ -269,7 +270,11 @@ int push_config(int fp64, int smem_nodes, int* warps, int* blocks_per_sm, size_t
 int push_blocks_per_sm(int fp64, int warps, int smem_nodes, int* blocks_per_sm);
 // mode 0: finish a step and plan the next; mode 1: plan only (one CTA).
 void launch_finish(const DeviceRefs& r, int mode, cudaStream_t s);
+// Shared-memory room of k_finish for the largest grid (0: read from global).
+int finish_config(int max_nodes, int* net_nodes);
 void launch_move(const DeviceRefs& r, int grid, cudaStream_t s);
+// Node potential of instance inst from its last deposit (Poisson mode).
+void launch_phi(const DeviceRefs& r, int inst, cudaStream_t s);
 // Scatter the null-collision candidates queued by the particle kernel.
 void launch_collide(const DeviceRefs& r, int grid, cudaStream_t s);
 // Seeding: n markers written contiguously from slot `base` of the current
