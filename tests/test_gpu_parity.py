@@ -347,3 +347,46 @@ def test_bad_markers_are_rejected(slpic):
     assert err.value.code == slpic.ERR_INVALID_ARG
     assert sim.count(0, 0) == 0
     sim.close()
+
+
+# ---------------------------------------------------------------------------
+# The benchmark's own size and launch shape
+# ---------------------------------------------------------------------------
+
+def test_full_size_step_matches_fp32_mirror(slpic, oracle_mod):
+    """One step of the benchmark workload at its full size: 3.2e7 electrons,
+    4096 cells, Poisson on, seeded on the GPU. The launch shape is the one the
+    benchmark picks with the autotuner. All markers and all counts are compared
+    with the oracle's FP32 mirror, started from the GPU's seeded state read
+    back."""
+    spec, run = inputs.microbench_config(n_markers=32_000_000)
+    n = run["n_seed"]
+    sim = slpic.Simulation(1)
+    sim.configure(0, spec, capacity=(int(1.25 * n), n // 4))
+    sim.seed(0, slpic.ELECTRON, n, slpic.SEED_GAP, e_lo=run["e_lo"], e_hi=run["e_hi"])
+    e0 = sim.particles(0, 0)
+    # the autotuner's timing steps advance the run: tune a copy, use its shape
+    tune = slpic.Simulation(1)
+    tune.configure(0, spec, capacity=(int(1.25 * n), n // 4))
+    tune.seed(0, slpic.ELECTRON, n, slpic.SEED_GAP, e_lo=run["e_lo"], e_hi=run["e_hi"])
+    shape = tune.autotune(steps_each=4)
+    tune.close()
+    sim.set_launch_shape(*shape)
+    sim.step(1)
+    ref = oracle_mod.Oracle(spec, precision=32)
+    ref.load(0, e0)
+    ref.step(1)
+    hg, hr = sim.history(0)[-1], ref.history()[-1]
+    for k in ("n_live", "n_coll", "n_candidates", "n_abs", "n_see", "n_clamp", "n_majorant",
+              "marker_steps"):
+        assert np.array_equal(hg[k], hr[k]), (k, hg[k], hr[k])
+    assert hr["n_candidates"] > 100_000 and min(hr["n_coll"]) > 1000
+    g, r = sim.particles(0, 0), ref.particles(0)
+    del e0
+    assert_same_markers(g, r, spec["vlim_e"], exact_values=False)
+    del g
+    gi, ri = sim.particles(0, 1), ref.particles(1)
+    assert_same_markers(gi, ri, spec["vlim_e"], exact_values=False)
+    qg, qr = sim.charge(0, 0), ref.charge(0)
+    assert np.allclose(qg, qr, rtol=REL, atol=REL * 2**32)
+    sim.close()
