@@ -105,6 +105,8 @@ typedef struct {
   int64_t n_clamp;         /* energies clamped at 0 after an inelastic event */
   int64_t n_majorant;      /* electrons whose beta*v exceeded the majorant's cap */
   int64_t marker_steps;    /* markers advanced (both species) */
+  double w_gain_gen0;      /* sum of yield * w_j of first-generation ions at
+                              the cathode (the gain's numerator) */
 } slpic_tallies;
 
 /* Library version as an integer MMmmpp. */
@@ -154,6 +156,15 @@ int slpic_set_species(slpic_ctx* ctx, int inst, int species, double mass,
 /* Ion-induced secondary-electron yield gamma at the cathode (constant; the
  * emitted electron starts at x = 0 with zero velocity, Sec. IV). */
 int slpic_set_emission(slpic_ctx* ctx, int inst, double gamma_se);
+/* Yield model: SLPIC_EMISSION_CONSTANT (gamma of slpic_set_emission, the
+ * default) or SLPIC_EMISSION_ENERGY, the energy-dependent yield of Eq. sey:
+ * 0.09 (eps_i / 700 eV)^0.05 below 700 eV and 0.09 (eps_i / 700 eV)^0.72
+ * from 700 eV on, eps_i the ion's kinetic energy when it crosses the
+ * cathode.  An ion emits when its Philox draw is below the yield; the
+ * expected yield of first-generation ions is tallied in w_gain_gen0. */
+#define SLPIC_EMISSION_CONSTANT 0
+#define SLPIC_EMISSION_ENERGY 1
+int slpic_set_emission_model(slpic_ctx* ctx, int inst, int model);
 /* Time step [s]. */
 int slpic_set_dt(slpic_ctx* ctx, int inst, double dt);
 /* Random stream: 64-bit Philox key of the instance. */
@@ -241,10 +252,11 @@ int slpic_read_history(slpic_ctx* ctx, int inst, slpic_tallies* out,
  * x = 0 -> d. */
 int slpic_read_current(slpic_ctx* ctx, int inst, double* I_anode,
                        double* I_cathode);
-/* First-generation secondary-emission gain G = gamma * (sum of w_j of
+/* First-generation secondary-emission gain G = (sum of yield * w_j over
  * first-generation ions absorbed at the cathode) / (sum of seeded w_j):
- * expected emitted electrons per seed electron; G >= 1 is the Townsend
- * breakdown criterion gamma (e^(alpha d) - 1) >= 1 (Sec. II.A). */
+ * expected emitted electrons per seed electron (with a constant yield,
+ * gamma times the ions' flux weight); G >= 1 is the Townsend breakdown
+ * criterion gamma (e^(alpha d) - 1) >= 1 (Sec. II.A). */
 int slpic_read_gain(slpic_ctx* ctx, int inst, double* G);
 
 /* Breakdown-voltage search over a batch (Sec. V, Fig. paschen): the context
@@ -258,24 +270,27 @@ int slpic_read_gain(slpic_ctx* ctx, int inst, double* G);
  *  - its markers are replaced by n_seed electrons at the cathode (energy e0,
  *    SLPIC_SEED_CATHODE, unit weight), with the instance's seed advanced by
  *    the round;
- *  - secondary emission is switched off during the run, and the gain
- *    G = gamma * (flux weight of first-generation ions reaching the cathode)
- *    / (seeded weight) is its expected value (Townsend: G >= 1 is
- *    breakdown, Sec. II.A);
+ *  - secondary emission is switched off during the run (the yield model
+ *    stays), and the gain G = (yield * flux weight of first-generation ions
+ *    reaching the cathode) / (seeded weight) is its expected value
+ *    (Townsend: G >= 1 is breakdown, Sec. II.A);
  *  - the batch steps until every instance has no marker left, or
  *    max_steps, in chunks of at most chunk_steps steps between checks of the
  *    live counts: a chunk is shortened so that no store can overflow in it
  *    (electrons at most double per step); an instance with more than
  *    (1 + 1/gamma) n_seed live electrons or at least n_seed/gamma live ions
  *    is above breakdown for certain (each ionization leaves an ion that
- *    reaches the cathode): it is emptied and counts as G = +inf.  Every
- *    instance needs gamma > 0 and capacities of at least
+ *    reaches the cathode; gamma is the constant yield, or for Eq. sey the
+ *    yield 0.09 (0.1 eV / 700 eV)^0.05 of an ion that fell through 0.1 V,
+ *    a bound for every ion born more than 0.1 V from the cathode): it is
+ *    emptied and counts as G = +inf.  Every instance needs gamma > 0 and
+ *    capacities of at least
  *    2 (1 + 1/gamma) n_seed electrons and n_seed/gamma + (1 + 1/gamma) n_seed
  *    ions, else SLPIC_ERR_INVALID_ARG.
  * Then each bracket shrinks to [V_{j-1}, V_j] around the first j with
  * G >= 1 (V_{-1} = lo, V_{n_v} = hi).  On return Vb_lo/Vb_hi [n_pd] hold the
  * final brackets and, if not NULL, gain [n_pd * n_v] the last round's G.  The
- * instances keep the last round's voltage, v_lim and dt; gamma is restored.
+ * instances keep the last round's voltage, v_lim and dt; emission is on again.
  * Errors as the other calls (a capacity error cannot occur: see above). */
 typedef struct {
   int n_pd;            /* pd points */
@@ -291,6 +306,23 @@ typedef struct {
 } slpic_paschen_spec;
 int slpic_paschen_bisect(slpic_ctx* ctx, const slpic_paschen_spec* spec, double* Vb_lo,
                          double* Vb_hi, double* gain);
+
+/* The paper's breakdown test (Sec. V): advance every instance by n_windows
+ * windows of steps_per_window steps and write each instance's mean number of
+ * live ions per window to means [n_inst * n_windows] (instance-major).
+ * - Below breakdown the ion population falls back to zero after its first
+ *   rise; above it, it keeps growing.
+ * - above [n_inst] (may be NULL) is 1 when the last window's mean is
+ *   positive and exceeds every earlier window's, else 0.
+ * - An instance whose live markers (both species) pass a third of the
+ *   smaller store's capacity is above breakdown. It is emptied, its
+ *   remaining windows read -1, and it counts as above.
+ * - Steps run in chunks short enough that no store can overflow in between
+ *   (growth at most x3 per step with emission).
+ * - With the paper's setup: seed electrons at rest (SLPIC_SEED_REST),
+ *   n_windows * steps_per_window = 30 ion crossing times, the Eq. sey yield. */
+int slpic_ion_trend(slpic_ctx* ctx, int64_t steps_per_window, int n_windows, double* means,
+                    int* above);
 
 /* Launch shape of the step: warps per CTA of the particle kernel (a
  * multiple of 4, at most what fits next to the largest charge grid; each

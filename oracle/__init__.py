@@ -42,6 +42,8 @@ class OracleConfig(ctypes.Structure):
         ("e_ex", ctypes.c_double),
         ("e_io", ctypes.c_double),
         ("precision", ctypes.c_int),
+        ("emission_model", ctypes.c_int),
+        ("emit", ctypes.c_int),
     ]
 
 
@@ -61,6 +63,7 @@ TALLY_DTYPE = np.dtype([
     ("n_clamp", np.int64),
     ("n_majorant", np.int64),
     ("marker_steps", np.int64),
+    ("w_gain_gen0", np.float64),
 ])
 
 
@@ -191,6 +194,8 @@ class Oracle:
         c.e_ex = float(s["e_ex"])
         c.e_io = float(s["e_io"])
         c.precision = int(precision)
+        c.emission_model = int(s.get("emission_model", 0))
+        c.emit = int(s.get("emit", 1))
         self.precision = int(precision)
         self._cfg = c
         self._h = lib().oracle_create(ctypes.byref(c))

@@ -30,7 +30,10 @@
 //    removed, ionization with a uniform split of the excess energy (the
 //    Kutasi sharing rule is not given in the paper), Ar+ born with a gas
 //    temperature Maxwellian;
-//  * constant secondary-emission yield gamma (Lieberman value, Sec. V).
+//  * secondary-emission yield either constant (gamma, the Lieberman value of
+//    Sec. V) or the energy-dependent yield of Eq. sey (Sec. IV) evaluated at
+//    the ion's kinetic energy when it crosses the cathode; the expected yield
+//    of first-generation ions is tallied for the gain.
 //
 // Parity unpinned: the ensemble quantities (Townsend alpha of the synthetic
 // gas, multiplication, breakdown voltage) have no printed value in the paper;
@@ -148,6 +151,8 @@ typedef struct {
   const float* sig_io;
   double e_ex, e_io;    // excitation and ionization thresholds [eV]
   int precision;        // 64: FP64 reference, 32: FP32 mirror
+  int emission_model;   // 0: constant gamma_se; 1: Eq. sey
+  int emit;             // 0: tally the yield but emit no electron
 } oracle_config;
 
 // Per-step record of what happened (all sums over markers, in the step).
@@ -167,6 +172,7 @@ typedef struct {
   int64_t n_clamp;         // energies clamped at 0 after an inelastic event
   int64_t n_majorant;      // markers whose beta*v exceeded the table's cap
   int64_t marker_steps;    // markers pushed in the step
+  double w_gain_gen0;      // sum of yield * w_j over first-generation ions at the cathode
 } oracle_tally;
 
 }  // extern "C"
@@ -190,7 +196,7 @@ struct Sim {
   std::vector<oracle_tally> history;
   // derived constants, in R
   R qmdt[2], dtdx, vlim[2], K_E, K_V[2], ndt, P0, vb_cap, R2, e_ex, e_io;
-  R sigT_ion, gamma, two_pi, wscale;
+  R sigT_ion, gamma, two_pi, wscale, K_Ei;
   bool limited[2];
 
   void init(const oracle_config& c) {
@@ -212,6 +218,7 @@ struct Sim {
     e_io = (R)c.e_io;
     sigT_ion = (R)std::sqrt(kKB * c.T_K / c.mass[ION]);
     gamma = (R)c.gamma_se;
+    K_Ei = (R)(0.5 * c.mass[ION] / kQe);  // eV per (m/s)^2 of an ion
     two_pi = (R)kTwoPi;
     wscale = (R)std::ldexp(1.0, c.charge_shift);
 
@@ -264,6 +271,16 @@ struct Sim {
     uint32_t out[4];
     philox4x32_10(ctr, (uint32_t)cfg.seed, (uint32_t)(cfg.seed >> 32), out);
     for (int i = 0; i < 4; ++i) u[i] = uniform01<R>(out[i]);
+  }
+
+  // Secondary-electron yield of an ion crossing the cathode: constant, or
+  // Eq. sey at the ion's kinetic energy eps_i [eV] (exponent 0.05 below
+  // 700 eV, 0.72 from 700 eV on).
+  R yield(const Marker<R>& m) const {
+    if (cfg.emission_model != 1) return gamma;
+    const R eps_i = (m.vx * m.vx + m.vy * m.vy + m.vz * m.vz) * K_Ei;
+    const R expo = eps_i < (R)700 ? (R)0.05 : (R)0.72;
+    return (R)0.09 * std::pow(eps_i / (R)700, expo);
   }
 
   // beta(v) = min(1, vlim / v), Eq. betaAbrupt.
@@ -405,10 +422,14 @@ struct Sim {
           t.w_abs[s][0] += (double)m.wj;
           if (s == ION) {
             t.w_cath_ion += (double)m.wj;
-            if (!(m.id & GEN_BIT)) t.w_cath_ion_gen0 += (double)m.wj;
+            const R g = yield(m);
+            if (!(m.id & GEN_BIT)) {
+              t.w_cath_ion_gen0 += (double)m.wj;
+              t.w_gain_gen0 += (double)(g * m.wj);
+            }
             R u[4];
             draws(m.id, s_now, ION, 0, u);
-            if (u[0] < gamma) {
+            if (cfg.emit && u[0] < g) {
               Marker<R> e;
               e.cell = 0; e.off = 0; e.vx = 0; e.vy = 0; e.vz = 0;
               e.wj = m.wj;  // flux weight carried over to the emitted electron

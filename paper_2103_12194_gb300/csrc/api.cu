@@ -48,6 +48,8 @@ struct HostInst {
   double e_ex = 0, e_io = 0;
   HostSpecies sp[2];
   double gamma = 0, dt = 0;
+  int emission_model = 0;  // SLPIC_EMISSION_*
+  int emit = 1;            // 0 while a breakdown search runs its avalanches
   uint64_t seed = 0;
   int shift = 32;
 };
@@ -176,6 +178,7 @@ void derive_consts(const HostInst& h, StepConsts<R>& K) {
   K.e_ex = (R)h.e_ex;
   K.e_io = (R)h.e_io;
   K.sigT_ion = (R)std::sqrt(kKB * h.T_K / I.mass);
+  K.K_Ei = (R)(0.5 * I.mass / kQe);
   K.gamma = (R)h.gamma;
   K.wscale = (R)std::ldexp(1.0, h.shift);
   K.two_pi = (R)kTwoPi;
@@ -212,6 +215,8 @@ void fill_constants(slpic_ctx* c, int i, InstDev& P) {
   P.key2 = (uint32_t)h.seed ^ (uint32_t)(h.seed >> 32) ^ (0x85EBCA6Bu * (uint32_t)(i + 1));
   derive_consts(h, P.c32);
   derive_consts(h, P.c64);
+  P.emission_model = h.emission_model;
+  P.emit = h.emit;
   P.dx = dx;
   P.d = h.d;
   P.V = h.V;
@@ -757,6 +762,25 @@ int slpic_set_emission(slpic_ctx* c, int inst, double g) {
   return SLPIC_OK;
 }
 
+namespace {
+
+// Re-derive and upload the constants of a committed instance.
+int refresh_inst(slpic_ctx* c, int inst) {
+  if (!c->committed) return SLPIC_OK;
+  fill_constants(c, inst, c->h_inst[inst]);
+  return upload_inst(c, inst);
+}
+
+}  // namespace
+
+int slpic_set_emission_model(slpic_ctx* c, int inst, int model) {
+  if (!valid_inst(c, inst) ||
+      (model != SLPIC_EMISSION_CONSTANT && model != SLPIC_EMISSION_ENERGY))
+    return fail(c, SLPIC_ERR_INVALID_ARG, "bad emission model");
+  c->hi[inst].emission_model = model;
+  return refresh_inst(c, inst);
+}
+
 int slpic_set_dt(slpic_ctx* c, int inst, double dt) {
   if (!valid_inst(c, inst) || !(dt >= 0) || !std::isfinite(dt))
     return fail(c, SLPIC_ERR_INVALID_ARG, "dt must be finite and >= 0");
@@ -1205,7 +1229,7 @@ int slpic_read_gain(slpic_ctx* c, int inst, double* G) {
   CK(cudaMemcpy(&is, c->d_istate + inst, sizeof is, cudaMemcpyDeviceToHost), "gain");
   const InstDev& P = c->h_inst[inst];
   const double seed = (double)is.w_seed / P.c64.wscale;
-  *G = seed > 0 ? c->hi[inst].gamma * t.w_cath_ion_gen0 / seed : 0.0;
+  *G = seed > 0 ? t.w_gain_gen0 / seed : 0.0;
   return rc;
 }
 
@@ -1423,7 +1447,10 @@ extern "C" int slpic_paschen_bisect(slpic_ctx* c, const slpic_paschen_spec* ps, 
   std::vector<int64_t> thr_e(n), thr_i(n);
   for (int i = 0; i < n; ++i) {
     if (int rc = check_config(c, i)) return rc;
-    const double g = c->hi[i].gamma;
+    // the least yield of the instance's model
+    const double g = c->hi[i].emission_model == SLPIC_EMISSION_ENERGY
+                         ? 0.09 * std::pow(0.1 / 700.0, 0.05)
+                         : c->hi[i].gamma;
     if (!(g > 0)) return fail(c, SLPIC_ERR_INVALID_ARG, "paschen: instance %d has gamma <= 0", i);
     thr_e[i] = (int64_t)std::ceil((1.0 + 1.0 / g) * (double)ps->n_seed);
     thr_i[i] = (int64_t)std::ceil((double)ps->n_seed / g);
@@ -1436,10 +1463,9 @@ extern "C" int slpic_paschen_bisect(slpic_ctx* c, const slpic_paschen_spec* ps, 
   }
   if (int rc = prepare(c)) return rc;
   std::vector<double> lo(ps->V_lo, ps->V_lo + np), hi(ps->V_hi, ps->V_hi + np);
-  std::vector<double> gam(n), G(n, 0.0), V(n);
+  std::vector<double> G(n, 0.0), V(n);
   std::vector<uint64_t> seed0(n);
   for (int i = 0; i < n; ++i) {
-    gam[i] = c->hi[i].gamma;
     seed0[i] = c->hi[i].seed;
   }
   std::vector<SpeciesState> st(2 * (size_t)n);
@@ -1464,7 +1490,8 @@ extern "C" int slpic_paschen_bisect(slpic_ctx* c, const slpic_paschen_spec* ps, 
         if ((rc = slpic_set_voltage(c, i, V[i]))) break;
         if ((rc = slpic_set_species(c, i, kElectron, se.mass, se.charge, vlim, se.cap))) break;
         if ((rc = slpic_set_dt(c, i, dt))) break;
-        if ((rc = slpic_set_emission(c, i, 0.0))) break;
+        c->hi[i].emit = 0;
+        if ((rc = refresh_inst(c, i))) break;
         if ((rc = slpic_set_seed(c, i, seed0[i] + 0x9E3779B97F4A7C15ull * (uint64_t)round)))
           break;
         if ((rc = load_common(c, i, kIon, Arrays{{}, c->fp64}, 0, 0, cudaMemcpyHostToDevice))) break;
@@ -1533,7 +1560,7 @@ extern "C" int slpic_paschen_bisect(slpic_ctx* c, const slpic_paschen_spec* ps, 
         break;
       }
       const double w_seed = (double)is.w_seed / c->h_inst[i].c64.wscale;
-      G[i] = w_seed > 0 ? gam[i] * t.w_cath_ion_gen0 / w_seed : 0.0;
+      G[i] = w_seed > 0 ? t.w_gain_gen0 / w_seed : 0.0;
     }
     if (rc) break;
     for (int p = 0; p < np; ++p) {
@@ -1546,7 +1573,8 @@ extern "C" int slpic_paschen_bisect(slpic_ctx* c, const slpic_paschen_spec* ps, 
     }
   }
   for (int i = 0; i < n; ++i) {
-    const int r2 = slpic_set_emission(c, i, gam[i]);
+    c->hi[i].emit = 1;
+    const int r2 = refresh_inst(c, i);
     if (!rc) rc = r2;
   }
   if (rc) return rc;
@@ -1556,6 +1584,82 @@ extern "C" int slpic_paschen_bisect(slpic_ctx* c, const slpic_paschen_spec* ps, 
   }
   if (gain)
     for (int i = 0; i < n; ++i) gain[i] = G[i];
+  return SLPIC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The paper's breakdown test (Sec. V): the trend of the ion population.
+// ---------------------------------------------------------------------------
+extern "C" int slpic_ion_trend(slpic_ctx* c, int64_t steps_per_window, int n_windows,
+                               double* means, int* above) {
+  if (!c) return SLPIC_ERR_INVALID_ARG;
+  if (!means || steps_per_window < 1 || n_windows < 2)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "ion trend: need means, steps_per_window >= 1 and "
+                                          "n_windows >= 2");
+  if (int rc = prepare(c)) return rc;
+  const int n = c->n_inst;
+  std::vector<SpeciesState> st(2 * (size_t)n);
+  std::vector<char> stopped(n, 0);
+  auto read_states = [&]() -> int {
+    if (int rc = sync(c)) return rc;
+    if (cudaMemcpy(st.data(), c->d_sstate, sizeof(SpeciesState) * st.size(),
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(c, SLPIC_ERR_CUDA, "ion trend: reading the live counts");
+    return SLPIC_OK;
+  };
+  if (int rc = read_states()) return rc;
+  for (int w = 0; w < n_windows; ++w) {
+    std::vector<double> acc(n, 0.0);
+    for (int64_t done = 0; done < steps_per_window;) {
+      // chunk length: per step the electrons grow at most to 2 e + i
+      // (ionization and emission) and the ions to i + e, so both stay below
+      // 3^k (e + i) after k steps; keep that inside the smaller store
+      int64_t k = steps_per_window - done;
+      for (int i = 0; i < n; ++i) {
+        if (stopped[i]) continue;
+        const int64_t m = (int64_t)st[2 * i].n_live + st[2 * i + 1].n_live;
+        if (m == 0) continue;
+        const int64_t cap = std::min(c->hi[i].sp[kElectron].cap, c->hi[i].sp[kIon].cap);
+        int64_t s = 0, grow = m;
+        while (s < k && grow * 3 <= cap && s < 36) {
+          grow *= 3;
+          ++s;
+        }
+        k = std::min(k, std::max<int64_t>(s, 1));
+      }
+      if (int rc = slpic_step(c, k)) return rc;
+      done += k;
+      if (int rc = read_states()) return rc;
+      for (int i = 0; i < n; ++i) {
+        if (stopped[i]) continue;
+        const int64_t e = st[2 * i].n_live, ni = st[2 * i + 1].n_live;
+        acc[i] += (double)ni * (double)k;
+        // the population has grown past a third of the smaller store (the
+        // next step could overflow it): above breakdown
+        if (3 * (e + ni) > std::min(c->hi[i].sp[kElectron].cap, c->hi[i].sp[kIon].cap)) {
+          stopped[i] = 1;
+          int rc = load_common(c, i, kIon, Arrays{{}, c->fp64}, 0, 0, cudaMemcpyHostToDevice);
+          if (!rc)
+            rc = load_common(c, i, kElectron, Arrays{{}, c->fp64}, 0, 0, cudaMemcpyHostToDevice);
+          if (rc) return rc;
+          st[2 * i].n_live = st[2 * i + 1].n_live = 0;
+        }
+      }
+    }
+    for (int i = 0; i < n; ++i)
+      means[(size_t)i * n_windows + w] = stopped[i] ? -1.0 : acc[i] / (double)steps_per_window;
+  }
+  if (above) {
+    for (int i = 0; i < n; ++i) {
+      const double* m = means + (size_t)i * n_windows;
+      bool grows = stopped[i] != 0;
+      if (!grows) {
+        grows = m[n_windows - 1] > 0.0;
+        for (int w = 0; w + 1 < n_windows; ++w) grows = grows && m[n_windows - 1] > m[w];
+      }
+      above[i] = grows ? 1 : 0;
+    }
+  }
   return SLPIC_OK;
 }
 

@@ -101,6 +101,8 @@ __device__ __forceinline__ float r_cos(float x) { return cosf(x); }
 __device__ __forceinline__ double r_cos(double x) { return cos(x); }
 __device__ __forceinline__ float r_sin(float x) { return sinf(x); }
 __device__ __forceinline__ double r_sin(double x) { return sin(x); }
+__device__ __forceinline__ float r_pow(float x, float y) { return powf(x, y); }
+__device__ __forceinline__ double r_pow(double x, double y) { return pow(x, y); }
 
 // Largest value of R below 1.
 template <typename R>

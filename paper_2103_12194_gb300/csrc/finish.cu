@@ -277,10 +277,10 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode, 
   // slot layout of TallyRec: 0 step, 1-2 n_live, 3-4 w_live, 5-7 n_coll,
   // 8 n_candidates, 9-12 n_abs, 13-16 w_abs, 17 n_see, 18 w_see, 19 w_ionz,
   // 20 w_cath_ion, 21 w_cath_ion_gen0, 22 n_clamp, 23 n_majorant,
-  // 24 marker_steps; slots 0-4 are states (replaced in the totals), the
-  // others sums
+  // 24 marker_steps, 25 w_gain_gen0; slots 0-4 are states (replaced in the
+  // totals), the others sums
   constexpr int kSlots = (int)(sizeof(TallyRec) / 8);
-  static_assert(kSlots == 25, "TallyRec layout");
+  static_assert(kSlots == 26, "TallyRec layout");
   if (t < kSlots) {
     const unsigned long long* q = s_acc;
     const double unit = 1.0 / P.c64.wscale;
@@ -319,8 +319,11 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode, 
       iv = (long long)q[ACC_CLAMP];
     } else if (t == 23) {
       iv = (long long)q[ACC_MAJ];
-    } else {
+    } else if (t == 24) {
       iv = (long long)q[ACC_MSTEPS];
+    } else {
+      dv = (double)(long long)q[ACC_GWCATH0] * unit;
+      is_double = true;
     }
     long long* ring = reinterpret_cast<long long*>(P.ring + is.n_steps_done % P.ring_len);
     long long* tot = reinterpret_cast<long long*>(P.total);

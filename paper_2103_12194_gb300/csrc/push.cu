@@ -182,17 +182,28 @@ __device__ __forceinline__ void load_tile(const DeviceRefs& r, const WarpTile& t
 // an electron is emitted.  Rare; kept out of line.
 template <typename R>
 __device__ __noinline__ bool absorb(const InstDev& P, int sp, int side, R wj, uint32_t id,
-                                    uint32_t step, unsigned long long* acc) {
+                                    uint32_t step, unsigned long long* acc, R vx, R vy, R vz) {
   const StepConsts<R>& K = consts<R>(P);
   const long long Qw = fixed_charge(wj, K.wscale);
   atomicAdd(&acc[ACC_NABS + sp * 2 + side], 1ull);
   atomicAdd(&acc[ACC_WABS + sp * 2 + side], (unsigned long long)Qw);
   if (sp != kIon || side != 0) return false;
   atomicAdd(&acc[ACC_WCATH], (unsigned long long)Qw);
-  if (!(id & kGenBit)) atomicAdd(&acc[ACC_WCATH0], (unsigned long long)Qw);
+  // secondary-electron yield: constant, or Eq. sey at the ion's kinetic
+  // energy (exponent 0.05 below 700 eV, 0.72 from 700 eV on)
+  R g = K.gamma;
+  if (P.emission_model == 1) {
+    const R eps_i = (vx * vx + vy * vy + vz * vz) * K.K_Ei;
+    const R expo = eps_i < (R)700 ? (R)0.05 : (R)0.72;
+    g = (R)0.09 * r_pow(eps_i / (R)700, expo);
+  }
+  if (!(id & kGenBit)) {
+    atomicAdd(&acc[ACC_WCATH0], (unsigned long long)Qw);
+    atomicAdd(&acc[ACC_GWCATH0], (unsigned long long)fixed_charge(g * wj, K.wscale));
+  }
   const uint4 rr =
       philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u + 1u, 0u), P.key0, P.key1);
-  if (!(uniform01r<R>(rr.x) < K.gamma)) return false;
+  if (!P.emit || !(uniform01r<R>(rr.x) < g)) return false;
   atomicAdd(&acc[ACC_SEE], 1ull);
   atomicAdd(&acc[ACC_WSEE], (unsigned long long)Qw);
   return true;
@@ -420,7 +431,8 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
 #pragma unroll
         for (int j = 0; j < kPerLane; ++j) {
           if (live[j] && !alive[j])
-            event[j] = absorb<R>(P, sp, cell[j] < 0 ? 0 : 1, wj[j], id[j], step, cs.s_acc);
+            event[j] = absorb<R>(P, sp, cell[j] < 0 ? 0 : 1, wj[j], id[j], step, cs.s_acc,
+                                 vx[j], vy[j], vz[j]);
         }
         if (electrons) {
           const uint32_t key2 = P.key2;

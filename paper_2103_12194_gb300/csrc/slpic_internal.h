@@ -59,6 +59,7 @@ enum Acc : int {
   ACC_CLAMP,
   ACC_MAJ,
   ACC_MSTEPS,
+  ACC_GWCATH0,  // yield * w_j of first-generation ions at the cathode
   ACC_COUNT
 };
 
@@ -79,6 +80,7 @@ struct TallyRec {
   long long n_clamp;
   long long n_majorant;
   long long marker_steps;
+  double w_gain_gen0;
 };
 
 // Structure-of-arrays marker store in the arithmetic type R of the marker
@@ -124,6 +126,7 @@ struct StepConsts {
   R R2;           // 2 m_e / M
   R e_ex, e_io;   // thresholds [eV]
   R sigT_ion;     // sqrt(k T / M)
+  R K_Ei;         // M / (2 e): eV per (m/s)^2 of an ion
   R gamma;        // secondary-emission yield
   R wscale;       // 2^charge_shift
   R two_pi;
@@ -182,6 +185,8 @@ struct InstDev {
   uint32_t key0, key1;
   uint32_t ctr_inst;  // counter word 2 = ctr_inst * 2 + species
   uint32_t key2;      // Philox2x32 key of the null-collision draw
+  int emission_model; // 0: constant gamma; 1: Eq. sey
+  int emit;           // 0: tally the yield, emit no electron
   StepConsts<float> c32;
   StepConsts<double> c64;
   double dx, d, V, area, dt;

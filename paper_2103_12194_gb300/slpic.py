@@ -16,6 +16,7 @@ OK = 0
 ERR_INVALID_ARG, ERR_STATE, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERIC = -1, -2, -3, -4, -5, -6
 ELECTRON, ION = 0, 1
 FIELD_FROZEN, FIELD_POISSON = 0, 1
+EMISSION_CONSTANT, EMISSION_ENERGY = 0, 1
 PHILOX_STATIC_MAX = 32768  # SLPIC_PHILOX_STATIC_MAX
 SEED_CATHODE, SEED_REST, SEED_GAP, SEED_THERMAL = 0, 1, 2, 3
 
@@ -49,6 +50,7 @@ TALLY_DTYPE = np.dtype([
     ("w_abs", np.float64, (2, 2)), ("n_see", np.int64), ("w_see", np.float64),
     ("w_ionz", np.float64), ("w_cath_ion", np.float64), ("w_cath_ion_gen0", np.float64),
     ("n_clamp", np.int64), ("n_majorant", np.int64), ("marker_steps", np.int64),
+    ("w_gain_gen0", np.float64),
 ])
 
 FIELDS = ("cell", "off", "vx", "vy", "vz", "wj", "id")
@@ -109,6 +111,8 @@ def lib():
         "slpic_philox_static": ([i32, u64, vp, i64, vp], i32),
         "slpic_paschen_bisect": ([vp, ctypes.POINTER(PaschenSpec), vp, vp, vp], i32),
         "slpic_set_precision": ([vp, i32], i32),
+        "slpic_set_emission_model": ([vp, i32, i32], i32),
+        "slpic_ion_trend": ([vp, i64, i32, vp, vp], i32),
         "slpic_set_launch_shape": ([vp, i32, i32], i32),
         "slpic_get_launch_shape": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
         "slpic_autotune": ([vp, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
@@ -229,6 +233,7 @@ class Simulation:
         self._ck(self._L.slpic_set_species(self._h, i, ION, s["mass_i"], s["charge_i"],
                                            s["vlim_i"], int(capacity[1])))
         self._ck(self._L.slpic_set_emission(self._h, i, s["gamma_se"]))
+        self._ck(self._L.slpic_set_emission_model(self._h, i, int(s.get("emission_model", 0))))
         self._ck(self._L.slpic_set_dt(self._h, i, s["dt"]))
         self._ck(self._L.slpic_set_seed(self._h, i, int(s["seed"]) & 0xFFFFFFFFFFFFFFFF))
         self._ck(self._L.slpic_set_charge_shift(self._h, i, int(s["charge_shift"])))
@@ -247,6 +252,10 @@ class Simulation:
 
     def set_emission(self, i, gamma):
         self._ck(self._L.slpic_set_emission(self._h, i, float(gamma)))
+
+    def set_emission_model(self, i, model):
+        """EMISSION_CONSTANT or EMISSION_ENERGY (Eq. sey)."""
+        self._ck(self._L.slpic_set_emission_model(self._h, i, int(model)))
 
     # ---- markers --------------------------------------------------------
     def seed(self, i, species, n, mode, e0=1.0, e_lo=0.1, e_hi=200.0, wj=1.0):
@@ -352,6 +361,14 @@ class Simulation:
         self._ck(self._L.slpic_paschen_bisect(self._h, ctypes.byref(spec), _ptr(out_lo),
                                               _ptr(out_hi), _ptr(gain)))
         return out_lo, out_hi, gain.reshape(n_pd, int(n_v))
+
+    def ion_trend(self, steps_per_window, n_windows):
+        """slpic_ion_trend: (means[n_inst, n_windows], above[n_inst])."""
+        means = np.empty((self.n_instances, int(n_windows)))
+        above = np.empty(self.n_instances, np.int32)
+        self._ck(self._L.slpic_ion_trend(self._h, int(steps_per_window), int(n_windows),
+                                         _ptr(means), _ptr(above)))
+        return means, above.astype(bool)
 
     def set_launch_shape(self, push_warps, collide_ctas_per_sm):
         self._ck(self._L.slpic_set_launch_shape(self._h, int(push_warps),

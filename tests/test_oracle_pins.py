@@ -591,3 +591,36 @@ def test_townsend_growth_is_exponential_in_gap_length(oracle_mod):
     err = math.sqrt(lnM[0][1] ** 2 + 2 * lnM[1][1] ** 2 + lnM[2][1] ** 2) + 0.05
     assert a1 > 0.3 and a2 > 0.3
     assert abs(a1 - a2) < 4 * err, (a1, a2, err)
+
+
+def test_energy_dependent_yield_follows_eq_sey(oracle_mod):
+    """Eq. sey (Sec. IV): ions crossing the cathode at a known energy emit
+    with probability 0.09 (eps/700 eV)^0.05 below 700 eV and
+    0.09 (eps/700 eV)^0.72 above; both branches give 0.09 at 700 eV.  The
+    emitted fraction agrees within 4 binomial standard deviations.  The
+    tallied expected yield is n * yield * w_j.  With emission off the yield
+    is tallied but no electron is born."""
+    n = 40_000
+    for eps, emit in ((700.0, 1), (7.0, 1), (7000.0, 1), (70.0, 0)):
+        spec = inputs.gap_spec(n_cells=64, V=1e-9, gamma_se=0.07, field_mode=0, vlim_i=math.inf)
+        spec["p_Pa"] = 0.0
+        spec["emission_model"] = 1
+        spec["emit"] = emit
+        v = math.sqrt(2.0 * inputs.QE * eps / inputs.M_AR)
+        st = inputs.beam_state(n, spec, -v, cell=0, off=0.25, species=1)
+        spec["dt"] = 0.5 * (spec["d"] / spec["n_cells"]) / v  # half a cell per step
+        o = oracle_mod.Oracle(spec, precision=64)
+        o.load(1, st)
+        o.step(1)
+        h = o.history()[-1]
+        assert h["n_abs"][1][0] == n
+        y = 0.09 * (eps / 700.0) ** (0.05 if eps < 700.0 else 0.72)
+        if eps == 700.0:
+            assert y == 0.09
+        # the speed is stored in FP32: the energy, hence the yield, to ~1e-7
+        assert h["w_gain_gen0"] == pytest.approx(n * y, rel=1e-6)
+        if emit:
+            sd = math.sqrt(n * y * (1 - y))
+            assert abs(h["n_see"] - n * y) <= 4 * sd, (eps, h["n_see"], n * y)
+        else:
+            assert h["n_see"] == 0
