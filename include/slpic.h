@@ -147,6 +147,18 @@ int slpic_set_cross_sections(slpic_ctx* ctx, int inst, int lo_exp2,
                              int log2_sub, int octaves, const float* sig_el,
                              const float* sig_ex, double e_ex,
                              const float* sig_io, double e_io);
+/* The same with n_exc (1..3) excitation levels: the five processes of
+ * Sec. IV (elastic, three excitations, ionization).
+ * - sig_ex[k] and e_ex[k] are level k's cross sections and threshold [eV].
+ * - A collision picks the first process, in the order elastic, level 1 ..
+ *   n_exc, ionization, whose cumulative rate exceeds the draw.
+ * - An excitation removes its level's threshold and scatters isotropically.
+ * - The tallies count every excitation level under n_coll[1]. */
+int slpic_set_cross_sections_levels(slpic_ctx* ctx, int inst, int lo_exp2,
+                                    int log2_sub, int octaves, const float* sig_el,
+                                    int n_exc, const float* const* sig_ex,
+                                    const double* e_ex, const float* sig_io,
+                                    double e_io);
 /* Species: mass [kg], charge [C], speed limit v_lim [m/s] of Eq. betaAbrupt
  * (beta = min(1, v_lim/|v|); v_lim <= 0 or +inf gives beta = 1, i.e. PIC),
  * capacity = maximum live markers (rounded up to whole tiles of 128 markers,

@@ -44,6 +44,11 @@ class OracleConfig(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("emission_model", ctypes.c_int),
         ("emit", ctypes.c_int),
+        ("n_exc", ctypes.c_int),
+        ("sig_ex2", ctypes.POINTER(ctypes.c_float)),
+        ("sig_ex3", ctypes.POINTER(ctypes.c_float)),
+        ("e_ex2", ctypes.c_double),
+        ("e_ex3", ctypes.c_double),
     ]
 
 
@@ -162,8 +167,9 @@ class Oracle:
     def __init__(self, spec, precision=64):
         self.spec = dict(spec)
         s = self.spec
-        self._sig = [np.ascontiguousarray(s[k], dtype=np.float32)
-                     for k in ("sig_el", "sig_ex", "sig_io")]
+        n_exc = int(s.get("n_exc", 1))
+        keys = ["sig_el", "sig_ex", "sig_io"] + ["sig_ex%d" % k for k in range(2, n_exc + 1)]
+        self._sig = [np.ascontiguousarray(s[k], dtype=np.float32) for k in keys]
         n_nodes = (int(s["tab_octaves"]) << int(s["tab_log2_sub"])) + 1
         for a in self._sig:
             if a.shape != (n_nodes,):
@@ -196,6 +202,13 @@ class Oracle:
         c.precision = int(precision)
         c.emission_model = int(s.get("emission_model", 0))
         c.emit = int(s.get("emit", 1))
+        c.n_exc = n_exc
+        if n_exc >= 2:
+            c.sig_ex2 = self._sig[3].ctypes.data_as(fp)
+            c.e_ex2 = float(s["e_ex2"])
+        if n_exc >= 3:
+            c.sig_ex3 = self._sig[4].ctypes.data_as(fp)
+            c.e_ex3 = float(s["e_ex3"])
         self.precision = int(precision)
         self._cfg = c
         self._h = lib().oracle_create(ctypes.byref(c))

@@ -153,6 +153,10 @@ typedef struct {
   int precision;        // 64: FP64 reference, 32: FP32 mirror
   int emission_model;   // 0: constant gamma_se; 1: Eq. sey
   int emit;             // 0: tally the yield but emit no electron
+  int n_exc;            // excitation levels (1..3): sig_ex/e_ex, then these
+  const float* sig_ex2;
+  const float* sig_ex3;
+  double e_ex2, e_ex3;
 } oracle_config;
 
 // Per-step record of what happened (all sums over markers, in the step).
@@ -187,15 +191,17 @@ struct Sim {
   std::vector<Marker<R>> sp[2];
   uint32_t next_id[2] = {0, 0};
   uint32_t step = 0;
-  // tables (cumulative cross sections, in R)
-  std::vector<R> S1, S2, S3;
+  // tables: cumulative cross sections of the processes in order (elastic,
+  // the excitation levels, ionization), in R
+  int n_exc = 1, n_proc = 3;
+  std::vector<R> S[5];
   // field at the nodes (FP64 solution, and its R copy used by the push)
   std::vector<double> phi, E64;
   std::vector<R> E;
   std::vector<int64_t> charge[2];  // deposit of the last step (fixed point)
   std::vector<oracle_tally> history;
   // derived constants, in R
-  R qmdt[2], dtdx, vlim[2], K_E, K_V[2], ndt, P0, vb_cap, R2, e_ex, e_io;
+  R qmdt[2], dtdx, vlim[2], K_E, K_V[2], ndt, P0, vb_cap, R2, e_ex[3], e_io;
   R sigT_ion, gamma, two_pi, wscale, K_Ei;
   bool limited[2];
 
@@ -214,7 +220,11 @@ struct Sim {
     const double n_g = c.p_Pa / (kKB * c.T_K);
     ndt = (R)(n_g * c.dt);
     R2 = (R)(2.0 * c.mass[ELECTRON] / c.mass[ION]);
-    e_ex = (R)c.e_ex;
+    n_exc = c.n_exc >= 1 && c.n_exc <= 3 ? c.n_exc : 1;
+    n_proc = n_exc + 2;
+    e_ex[0] = (R)c.e_ex;
+    e_ex[1] = (R)c.e_ex2;
+    e_ex[2] = (R)c.e_ex3;
     e_io = (R)c.e_io;
     sigT_ion = (R)std::sqrt(kKB * c.T_K / c.mass[ION]);
     gamma = (R)c.gamma_se;
@@ -225,19 +235,16 @@ struct Sim {
     // Cumulative cross sections at the nodes, plus one padding node equal to
     // the last so that interpolation at the top node reads a valid neighbour.
     n_nodes_tab = (c.tab_octaves << c.tab_log2_sub) + 1;
-    S1.assign(n_nodes_tab + 1, 0);
-    S2.assign(n_nodes_tab + 1, 0);
-    S3.assign(n_nodes_tab + 1, 0);
+    const float* part[5] = {c.sig_el, c.sig_ex, c.sig_ex2, c.sig_ex3, nullptr};
+    part[n_exc + 1] = c.sig_io;
+    for (int k = 0; k < n_proc; ++k) S[k].assign(n_nodes_tab + 1, 0);
     R smax = 0;
     for (int j = 0; j < n_nodes_tab; ++j) {
-      S1[j] = (R)c.sig_el[j];
-      S2[j] = S1[j] + (R)c.sig_ex[j];
-      S3[j] = S2[j] + (R)c.sig_io[j];
-      smax = std::max(smax, S3[j]);
+      S[0][j] = (R)part[0][j];
+      for (int k = 1; k < n_proc; ++k) S[k][j] = S[k - 1][j] + (R)part[k][j];
+      smax = std::max(smax, S[n_proc - 1][j]);
     }
-    S1[n_nodes_tab] = S1[n_nodes_tab - 1];
-    S2[n_nodes_tab] = S2[n_nodes_tab - 1];
-    S3[n_nodes_tab] = S3[n_nodes_tab - 1];
+    for (int k = 0; k < n_proc; ++k) S[k][n_nodes_tab] = S[k][n_nodes_tab - 1];
     // Majorant of n_g sigma_tot(eps) min(v, vlim) dt over the table.  Above
     // the table's top energy the cross sections are held at the top node and
     // beta*v is capped at the speed of that energy (only matters for beta=1).
@@ -288,7 +295,7 @@ struct Sim {
 
   // Linear interpolation of the cumulative cross sections at eps.  Nodes sit
   // at 2^(lo + o) (1 + m / 2^sub) eV: 2^sub equal steps inside each octave.
-  void xsec(R eps, R& s1, R& s2, R& s3) const {
+  void xsec(R eps, R* s) const {
     const int L = cfg.tab_lo_exp2, sub = cfg.tab_log2_sub;
     const R e_lo = (R)std::ldexp(1.0, L);
     const R e_hi = (R)std::ldexp(1.0, L + cfg.tab_octaves);
@@ -309,9 +316,7 @@ struct Sim {
       j = (octave << sub) + (int)fl;
       t = pos - fl;
     }
-    s1 = S1[j] + t * (S1[j + 1] - S1[j]);
-    s2 = S2[j] + t * (S2[j + 1] - S2[j]);
-    s3 = S3[j] + t * (S3[j + 1] - S3[j]);
+    for (int k = 0; k < n_proc; ++k) s[k] = S[k][j] + t * (S[k][j + 1] - S[k][j]);
   }
 
   // Isotropic direction with cos(theta) = 1 - 2 ua about x, phi = 2 pi ub.
@@ -494,14 +499,15 @@ struct Sim {
     }
     R c = ndt * vb;
     R eps = s1 * K_E;
-    R x1, x2, x3;
-    xsec(eps, x1, x2, x3);
+    R xs[5];
+    xsec(eps, xs);
     R r = u[1] * P0;
-    int proc;
-    if (r < c * x1) proc = 0;
-    else if (r < c * x2) proc = 1;
-    else if (r < c * x3) proc = 2;
-    else return;  // null collision
+    // the first process whose cumulative rate exceeds the draw: elastic,
+    // excitation level 1..n_exc, ionization; none: a null collision
+    int k = 0;
+    while (k < n_proc && !(r < c * xs[k])) ++k;
+    if (k == n_proc) return;
+    const int proc = k == 0 ? 0 : (k <= n_exc ? 1 : 2);
     t.n_coll[proc]++;
     const R kv = K_V[ELECTRON];
     if (proc == 0) {
@@ -531,7 +537,7 @@ struct Sim {
       m.vy = v_new * uy;
       m.vz = v_new * uz;
     } else if (proc == 1) {
-      R e_new = eps - e_ex;
+      R e_new = eps - e_ex[k - 1];
       if (e_new < (R)0) {
         e_new = 0;
         t.n_clamp++;
@@ -852,18 +858,19 @@ int oracle_constants(void* hp, double* out3) {
   return 0;
 }
 
-// Interpolated cumulative cross sections at energies eps[n] (tests).
+// Interpolated cumulative cross sections at energies eps[n] (tests): elastic,
+// elastic plus every excitation level, total.
 int oracle_xsec(void* hp, const double* eps, int64_t n, double* out) {
   Handle* h = (Handle*)hp;
   if (!h) return -1;
   visit(h, [&](auto& sim) {
     using R = decltype(sim.K_E);
     for (int64_t i = 0; i < n; ++i) {
-      R a, b, c;
-      sim.xsec((R)eps[i], a, b, c);
-      out[3 * i] = (double)a;
-      out[3 * i + 1] = (double)b;
-      out[3 * i + 2] = (double)c;
+      R xs[5];
+      sim.xsec((R)eps[i], xs);
+      out[3 * i] = (double)xs[0];
+      out[3 * i + 1] = (double)xs[sim.n_exc];
+      out[3 * i + 2] = (double)xs[sim.n_proc - 1];
     }
   });
   return 0;

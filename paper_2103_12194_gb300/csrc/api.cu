@@ -44,8 +44,11 @@ struct HostInst {
   int n_cells = 0, field_mode = 0;
   double p_Pa = 0, T_K = 300;
   int lo_exp2 = 0, log2_sub = 0, octaves = 0;
-  std::vector<float> el, ex, io;
-  double e_ex = 0, e_io = 0;
+  std::vector<float> el, io;
+  int n_exc = 1;                  // excitation levels
+  std::vector<float> ex[kMaxExc];  // their cross sections, in order
+  double e_ex[kMaxExc] = {0, 0, 0};
+  double e_io = 0;
   HostSpecies sp[2];
   double gamma = 0, dt = 0;
   int emission_model = 0;  // SLPIC_EMISSION_*
@@ -175,7 +178,7 @@ void derive_consts(const HostInst& h, StepConsts<R>& K) {
   const double n_g = h.p_Pa / (kKB * h.T_K);
   K.ndt = (R)(n_g * h.dt);
   K.R2 = (R)(2.0 * E.mass / I.mass);
-  K.e_ex = (R)h.e_ex;
+  for (int k = 0; k < kMaxExc; ++k) K.e_ex[k] = (R)h.e_ex[k];
   K.e_io = (R)h.e_io;
   K.sigT_ion = (R)std::sqrt(kKB * h.T_K / I.mass);
   K.K_Ei = (R)(0.5 * I.mass / kQe);
@@ -187,10 +190,10 @@ void derive_consts(const HostInst& h, StepConsts<R>& K) {
   // majorant of n_g sigma_tot(eps) min(v, vlim) dt over the table
   R smax = 0;
   for (size_t j = 0; j < h.el.size(); ++j) {
-    const R s1 = (R)h.el[j];
-    const R s2 = s1 + (R)h.ex[j];
-    const R s3 = s2 + (R)h.io[j];
-    smax = std::max(smax, s3);
+    R s = (R)h.el[j];
+    for (int k = 0; k < h.n_exc; ++k) s = s + (R)h.ex[k][j];
+    s = s + (R)h.io[j];
+    smax = std::max(smax, s);
   }
   const R v_top = std::sqrt(K.e_hi * K.K_V[kElectron]);
   K.vb_cap = std::min(K.vlim[kElectron], v_top);
@@ -208,6 +211,7 @@ void fill_constants(slpic_ctx* c, int i, InstDev& P) {
   P.tab_lo_exp2 = h.lo_exp2;
   P.tab_log2_sub = h.log2_sub;
   P.tab_nodes = (h.octaves << h.log2_sub) + 1;
+  P.n_exc = h.n_exc;
   P.key0 = (uint32_t)h.seed;
   P.key1 = (uint32_t)(h.seed >> 32);
   P.ctr_inst = (uint32_t)i;
@@ -331,8 +335,10 @@ int commit(slpic_ctx* c) {
     max_nodes = std::max(max_nodes, nn);
     // per-instance arrays
     const size_t tab_n = h.el.size() + 1;
+    const int n_proc = h.n_exc + 2;
+    const int stride = n_proc > 4 ? 2 : 1;  // float4s per node
     size_t bytes = 0;
-    bytes += (tab_n * 16 + 255) & ~size_t(255);
+    bytes += (tab_n * 16 * stride + 255) & ~size_t(255);
     if (c->fp64) bytes += (tab_n * sizeof(TabNode64) + 255) & ~size_t(255);
     bytes += ((nn * 4 + 255) & ~size_t(255));
     bytes += 2 * ((nn * 8 + 255) & ~size_t(255));
@@ -341,8 +347,9 @@ int commit(slpic_ctx* c) {
     void* blk;
     if (int rc = dmalloc(c, &blk, bytes, "instance arrays")) return rc;
     char* p = (char*)blk;
-    float4* tab = carve<float4>(p, tab_n);
+    float4* tab = carve<float4>(p, tab_n * stride);
     P.table = tab;
+    P.tab_stride = stride;
     TabNode64* tab64 = c->fp64 ? carve<TabNode64>(p, tab_n) : nullptr;
     P.table64 = tab64;
     P.E32 = carve<float>(p, nn);
@@ -356,29 +363,30 @@ int commit(slpic_ctx* c) {
     P.ring = carve<TallyRec>(p, kRingLen);
     P.total = carve<TallyRec>(p, 1);
     P.ring_len = kRingLen;
-    // cumulative table (S1, S2, S3) in FP32 plus one padding node
-    std::vector<float4> ht(tab_n);
+    // cumulative tables: elastic, + each excitation level, + ionization, in
+    // FP32 (and FP64) with one padding node equal to the last
+    std::vector<float> hs((size_t)tab_n * 4 * stride, 0.0f);
+    std::vector<TabNode64> hd(tab64 ? tab_n : 0);
     for (size_t j = 0; j + 1 < tab_n; ++j) {
-      const float s1 = h.el[j];
-      const float s2 = s1 + h.ex[j];
-      const float s3 = s2 + h.io[j];
-      ht[j] = make_float4(s1, s2, s3, 0.0f);
-    }
-    ht[tab_n - 1] = ht[tab_n - 2];
-    CK(cudaMemcpy(tab, ht.data(), tab_n * 16, cudaMemcpyHostToDevice), "table");
-    if (tab64) {
-      // the same cumulative sums in double
-      std::vector<TabNode64> hd(tab_n);
-      for (size_t j = 0; j + 1 < tab_n; ++j) {
-        const double s1 = h.el[j];
-        const double s2 = s1 + (double)h.ex[j];
-        const double s3 = s2 + (double)h.io[j];
-        hd[j] = TabNode64{s1, s2, s3, 0.0};
+      float sf = h.el[j];
+      double sd = h.el[j];
+      float* node = &hs[j * 4 * stride];
+      node[0] = sf;
+      if (tab64) hd[j].s[0] = sd;
+      for (int k = 1; k < n_proc; ++k) {
+        const float part = k <= h.n_exc ? h.ex[k - 1][j] : h.io[j];
+        sf = sf + part;
+        sd = sd + (double)part;
+        node[k] = sf;
+        if (tab64) hd[j].s[k] = sd;
       }
-      hd[tab_n - 1] = hd[tab_n - 2];
+    }
+    std::copy(hs.end() - 8 * stride, hs.end() - 4 * stride, hs.end() - 4 * stride);
+    if (tab64) hd[tab_n - 1] = hd[tab_n - 2];
+    CK(cudaMemcpy(tab, hs.data(), hs.size() * 4, cudaMemcpyHostToDevice), "table");
+    if (tab64)
       CK(cudaMemcpy(tab64, hd.data(), tab_n * sizeof(TabNode64), cudaMemcpyHostToDevice),
          "table");
-    }
     // marker stores: tiles of kTile slots (two buffers for repacking);
     // electrons emitted at the cathode are staged in slots of the ion tile
     // that emitted them; collision candidates are queued per electron tile
@@ -700,19 +708,27 @@ int slpic_set_gas(slpic_ctx* c, int inst, double p_Pa, double T_K) {
   return SLPIC_OK;
 }
 
-int slpic_set_cross_sections(slpic_ctx* c, int inst, int lo_exp2, int log2_sub, int octaves,
-                             const float* el, const float* ex, double e_ex, const float* io,
-                             double e_io) {
+int slpic_set_cross_sections_levels(slpic_ctx* c, int inst, int lo_exp2, int log2_sub,
+                                    int octaves, const float* el, int n_exc,
+                                    const float* const* ex, const double* e_ex,
+                                    const float* io, double e_io) {
   if (!c) return SLPIC_ERR_INVALID_ARG;
   if (inst < -1 || inst >= c->n_inst) return fail(c, SLPIC_ERR_INVALID_ARG, "bad instance");
-  if (!el || !ex || !io || log2_sub < 0 || log2_sub > 16 || octaves < 1 || octaves > 64 ||
-      lo_exp2 < -100 || lo_exp2 + octaves > 100 || !(e_ex >= 0) || !(e_io >= 0))
+  if (n_exc < 1 || n_exc > kMaxExc || !ex || !e_ex)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "n_exc must be in [1, %d]", kMaxExc);
+  if (!el || !io || log2_sub < 0 || log2_sub > 16 || octaves < 1 || octaves > 64 ||
+      lo_exp2 < -100 || lo_exp2 + octaves > 100 || !(e_io >= 0))
     return fail(c, SLPIC_ERR_INVALID_ARG, "bad cross-section table");
+  for (int k = 0; k < n_exc; ++k)
+    if (!ex[k] || !(e_ex[k] >= 0))
+      return fail(c, SLPIC_ERR_INVALID_ARG, "bad excitation level %d", k);
   const size_t n = ((size_t)octaves << log2_sub) + 1;
-  for (size_t j = 0; j < n; ++j)
-    if (!(el[j] >= 0) || !(ex[j] >= 0) || !(io[j] >= 0) || !std::isfinite(el[j]) ||
-        !std::isfinite(ex[j]) || !std::isfinite(io[j]))
-      return fail(c, SLPIC_ERR_INVALID_ARG, "cross sections must be finite and >= 0");
+  auto ok = [](float v) { return v >= 0 && std::isfinite(v); };
+  for (size_t j = 0; j < n; ++j) {
+    bool good = ok(el[j]) && ok(io[j]);
+    for (int k = 0; k < n_exc; ++k) good = good && ok(ex[k][j]);
+    if (!good) return fail(c, SLPIC_ERR_INVALID_ARG, "cross sections must be finite and >= 0");
+  }
   if (c->committed) return fail(c, SLPIC_ERR_STATE, "tables cannot change after the first use");
   const int lo = inst < 0 ? 0 : inst, hi = inst < 0 ? c->n_inst : inst + 1;
   for (int i = lo; i < hi; ++i) {
@@ -721,13 +737,31 @@ int slpic_set_cross_sections(slpic_ctx* c, int inst, int lo_exp2, int log2_sub, 
     h.log2_sub = log2_sub;
     h.octaves = octaves;
     h.el.assign(el, el + n);
-    h.ex.assign(ex, ex + n);
+    h.n_exc = n_exc;
+    for (int k = 0; k < kMaxExc; ++k) {
+      if (k < n_exc) {
+        h.ex[k].assign(ex[k], ex[k] + n);
+        h.e_ex[k] = e_ex[k];
+      } else {
+        h.ex[k].clear();
+        h.e_ex[k] = 0;
+      }
+    }
     h.io.assign(io, io + n);
-    h.e_ex = e_ex;
     h.e_io = e_io;
     h.xs_set = true;
   }
   return SLPIC_OK;
+}
+
+int slpic_set_cross_sections(slpic_ctx* c, int inst, int lo_exp2, int log2_sub, int octaves,
+                             const float* el, const float* ex, double e_ex, const float* io,
+                             double e_io) {
+  if (!ex) return fail(c, SLPIC_ERR_INVALID_ARG, "bad cross-section table");
+  const float* levels[1] = {ex};
+  const double th[1] = {e_ex};
+  return slpic_set_cross_sections_levels(c, inst, lo_exp2, log2_sub, octaves, el, 1, levels, th,
+                                         io, e_io);
 }
 
 int slpic_set_species(slpic_ctx* c, int inst, int species, double mass, double charge,

@@ -28,10 +28,10 @@ namespace {
 constexpr int kCollThreads = 256;
 
 // Interpolated cumulative cross sections at eps (linear between the nodes of
-// the octave-uniform grid, held constant outside it).  The node index and the
-// fraction come exactly from the exponent and mantissa bits of eps.
-__device__ __forceinline__ void xsec(const InstDev& P, float eps, float& s1, float& s2,
-                                     float& s3) {
+// the octave-uniform grid, held constant outside it): xs[0 .. n_exc + 1].
+// The node index and the fraction come exactly from the exponent and
+// mantissa bits of eps.
+__device__ __forceinline__ void xsec(const InstDev& P, float eps, float* xs) {
   const StepConsts<float>& K = P.c32;
   int j;
   float t;
@@ -50,15 +50,21 @@ __device__ __forceinline__ void xsec(const InstDev& P, float eps, float& s1, flo
     const float scale = __int_as_float((127 - sh) << 23);  // 2^-sh
     t = __uint2float_rn(mant & ((1u << sh) - 1u)) * scale;
   }
-  const float4 a = __ldg(P.table + j);
-  const float4 c = __ldg(P.table + j + 1);
-  s1 = a.x + t * (c.x - a.x);
-  s2 = a.y + t * (c.y - a.y);
-  s3 = a.z + t * (c.z - a.z);
+  const int st = P.tab_stride;
+  const float4 a = __ldg(P.table + j * st);
+  const float4 c = __ldg(P.table + (j + 1) * st);
+  xs[0] = a.x + t * (c.x - a.x);
+  xs[1] = a.y + t * (c.y - a.y);
+  xs[2] = a.z + t * (c.z - a.z);
+  xs[3] = a.w + t * (c.w - a.w);
+  if (st > 1) {
+    const float4 a1 = __ldg(P.table + j * st + 1);
+    const float4 c1 = __ldg(P.table + (j + 1) * st + 1);
+    xs[4] = a1.x + t * (c1.x - a1.x);
+  }
 }
 
-__device__ __forceinline__ void xsec(const InstDev& P, double eps, double& s1, double& s2,
-                                     double& s3) {
+__device__ __forceinline__ void xsec(const InstDev& P, double eps, double* xs) {
   const StepConsts<double>& K = P.c64;
   int j;
   double t;
@@ -77,11 +83,12 @@ __device__ __forceinline__ void xsec(const InstDev& P, double eps, double& s1, d
     const double scale = __longlong_as_double((long long)(1023 - sh) << 52);  // 2^-sh
     t = (double)(mant & ((1ull << sh) - 1ull)) * scale;
   }
-  const TabNode64 a = P.table64[j];
-  const TabNode64 c = P.table64[j + 1];
-  s1 = a.s1 + t * (c.s1 - a.s1);
-  s2 = a.s2 + t * (c.s2 - a.s2);
-  s3 = a.s3 + t * (c.s3 - a.s3);
+  const TabNode64& a = P.table64[j];
+  const TabNode64& c = P.table64[j + 1];
+  const int n_proc = P.n_exc + 2;
+#pragma unroll
+  for (int k = 0; k < kMaxProc; ++k)
+    if (k < n_proc) xs[k] = a.s[k] + t * (c.s[k] - a.s[k]);
 }
 
 template <typename R>
@@ -116,13 +123,15 @@ __device__ Velocity<R> collide(const InstDev& P, R kv, R vlim, R vx, R vy, R vz,
   }
   const R c = K.ndt * vb;
   const R eps = s1 * K.K_E;
-  R x1, x2, x3;
-  xsec(P, eps, x1, x2, x3);
+  R xs[kMaxProc];
+  xsec(P, eps, xs);
   const R rsel = u[1] * K.P0;
-  int proc = 3;
-  if (rsel < c * x1) proc = 0;
-  else if (rsel < c * x2) proc = 1;
-  else if (rsel < c * x3) proc = 2;
+  // the first process whose cumulative rate exceeds the draw: elastic,
+  // excitation level 1..n_exc, ionization; none: a null collision
+  const int n_proc = P.n_exc + 2;
+  int k = 0;
+  while (k < n_proc && !(rsel < c * xs[k])) ++k;
+  const int proc = k == n_proc ? 3 : (k == 0 ? 0 : (k <= P.n_exc ? 1 : 2));
   *proc_out = proc;
   Velocity<R> o = {vx, vy, vz};
   if (proc == 3) return o;
@@ -150,7 +159,7 @@ __device__ Velocity<R> collide(const InstDev& P, R kv, R vlim, R vx, R vy, R vz,
     o.vy = vn * uy;
     o.vz = vn * uz;
   } else if (proc == 1) {
-    R e_new = eps - K.e_ex;
+    R e_new = eps - K.e_ex[k - 1];
     if (e_new < (R)0) {
       e_new = (R)0;
       atomicAdd(&acc[ACC_CLAMP], 1ull);

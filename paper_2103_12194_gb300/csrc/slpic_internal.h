@@ -106,9 +106,16 @@ __host__ __device__ inline SoAT<R> soa_as(const SoA& s) {
                  reinterpret_cast<R*>(s.wj), s.id};
 }
 
-// One node of the FP64 cross-section table: cumulative (S1, S2, S3) and a pad.
-struct alignas(32) TabNode64 {
-  double s1, s2, s3, pad;
+// Processes of an electron collision: elastic, up to three excitation
+// levels, ionization.
+constexpr int kMaxExc = 3;
+constexpr int kMaxProc = kMaxExc + 2;
+
+// One node of the FP64 cross-section table: the cumulative cross sections of
+// the processes in order, and a pad.
+struct alignas(64) TabNode64 {
+  double s[kMaxProc];
+  double pad[8 - kMaxProc];
 };
 
 // Constants of the step in the marker path's arithmetic type R; the host
@@ -124,7 +131,8 @@ struct StepConsts {
   R P0;           // null-collision majorant probability
   R vb_cap;       // cap of beta v in the majorant
   R R2;           // 2 m_e / M
-  R e_ex, e_io;   // thresholds [eV]
+  R e_ex[kMaxExc];  // excitation thresholds [eV]
+  R e_io;           // ionization threshold [eV]
   R sigT_ion;     // sqrt(k T / M)
   R K_Ei;         // M / (2 e): eV per (m/s)^2 of an ion
   R gamma;        // secondary-emission yield
@@ -185,13 +193,15 @@ struct InstDev {
   uint32_t key0, key1;
   uint32_t ctr_inst;  // counter word 2 = ctr_inst * 2 + species
   uint32_t key2;      // Philox2x32 key of the null-collision draw
+  int n_exc;          // excitation levels (1..kMaxExc)
+  int tab_stride;     // float4s per node of the FP32 table (1, or 2 with more levels)
   int emission_model; // 0: constant gamma; 1: Eq. sey
   int emit;           // 0: tally the yield, emit no electron
   StepConsts<float> c32;
   StepConsts<double> c64;
   double dx, d, V, area, dt;
   double pois_C;      // e dx 2^-shift / (area eps0)
-  const float4* table;          // FP32: cumulative (S1, S2, S3, 0) per node
+  const float4* table;          // FP32: cumulative cross sections per node, n_exc + 2 of them, in tab_stride float4s
   const TabNode64* table64;     // FP64: the same in double
   float* E32;                   // node field used by the FP32 push
   double* phi;                  // node potential

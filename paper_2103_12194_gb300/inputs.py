@@ -60,16 +60,34 @@ def argon_like_xsec(eps):
     return el, ex, io
 
 
-def make_table(lo_exp2=-7, log2_sub=8, octaves=16, scale=(1.0, 1.0, 1.0)):
+# Three argon-like excitation levels (the paper's five processes: elastic,
+# three excitations and ionization), as (threshold [eV], peak energy [eV],
+# peak cross section [m^2]) with the shape of argon_like_xsec.
+EXC_LEVELS = ((E_EXC, 25.0, 0.6e-20), (13.0, 30.0, 0.3e-20), (14.0, 35.0, 0.2e-20))
+
+
+def make_table(lo_exp2=-7, log2_sub=8, octaves=16, scale=(1.0, 1.0, 1.0), levels=1):
+    """Cross-section table of the octave grid.  levels = 1: one excitation
+    level at 11.55 eV; levels = 3: the three levels of EXC_LEVELS (keys
+    sig_ex/e_ex, sig_ex2/e_ex2, sig_ex3/e_ex3)."""
     e = table_grid(lo_exp2, log2_sub, octaves)
     el, ex, io = argon_like_xsec(e)
-    return {
+    t = {
         "tab_lo_exp2": lo_exp2, "tab_log2_sub": log2_sub, "tab_octaves": octaves,
         "sig_el": (el * scale[0]).astype(np.float32),
         "sig_ex": (ex * scale[1]).astype(np.float32),
         "sig_io": (io * scale[2]).astype(np.float32),
-        "e_ex": E_EXC, "e_io": E_ION,
+        "e_ex": E_EXC, "e_io": E_ION, "n_exc": 1,
     }
+    if levels == 3:
+        t["n_exc"] = 3
+        for k, (th, pk, peak) in enumerate(EXC_LEVELS):
+            x = (e - th) / (pk - th)
+            sig = np.where(e > th, peak * 2.0 * x / (1.0 + x * x), 0.0) * scale[1]
+            name = "sig_ex" if k == 0 else "sig_ex%d" % (k + 1)
+            t[name] = sig.astype(np.float32)
+            t["e_ex" if k == 0 else "e_ex%d" % (k + 1)] = th
+    return t
 
 
 def ion_speed(V):

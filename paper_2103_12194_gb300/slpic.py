@@ -112,6 +112,8 @@ def lib():
         "slpic_paschen_bisect": ([vp, ctypes.POINTER(PaschenSpec), vp, vp, vp], i32),
         "slpic_set_precision": ([vp, i32], i32),
         "slpic_set_emission_model": ([vp, i32, i32], i32),
+        "slpic_set_cross_sections_levels": ([vp, i32, i32, i32, i32, vp, i32, vp, vp, vp,
+                                             f64], i32),
         "slpic_ion_trend": ([vp, i64, i32, vp, vp], i32),
         "slpic_set_launch_shape": ([vp, i32, i32], i32),
         "slpic_get_launch_shape": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
@@ -223,11 +225,15 @@ class Simulation:
         self.n_cells[i] = int(s["n_cells"])
         self._ck(self._L.slpic_set_gas(self._h, i, s["p_Pa"], s["T_K"]))
         el = np.ascontiguousarray(s["sig_el"], np.float32)
-        ex = np.ascontiguousarray(s["sig_ex"], np.float32)
         io = np.ascontiguousarray(s["sig_io"], np.float32)
-        self._ck(self._L.slpic_set_cross_sections(self._h, i, s["tab_lo_exp2"], s["tab_log2_sub"],
-                                                  s["tab_octaves"], _ptr(el), _ptr(ex), s["e_ex"],
-                                                  _ptr(io), s["e_io"]))
+        n_exc = int(s.get("n_exc", 1))
+        names = ["sig_ex"] + ["sig_ex%d" % k for k in range(2, n_exc + 1)]
+        exs = [np.ascontiguousarray(s[k], np.float32) for k in names]
+        ths = np.array([s["e_ex"]] + [s["e_ex%d" % k] for k in range(2, n_exc + 1)], np.float64)
+        ptrs = (ctypes.c_void_p * n_exc)(*[a.ctypes.data for a in exs])
+        self._ck(self._L.slpic_set_cross_sections_levels(
+            self._h, i, s["tab_lo_exp2"], s["tab_log2_sub"], s["tab_octaves"], _ptr(el), n_exc,
+            ctypes.cast(ptrs, ctypes.c_void_p), _ptr(ths), _ptr(io), s["e_io"]))
         self._ck(self._L.slpic_set_species(self._h, i, ELECTRON, s["mass_e"], s["charge_e"],
                                            s["vlim_e"], int(capacity[0])))
         self._ck(self._L.slpic_set_species(self._h, i, ION, s["mass_i"], s["charge_i"],

@@ -390,3 +390,38 @@ def test_full_size_step_matches_fp32_mirror(slpic, oracle_mod):
     qg, qr = sim.charge(0, 0), ref.charge(0)
     assert np.allclose(qg, qr, rtol=REL, atol=REL * 2**32)
     sim.close()
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_three_excitation_levels_match_oracle(slpic, oracle_mod, precision):
+    """The five processes of Sec. IV (elastic, three excitation levels,
+    ionization): one step from an identical state. Every count is bit-exact
+    against the oracle in the same precision. Every excited electron has
+    lost one of the three thresholds."""
+    table = inputs.make_table(levels=3)
+    spec = inputs.gap_spec(n_cells=512, V=300.0, pd_torr_cm=30.0, gamma_se=0.5,
+                           field_mode=0, table=table)
+    e, i = mixed_state(spec, 200_000, 20_000, seed=51)
+    sim = slpic.Simulation(1, precision=precision)
+    sim.configure(0, spec)
+    sim.load(0, 0, e)
+    sim.load(0, 1, i)
+    sim.step(1)
+    ref = oracle_mod.Oracle(spec, precision=precision)
+    ref.load(0, e)
+    ref.load(1, i)
+    ref.step(1)
+    hg, hr = sim.history(0)[-1], ref.history()[-1]
+    for k in ("n_live", "n_coll", "n_candidates", "n_abs", "n_see", "n_clamp", "n_majorant",
+              "marker_steps"):
+        assert np.array_equal(hg[k], hr[k]), (k, hg[k], hr[k])
+    assert hr["n_coll"][1] > 1000
+    g, r = sim.particles(0, 0), ref.particles(0)
+    assert np.array_equal(g["id"], r["id"].astype(np.uint32))
+    assert np.array_equal(g["cell"], r["cell"])
+    vg = np.stack([g["vx"], g["vy"], g["vz"]]).astype(np.float64)
+    vr = np.stack([r["vx"], r["vy"], r["vz"]])
+    tol = REL if precision == 32 else 1e-12
+    err = np.linalg.norm(vg - vr, axis=0) / np.maximum(np.linalg.norm(vr, axis=0), spec["vlim_e"])
+    assert err.max() <= tol
+    sim.close()

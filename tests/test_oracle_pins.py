@@ -624,3 +624,44 @@ def test_energy_dependent_yield_follows_eq_sey(oracle_mod):
             assert abs(h["n_see"] - n * y) <= 4 * sd, (eps, h["n_see"], n * y)
         else:
             assert h["n_see"] == 0
+
+
+def test_three_excitation_levels_are_chosen_by_their_cross_sections(oracle_mod):
+    """Five processes as in Sec. IV (elastic, three excitation levels,
+    ionization).  A monoenergetic beam at 50 eV in a dense gap, one step:
+    - every excited electron has lost exactly one of the three thresholds;
+    - the three levels are hit in proportion to their cross sections at
+      50 eV (chi-squared against the analytic shapes);
+    - excitation as a whole against elastic and ionization in proportion too."""
+    table = inputs.make_table(levels=3)
+    spec = inputs.gap_spec(n_cells=64, V=1e-9, pd_torr_cm=20.0, field_mode=0,
+                           vlim_e=math.inf, table=table)
+    eps = 50.0
+    v = math.sqrt(2.0 * inputs.QE * eps / inputs.ME)
+    spec["dt"] = 0.25 * (spec["d"] / spec["n_cells"]) / v
+    n = 200_000
+    st = inputs.beam_state(n, spec, v, cell=32, off=0.5)
+    o = oracle_mod.Oracle(spec, precision=64)
+    o.load(0, st)
+    o.step(1)
+    h = o.history()[-1]
+    p = o.particles(0)
+    e_in = 0.5 * inputs.ME * float(np.float32(v)) ** 2 / inputs.QE
+    e_out = 0.5 * inputs.ME * (p["vx"] ** 2 + p["vy"] ** 2 + p["vz"] ** 2) / inputs.QE
+    th = [lv[0] for lv in inputs.EXC_LEVELS]
+    hits = [int(np.sum(np.abs(e_out - (e_in - t)) < 1e-9 * e_in)) for t in th]
+    assert sum(hits) == h["n_coll"][1] > 1000
+    # expected shares from the analytic shapes at 50 eV
+    sig = []
+    for t, pk, peak in inputs.EXC_LEVELS:
+        x = (eps - t) / (pk - t)
+        sig.append(peak * 2 * x / (1 + x * x))
+    exp = np.array(sig) / sum(sig) * sum(hits)
+    chi2 = float(np.sum((np.array(hits) - exp) ** 2 / exp))
+    assert chi2 < stats.chi2.ppf(0.999, df=2), (hits, exp)
+    el, _, io = inputs.argon_like_xsec(np.array([eps]))
+    tot = np.array([el[0], sum(sig), io[0]])
+    got = np.array(h["n_coll"], dtype=float)
+    exp3 = tot / tot.sum() * got.sum()
+    chi2 = float(np.sum((got - exp3) ** 2 / exp3))
+    assert chi2 < stats.chi2.ppf(0.999, df=2), (got, exp3)
