@@ -425,3 +425,73 @@ def test_three_excitation_levels_match_oracle(slpic, oracle_mod, precision):
     err = np.linalg.norm(vg - vr, axis=0) / np.maximum(np.linalg.norm(vr, axis=0), spec["vlim_e"])
     assert err.max() <= tol
     sim.close()
+
+
+# ---------------------------------------------------------------------------
+# Grids beyond shared memory (the high-pd rows of Table tab:sims)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n_cells", [20000, 65494])
+def test_large_grid_step_matches_fp32_mirror(slpic, oracle_mod, n_cells):
+    """Grids too large for the particle kernel's shared copy of the charge
+    grid (its deposits go to global int64 atomics); at 65494 cells, the
+    300 Torr cm row of Table tab:sims, the net deposit of the field solve is
+    read from global memory too. One dense step with Poisson on: counts and
+    the deposit's integer sums exactly as the FP32 mirror, markers as in the
+    one-step test, the field to rounding."""
+    pd = n_cells / 218.3  # dx = lambda_min / 4 at 1 cm
+    spec = inputs.gap_spec(n_cells=n_cells, V=40.0 * pd / 4.0 + 300.0, pd_torr_cm=pd,
+                           gamma_se=0.5, field_mode=1)
+    e, i = mixed_state(spec, 300_000, 100_000, seed=61)
+    sim = make_sim(slpic, spec)
+    sim.load(0, 0, e)
+    sim.load(0, 1, i)
+    sim.step(1)
+    ref = oracle_mod.Oracle(spec, precision=32)
+    ref.load(0, e)
+    ref.load(1, i)
+    ref.step(1)
+    hg, hr = sim.history(0)[-1], ref.history()[-1]
+    for k in ("n_live", "n_coll", "n_candidates", "n_abs", "n_see", "n_clamp", "n_majorant",
+              "marker_steps"):
+        assert np.array_equal(hg[k], hr[k]), (k, hg[k], hr[k])
+    assert min(hr["n_coll"]) > 100 and hr["n_see"] > 20
+    for s in (0, 1):
+        assert_same_markers(sim.particles(0, s), ref.particles(s), spec["vlim_e"],
+                            exact_values=False)
+        qg, qr = sim.charge(0, s), ref.charge(s)
+        assert qg.shape == (n_cells + 1,)
+        # every marker's charge arrives: the integer totals agree to the
+        # density weights of the collided markers
+        assert np.allclose(qg, qr, rtol=REL, atol=REL * 2**32)
+    phi_g, E_g = sim.field(0)
+    phi_r, E_r = ref.field()
+    assert np.allclose(phi_g, phi_r, rtol=1e-6, atol=1e-6 * spec["V"])
+    assert np.allclose(E_g, E_r, rtol=1e-5, atol=1e-5 * np.abs(E_r).max())
+    sim.close()
+
+
+def test_large_grid_vacuum_steps_bit_exact(slpic, oracle_mod):
+    """65494 cells without gas, imposed field: many steps bit for bit against
+    the FP32 mirror through the global-memory deposit, absorption and
+    emission births."""
+    spec = inputs.gap_spec(n_cells=65494, V=3100.0, pd_torr_cm=300.0, gamma_se=0.4,
+                           field_mode=0)
+    spec["p_Pa"] = 0.0
+    e, i = mixed_state(spec, 60_000, 40_000, seed=63)
+    i["cell"] = i["cell"] % 4  # ions near the cathode: absorptions within a few steps
+    sim = make_sim(slpic, spec)
+    sim.load(0, 0, e)
+    sim.load(0, 1, i)
+    ref = oracle_mod.Oracle(spec, precision=32)
+    ref.load(0, e)
+    ref.load(1, i)
+    for chunk in (1, 7, 40):
+        sim.step(chunk)
+        ref.step(chunk)
+        for s in (0, 1):
+            assert_same_markers(sim.particles(0, s), ref.particles(s), spec["vlim_e"], True)
+            assert np.array_equal(sim.charge(0, s), ref.charge(s))
+    hr = ref.history()
+    assert np.array_equal(sim.history(0)["n_see"], hr["n_see"]) and hr["n_see"].sum() > 20
+    sim.close()
