@@ -46,6 +46,15 @@ def parse():
     ap.add_argument("--paschen", action="store_true",
                     help="also time the batched FP32 breakdown-voltage sweep against the "
                          "plain one-instance FP64 bisection")
+    ap.add_argument("--tab-sims", default=None, metavar="ROWS",
+                    help="instead of the benchmark, run the PIC vs SLPIC study shaped like "
+                         "Table tab:sims on the rows given (comma-separated indices 0-10, "
+                         "or 'all') and print one JSON line")
+    ap.add_argument("--tab-sims-pic-max", type=float, default=4.0,
+                    help="largest pressure [Torr] with a PIC run (the paper's: 4)")
+    ap.add_argument("--tab-sims-pic-full-max", type=float, default=1.0,
+                    help="above this pressure [Torr] a PIC run covers its first 3 of 15 "
+                         "windows and its wall time is extrapolated")
     return ap.parse_args()
 
 
@@ -220,6 +229,122 @@ def paschen_sweep(slpic, inputs, local, stream, pds=(0.5, 1.0, 2.0, 4.0), n_v=8,
             "speedup": t64 / t32}
 
 
+# Table tab:sims: pressure [Torr] at d = 1 cm, voltage [V] near the paper's
+# breakdown voltage, and cells (dx = a quarter of the mean free path).
+TAB_SIMS = ((0.3, 260.0, 66), (0.4, 195.0, 88), (0.6, 175.0, 131), (1.0, 170.0, 219),
+            (2.0, 185.0, 437), (4.0, 225.0, 874), (6.0, 262.0, 1310), (10.0, 340.0, 2184),
+            (30.0, 620.0, 6550), (100.0, 1400.0, 21832), (300.0, 3100.0, 65494))
+
+
+def tab_sims_spec(inputs, p, V, cells, pic, seed, instance=0):
+    """A Table tab:sims gap set up as in Sec. IV: d = 1 cm, the field V/d
+    imposed, the five electron-argon processes, the Eq. sey yield.  SLPIC:
+    v_lim = v0 = sqrt(2 e V / M), dt = dx / v0; PIC: no speed limit and
+    dt = dx / v_max, v_max = sqrt(2 e V / m_e)."""
+    dx = 0.01 / cells
+    v0 = inputs.ion_speed(V)
+    vmax = math.sqrt(2 * inputs.QE * V / inputs.ME)
+    spec = inputs.gap_spec(n_cells=cells, V=V, pd_torr_cm=p, gamma_se=0.07, field_mode=0,
+                           vlim_e=math.inf if pic else v0, dt=dx / (vmax if pic else v0),
+                           seed=seed, instance=instance, table=inputs.make_table(levels=3))
+    spec["emission_model"] = 1
+    return spec
+
+
+def tab_sims_bracket(slpic, inputs, rows, local, stream, n_v=8, rounds=2, n_seed=2000):
+    """Breakdown brackets of the synthetic gas at the rows' pressures: the
+    batched search on the gain G >= 1 (Sec. II.A) over all rows at once,
+    with the SLPIC setup of the runs (v_lim = v0), from [V / 2, 2 V]."""
+    import torch
+    sim = slpic.Simulation(len(rows) * n_v, device=local, stream=stream)
+    for a, r in enumerate(rows):
+        p, V, cells = TAB_SIMS[r]
+        for j in range(n_v):
+            i = a * n_v + j
+            sim.configure(i, tab_sims_spec(inputs, p, V, cells, False, 500 + i, i),
+                          capacity=(1 << 20, 1 << 20))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lo, hi, _ = sim.paschen_bisect([0.5 * TAB_SIMS[r][1] for r in rows],
+                                   [2.0 * TAB_SIMS[r][1] for r in rows], n_v=n_v,
+                                   rounds=rounds, n_seed=n_seed, e0=1.0, vlim_factor=1.0)
+    wall = time.perf_counter() - t0
+    sim.close()
+    return [float(x) for x in lo], [float(x) for x in hi], wall
+
+
+def tab_sims_run(slpic, inputs, p, V, cells, pic, local, stream, seed=1, windows=15,
+                 run_windows=None):
+    """One breakdown run of Table tab:sims on the GPU (Sec. IV and V): 100
+    electrons at rest at the cathode, the ion population tracked over 30 ion
+    crossing times in `windows` windows.  SLPIC: 30 crossings (of 2 d / v0
+    each) are 60 cells steps of dx / v0; PIC takes sqrt(M / m_e) times more
+    steps.  With run_windows < windows only the first run_windows windows
+    run and the wall time is extrapolated to the whole run (no
+    classification).  An ion population past a third of its store (above
+    breakdown for certain) ends the run."""
+    import numpy as np
+    import torch
+    spec = tab_sims_spec(inputs, p, V, cells, pic, seed)
+    n_t = 60 * cells * (math.sqrt(inputs.M_AR / inputs.ME) if pic else 1.0)
+    spw = int(math.ceil(n_t / windows))
+    nw = windows if run_windows is None else run_windows
+    sim = slpic.Simulation(1, device=local, stream=stream)
+    sim.configure(0, spec, capacity=(1 << 19, 1 << 19))
+    sim.seed(0, slpic.ELECTRON, 100, slpic.SEED_REST)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    means, above = sim.ion_trend(spw, max(nw, 2))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    tot = sim.tallies(0)
+    sim.close()
+    m = means[0]
+    steps = int(tot["step"]) + 1  # the step index of the last step run
+    rec = {"method": "PIC" if pic else "SLPIC", "dt_s": spec["dt"], "steps_planned": spw * windows,
+           "steps_run": steps, "wall_s": wall, "us_per_step": wall / max(steps, 1) * 1e6,
+           "marker_steps": int(tot["marker_steps"]), "collisions": int(np.sum(tot["n_coll"])),
+           "ion_means": [float(x) for x in m]}
+    if nw < windows:
+        rec["wall_s_extrapolated"] = wall * windows / max(nw, 2)
+        rec["class"] = None
+    else:
+        rec["class"] = "above" if above[0] else "below"
+        rec["saturated"] = bool((m < 0).any())
+    return rec
+
+
+def tab_sims(slpic, inputs, rows, pic_max, pic_full_max, local, stream, margin=0.03):
+    lo, hi, t_bracket = tab_sims_bracket(slpic, inputs, rows, local, stream)
+    out = {"bracket_search_s": t_bracket, "rows": []}
+    for a, r in enumerate(rows):
+        p, V, cells = TAB_SIMS[r]
+        rec = {"row": r, "p_torr": p, "V_paper": V, "cells": cells,
+               "Vb_bracket": [lo[a], hi[a]],
+               "V_runs": [(1 - margin) * lo[a], (1 + margin) * hi[a]], "runs": []}
+        for Vr in rec["V_runs"]:
+            run = {"V": Vr, "slpic": tab_sims_run(slpic, inputs, p, Vr, cells, False, local,
+                                                  stream)}
+            if p <= pic_max:
+                part = None if p <= pic_full_max else 3
+                run["pic"] = tab_sims_run(slpic, inputs, p, Vr, cells, True, local, stream,
+                                          run_windows=part)
+            rec["runs"].append(run)
+        sl = sum(x["slpic"]["wall_s"] for x in rec["runs"])
+        rec["slpic_wall_s"] = sl
+        if p <= pic_max:
+            pc = sum(x["pic"].get("wall_s_extrapolated", x["pic"]["wall_s"]) for x in rec["runs"])
+            rec["pic_wall_s"] = pc
+            rec["pic_extrapolated"] = p > pic_full_max
+            rec["speedup"] = pc / sl
+            if p <= pic_full_max:
+                rec["same_class"] = all(x["pic"]["class"] == x["slpic"]["class"]
+                                        for x in rec["runs"])
+        print(json.dumps({"tab_sims_row": rec}), file=sys.stderr, flush=True)
+        out["rows"].append(rec)
+    return out
+
+
 def combine_ranks(elapsed_ms, marker_steps, world, device):
     """Whole-job figures of a weak-scaling run: every rank advances its own
     independent instance, so the job's time is the slowest rank's and its
@@ -272,6 +397,19 @@ def run_ours(args):
     torch.cuda.set_device(local)
     build.build()
     stream = torch.cuda.current_stream()
+    if args.tab_sims is not None:
+        if rank == 0:
+            rows = (range(len(TAB_SIMS)) if args.tab_sims == "all"
+                    else [int(x) for x in args.tab_sims.split(",")])
+            res = tab_sims(slpic, inputs, rows, args.tab_sims_pic_max,
+                           args.tab_sims_pic_full_max, local, stream)
+            res.update({"study": "Table tab:sims, PIC vs SLPIC on one GB300",
+                        "setup": "d = 1 cm, 100 electrons at rest, E = V/d imposed, five "
+                                 "processes, Eq. sey yield, 30 ion crossings in 15 windows; "
+                                 "runs at 0.97 x the lower and 1.03 x the upper end of the "
+                                 "synthetic gas's breakdown bracket"})
+            print(json.dumps(res), flush=True)
+        return
     spec, run = inputs.microbench_config(n_markers=args.markers, seed=rank)
     spec["instance"] = 0
     n = args.markers

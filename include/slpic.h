@@ -230,6 +230,25 @@ int slpic_reset_counters(slpic_ctx* ctx, int inst);
  * secondary emission, null-collision MCC with births, stable compaction and
  * append, fixed-point deposit, field solve, tallies. */
 int slpic_step(slpic_ctx* ctx, int64_t n_steps);
+/* Steps of small populations (Sec. V: the breakdown runs start from 100
+ * electrons and stay near that size): up to n_steps steps of every instance
+ * in one launch, one CTA of the device per instance, with no per-step launch.
+ * Synchronous.  Runs only while every store has at most the small-path limit
+ * of tiles (128 markers each, slpic_set_small_limit) when a step starts, and
+ * stops before the first step at which one has more; *steps_done gets the
+ * steps run (0 when the path does not apply: a store above the limit, a store
+ * too small to take one step's births from there (3 x the limit for
+ * electrons, 2 x for ions), a field-mode-1 grid too large for shared memory,
+ * more instances than fit on the device at once, or profiling on).  The
+ * results are those of slpic_step, bit for bit; continue with slpic_step for
+ * the remaining steps.  The tallies, history, counts and fields read after
+ * it are those of the last step run. */
+int slpic_step_small(slpic_ctx* ctx, int64_t n_steps, int64_t* steps_done);
+/* Small-path limit: most tiles (128 marker slots each) a store may hold when
+ * a step of slpic_step_small starts, 0..32 (default 32; 0 switches the path
+ * off).  slpic_ion_trend and slpic_paschen_bisect take the small path by
+ * themselves while the populations are within it. */
+int slpic_set_small_limit(slpic_ctx* ctx, int max_tiles);
 /* Wait for the context's work; returns the latched device error, if any. */
 int slpic_synchronize(slpic_ctx* ctx);
 /* Forget a latched device error (load or seed the markers again after it). */
@@ -328,7 +347,8 @@ int slpic_paschen_bisect(slpic_ctx* ctx, const slpic_paschen_spec* spec, double*
  *   positive and exceeds every earlier window's, else 0.
  * - An instance whose live markers (both species) pass a third of the
  *   smaller store's capacity is above breakdown. It is emptied, its
- *   remaining windows read -1, and it counts as above.
+ *   remaining windows read -1, and it counts as above.  When every instance
+ *   has stopped so, no further step is taken.
  * - Steps run in chunks short enough that no store can overflow in between
  *   (growth at most x3 per step with emission).
  * - With the paper's setup: seed electrons at rest (SLPIC_SEED_REST),

@@ -19,8 +19,11 @@
 // Readings of the paper that this file fixes (the paper is silent on them):
 //  * cathode at x = 0 with phi = 0, anode at x = d with phi = V (Sec. IV);
 //  * linear (cloud-in-cell) shape for gather and deposit (Eq. Ansatz);
-//  * leapfrog: the kick uses beta of the pre-kick speed, the drift beta of the
-//    post-kick speed (Eqs. slpicEOMx, slpicEOMv, betaAbrupt);
+//  * leapfrog below the speed limit; across and above it the kick integrates
+//    Eq. slpicEOMv in the speed-limited time (the trapezoid rule, exact for
+//    motion along the field: the energy gained is q E_x times the distance
+//    moved); the drift uses beta of the post-kick speed (Eqs. slpicEOMx,
+//    slpicEOMv, betaAbrupt);
 //  * collision probability of a marker per step = beta v dt / lambda_mfp
 //    = n_g sigma(eps) beta v dt (Sec. III, the d'/lambda_mfp rule and
 //    Eq. SLPICcollisionNumber with beta_n = 1, whole-marker collisions),
@@ -293,6 +296,47 @@ struct Sim {
   // beta(v) = min(1, vlim / v), Eq. betaAbrupt.
   R beta(R v, int s) const { return v > vlim[s] ? vlim[s] / v : (R)1; }
 
+  // New v_x after the kick of one step, A = q E_x dt / m (Eq. slpicEOMv:
+  // dv_x/dt = beta(|v|) q E_x / m; v_y, v_z unchanged).  Unlimited species,
+  // and a marker below the limit at both ends of the step: v_x + A
+  // (leapfrog).  Otherwise, with L the limit: the part of the step up to
+  // |v| = L is unlimited; over the rest (a fraction f of dt) the motion is
+  // unlimited in the time tau = integral of beta dt, u = v_1 + A tau / dt,
+  // and f dt = integral of |v| / L dtau, taken by the trapezoid rule:
+  // z (s_1 + s') = 2 f |A| L for the gain z of v_x along A, with s_1 and s'
+  // the speeds at the ends of that part.  Its root is taken by one Newton
+  // step from the root with v_y = v_z = 0.
+  R kick(const Marker<R>& m, R A, int s) const {
+    if (!limited[s]) return m.vx + A;
+    const R L = vlim[s];
+    const R sp = std::sqrt(m.vx * m.vx + m.vy * m.vy + m.vz * m.vz);
+    const R vt = m.vx + A;
+    const R st = std::sqrt(vt * vt + m.vy * m.vy + m.vz * m.vz);
+    if (sp <= L && st <= L) return vt;
+    const R g = A > (R)0 ? (R)1 : (R)-1;
+    const R aA = g * A;
+    const R p2 = m.vy * m.vy + m.vz * m.vz;
+    R f, s1, v1;
+    if (sp < L) {
+      // reaches the limit inside the step, at speed L with v_x = g q
+      const R q = std::sqrt(std::max((R)0, L * L - p2));
+      f = std::min((R)1, std::max((R)0, (R)1 - (q - g * m.vx) / aA));
+      s1 = L;
+      v1 = q;
+    } else {
+      f = (R)1;
+      s1 = sp;
+      v1 = g * m.vx;
+    }
+    const R K = (R)2 * f * aA * L;
+    const R c = s1 + v1;
+    R z = std::min((std::sqrt(c * c + (R)4 * K) - c) * (R)0.5, K / s1);
+    const R w = v1 + z;
+    const R sn = std::sqrt(w * w + p2);
+    if (sn > (R)0) z = std::max((R)0, z - (z * (s1 + sn) - K) / (s1 + sn + z * w / sn));
+    return g * (v1 + z);
+  }
+
   // Linear interpolation of the cumulative cross sections at eps.  Nodes sit
   // at 2^(lo + o) (1 + m / 2^sub) eV: 2^sub equal steps inside each octave.
   void xsec(R eps, R* s) const {
@@ -406,9 +450,7 @@ struct Sim {
         // Field at the marker (linear interpolation between its nodes).
         R Ex = E[m.cell] + m.off * (E[m.cell + 1] - E[m.cell]);
         // Speed-limited kick and drift (Eqs. slpicEOMx, slpicEOMv).
-        R s0 = m.vx * m.vx + m.vy * m.vy + m.vz * m.vz;
-        R b0 = beta(std::sqrt(s0), s);
-        m.vx = m.vx + b0 * (qmdt[s] * Ex);
+        m.vx = kick(m, qmdt[s] * Ex, s);
         R s1 = m.vx * m.vx + m.vy * m.vy + m.vz * m.vz;
         R v1 = std::sqrt(s1);
         R b1 = beta(v1, s);

@@ -18,8 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libslpic.so")
-SOURCES = ["push.cu", "collide.cu", "finish.cu", "api.cu"]
-HEADERS = ["slpic_internal.h", "device_common.cuh"]
+SOURCES = ["push.cu", "collide.cu", "finish.cu", "small.cu", "api.cu"]
+HEADERS = ["slpic_internal.h", "device_common.cuh", "step_ops.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -7,8 +7,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <limits>
 #include <mutex>
 #include <string>
@@ -89,6 +91,7 @@ struct slpic_ctx {
   int sms = 0;             // multiprocessors of the device
   int max_push_warps = 0;  // most particle-kernel warps per CTA that fit
   int collide_per_sm = 8;  // collision CTAs per SM
+  int small_limit = kSmallMaxTiles;  // single-CTA path: most tiles per store (0: off)
   // per instance: stepped since its field was last reset (phi is then formed
   // from the last deposit when read)
   std::vector<char> stepped;
@@ -309,6 +312,7 @@ int zero_counters(slpic_ctx* c, int i) {
   is.step = 0;
   is.n_steps_done = 0;
   is.w_seed = 0;
+  is.ion_steps = 0;
   CK(cudaMemcpyAsync(c->d_istate + i, &is, sizeof is, cudaMemcpyHostToDevice, c->stream), "reset");
   for (int s = 0; s < 2; ++s) {
     CK(cudaMemsetAsync(P.rho_acc[s], 0, (P.n_cells + 1) * 8, c->stream), "reset");
@@ -520,6 +524,53 @@ int prepare(slpic_ctx* c) {
   if (int rc = commit(c)) return rc;
   if (int rc = set_device(c)) return rc;
   return SLPIC_OK;
+}
+
+// Single-CTA path (small.cu): up to n steps while every store has at most
+// c->small_limit tiles; synchronous.  *done = steps run (0 when the path does
+// not apply now).  It applies when every store is that small, every store
+// can take the births of one step from there (so no capacity error can occur
+// in it), the field-mode-1 grids fit in shared memory, and all instances fit
+// on the device at once.  extra_ok (may be NULL) adds a condition per
+// instance on its live counts.
+int run_small(slpic_ctx* c, int64_t n, int64_t* done,
+              const std::function<bool(int, int64_t, int64_t)>& extra_ok = nullptr) {
+  *done = 0;
+  if (n <= 0 || c->small_limit <= 0 || c->profiling) return SLPIC_OK;
+  if (int rc = sync(c)) return rc;
+  std::vector<SpeciesState> st(2 * (size_t)c->n_inst);
+  CK(cudaMemcpy(st.data(), c->d_sstate, sizeof(SpeciesState) * st.size(),
+                cudaMemcpyDeviceToHost),
+     "small path");
+  const int64_t L = (int64_t)c->small_limit * kTile;
+  int max_pn = 0;
+  for (int i = 0; i < c->n_inst; ++i) {
+    const SpeciesState &e = st[2 * i], &o = st[2 * i + 1];
+    if ((int)e.n_tiles > c->small_limit || (int)o.n_tiles > c->small_limit) return SLPIC_OK;
+    if (c->hi[i].sp[kElectron].cap < 3 * L || c->hi[i].sp[kIon].cap < 2 * L) return SLPIC_OK;
+    if (extra_ok && !extra_ok(i, e.n_live, o.n_live)) return SLPIC_OK;
+    if (c->h_inst[i].field_mode == 1) max_pn = std::max(max_pn, c->h_inst[i].n_cells + 1);
+  }
+  size_t smem = 0;
+  int bps = 0;
+  if (int e = small_config(c->fp64, max_pn, &smem, &bps))
+    return cuda_fail(c, (cudaError_t)e, "small path configuration");
+  if (bps == 0 || (c->n_inst > 1 && (int64_t)bps * c->sms < c->n_inst)) return SLPIC_OK;
+  const size_t off0 = offsetof(Control, small_bar);
+  CK(cudaMemsetAsync((char*)c->d_ctrl + off0, 0, offsetof(Control, small_done) + 8 - off0,
+                     c->stream),
+     "small path");
+  if (int e = launch_small(c->refs, n, c->small_limit, smem, c->stream))
+    return cuda_fail(c, (cudaError_t)e, "small path launch");
+  launch_finish(c->refs, 1, c->stream);  // the batched path's next step
+  CK(cudaGetLastError(), "small path");
+  CK(cudaStreamSynchronize(c->stream), "small path");
+  long long d = 0;
+  CK(cudaMemcpy(&d, &c->d_ctrl->small_done, sizeof d, cudaMemcpyDeviceToHost), "small path");
+  *done = d;
+  c->last_launches = 2;
+  if (d > 0) std::fill(c->stepped.begin(), c->stepped.end(), 1);
+  return device_error(c);
 }
 
 void drop_graph(slpic_ctx* c) {
@@ -1079,6 +1130,20 @@ int slpic_step(slpic_ctx* c, int64_t n) {
   return SLPIC_OK;
 }
 
+int slpic_step_small(slpic_ctx* c, int64_t n, int64_t* done) {
+  if (!c || n < 0 || !done) return fail(c, SLPIC_ERR_INVALID_ARG, "bad arguments");
+  *done = 0;
+  if (int rc = prepare(c)) return rc;
+  return run_small(c, n, done);
+}
+
+int slpic_set_small_limit(slpic_ctx* c, int max_tiles) {
+  if (!c || max_tiles < 0 || max_tiles > kSmallMaxTiles)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "small-path limit must be 0..%d tiles", kSmallMaxTiles);
+  c->small_limit = max_tiles;
+  return SLPIC_OK;
+}
+
 int slpic_synchronize(slpic_ctx* c) {
   if (!c) return SLPIC_ERR_INVALID_ARG;
   return sync(c);
@@ -1542,8 +1607,21 @@ extern "C" int slpic_paschen_bisect(slpic_ctx* c, const slpic_paschen_spec* ps, 
     // ---- step the batch until every avalanche has left the gap --------------
     int64_t k = 1;  // next chunk: no instance can outgrow its stores in it
     for (int64_t done = 0; done < ps->max_steps && !rc;) {
-      k = std::min<int64_t>(k, ps->max_steps - done);
-      if ((rc = slpic_step(c, k))) break;
+      // small avalanches: runs of up to chunk_steps steps in the single-CTA
+      // path while no store could pass its saturation threshold inside it
+      int64_t ks = 0;
+      rc = run_small(c, std::min(ps->chunk_steps, ps->max_steps - done), &ks,
+                     [&](int i, int64_t, int64_t) {
+                       const int64_t L = (int64_t)c->small_limit * kTile;
+                       return saturated[i] || (thr_e[i] >= 3 * L && thr_i[i] > 2 * L);
+                     });
+      if (rc) break;
+      if (ks > 0) {
+        k = ks;
+      } else {
+        k = std::min<int64_t>(k, ps->max_steps - done);
+        if ((rc = slpic_step(c, k))) break;
+      }
       done += k;
       if ((rc = sync(c))) break;
       if (cudaMemcpy(st.data(), c->d_sstate, sizeof(SpeciesState) * st.size(),
@@ -1633,41 +1711,53 @@ extern "C" int slpic_ion_trend(slpic_ctx* c, int64_t steps_per_window, int n_win
   if (int rc = prepare(c)) return rc;
   const int n = c->n_inst;
   std::vector<SpeciesState> st(2 * (size_t)n);
+  std::vector<InstState> is(n);
   std::vector<char> stopped(n, 0);
   auto read_states = [&]() -> int {
     if (int rc = sync(c)) return rc;
     if (cudaMemcpy(st.data(), c->d_sstate, sizeof(SpeciesState) * st.size(),
+                   cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(is.data(), c->d_istate, sizeof(InstState) * is.size(),
                    cudaMemcpyDeviceToHost) != cudaSuccess)
       return fail(c, SLPIC_ERR_CUDA, "ion trend: reading the live counts");
     return SLPIC_OK;
   };
   if (int rc = read_states()) return rc;
   for (int w = 0; w < n_windows; ++w) {
-    std::vector<double> acc(n, 0.0);
+    // live ions summed over the window's steps, from the per-step running sum
+    std::vector<long long> ion0(n);
+    for (int i = 0; i < n; ++i) ion0[i] = is[i].ion_steps;
     for (int64_t done = 0; done < steps_per_window;) {
-      // chunk length: per step the electrons grow at most to 2 e + i
-      // (ionization and emission) and the ions to i + e, so both stay below
-      // 3^k (e + i) after k steps; keep that inside the smaller store
-      int64_t k = steps_per_window - done;
-      for (int i = 0; i < n; ++i) {
-        if (stopped[i]) continue;
-        const int64_t m = (int64_t)st[2 * i].n_live + st[2 * i + 1].n_live;
-        if (m == 0) continue;
-        const int64_t cap = std::min(c->hi[i].sp[kElectron].cap, c->hi[i].sp[kIon].cap);
-        int64_t s = 0, grow = m;
-        while (s < k && grow * 3 <= cap && s < 36) {
-          grow *= 3;
-          ++s;
+      // every instance is above breakdown for certain: nothing left to follow
+      if (std::all_of(stopped.begin(), stopped.end(), [](char x) { return x != 0; })) break;
+      // small populations: whole runs of steps in the single-CTA path, which
+      // stops by itself before a store outgrows it
+      int64_t k = 0;
+      if (int rc = run_small(c, steps_per_window - done, &k)) return rc;
+      if (k == 0) {
+        // chunk length: per step the electrons grow at most to 2 e + i
+        // (ionization and emission) and the ions to i + e, so both stay below
+        // 3^k (e + i) after k steps; keep that inside the smaller store
+        k = steps_per_window - done;
+        for (int i = 0; i < n; ++i) {
+          if (stopped[i]) continue;
+          const int64_t m = (int64_t)st[2 * i].n_live + st[2 * i + 1].n_live;
+          if (m == 0) continue;
+          const int64_t cap = std::min(c->hi[i].sp[kElectron].cap, c->hi[i].sp[kIon].cap);
+          int64_t s = 0, grow = m;
+          while (s < k && grow * 3 <= cap && s < 36) {
+            grow *= 3;
+            ++s;
+          }
+          k = std::min(k, std::max<int64_t>(s, 1));
         }
-        k = std::min(k, std::max<int64_t>(s, 1));
+        if (int rc = slpic_step(c, k)) return rc;
       }
-      if (int rc = slpic_step(c, k)) return rc;
       done += k;
       if (int rc = read_states()) return rc;
       for (int i = 0; i < n; ++i) {
         if (stopped[i]) continue;
         const int64_t e = st[2 * i].n_live, ni = st[2 * i + 1].n_live;
-        acc[i] += (double)ni * (double)k;
         // the population has grown past a third of the smaller store (the
         // next step could overflow it): above breakdown
         if (3 * (e + ni) > std::min(c->hi[i].sp[kElectron].cap, c->hi[i].sp[kIon].cap)) {
@@ -1681,7 +1771,8 @@ extern "C" int slpic_ion_trend(slpic_ctx* c, int64_t steps_per_window, int n_win
       }
     }
     for (int i = 0; i < n; ++i)
-      means[(size_t)i * n_windows + w] = stopped[i] ? -1.0 : acc[i] / (double)steps_per_window;
+      means[(size_t)i * n_windows + w] =
+          stopped[i] ? -1.0 : (double)(is[i].ion_steps - ion0[i]) / (double)steps_per_window;
   }
   if (above) {
     for (int i = 0; i < n; ++i) {

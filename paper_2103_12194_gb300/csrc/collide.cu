@@ -20,232 +20,13 @@
 // the scheduling.
 #include "device_common.cuh"
 #include "slpic_internal.h"
+#include "step_ops.cuh"
 
 namespace slpic {
 
 namespace {
 
 constexpr int kCollThreads = 256;
-
-// Interpolated cumulative cross sections at eps (linear between the nodes of
-// the octave-uniform grid, held constant outside it): xs[0 .. n_exc + 1].
-// The node index and the fraction come exactly from the exponent and
-// mantissa bits of eps.
-__device__ __forceinline__ void xsec(const InstDev& P, float eps, float* xs) {
-  const StepConsts<float>& K = P.c32;
-  int j;
-  float t;
-  if (!(eps >= K.e_lo)) {
-    j = 0;
-    t = 0.0f;
-  } else if (eps >= K.e_hi) {
-    j = P.tab_nodes - 1;
-    t = 0.0f;
-  } else {
-    const uint32_t b = __float_as_uint(eps);
-    const int octave = (int)(b >> 23) - 127 - P.tab_lo_exp2;
-    const uint32_t mant = b & 0x7FFFFFu;
-    const int sh = 23 - P.tab_log2_sub;
-    j = (octave << P.tab_log2_sub) + (int)(mant >> sh);
-    const float scale = __int_as_float((127 - sh) << 23);  // 2^-sh
-    t = __uint2float_rn(mant & ((1u << sh) - 1u)) * scale;
-  }
-  const int st = P.tab_stride;
-  const float4 a = __ldg(P.table + j * st);
-  const float4 c = __ldg(P.table + (j + 1) * st);
-  xs[0] = a.x + t * (c.x - a.x);
-  xs[1] = a.y + t * (c.y - a.y);
-  xs[2] = a.z + t * (c.z - a.z);
-  xs[3] = a.w + t * (c.w - a.w);
-  if (st > 1) {
-    const float4 a1 = __ldg(P.table + j * st + 1);
-    const float4 c1 = __ldg(P.table + (j + 1) * st + 1);
-    xs[4] = a1.x + t * (c1.x - a1.x);
-  }
-}
-
-__device__ __forceinline__ void xsec(const InstDev& P, double eps, double* xs) {
-  const StepConsts<double>& K = P.c64;
-  int j;
-  double t;
-  if (!(eps >= K.e_lo)) {
-    j = 0;
-    t = 0.0;
-  } else if (eps >= K.e_hi) {
-    j = P.tab_nodes - 1;
-    t = 0.0;
-  } else {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(eps);
-    const int octave = (int)(b >> 52) - 1023 - P.tab_lo_exp2;
-    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
-    const int sh = 52 - P.tab_log2_sub;
-    j = (octave << P.tab_log2_sub) + (int)(mant >> sh);
-    const double scale = __longlong_as_double((long long)(1023 - sh) << 52);  // 2^-sh
-    t = (double)(mant & ((1ull << sh) - 1ull)) * scale;
-  }
-  const TabNode64& a = P.table64[j];
-  const TabNode64& c = P.table64[j + 1];
-  const int n_proc = P.n_exc + 2;
-#pragma unroll
-  for (int k = 0; k < kMaxProc; ++k)
-    if (k < n_proc) xs[k] = a.s[k] + t * (c.s[k] - a.s[k]);
-}
-
-template <typename R>
-__device__ __forceinline__ void deposit(unsigned long long* rho, int cell, R off, long long Q) {
-  const long long right = right_share(Q, off);
-  const long long left = Q - right;
-  if (left) atomicAdd(rho + cell, (unsigned long long)left);
-  if (right) atomicAdd(rho + cell + 1, (unsigned long long)right);
-}
-
-template <typename R>
-struct Velocity {
-  R vx, vy, vz;
-};
-
-// Choose the process with u[1] against the cumulative rates and scatter
-// (u[0] is unused: the candidate test drew from Philox2x32).
-// Returns the new velocity; *proc_out = 0 elastic, 1 excitation,
-// 2 ionization, 3 null (velocity unchanged).
-template <typename R>
-__device__ Velocity<R> collide(const InstDev& P, R kv, R vlim, R vx, R vy, R vz, R v1, R s1,
-                               uint4 rr, uint32_t id, uint32_t step, R wj,
-                               unsigned long long* acc, R* e_sec_out, int* proc_out) {
-  const StepConsts<R>& K = consts<R>(P);
-  R u[4];
-  uniform4<R>(rr, u);
-  atomicAdd(&acc[ACC_CAND], 1ull);
-  R vb = v1 > vlim ? vlim : v1;
-  if (vb > K.vb_cap) {
-    vb = K.vb_cap;
-    atomicAdd(&acc[ACC_MAJ], 1ull);
-  }
-  const R c = K.ndt * vb;
-  const R eps = s1 * K.K_E;
-  R xs[kMaxProc];
-  xsec(P, eps, xs);
-  const R rsel = u[1] * K.P0;
-  // the first process whose cumulative rate exceeds the draw: elastic,
-  // excitation level 1..n_exc, ionization; none: a null collision
-  const int n_proc = P.n_exc + 2;
-  int k = 0;
-  while (k < n_proc && !(rsel < c * xs[k])) ++k;
-  const int proc = k == n_proc ? 3 : (k == 0 ? 0 : (k <= P.n_exc ? 1 : 2));
-  *proc_out = proc;
-  Velocity<R> o = {vx, vy, vz};
-  if (proc == 3) return o;
-  atomicAdd(&acc[ACC_COLL0 + proc], 1ull);
-  if (proc == 0) {
-    // Vahedi-Surendra: cos chi = (2 + eps - 2 (1 + eps)^u) / eps, with
-    // 1 - cos chi and 1 + cos chi each formed without cancellation so that
-    // sin chi keeps its relative precision at both ends
-    const R L = r_log1p(eps);
-    const R em = r_expm1(u[2] * L);
-    const R ep = -r_expm1(-((R)1 - u[2]) * L);
-    R omc = (em + em) / eps;
-    R opc = (((R)1 + eps) * (ep + ep)) / eps;
-    omc = r_min((R)2, r_max((R)0, omc));
-    opc = r_min((R)2, r_max((R)0, opc));
-    const R cc = omc <= (R)1 ? (R)1 - omc : opc - (R)1;
-    const R sc = r_sqrt(omc * opc);
-    const R ph = K.two_pi * u[3];
-    const R cp = r_cos(ph), sn = r_sin(ph);
-    const R e_new = eps * ((R)1 - K.R2 * omc);
-    R ux = vx / v1, uy = vy / v1, uz = vz / v1;
-    rotate(ux, uy, uz, cc, sc, cp, sn);
-    const R vn = r_sqrt(e_new * kv);
-    o.vx = vn * ux;
-    o.vy = vn * uy;
-    o.vz = vn * uz;
-  } else if (proc == 1) {
-    R e_new = eps - K.e_ex[k - 1];
-    if (e_new < (R)0) {
-      e_new = (R)0;
-      atomicAdd(&acc[ACC_CLAMP], 1ull);
-    }
-    isotropic(r_sqrt(e_new * kv), u[2], u[3], K.two_pi, o.vx, o.vy, o.vz);
-  } else {
-    R e_av = eps - K.e_io;
-    if (e_av < (R)0) {
-      e_av = (R)0;
-      atomicAdd(&acc[ACC_CLAMP], 1ull);
-    }
-    atomicAdd(&acc[ACC_WIONZ], (unsigned long long)fixed_charge(wj, K.wscale));
-    const uint4 r1 =
-        philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u, 1u), P.key0, P.key1);
-    const R es = uniform01r<R>(r1.x) * e_av;
-    const R ep = e_av - es;
-    isotropic(r_sqrt(ep * kv), u[2], u[3], K.two_pi, o.vx, o.vy, o.vz);
-    *e_sec_out = es;
-  }
-  return o;
-}
-
-// Write the electron and Ar+ born by an ionization at slots pe (electron
-// store) and pi (ion store) with their serial numbers, and deposit both.  The
-// secondary gets energy es along an isotropic direction (block 1 of the
-// primary's draws); the ion a gas-temperature Maxwellian (Box-Muller on
-// block 2).
-template <typename R>
-__device__ void born_pair(const InstDev& P, const SoAT<R>& me, const SoAT<R>& mi, uint32_t pe,
-                          uint32_t pi, int cell, R off, R wj, uint32_t id, uint32_t step, R es,
-                          uint32_t serial_e, uint32_t serial_i) {
-  const StepConsts<R>& K = consts<R>(P);
-  const uint32_t gen = id & kGenBit;
-  const uint4 r1 = philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u, 1u), P.key0, P.key1);
-  R bx, by, bz;
-  isotropic(r_sqrt(es * K.K_V[kElectron]), uniform01r<R>(r1.y), uniform01r<R>(r1.z), K.two_pi,
-            bx, by, bz);
-  me.cell[pe] = cell;
-  me.off[pe] = off;
-  me.vx[pe] = bx;
-  me.vy[pe] = by;
-  me.vz[pe] = bz;
-  me.wj[pe] = wj;
-  me.id[pe] = gen | (serial_e & kSerialMask);
-  deposit(P.rho_acc[kElectron], cell, off,
-          fixed_charge(beta_of(r_sqrt(bx * bx + by * by + bz * bz), K.vlim[kElectron]) * wj,
-                       K.wscale));
-  const uint4 r2 = philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u, 2u), P.key0, P.key1);
-  R g[4];
-  uniform4<R>(r2, g);
-  const R rr1 = r_sqrt((R)-2 * r_log(g[0]));
-  const R rr2 = r_sqrt((R)-2 * r_log(g[2]));
-  const R a1 = K.two_pi * g[1], a2 = K.two_pi * g[3];
-  const R ix = K.sigT_ion * (rr1 * r_cos(a1));
-  const R iy = K.sigT_ion * (rr1 * r_sin(a1));
-  const R iz = K.sigT_ion * (rr2 * r_cos(a2));
-  mi.cell[pi] = cell;
-  mi.off[pi] = off;
-  mi.vx[pi] = ix;
-  mi.vy[pi] = iy;
-  mi.vz[pi] = iz;
-  mi.wj[pi] = wj;
-  mi.id[pi] = gen | (serial_i & kSerialMask);
-  deposit(P.rho_acc[kIon], cell, off,
-          fixed_charge(beta_of(r_sqrt(ix * ix + iy * iy + iz * iz), K.vlim[kIon]) * wj,
-                       K.wscale));
-}
-
-// Slot after the last live marker of a store (the particle kernel has
-// compacted every tile of this step).
-__device__ __forceinline__ uint32_t tail_slot(const SpeciesDev& S, const SpeciesState& st) {
-  return st.n_tiles ? (st.n_tiles - 1) * (uint32_t)kTile + S.fill[st.cur][st.n_tiles - 1]
-                    : 0u;
-}
-
-template <typename R>
-__device__ __forceinline__ void write_marker(const SoAT<R>& d, size_t o, int cell, R off, R vx,
-                                             R vy, R vz, R wj, uint32_t id) {
-  d.cell[o] = cell;
-  d.off[o] = off;
-  d.vx[o] = vx;
-  d.vy[o] = vy;
-  d.vz[o] = vz;
-  d.wj[o] = wj;
-  d.id[o] = id;
-}
 
 }  // namespace
 

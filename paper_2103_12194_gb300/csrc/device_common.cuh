@@ -138,6 +138,49 @@ __device__ __forceinline__ R beta_of(R v, R vlim) {
   return r_min((R)1, vlim / v);
 }
 
+// Speed-limited kick over one step of a species with a finite limit L
+// (Eq. slpicEOMv: dv_x/dt = beta(|v|) q E_x / m, v_y and v_z unchanged).
+// A = q E_x dt / m is the unlimited velocity increment.  Returns the new v_x.
+//  - Below the limit at both ends of the step: the leapfrog kick v_x + A.
+//  - Otherwise the marker moves at the limit for a fraction f of the step
+//    (f < 1 when it starts below L: the first part, up to |v| = L, is an
+//    unlimited kick).  Along the speed-limited part, in the time
+//    tau = integral of beta dt the motion is unlimited (u = v_1 + (A / dt) tau
+//    along x), and f dt = integral of |v| / L dtau; the trapezoid rule for
+//    that integral gives z (s_1 + s') = K with z = u - v_1 (in the direction
+//    of A), K = 2 f |A| L, s_1 and s' the speeds at the ends.  Exact for
+//    motion along x (the energy gained is q E_x times the distance moved,
+//    as Eqs. slpicEOMx and slpicEOMv imply), second order otherwise.  Solved
+//    by one Newton step from its root for v_y = v_z = 0, an upper bound.
+template <typename R>
+__device__ __forceinline__ R limited_kick(R vx, R vy, R vz, R A, R L) {
+  const R sp = r_sqrt(vx * vx + vy * vy + vz * vz);
+  const R vt = vx + A;
+  const R st = r_sqrt(vt * vt + vy * vy + vz * vz);
+  if (sp <= L && st <= L) return vt;
+  const R g = A > (R)0 ? (R)1 : (R)-1;
+  const R aA = g * A;
+  const R p2 = vy * vy + vz * vz;
+  R f, s1, v1;
+  if (sp < L) {
+    const R q = r_sqrt(r_max((R)0, L * L - p2));
+    f = r_min((R)1, r_max((R)0, (R)1 - (q - g * vx) / aA));
+    s1 = L;
+    v1 = q;
+  } else {
+    f = (R)1;
+    s1 = sp;
+    v1 = g * vx;
+  }
+  const R K = (R)2 * f * aA * L;
+  const R c = s1 + v1;
+  R z = r_min((r_sqrt(c * c + (R)4 * K) - c) * (R)0.5, K / s1);
+  const R w = v1 + z;
+  const R s = r_sqrt(w * w + p2);
+  if (s > (R)0) z = r_max((R)0, z - (z * (s1 + s) - K) / (s1 + s + z * w / s));
+  return g * (v1 + z);
+}
+
 // Direction with cos(theta) = 1 - 2 ua about x and azimuth 2 pi ub.
 template <typename R>
 __device__ __forceinline__ void isotropic(R speed, R ua, R ub, R two_pi, R& vx, R& vy, R& vz) {

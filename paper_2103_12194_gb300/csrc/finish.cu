@@ -7,48 +7,13 @@
 // validation and the Philox self-check kernel.
 #include "device_common.cuh"
 #include "slpic_internal.h"
+#include "step_ops.cuh"
 
 namespace slpic {
 
 namespace {
 
-constexpr int kFinThreads = 1024;
 constexpr int kMoveThreads = 256;
-
-__device__ __forceinline__ long long shfl_up(long long v, int o) {
-  return __shfl_up_sync(0xFFFFFFFFu, v, o);
-}
-__device__ __forceinline__ __int128 shfl_up(__int128 v, int o) {
-  const unsigned long long lo = __shfl_up_sync(0xFFFFFFFFu, (unsigned long long)v, o);
-  const long long hi = __shfl_up_sync(0xFFFFFFFFu, (long long)(v >> 64), o);
-  return (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | lo);
-}
-
-// Inclusive block scan: shuffle scans within the warps, then one warp scans
-// the 32 warp totals (buf holds 32 entries).  Integer sums, so exact.
-template <typename T>
-__device__ T block_incl_scan(T v, T* buf) {
-  static_assert(kFinThreads == 1024, "one warp scans the 32 warp totals");
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int o = 1; o < 32; o <<= 1) {
-    const T y = shfl_up(v, o);
-    if (lane >= o) v += y;
-  }
-  if (lane == 31) buf[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    T t = buf[lane];
-    for (int o = 1; o < 32; o <<= 1) {
-      const T y = shfl_up(t, o);
-      if (lane >= o) t += y;
-    }
-    buf[lane] = t;
-  }
-  __syncthreads();
-  const T r = v + (w ? buf[w - 1] : T(0));
-  __syncthreads();
-  return r;
-}
 
 // Plan the next step from the tiles in use (all threads of one CTA):
 // particle-kernel super-tiles (push_warps tiles each) and their weights per
@@ -118,37 +83,6 @@ __device__ void plan_next(const DeviceRefs& r, long long* s_buf) {
 }
 
 }  // namespace
-
-// Net deposit (ions minus electrons) at node k of the last step: from the
-// CTA's shared copy when there is one, else from the last deposit.
-__device__ __forceinline__ long long net_at(const InstDev& P, const long long* s_net, int k) {
-  return s_net ? s_net[k] : P.rho_last[kIon][k] - P.rho_last[kElectron][k];
-}
-
-// The exact integer sums of the 1D Poisson solve over the last step's net
-// deposit (all threads of a kFinThreads CTA; thread t covers k = k0 ..
-// k0 + chunk - 1 of 1..N): returns D_1 = (V + C J_N) / N and writes I_{k0}.
-__device__ double poisson_d1(const InstDev& P, const long long* s_net, int k0, int chunk,
-                             long long* s_i64, __int128* s_i128, long long* I_k0) {
-  const int N = P.n_cells;
-  long long loc = 0;
-  for (int k = k0; k < k0 + chunk && k <= N - 1; ++k) loc += net_at(P, s_net, k);
-  const long long inc = block_incl_scan<long long>(loc, s_i64);
-  long long Ik = inc - loc;  // I_k at the chunk start (exclusive of net_k)
-  *I_k0 = Ik;
-  __int128 locJ = 0;
-  for (int k = k0; k < k0 + chunk && k <= N; ++k) {
-    locJ += (__int128)Ik;
-    if (k <= N - 1) Ik += net_at(P, s_net, k);
-  }
-  const __int128 incJ = block_incl_scan<__int128>(locJ, s_i128);
-  __shared__ __int128 s_JN;
-  if (threadIdx.x == kFinThreads - 1) s_JN = incJ;
-  __syncthreads();
-  const __int128 JN = s_JN;
-  __syncthreads();
-  return (P.V + P.pois_C * (double)JN) / (double)N;
-}
 
 // mode 0: finish a step (one CTA per instance; the last one plans the next
 // step); mode 1: plan only (one CTA).  Dynamic shared memory: net_nodes
@@ -274,69 +208,9 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode, 
   }
 
   // ---- tallies: one thread per 8-byte slot of the record ---------------------
-  // slot layout of TallyRec: 0 step, 1-2 n_live, 3-4 w_live, 5-7 n_coll,
-  // 8 n_candidates, 9-12 n_abs, 13-16 w_abs, 17 n_see, 18 w_see, 19 w_ionz,
-  // 20 w_cath_ion, 21 w_cath_ion_gen0, 22 n_clamp, 23 n_majorant,
-  // 24 marker_steps, 25 w_gain_gen0; slots 0-4 are states (replaced in the
-  // totals), the others sums
-  constexpr int kSlots = (int)(sizeof(TallyRec) / 8);
-  static_assert(kSlots == 26, "TallyRec layout");
-  if (t < kSlots) {
-    const unsigned long long* q = s_acc;
-    const double unit = 1.0 / P.c64.wscale;
-    long long iv = 0;
-    double dv = 0.0;
-    bool is_double = false;
-    if (t == 0) {
-      iv = is.step;
-    } else if (t <= 2) {
-      iv = r.sstate[inst * 2 + t - 1].n_live;
-    } else if (t <= 4) {
-      // live weight by its changes: minus what left through the electrodes,
-      // plus the births (ionization pairs; emitted electrons)
-      const int sp = t - 3;
-      unsigned long long w = is.w_live[sp] - q[ACC_WABS + 2 * sp] - q[ACC_WABS + 2 * sp + 1] +
-                             q[ACC_WIONZ] + (sp == 0 ? q[ACC_WSEE] : 0ull);
-      is.w_live[sp] = w;
-      dv = (double)(long long)w * unit;
-      is_double = true;
-    } else if (t <= 7) {
-      iv = (long long)q[ACC_COLL0 + t - 5];
-    } else if (t == 8) {
-      iv = (long long)q[ACC_CAND];
-    } else if (t <= 12) {
-      iv = (long long)q[ACC_NABS + t - 9];
-    } else if (t <= 16) {
-      dv = (double)(long long)q[ACC_WABS + t - 13] * unit;
-      is_double = true;
-    } else if (t == 17) {
-      iv = (long long)q[ACC_SEE];
-    } else if (t <= 21) {
-      const int acc_of[4] = {ACC_WSEE, ACC_WIONZ, ACC_WCATH, ACC_WCATH0};
-      dv = (double)(long long)q[acc_of[t - 18]] * unit;
-      is_double = true;
-    } else if (t == 22) {
-      iv = (long long)q[ACC_CLAMP];
-    } else if (t == 23) {
-      iv = (long long)q[ACC_MAJ];
-    } else if (t == 24) {
-      iv = (long long)q[ACC_MSTEPS];
-    } else {
-      dv = (double)(long long)q[ACC_GWCATH0] * unit;
-      is_double = true;
-    }
-    long long* ring = reinterpret_cast<long long*>(P.ring + is.n_steps_done % P.ring_len);
-    long long* tot = reinterpret_cast<long long*>(P.total);
-    if (is_double) {
-      reinterpret_cast<double*>(ring)[t] = dv;
-      if (t <= 4) reinterpret_cast<double*>(tot)[t] = dv;
-      else reinterpret_cast<double*>(tot)[t] += dv;
-    } else {
-      ring[t] = iv;
-      if (t <= 4) tot[t] = iv;
-      else tot[t] += iv;
-    }
-  }
+  if (t < kTallySlots)
+    commit_tally_slot(P, t, s_acc, is.step, is.n_steps_done, r.sstate[inst * 2].n_live,
+                      r.sstate[inst * 2 + 1].n_live, is.w_live, &is.ion_steps);
   __syncthreads();
   if (t == 0) {
     is.step += 1u;

@@ -33,6 +33,7 @@
 // order of the additions.
 #include "device_common.cuh"
 #include "slpic_internal.h"
+#include "step_ops.cuh"
 
 namespace slpic {
 
@@ -175,53 +176,6 @@ __device__ __forceinline__ void load_tile(const DeviceRefs& r, const WarpTile& t
   bulk_load(st.f[2], in.vy + base, br, bar);
   bulk_load(st.f[3], in.vz + base, br, bar);
   bulk_load(st.f[4], in.wj + base, br, bar);
-}
-
-// A marker left the gap: tally the flux through the electrode (Eq. j); an ion
-// at the cathode emits an electron with probability gamma.  Returns true when
-// an electron is emitted.  Rare; kept out of line.
-template <typename R>
-__device__ __noinline__ bool absorb(const InstDev& P, int sp, int side, R wj, uint32_t id,
-                                    uint32_t step, unsigned long long* acc, R vx, R vy, R vz) {
-  const StepConsts<R>& K = consts<R>(P);
-  const long long Qw = fixed_charge(wj, K.wscale);
-  atomicAdd(&acc[ACC_NABS + sp * 2 + side], 1ull);
-  atomicAdd(&acc[ACC_WABS + sp * 2 + side], (unsigned long long)Qw);
-  if (sp != kIon || side != 0) return false;
-  atomicAdd(&acc[ACC_WCATH], (unsigned long long)Qw);
-  // secondary-electron yield: constant, or Eq. sey at the ion's kinetic
-  // energy (exponent 0.05 below 700 eV, 0.72 from 700 eV on)
-  R g = K.gamma;
-  if (P.emission_model == 1) {
-    const R eps_i = (vx * vx + vy * vy + vz * vz) * K.K_Ei;
-    const R expo = eps_i < (R)700 ? (R)0.05 : (R)0.72;
-    g = (R)0.09 * r_pow(eps_i / (R)700, expo);
-  }
-  if (!(id & kGenBit)) {
-    atomicAdd(&acc[ACC_WCATH0], (unsigned long long)Qw);
-    atomicAdd(&acc[ACC_GWCATH0], (unsigned long long)fixed_charge(g * wj, K.wscale));
-  }
-  const uint4 rr =
-      philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u + 1u, 0u), P.key0, P.key1);
-  if (!P.emit || !(uniform01r<R>(rr.x) < g)) return false;
-  atomicAdd(&acc[ACC_SEE], 1ull);
-  atomicAdd(&acc[ACC_WSEE], (unsigned long long)Qw);
-  return true;
-}
-
-// Stage an electron emitted at the cathode (x = 0, at rest, the ion's w_j).
-template <typename R>
-__device__ __noinline__ void stage_emission(const InstDev& P, size_t o, R wj) {
-  const SoAT<R> sb = soa_as<R>(P.sp[kElectron].stage_b);
-  sb.cell[o] = 0;
-  sb.off[o] = (R)0;
-  sb.vx[o] = (R)0;
-  sb.vy[o] = (R)0;
-  sb.vz[o] = (R)0;
-  sb.wj[o] = wj;
-  sb.id[o] = kGenBit;
-  // at rest: beta = 1, all the charge on node 0
-  atomicAdd(P.rho_acc[kElectron], (unsigned long long)fixed_charge(wj, consts<R>(P).wscale));
 }
 
 }  // namespace
@@ -390,14 +344,12 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
           const R E0 = __ldg(Enode + cell[j]), E1 = __ldg(Enode + cell[j] + 1);
           a[j] = qmdt * (E0 + off[j] * (E1 - E0));
         }
-        // speed-limited kick (beta of the pre-kick speed) and drift (beta of the
-        // post-kick speed); an unlimited species has beta = 1 exactly
+        // speed-limited kick (limited_kick: leapfrog below the limit, the
+        // proper-time trapezoid rule across and above it) and drift (beta of
+        // the post-kick speed); an unlimited species has beta = 1 exactly
         if (limited) {
 #pragma unroll
-          for (int j = 0; j < kPerLane; ++j) {
-            const R b0 = beta_of(r_sqrt(vx[j] * vx[j] + vy[j] * vy[j] + vz[j] * vz[j]), vlim);
-            vx[j] = vx[j] + b0 * a[j];
-          }
+          for (int j = 0; j < kPerLane; ++j) vx[j] = limited_kick(vx[j], vy[j], vz[j], a[j], vlim);
 #pragma unroll
           for (int j = 0; j < kPerLane; ++j)
             b1[j] = beta_of(r_sqrt(vx[j] * vx[j] + vy[j] * vy[j] + vz[j] * vz[j]), vlim);

@@ -223,6 +223,7 @@ struct InstState {
   long long n_steps_done;
   unsigned long long w_seed;     // fixed-point sum of seeded electron weights
   unsigned long long w_live[2];  // fixed-point sum of live weights per species
+  long long ion_steps;           // sum over the steps of the live ions after each
 };
 
 // Global state of the batched step.
@@ -240,6 +241,9 @@ struct Control {
   unsigned int n_coll_chunks;
   unsigned int move_counter; // next repacking chunk to hand out
   unsigned int n_move_chunks;
+  unsigned int small_bar;    // single-CTA path: arrivals at its grid barriers
+  int small_stop;            // single-CTA path: a store outgrew it
+  long long small_done;      // single-CTA path: steps run by the last launch
 };
 
 // Look-back record of one chunk of an ordered scan.
@@ -256,6 +260,9 @@ constexpr int kCollWarps = 8;
 constexpr int kCollWarpTiles = 32;
 constexpr int kCollChunkTiles = kCollWarps * kCollWarpTiles;
 constexpr int kMoveChunkTiles = 128;
+// Single-CTA path (small.cu): at most this many tiles per store and instance
+// when a step starts.
+constexpr int kSmallMaxTiles = 32;
 
 struct DeviceRefs {
   InstDev* inst;          // [n_inst]
@@ -304,5 +311,12 @@ void launch_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, uint32_t* out,
                    long long n, cudaStream_t s);
 void launch_philox2(uint32_t k, const uint32_t* ctr, uint32_t* out, long long n,
                     cudaStream_t s);
+// Single-CTA path: shared memory for field-mode-1 grids of up to
+// max_poisson_nodes nodes and resident CTAs per SM (0: does not fit); then up
+// to n_steps steps of every instance (one CTA each), stopping before a step
+// when a store has more than max_tiles tiles.  Steps run: Control::small_done.
+int small_config(int fp64, int max_poisson_nodes, size_t* smem_bytes, int* blocks_per_sm);
+int launch_small(const DeviceRefs& r, long long n_steps, int max_tiles, size_t smem_bytes,
+                 cudaStream_t s);
 
 }  // namespace slpic

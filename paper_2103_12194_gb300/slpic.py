@@ -91,6 +91,8 @@ def lib():
         "slpic_load_particles_device": ([vp, i32, i32, ctypes.POINTER(SoA), i64, u32], i32),
         "slpic_reset_counters": ([vp, i32], i32),
         "slpic_step": ([vp, i64], i32),
+        "slpic_step_small": ([vp, i64, ctypes.POINTER(i64)], i32),
+        "slpic_set_small_limit": ([vp, i32], i32),
         "slpic_synchronize": ([vp], i32),
         "slpic_clear_error": ([vp], i32),
         "slpic_count": ([vp, i32, i32, ctypes.POINTER(i64)], i32),
@@ -304,6 +306,28 @@ class Simulation:
     # ---- stepping -------------------------------------------------------
     def step(self, n=1):
         self._ck(self._L.slpic_step(self._h, int(n)))
+
+    def step_small(self, n):
+        """slpic_step_small: up to n steps in the single-CTA path; returns the
+        steps run (synchronous)."""
+        done = ctypes.c_int64(0)
+        self._ck(self._L.slpic_step_small(self._h, int(n), ctypes.byref(done)))
+        return int(done.value)
+
+    def step_auto(self, n):
+        """n steps: the single-CTA path while the populations are small, the
+        batched kernels otherwise (synchronous when the small path runs)."""
+        left = int(n)
+        while left > 0:
+            k = self.step_small(left)
+            left -= k
+            if left > 0 and k == 0:
+                k = min(left, 256)
+                self.step(k)
+                left -= k
+
+    def set_small_limit(self, max_tiles):
+        self._ck(self._L.slpic_set_small_limit(self._h, int(max_tiles)))
 
     def synchronize(self):
         return self._ck(self._L.slpic_synchronize(self._h))

@@ -86,6 +86,38 @@ class ScalarSim:
             return 1.0
         return vl / v if v > vl else 1.0
 
+    def kick(self, vx, vy, vz, A, sp):
+        """v_x after one step's kick, A = q E dt / m.  Below the speed limit
+        at both ends: v_x + A.  Else: the unlimited part up to |v| = L, then
+        the speed-limited part (fraction f of the step), where with
+        z = (v_x' - v_1) sign(A) the trapezoid rule for the elapsed time
+        gives z (s_1 + |v'|) = 2 f |A| L; z from the v_y = v_z = 0 root and
+        one Newton step."""
+        L = self.vl[sp]
+        if not (L > 0 and math.isfinite(L)):
+            return vx + A
+        speed = math.sqrt(vx * vx + vy * vy + vz * vz)
+        vt = vx + A
+        if speed <= L and math.sqrt(vt * vt + vy * vy + vz * vz) <= L:
+            return vt
+        sign = 1.0 if A > 0 else -1.0
+        mag = sign * A
+        perp2 = vy * vy + vz * vz
+        if speed < L:
+            along = math.sqrt(max(0.0, L * L - perp2))
+            frac = min(1.0, max(0.0, 1.0 - (along - sign * vx) / mag))
+            s_a, u_a = L, along
+        else:
+            frac, s_a, u_a = 1.0, speed, sign * vx
+        K = 2.0 * frac * mag * L
+        c = s_a + u_a
+        z = min((math.sqrt(c * c + 4.0 * K) - c) * 0.5, K / s_a)
+        w = u_a + z
+        s_b = math.sqrt(w * w + perp2)
+        if s_b > 0:
+            z = max(0.0, z - (z * (s_a + s_b) - K) / (s_a + s_b + z * w / s_b))
+        return sign * (u_a + z)
+
     def draws(self, ident, step, sp, blk):
         c = [ident, step & MASK32, (self.s.get("instance", 0) * 2 + sp) & MASK32, blk]
         return [unif(w) for w in philox(c, self.s["seed"])]
@@ -128,7 +160,7 @@ class ScalarSim:
                 f = x / self.dx - k
                 Ex = self.E[k] * (1.0 - f) + self.E[k + 1] * f
                 a = self.q[sp] / self.m[sp] * Ex
-                vx += self.beta(math.sqrt(vx * vx + vy * vy + vz * vz), sp) * a * self.dt
+                vx = self.kick(vx, vy, vz, a * self.dt, sp)
                 v1 = math.sqrt(vx * vx + vy * vy + vz * vz)
                 x += self.beta(v1, sp) * vx * self.dt
                 if x < 0.0:

@@ -70,3 +70,35 @@ def test_ion_trend_agrees_with_the_gain_criterion(slpic):
     # below breakdown the population has died out by the end
     assert means[0, -1] == 0.0 and means[1, -1] < 0.05 * means[1].max()
     sim.close()
+
+
+def test_pic_and_slpic_classify_alike(slpic):
+    """Sec. V: PIC and SLPIC give the same brackets.  The paper's setup
+    (Sec. IV): 100 electrons at rest, Eq. sey yield, five processes, SLPIC
+    with v_lim = v0 and dt = dx / v0, PIC with dt = dx / v_max, both over 30
+    ion crossing times (PIC in sqrt(M / m_e) times more steps).  pd = 1 Torr
+    cm, 96 cells; V_b of this gas is near 165 V."""
+    import math
+    volts = (115.0, 260.0)
+    cells = 96
+    table = inputs.make_table(levels=3)
+    got = {}
+    for pic in (False, True):
+        sim = slpic.Simulation(len(volts))
+        for j, V in enumerate(volts):
+            dx = 0.01 / cells
+            v0 = inputs.ion_speed(V)
+            vmax = math.sqrt(2 * inputs.QE * V / inputs.ME)
+            spec = inputs.gap_spec(n_cells=cells, V=V, pd_torr_cm=1.0, gamma_se=0.07,
+                                   field_mode=0, vlim_e=math.inf if pic else v0,
+                                   dt=dx / (vmax if pic else v0), seed=61 + j, instance=j,
+                                   table=table)
+            spec["emission_model"] = 1
+            sim.configure(j, spec, capacity=(1 << 19, 1 << 19))
+        for j in range(len(volts)):
+            sim.seed(j, slpic.ELECTRON, 100, slpic.SEED_REST)
+        n_t = 60 * cells * (math.sqrt(inputs.M_AR / inputs.ME) if pic else 1.0)
+        means, above = sim.ion_trend(int(math.ceil(n_t / 15)), 15)
+        got[pic] = (list(above), means)
+        sim.close()
+    assert got[False][0] == got[True][0] == [False, True], got

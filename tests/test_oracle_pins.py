@@ -240,12 +240,38 @@ def test_slpic_transit_time_and_energy(oracle_mod):
     p = o2.particles(0)
     e = 0.5 * inputs.ME * p["vx"][0] ** 2 / inputs.QE
     x = (p["cell"][0] + p["off"][0]) * spec["d"] / spec["n_cells"]
-    # O(dt) discretisation error: the first kick (beta = 1 at rest) gives
-    # a dt in one step, worth m (a dt)^2 / 2, while the marker moves one
-    # cell; the staggered velocity adds at most half a cell of field energy.
-    first_kick = 0.5 * inputs.ME * (a * spec["dt"]) ** 2 / inputs.QE
-    assert abs(e - spec["V"] * x / spec["d"]) < first_kick + 2 * spec["V"] / spec["n_cells"]
-    assert e == pytest.approx(spec["V"], rel=0.03)
+    # the energy is e E times the distance moved, less m v0^2 / 2 (the
+    # unlimited start moves v0 dt in the first step), up to rounding
+    e_lim = 0.5 * inputs.ME * v0 ** 2 / inputs.QE
+    assert e == pytest.approx(spec["V"] * x / spec["d"] - e_lim, rel=1e-9)
+    assert e == pytest.approx(spec["V"], rel=0.01)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_speed_limited_energy_equals_work_from_rest(oracle_mod, precision):
+    """The paper's own setup (Sec. IV): v_lim = v0 = sqrt(2 e V / M) and
+    dt = dx / v0, an electron at rest at the cathode; one step's unlimited
+    kick a dt is hundreds of times v0 here.  Along a speed-limited path
+    Eqs. slpicEOMx and slpicEOMv give d(m v^2 / 2) = e E dx: after n steps
+    the marker is n cells out (it moves v0 dt = dx per step) and its energy
+    is e E n dx - m v0^2 / 2, the m v0^2 / 2 being gained in the unlimited
+    start of the first step over a shorter distance."""
+    V, N = 214.8, 66
+    v0 = inputs.ion_speed(V)
+    spec = vacuum(inputs.gap_spec(n_cells=N, V=V, pd_torr_cm=0.3, vlim_e=v0, field_mode=0,
+                                  dt=0.01 / N / v0))
+    a_dt = inputs.QE * V / spec["d"] / inputs.ME * spec["dt"]
+    assert a_dt > 300 * v0
+    o = oracle_mod.Oracle(spec, precision)
+    o.load(0, inputs.rest_state(1))
+    tol = 1e-12 if precision == 64 else 2e-6
+    for n in range(1, 40):
+        o.step(1)
+        p = o.particles(0)
+        assert p["cell"][0] + float(p["off"][0]) == pytest.approx(n, abs=tol * n)
+        e = 0.5 * inputs.ME * float(p["vx"][0]) ** 2 / inputs.QE
+        e_want = V * n / N - 0.5 * inputs.ME * v0 ** 2 / inputs.QE
+        assert e == pytest.approx(e_want, rel=10 * tol)
 
 
 def test_displacement_bounded_by_speed_limit(oracle_mod):
