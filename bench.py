@@ -50,9 +50,13 @@ def parse():
                     help="instead of the benchmark, run the PIC vs SLPIC study shaped like "
                          "Table tab:sims on the rows given (comma-separated indices 0-10, "
                          "or 'all') and print one JSON line")
+    ap.add_argument("--small-pop", action="store_true",
+                    help="instead of the benchmark, time the paper's breakdown run at 1 Torr cm "
+                         "(Table tab:sims row 4) with and without the single-CTA path")
+    ap.add_argument("--small-pop-steps", type=int, default=13140)
     ap.add_argument("--tab-sims-pic-max", type=float, default=4.0,
                     help="largest pressure [Torr] with a PIC run (the paper's: 4)")
-    ap.add_argument("--tab-sims-pic-full-max", type=float, default=1.0,
+    ap.add_argument("--tab-sims-pic-full-max", type=float, default=0.4,
                     help="above this pressure [Torr] a PIC run covers its first 3 of 15 "
                          "windows and its wall time is extrapolated")
     return ap.parse_args()
@@ -84,7 +88,7 @@ def push_source_hash():
     """Hash of the particle kernel's sources (the kernel and its headers)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2103_12194_gb300", "csrc")
-    for name in ("push.cu", "device_common.cuh", "slpic_internal.h"):
+    for name in ("push.cu", "device_common.cuh", "slpic_internal.h", "step_ops.cuh"):
         h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
 
@@ -290,7 +294,7 @@ def tab_sims_run(slpic, inputs, p, V, cells, pic, local, stream, seed=1, windows
     spw = int(math.ceil(n_t / windows))
     nw = windows if run_windows is None else run_windows
     sim = slpic.Simulation(1, device=local, stream=stream)
-    sim.configure(0, spec, capacity=(1 << 19, 1 << 19))
+    sim.configure(0, spec, capacity=(1 << 18, 1 << 18))
     sim.seed(0, slpic.ELECTRON, 100, slpic.SEED_REST)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -342,6 +346,40 @@ def tab_sims(slpic, inputs, rows, pic_max, pic_full_max, local, stream, margin=0
                                         for x in rec["runs"])
         print(json.dumps({"tab_sims_row": rec}), file=sys.stderr, flush=True)
         out["rows"].append(rec)
+    return out
+
+
+def small_pop(slpic, inputs, steps, local, stream, V=171.5):
+    """The paper's breakdown run at 1 Torr cm (219 cells, V near this gas's
+    V_b, SLPIC with v_lim = v0, 100 electrons at rest, Eq. sey yield, five
+    processes), followed for `steps` steps (13140 = 30 ion crossings) with
+    the ion-trend protocol: once with the single-CTA path for small
+    populations, once with the batched kernels only.  Both give the same
+    markers; the wall times differ."""
+    import numpy as np
+    import torch
+    p, _, cells = TAB_SIMS[3]
+    out = {}
+    for name, limit in (("single_cta", 32), ("batched", 0)):
+        spec = tab_sims_spec(inputs, p, V, cells, False, seed=7)
+        sim = slpic.Simulation(1, device=local, stream=stream)
+        sim.configure(0, spec, capacity=(1 << 18, 1 << 18))
+        sim.seed(0, slpic.ELECTRON, 100, slpic.SEED_REST)
+        sim.set_small_limit(limit)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        means, _ = sim.ion_trend(max(1, steps // 15), 15)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        tot = sim.tallies(0)
+        n = int(tot["step"]) + 1
+        out[name] = {"wall_s": wall, "steps": n, "us_per_step": wall / n * 1e6,
+                     "marker_steps": int(tot["marker_steps"]),
+                     "mean_live_markers": int(tot["marker_steps"]) / n,
+                     "final_live": [int(x) for x in tot["n_live"]]}
+        sim.close()
+    out["same_markers"] = out["single_cta"]["marker_steps"] == out["batched"]["marker_steps"]
+    out["speedup"] = out["batched"]["wall_s"] / out["single_cta"]["wall_s"]
     return out
 
 
@@ -397,6 +435,13 @@ def run_ours(args):
     torch.cuda.set_device(local)
     build.build()
     stream = torch.cuda.current_stream()
+    if args.small_pop:
+        if rank == 0:
+            res = small_pop(slpic, inputs, args.small_pop_steps, local, stream)
+            res["study"] = ("the paper's breakdown run at 1 Torr cm, 219 cells, 100 electrons at "
+                            "rest: single-CTA path against the batched kernels")
+            print(json.dumps(res), flush=True)
+        return
     if args.tab_sims is not None:
         if rank == 0:
             rows = (range(len(TAB_SIMS)) if args.tab_sims == "all"

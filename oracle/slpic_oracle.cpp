@@ -310,9 +310,10 @@ struct Sim {
     if (!limited[s]) return m.vx + A;
     const R L = vlim[s];
     const R sp = std::sqrt(m.vx * m.vx + m.vy * m.vy + m.vz * m.vz);
-    const R vt = m.vx + A;
-    const R st = std::sqrt(vt * vt + m.vy * m.vy + m.vz * m.vz);
-    if (sp <= L && st <= L) return vt;
+    if (sp <= L) {
+      const R vt = m.vx + A;
+      if (std::sqrt(vt * vt + m.vy * m.vy + m.vz * m.vz) <= L) return vt;
+    }
     const R g = A > (R)0 ? (R)1 : (R)-1;
     const R aA = g * A;
     const R p2 = m.vy * m.vy + m.vz * m.vz;
@@ -330,10 +331,13 @@ struct Sim {
     }
     const R K = (R)2 * f * aA * L;
     const R c = s1 + v1;
-    R z = std::min((std::sqrt(c * c + (R)4 * K) - c) * (R)0.5, K / s1);
+    R z = (std::sqrt(c * c + (R)4 * K) - c) * (R)0.5;
+    if (z * s1 > K) z = K / s1;  // the root is at most K / s_1
     const R w = v1 + z;
     const R sn = std::sqrt(w * w + p2);
-    if (sn > (R)0) z = std::max((R)0, z - (z * (s1 + sn) - K) / (s1 + sn + z * w / sn));
+    const R t = s1 + sn;
+    const R den = t * sn + z * w;  // sn times the slope of z (s_1 + s') - K
+    if (den > (R)0) z = std::max((R)0, z - (z * t - K) * sn / den);
     return g * (v1 + z);
   }
 

@@ -155,9 +155,10 @@ __device__ __forceinline__ R beta_of(R v, R vlim) {
 template <typename R>
 __device__ __forceinline__ R limited_kick(R vx, R vy, R vz, R A, R L) {
   const R sp = r_sqrt(vx * vx + vy * vy + vz * vz);
-  const R vt = vx + A;
-  const R st = r_sqrt(vt * vt + vy * vy + vz * vz);
-  if (sp <= L && st <= L) return vt;
+  if (sp <= L) {
+    const R vt = vx + A;
+    if (r_sqrt(vt * vt + vy * vy + vz * vz) <= L) return vt;
+  }
   const R g = A > (R)0 ? (R)1 : (R)-1;
   const R aA = g * A;
   const R p2 = vy * vy + vz * vz;
@@ -174,10 +175,13 @@ __device__ __forceinline__ R limited_kick(R vx, R vy, R vz, R A, R L) {
   }
   const R K = (R)2 * f * aA * L;
   const R c = s1 + v1;
-  R z = r_min((r_sqrt(c * c + (R)4 * K) - c) * (R)0.5, K / s1);
+  R z = (r_sqrt(c * c + (R)4 * K) - c) * (R)0.5;
+  if (z * s1 > K) z = K / s1;  // z <= K / s_1: the root's other bound
   const R w = v1 + z;
   const R s = r_sqrt(w * w + p2);
-  if (s > (R)0) z = r_max((R)0, z - (z * (s1 + s) - K) / (s1 + s + z * w / s));
+  const R t = s1 + s;
+  const R den = t * s + z * w;  // s times the derivative of z (s_1 + s') - K
+  if (den > (R)0) z = r_max((R)0, z - (z * t - K) * s / den);
   return g * (v1 + z);
 }
 

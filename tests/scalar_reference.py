@@ -111,11 +111,14 @@ class ScalarSim:
             frac, s_a, u_a = 1.0, speed, sign * vx
         K = 2.0 * frac * mag * L
         c = s_a + u_a
-        z = min((math.sqrt(c * c + 4.0 * K) - c) * 0.5, K / s_a)
+        z = (math.sqrt(c * c + 4.0 * K) - c) * 0.5
+        if z * s_a > K:
+            z = K / s_a
         w = u_a + z
         s_b = math.sqrt(w * w + perp2)
-        if s_b > 0:
-            z = max(0.0, z - (z * (s_a + s_b) - K) / (s_a + s_b + z * w / s_b))
+        slope = (s_a + s_b) * s_b + z * w
+        if slope > 0:
+            z = max(0.0, z - (z * (s_a + s_b) - K) * s_b / slope)
         return sign * (u_a + z)
 
     def draws(self, ident, step, sp, blk):
