@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--tab-sims-pic-full-max", type=float, default=0.4,
                     help="above this pressure [Torr] a PIC run covers its first 3 of 15 "
                          "windows and its wall time is extrapolated")
+    ap.add_argument("--tab-sims-slpic-full-max", type=float, default=30.0,
+                    help="above this pressure [Torr] an SLPIC run covers its first 3 of 15 "
+                         "windows and its wall time is extrapolated")
     return ap.parse_args()
 
 
@@ -318,7 +321,8 @@ def tab_sims_run(slpic, inputs, p, V, cells, pic, local, stream, seed=1, windows
     return rec
 
 
-def tab_sims(slpic, inputs, rows, pic_max, pic_full_max, local, stream, margin=0.03):
+def tab_sims(slpic, inputs, rows, pic_max, pic_full_max, local, stream, margin=0.03,
+             slpic_full_max=30.0):
     lo, hi, t_bracket = tab_sims_bracket(slpic, inputs, rows, local, stream)
     out = {"bracket_search_s": t_bracket, "rows": []}
     for a, r in enumerate(rows):
@@ -328,14 +332,16 @@ def tab_sims(slpic, inputs, rows, pic_max, pic_full_max, local, stream, margin=0
                "V_runs": [(1 - margin) * lo[a], (1 + margin) * hi[a]], "runs": []}
         for Vr in rec["V_runs"]:
             run = {"V": Vr, "slpic": tab_sims_run(slpic, inputs, p, Vr, cells, False, local,
-                                                  stream)}
+                                                  stream,
+                                                  run_windows=None if p <= slpic_full_max else 3)}
             if p <= pic_max:
                 part = None if p <= pic_full_max else 3
                 run["pic"] = tab_sims_run(slpic, inputs, p, Vr, cells, True, local, stream,
                                           run_windows=part)
             rec["runs"].append(run)
-        sl = sum(x["slpic"]["wall_s"] for x in rec["runs"])
+        sl = sum(x["slpic"].get("wall_s_extrapolated", x["slpic"]["wall_s"]) for x in rec["runs"])
         rec["slpic_wall_s"] = sl
+        rec["slpic_extrapolated"] = p > slpic_full_max
         if p <= pic_max:
             pc = sum(x["pic"].get("wall_s_extrapolated", x["pic"]["wall_s"]) for x in rec["runs"])
             rec["pic_wall_s"] = pc
@@ -447,7 +453,8 @@ def run_ours(args):
             rows = (range(len(TAB_SIMS)) if args.tab_sims == "all"
                     else [int(x) for x in args.tab_sims.split(",")])
             res = tab_sims(slpic, inputs, rows, args.tab_sims_pic_max,
-                           args.tab_sims_pic_full_max, local, stream)
+                           args.tab_sims_pic_full_max, local, stream,
+                           slpic_full_max=args.tab_sims_slpic_full_max)
             res.update({"study": "Table tab:sims, PIC vs SLPIC on one GB300",
                         "setup": "d = 1 cm, 100 electrons at rest, E = V/d imposed, five "
                                  "processes, Eq. sey yield, 30 ion crossings in 15 windows; "

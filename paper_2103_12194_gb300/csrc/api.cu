@@ -95,6 +95,10 @@ struct slpic_ctx {
   // per instance: stepped since its field was last reset (phi is then formed
   // from the last deposit when read)
   std::vector<char> stepped;
+  // per instance with an imposed field: stepped since its last-step deposit
+  // was formed (the step deposits nothing then; the deposit is formed from
+  // the markers when read, or before they change)
+  std::vector<char> dep_dirty;
   int blocks_per_sm = 0;
   // graph of kGraphSteps steps
   cudaGraphExec_t graph = nullptr;
@@ -318,6 +322,7 @@ int zero_counters(slpic_ctx* c, int i) {
     CK(cudaMemsetAsync(P.rho_acc[s], 0, (P.n_cells + 1) * 8, c->stream), "reset");
     CK(cudaMemsetAsync(P.rho_last[s], 0, (P.n_cells + 1) * 8, c->stream), "reset");
   }
+  if ((int)c->dep_dirty.size() == c->n_inst) c->dep_dirty[i] = 0;
   CK(cudaStreamSynchronize(c->stream), "reset");
   return SLPIC_OK;
 }
@@ -514,6 +519,31 @@ int write_state(slpic_ctx* c, int inst, int sp, const SpeciesState& st) {
   return SLPIC_OK;
 }
 
+// With an imposed field the step deposits nothing: form the last step's
+// deposit of instance i from its markers (a function of them) if it has
+// stepped since the deposit was last formed.  Called before the deposit is
+// read and before the markers change.
+int materialize_deposit(slpic_ctx* c, int i) {
+  if (c->h_inst[i].field_mode == 1 || !c->dep_dirty[i]) return SLPIC_OK;
+  SpeciesState st[2];
+  CK(cudaMemcpyAsync(st, c->d_sstate + 2 * i, sizeof st, cudaMemcpyDeviceToHost, c->stream),
+     "deposit");
+  CK(cudaStreamSynchronize(c->stream), "deposit");
+  const InstDev& P = c->h_inst[i];
+  for (int s = 0; s < 2; ++s)
+    CK(cudaMemsetAsync(P.rho_last[s], 0, (P.n_cells + 1) * 8, c->stream), "deposit");
+  launch_deposit(c->refs, i, (int)(st[0].n_tiles + st[1].n_tiles), c->stream);
+  CK(cudaGetLastError(), "deposit");
+  c->dep_dirty[i] = 0;
+  return SLPIC_OK;
+}
+
+void mark_stepped(slpic_ctx* c) {
+  std::fill(c->stepped.begin(), c->stepped.end(), 1);
+  for (int i = 0; i < c->n_inst; ++i)
+    if (c->h_inst[i].field_mode != 1) c->dep_dirty[i] = 1;
+}
+
 int replan(slpic_ctx* c) {
   launch_finish(c->refs, 1, c->stream);
   CK(cudaGetLastError(), "plan");
@@ -569,7 +599,7 @@ int run_small(slpic_ctx* c, int64_t n, int64_t* done,
   CK(cudaMemcpy(&d, &c->d_ctrl->small_done, sizeof d, cudaMemcpyDeviceToHost), "small path");
   *done = d;
   c->last_launches = 2;
-  if (d > 0) std::fill(c->stepped.begin(), c->stepped.end(), 1);
+  if (d > 0) mark_stepped(c);
   return device_error(c);
 }
 
@@ -693,6 +723,7 @@ int slpic_create(slpic_ctx** out, int device, int n_instances) {
   c->n_inst = n_instances;
   c->hi.resize(n_instances);
   c->stepped.assign(n_instances, 0);
+  c->dep_dirty.assign(n_instances, 0);
   *out = c;
   return SLPIC_OK;
 }
@@ -943,6 +974,7 @@ extern "C" int slpic_seed(slpic_ctx* c, int inst, int species, int64_t n, int mo
     return fail(c, SLPIC_ERR_INVALID_ARG, "bad seed energies or weight");
   if (int rc = prepare(c)) return rc;
   if (int rc = sync(c)) return rc;
+  if (int rc = materialize_deposit(c, inst)) return rc;
   SpeciesState st;
   if (int rc = read_state(c, inst, species, &st)) return rc;
   const InstDev& P = c->h_inst[inst];
@@ -997,6 +1029,7 @@ int load_common(slpic_ctx* c, int inst, int species, const Arrays& src, int64_t 
   if (next_id > kSerialMask) return fail(c, SLPIC_ERR_INVALID_ARG, "next_id beyond 2^31 - 1");
   if (int rc = prepare(c)) return rc;
   if (int rc = sync(c)) return rc;
+  if (int rc = materialize_deposit(c, inst)) return rc;
   const InstDev& P = c->h_inst[inst];
   const SpeciesDev& S = P.sp[species];
   if ((uint64_t)n > (uint64_t)S.cap_tiles * kTile)
@@ -1086,7 +1119,7 @@ int slpic_reset_counters(slpic_ctx* c, int inst) {
 int slpic_step(slpic_ctx* c, int64_t n) {
   if (!c || n < 0) return fail(c, SLPIC_ERR_INVALID_ARG, "bad step count");
   if (int rc = prepare(c)) return rc;
-  if (n > 0) std::fill(c->stepped.begin(), c->stepped.end(), 1);
+  if (n > 0) mark_stepped(c);
   c->last_launches = 0;
   if (c->profiling) {
     for (int64_t k = 0; k < n; ++k) {
@@ -1233,6 +1266,7 @@ int slpic_read_charge(slpic_ctx* c, int inst, int species, int64_t* host, int64_
   int rc = sync(c);
   const InstDev& P = c->h_inst[inst];
   if (n != P.n_cells + 1) return fail(c, SLPIC_ERR_INVALID_ARG, "need n_cells + 1 values");
+  if (int r2 = materialize_deposit(c, inst)) return r2;
   CK(cudaMemcpy(host, P.rho_last[species], n * 8, cudaMemcpyDeviceToHost), "read charge");
   return rc;
 }

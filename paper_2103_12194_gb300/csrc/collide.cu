@@ -149,9 +149,10 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
               esec[base + q] = es;
             }
           }
-          deposit(P.rho_acc[kElectron], cell, off,
-                  fixed_charge(beta_of(r_sqrt(vx * vx + vy * vy + vz * vz), vlim) * wj,
-                               K.wscale));
+          if (P.field_mode == 1)  // imposed field: the deposit is formed when read
+            deposit(P.rho_acc[kElectron], cell, off,
+                    fixed_charge(beta_of(r_sqrt(vx * vx + vy * vy + vz * vz), vlim) * wj,
+                                 K.wscale));
         }
         warp_births += __popc(__ballot_sync(0xFFFFFFFFu, ionized));
       }
@@ -194,8 +195,12 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
             if (pe >= cap_e || pi >= cap_i) {
               atomicCAS(&ctrl->error, 0, kErrCapacity);
             } else {
-              born_pair<R>(P, me, mi, pe, pi, me.cell[o], me.off[o], me.wj[o], me.id[o], step,
-                           esec[base + q], se.next_id + rank, si.next_id + rank);
+              if (P.field_mode == 1)
+                born_pair<R>(P, me, mi, pe, pi, me.cell[o], me.off[o], me.wj[o], me.id[o], step,
+                             esec[base + q], se.next_id + rank, si.next_id + rank);
+              else
+                born_pair<R, false>(P, me, mi, pe, pi, me.cell[o], me.off[o], me.wj[o], me.id[o],
+                                    step, esec[base + q], se.next_id + rank, si.next_id + rank);
             }
           }
           ranked += __popc(b);

@@ -5,6 +5,8 @@
 // step's field and commits the step's tallies; the last CTA plans the next
 // step.  k_move repacks the stores that became sparse.  Also: seeding, load
 // validation and the Philox self-check kernel.
+#include <algorithm>
+
 #include "device_common.cuh"
 #include "slpic_internal.h"
 #include "step_ops.cuh"
@@ -115,7 +117,9 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode, 
     s_acc[t] = a[t];
     a[t] = 0ull;
   }
-  for (int k = t; k < nn; k += kFinThreads) {
+  // (with an imposed field nothing was deposited: the deposit is formed from
+  // the markers when it is read)
+  for (int k = t; k < nn && P.field_mode == 1; k += kFinThreads) {
     const long long qe = (long long)P.rho_acc[kElectron][k];
     const long long qi = (long long)P.rho_acc[kIon][k];
     P.rho_last[kElectron][k] = qe;
@@ -229,6 +233,45 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode, 
     __threadfence();
     plan_next(r, s_i64);
   }
+}
+
+// The deposit of instance inst's live markers into its last-step grids
+// (zeroed by the caller): each marker adds fixed_charge(beta(|v|) w_j) at its
+// position, as the step deposits it.  A step's deposit is a function of the
+// markers after it, so with an imposed field it is formed here, when read,
+// instead of during every step.  One warp per tile, tiles of both species in
+// a grid-stride loop.
+template <typename R>
+__global__ void __launch_bounds__(256) k_deposit(DeviceRefs r, int inst) {
+  const InstDev& P = r.inst[inst];
+  const StepConsts<R>& K = consts<R>(P);
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int n_warps = (gridDim.x * blockDim.x) >> 5;
+  const SpeciesState se = r.sstate[inst * 2], si = r.sstate[inst * 2 + 1];
+  const uint32_t ne = se.n_tiles, n_items = se.n_tiles + si.n_tiles;
+  for (uint32_t it = warp; it < n_items; it += n_warps) {
+    const int sp = it < ne ? 0 : 1;
+    const uint32_t k = it < ne ? it : it - ne;
+    const SpeciesState& st = sp ? si : se;
+    const SoAT<R> m = soa_as<R>(P.sp[sp].buf[st.cur]);
+    const R vlim = K.vlim[sp];
+    const bool limited = vlim < (R)INFINITY;
+    unsigned long long* rho = reinterpret_cast<unsigned long long*>(P.rho_last[sp]);
+    const uint32_t n = P.sp[sp].fill[st.cur][k];
+    for (uint32_t i = lane; i < n; i += 32) {
+      const size_t o = (size_t)k * kTile + i;
+      const R vx = m.vx[o], vy = m.vy[o], vz = m.vz[o];
+      const R b = limited ? beta_of(r_sqrt(vx * vx + vy * vy + vz * vz), vlim) : (R)1;
+      deposit(rho, m.cell[o], m.off[o], fixed_charge(b * m.wj[o], K.wscale));
+    }
+  }
+}
+
+void launch_deposit(const DeviceRefs& r, int inst, int n_tiles, cudaStream_t s) {
+  const int grid = std::max(1, std::min((n_tiles + 7) / 8, 4096));
+  if (r.fp64) k_deposit<double><<<grid, 256, 0, s>>>(r, inst);
+  else k_deposit<float><<<grid, 256, 0, s>>>(r, inst);
 }
 
 // phi_k = k D_1 - C J_k, J_k = sum_{0<i<=k} I_i, from the last step's deposit

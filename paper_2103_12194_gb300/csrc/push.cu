@@ -263,7 +263,10 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
     if (d[0].sseg != cur_seg) {
       if (cur_seg >= 0) flush_segment(r, cur_seg, s_rho, cs, use_smem);
       cur_seg = d[0].sseg;
-      use_smem = r.inst[cur_seg >> 1].n_cells + 1 <= r.smem_nodes;
+      // with an imposed field the deposit is formed when it is read
+      // (deposit_markers), so nothing is deposited here
+      use_smem = r.inst[cur_seg >> 1].field_mode == 1 &&
+                 r.inst[cur_seg >> 1].n_cells + 1 <= r.smem_nodes;
     }
 
     const WarpTile t = d[0];
@@ -333,6 +336,7 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
         const R* Enode = node_field<R>(P);
         const bool electrons = sp == kElectron;
         const bool limited = vlim < (R)INFINITY;  // beta = 1 for an unlimited species
+        const bool dep = P.field_mode == 1;       // deposit during the step
 
         // ---- 4. advance the lane's slots ---------------------------------------
         // straight-line over the kPerLane slots so that their dependency chains
@@ -397,7 +401,7 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
 #pragma unroll
         for (int j = 0; j < kPerLane; ++j) {
           // deposit w_p = beta w_j now unless a collision may change v
-          if (alive[j] && !event[j]) {
+          if (dep && alive[j] && !event[j]) {
             const long long Q = fixed_charge(b1[j] * wj[j], wscale);
             const long long right = right_share(Q, off[j]);
             atomicAdd(rho + cell[j], (unsigned long long)(Q - right));
@@ -426,8 +430,10 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
               // the candidate's slot after compaction = its rank among survivors
               const uint32_t r_a = pre_alive[j] + (uint32_t)__popc(b_alive[j] & lanemask_lt);
               S.cand[tbase + e] = (uint16_t)r_a;
-            } else {
+            } else if (dep) {
               stage_emission<R>(P, tbase + e, wj[j]);
+            } else {
+              stage_emission<R, false>(P, tbase + e, wj[j]);
             }
           }
         }

@@ -297,6 +297,10 @@ int finish_config(int max_nodes, int* net_nodes);
 void launch_move(const DeviceRefs& r, int grid, cudaStream_t s);
 // Node potential of instance inst from its last deposit (Poisson mode).
 void launch_phi(const DeviceRefs& r, int inst, cudaStream_t s);
+// Deposit of instance inst's live markers (n_tiles tiles of both species)
+// added to its last-step grids; used with an imposed field, where the step
+// itself deposits nothing.
+void launch_deposit(const DeviceRefs& r, int inst, int n_tiles, cudaStream_t s);
 // Scatter the null-collision candidates queued by the particle kernel.
 void launch_collide(const DeviceRefs& r, int grid, cudaStream_t s);
 // Seeding: n markers written contiguously from slot `base` of the current

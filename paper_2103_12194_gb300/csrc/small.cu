@@ -18,8 +18,7 @@
 // The deposit of a step is a function of the markers after it (each live
 // marker adds fixed_charge(beta(|v|) w_j) at its position), so it is formed
 // in one pass at the end of the step, into shared memory; with an imposed
-// field nothing reads it during the run, and it is formed once, after the
-// last step, into the instance's last-step deposit.
+// field nothing reads it during the run, and it is formed when it is read.
 // With several instances, every CTA waits at a grid barrier before each
 // step (a cooperative launch keeps them resident), so that all stop at the
 // same step when one store outgrows the path; the host then continues with
@@ -589,7 +588,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(DeviceRefs r, long l
       P.E32[k] = (float)s_E[k];
     }
   }
-  // the last step's deposit
+  // the last step's deposit (with an imposed field it is formed when read)
+  if (!poisson) return;
   for (int k = t; k < nn; k += kSmallThreads) {
     P.rho_last[kElectron][k] = 0;
     P.rho_last[kIon][k] = 0;
