@@ -691,3 +691,50 @@ def test_three_excitation_levels_are_chosen_by_their_cross_sections(oracle_mod):
     exp3 = tot / tot.sum() * got.sum()
     chi2 = float(np.sum((got - exp3) ** 2 / exp3))
     assert chi2 < stats.chi2.ppf(0.999, df=2), (got, exp3)
+
+
+# ---------------------------------------------------------------------------
+# SLPIC against PIC (Sec. II and V): same physics, different time steps
+# ---------------------------------------------------------------------------
+
+def _ionizations_per_seed(oracle_mod, pic, cells, batches=6, n=300, V=240.0, pd=0.3):
+    """Mean and standard error over batches of the ionizations per seed
+    electron of avalanches from n electrons at rest (gamma = 0, imposed
+    field), run until every electron has left.  SLPIC: v_lim = v0,
+    dt = dx / v0; PIC: dt = dx / v_max."""
+    dx = 0.01 / cells
+    v0 = inputs.ion_speed(V)
+    vmax = math.sqrt(2 * inputs.QE * V / inputs.ME)
+    out = []
+    for b in range(batches):
+        spec = inputs.gap_spec(n_cells=cells, V=V, pd_torr_cm=pd, gamma_se=0.0, field_mode=0,
+                               vlim_e=math.inf if pic else v0, dt=dx / (vmax if pic else v0),
+                               seed=100 + b)
+        o = oracle_mod.Oracle(spec, 64)
+        o.seed(0, n, 1)
+        steps = 0
+        while o.count(0) and steps < 100_000:
+            o.step(512)
+            steps += 512
+        assert o.count(0) == 0
+        out.append(o.history()["n_coll"][:, 2].sum() / n)
+    out = np.array(out)
+    return out.mean(), out.std(ddof=1) / math.sqrt(batches)
+
+
+def test_slpic_ionization_converges_to_pic(oracle_mod):
+    """The speed limit changes the time step and not the physics (Sec. II:
+    a steady state is reproduced; Sec. V: the same breakdown brackets):
+    at 0.3 Torr cm and 240 V, the ionizations per seed electron of SLPIC at
+    v_lim = v0 agree with PIC within three standard errors once the cell is
+    a sixteenth of the mean free path.  At the paper's dx = lambda / 4
+    (66 cells) SLPIC, which moves a limited marker a whole cell per step,
+    carries a first-order error of a few per cent, and it shrinks as the
+    cell does."""
+    s66, e66 = _ionizations_per_seed(oracle_mod, False, 66)
+    p66, f66 = _ionizations_per_seed(oracle_mod, True, 66)
+    s264, e264 = _ionizations_per_seed(oracle_mod, False, 264)
+    p264, f264 = _ionizations_per_seed(oracle_mod, True, 264)
+    assert abs(s264 - p264) <= 3.0 * math.hypot(e264, f264), (s264, p264)
+    assert abs(s66 - p66) <= 0.15 * p66, (s66, p66)
+    assert abs(s264 - p264) < abs(s66 - p66)
