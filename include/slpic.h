@@ -263,7 +263,14 @@ int slpic_read_particles(slpic_ctx* ctx, int inst, int species,
 int slpic_read_particles_f64(slpic_ctx* ctx, int inst, int species,
                              const slpic_soa_f64* host, int64_t capacity,
                              int64_t* n_out);
-/* Fixed-point deposit of the last step (n_cells + 1 int64 node values). */
+/* Fixed-point deposit of the last step (n_cells + 1 int64 node values;
+ * all zero before the first step and after slpic_reset_counters).  A step's
+ * deposit is a function of the markers after it: each live marker adds
+ * round(beta(|v|) w_j 2^shift) split linearly between its cell's nodes.
+ * With field_mode 1 the step forms it (the Poisson solve needs it); with an
+ * imposed field the step deposits nothing and this call (or a load or seed,
+ * before it changes the markers) forms it from the markers.  The integers are
+ * the same either way.  Synchronises; returns a latched device error. */
 int slpic_read_charge(slpic_ctx* ctx, int inst, int species, int64_t* host,
                       int64_t n);
 /* Number density at the nodes [m^-3] of the last step's deposit (boundary

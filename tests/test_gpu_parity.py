@@ -495,3 +495,30 @@ def test_large_grid_vacuum_steps_bit_exact(slpic, oracle_mod):
     hr = ref.history()
     assert np.array_equal(sim.history(0)["n_see"], hr["n_see"]) and hr["n_see"].sum() > 20
     sim.close()
+
+
+def test_imposed_field_deposit_is_formed_when_read(slpic, oracle_mod):
+    """With an imposed field the step deposits nothing; the last step's
+    deposit is formed from the markers when it is read, or before a load
+    changes them.  Either way it equals, bit for bit, the oracle's deposit of
+    the markers the step left."""
+    spec = dense_spec(n_cells=512, pd=30.0)
+    assert spec["field_mode"] == 0
+    e, i = mixed_state(spec, 60_000, 20_000, seed=71)
+    sim = make_sim(slpic, spec)
+    sim.load(0, 0, e)
+    sim.load(0, 1, i)
+    for _ in range(2):
+        sim.step(4)
+        after = [sim.particles(0, s) for s in (0, 1)]
+        ref = oracle_mod.Oracle(spec, precision=32)
+        ref.load(0, after[0])
+        ref.load(1, after[1])
+        ref.deposit()
+        want = [ref.charge(s) for s in (0, 1)]
+        assert want[0].any() and want[1].any()
+        # read straight after the steps, then after a load replaced the ions
+        assert all(np.array_equal(sim.charge(0, s), want[s]) for s in (0, 1))
+        sim.load(0, 1, {k: v[:10] for k, v in i.items()})
+        assert all(np.array_equal(sim.charge(0, s), want[s]) for s in (0, 1))
+    sim.close()
