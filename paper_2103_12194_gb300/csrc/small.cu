@@ -2,13 +2,13 @@
 // start from 100 electrons at rest and stay at hundreds to thousands of
 // markers near breakdown (Sec. V), where a step of the batched kernels is
 // bound by its four launches and their grid-wide hand-offs, not by the
-// markers.  Here one CTA of 1024 threads owns one instance and runs the
+// markers.  Here one CTA of 512 threads owns one instance and runs the
 // steps back to back with block barriers only:
-//   1. push: warp w advances tiles w, w + 32, ... of both species with the
+//   1. push: warp w advances tiles w, w + 16, ... of both species with the
 //      same arithmetic as the particle kernel (gather, speed-limited kick and
 //      drift, electrodes and emission, the candidate draw, in-tile
 //      compaction), straight from global memory;
-//   2. collisions: thread t takes candidates t, t + 1024, ... in (tile, slot)
+//   2. collisions: thread t takes candidates t, t + 512, ... in (tile, slot)
 //      order; the births get their slots from one block scan (ionization
 //      pairs in candidate order, then the emitted electrons in ion-tile
 //      order), exactly the order of the batched path;
@@ -31,7 +31,7 @@ namespace slpic {
 
 namespace {
 
-constexpr int kSmallThreads = kFinThreads;  // the block scans and the Poisson sums
+constexpr int kSmallThreads = 512;
 constexpr int kSmallWarps = kSmallThreads / 32;
 // Tiles a store can reach in one step from at most kSmallMaxTiles tiles of
 // each species: electrons double at most and gain one emitted electron per
@@ -40,7 +40,7 @@ constexpr int kSmallFillCap = 4 * kSmallMaxTiles;
 constexpr int kSmallCandRows = kSmallMaxTiles * kTile / kSmallThreads;
 static_assert(kSmallMaxTiles <= 32, "one lane per tile in the prefix scans");
 static_assert(kSmallCandRows * kSmallThreads == kSmallMaxTiles * kTile, "candidate rows");
-static_assert(kSmallCandRows <= 4, "16-bit row counters in one 64-bit scan value");
+static_assert(kSmallCandRows <= 8, "16-bit row counters in one 128-bit scan value");
 
 struct SmallShared {
   unsigned long long acc[ACC_COUNT];
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(DeviceRefs r, long l
       const R kv = K.K_V[kElectron], vlim = K.vlim[kElectron];
       uint32_t slot[kSmallCandRows];
       R es[kSmallCandRows];
-      unsigned long long flags = 0;  // 16-bit ionization count per row
+      unsigned __int128 flags = 0;  // 16-bit ionization count per row
 #pragma unroll
       for (int u = 0; u < kSmallCandRows; ++u) {
         const uint32_t c = (uint32_t)t + (uint32_t)u * kSmallThreads;
@@ -396,28 +396,29 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(DeviceRefs r, long l
           me.vy[o] = nv.vy;
           me.vz[o] = nv.vz;
           if (proc == 2) {
-            flags |= 1ull << (16 * u);
+            flags |= (unsigned __int128)1 << (16 * u);
             es[u] = e2;
           }
         }
       }
-      // ranks of the ionizations in candidate order: c = t + 1024 u, so row u
-      // precedes row u + 1 and inside a row the threads are in order (the
-      // scan is skipped in the many steps without an ionization)
-      unsigned long long incl = 0, rows = 0;
-      if (__syncthreads_or(flags != 0ull)) {
-        incl = (unsigned long long)block_incl_scan<long long>((long long)flags, sh.i64);
-        if (t == kSmallThreads - 1) sh.i64[0] = (long long)incl;  // row totals
+      // ranks of the ionizations in candidate order: c = t + kSmallThreads u,
+      // so row u precedes row u + 1 and inside a row the threads are in order
+      // (the scan is skipped in the many steps without an ionization)
+      unsigned __int128 incl = 0, rows = 0;
+      if (__syncthreads_or(flags != 0)) {
+        incl = (unsigned __int128)block_incl_scan<__int128, kSmallThreads>((__int128)flags,
+                                                                           sh.i128);
+        if (t == kSmallThreads - 1) sh.i128[0] = (__int128)incl;  // row totals
         __syncthreads();
-        rows = (unsigned long long)sh.i64[0];
+        rows = (unsigned __int128)sh.i128[0];
         __syncthreads();
       }
-      const unsigned long long excl = incl - flags;
+      const unsigned __int128 excl = incl - flags;
       uint32_t before = 0;  // ionizations in the rows above
 #pragma unroll
       for (int u = 0; u < kSmallCandRows; ++u) {
-        if (flags >> (16 * u) & 1ull) {
-          const uint32_t rank = before + (uint32_t)(excl >> (16 * u) & 0xFFFFull);
+        if ((uint32_t)(flags >> (16 * u)) & 1u) {
+          const uint32_t rank = before + ((uint32_t)(excl >> (16 * u)) & 0xFFFFu);
           const uint32_t pe = app_e + rank, pi = app_i + rank;
           const uint32_t o = slot[u];
           if (pe >= cap_e || pi >= cap_i) {
@@ -427,7 +428,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(DeviceRefs r, long l
                                 step, es[u], se.next_id + rank, si.next_id + rank);
           }
         }
-        before += (uint32_t)(rows >> (16 * u) & 0xFFFFull);
+        before += (uint32_t)(rows >> (16 * u)) & 0xFFFFu;
       }
       // electrons emitted at the cathode, after every ionization electron
       const uint32_t n_ionz = before;
@@ -532,7 +533,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(DeviceRefs r, long l
       const int chunk = (N + kSmallThreads - 1) / kSmallThreads;  // over k = 1..N
       const int k0 = 1 + t * chunk;
       long long I0;
-      const double D1 = poisson_d1(P, s_net, k0, chunk, sh.i64, sh.i128, &I0);
+      const double D1 = poisson_d1<kSmallThreads>(P, s_net, k0, chunk, sh.i64, sh.i128, &I0);
       const double C = P.pois_C;
       const double inv2dx = 1.0 / (2.0 * P.dx);
       const double twoD1 = D1 + D1;

@@ -295,11 +295,13 @@ __device__ __forceinline__ __int128 shfl_up(__int128 v, int o) {
   return (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | lo);
 }
 
-// Inclusive block scan: shuffle scans within the warps, then one warp scans
-// the 32 warp totals (buf holds 32 entries).  Integer sums, so exact.
-template <typename T>
+// Inclusive block scan over a CTA of kThreads threads: shuffle scans within
+// the warps, then one warp scans the warp totals (buf holds 32 entries).
+// Integer sums, so exact.
+template <typename T, int kThreads = kFinThreads>
 __device__ T block_incl_scan(T v, T* buf) {
-  static_assert(kFinThreads == 1024, "one warp scans the 32 warp totals");
+  static_assert(kThreads % 32 == 0 && kThreads <= 1024, "whole warps, at most 32");
+  constexpr int kWarps = kThreads / 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int o = 1; o < 32; o <<= 1) {
     const T y = shfl_up(v, o);
@@ -308,12 +310,12 @@ __device__ T block_incl_scan(T v, T* buf) {
   if (lane == 31) buf[w] = v;
   __syncthreads();
   if (w == 0) {
-    T t = buf[lane];
+    T t = lane < kWarps ? buf[lane] : T(0);
     for (int o = 1; o < 32; o <<= 1) {
       const T y = shfl_up(t, o);
       if (lane >= o) t += y;
     }
-    buf[lane] = t;
+    if (lane < kWarps) buf[lane] = t;
   }
   __syncthreads();
   const T r = v + (w ? buf[w - 1] : T(0));
@@ -328,14 +330,15 @@ __device__ __forceinline__ long long net_at(const InstDev& P, const long long* s
 }
 
 // The exact integer sums of the 1D Poisson solve over the last step's net
-// deposit (all threads of a kFinThreads CTA; thread t covers k = k0 ..
+// deposit (all threads of a kThreads CTA; thread t covers k = k0 ..
 // k0 + chunk - 1 of 1..N): returns D_1 = (V + C J_N) / N and writes I_{k0}.
+template <int kThreads = kFinThreads>
 __device__ double poisson_d1(const InstDev& P, const long long* s_net, int k0, int chunk,
                              long long* s_i64, __int128* s_i128, long long* I_k0) {
   const int N = P.n_cells;
   long long loc = 0;
   for (int k = k0; k < k0 + chunk && k <= N - 1; ++k) loc += net_at(P, s_net, k);
-  const long long inc = block_incl_scan<long long>(loc, s_i64);
+  const long long inc = block_incl_scan<long long, kThreads>(loc, s_i64);
   long long Ik = inc - loc;  // I_k at the chunk start (exclusive of net_k)
   *I_k0 = Ik;
   __int128 locJ = 0;
@@ -343,9 +346,9 @@ __device__ double poisson_d1(const InstDev& P, const long long* s_net, int k0, i
     locJ += (__int128)Ik;
     if (k <= N - 1) Ik += net_at(P, s_net, k);
   }
-  const __int128 incJ = block_incl_scan<__int128>(locJ, s_i128);
+  const __int128 incJ = block_incl_scan<__int128, kThreads>(locJ, s_i128);
   __shared__ __int128 s_JN;
-  if (threadIdx.x == kFinThreads - 1) s_JN = incJ;
+  if (threadIdx.x == kThreads - 1) s_JN = incJ;
   __syncthreads();
   const __int128 JN = s_JN;
   __syncthreads();
