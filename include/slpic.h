@@ -364,9 +364,11 @@ int slpic_ion_trend(slpic_ctx* ctx, int64_t steps_per_window, int n_windows, dou
                     int* above);
 
 /* Launch shape of the step: warps per CTA of the particle kernel (a
- * multiple of 4, at most what fits next to the largest charge grid; each
- * warp owns a 128-slot tile) and CTAs per SM of the collision kernel
- * (1..32).  The library's own choice is the largest warp count and 8.
+ * multiple of 4, at most 16; each warp owns a 128-slot tile) and CTAs per
+ * SM of the collision kernel (1..32).  While the warps' stages leave room
+ * for the largest instance's charge grid in shared memory the kernel
+ * deposits there; with more warps it deposits to global memory.  The
+ * library's own choice is the most warps that leave that room, and 8.
  * Results do not depend on the shape, bit for bit: tiles are independent,
  * deposits are integer sums and births are ordered by (tile, slot). */
 int slpic_set_launch_shape(slpic_ctx* ctx, int push_warps, int collide_ctas_per_sm);

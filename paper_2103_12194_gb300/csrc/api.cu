@@ -90,6 +90,11 @@ struct slpic_ctx {
   int collide_grid = 0;
   int sms = 0;             // multiprocessors of the device
   int max_push_warps = 0;  // most particle-kernel warps per CTA that fit
+  // shared-memory charge grid of the particle kernel (nodes of the largest
+  // instance; 0: none fits) and the most warps that fit next to it; shapes
+  // with more warps deposit to global memory
+  int smem_nodes_full = 0;
+  int max_push_warps_smem = 0;
   int collide_per_sm = 8;  // collision CTAs per SM
   int small_limit = kSmallMaxTiles;  // single-CTA path: most tiles per store (0: off)
   // per instance: stepped since its field was last reset (phi is then formed
@@ -480,6 +485,17 @@ int commit(slpic_ctx* c) {
   c->refs.smem_nodes = smem_nodes;
   c->refs.push_warps = warps;
   c->refs.fp64 = c->fp64;
+  c->smem_nodes_full = smem_nodes;
+  c->max_push_warps_smem = smem_nodes ? warps : 0;
+  int max_warps = warps;
+  if (smem_nodes) {
+    // more warps per CTA may fit when the deposits go to global memory
+    int gw = 0, gbps = 0;
+    size_t gbytes = 0;
+    if (int e2 = push_config(c->fp64, 0, &gw, &gbps, &gbytes))
+      return cuda_fail(c, (cudaError_t)e2, "particle kernel configuration");
+    if (gbps > 0 && gw > warps) max_warps = gw;
+  }
   {
     int net_nodes = 0;
     if (int e2 = finish_config(max_nodes, &net_nodes))
@@ -489,7 +505,7 @@ int commit(slpic_ctx* c) {
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device), "attributes");
   c->sms = sms;
-  c->max_push_warps = warps;
+  c->max_push_warps = max_warps;
   c->blocks_per_sm = bps;
   c->push_grid = sms * bps;
   c->move_grid = sms * 2;
@@ -638,12 +654,16 @@ int apply_shape(slpic_ctx* c, int warps, int coll_per_sm) {
                 "launch shape: push warps must be a multiple of 4 in [4, %d], collision CTAs "
                 "per SM in [1, 32]",
                 c->max_push_warps);
+  // the shared charge grid while it fits next to the warps' stages, else
+  // deposits to global memory (the same integers either way)
+  const int nodes = warps <= c->max_push_warps_smem ? c->smem_nodes_full : 0;
   int bps = 0;
-  if (int e = push_blocks_per_sm(c->fp64, warps, c->refs.smem_nodes, &bps))
+  if (int e = push_blocks_per_sm(c->fp64, warps, nodes, &bps))
     return cuda_fail(c, (cudaError_t)e, "launch shape");
   if (bps < 1) return fail(c, SLPIC_ERR_CUDA, "launch shape: particle kernel does not fit");
   if (int rc = sync(c)) return rc;
   drop_graph(c);
+  c->refs.smem_nodes = nodes;
   c->refs.push_warps = warps;
   c->blocks_per_sm = bps;
   c->push_grid = c->sms * bps;

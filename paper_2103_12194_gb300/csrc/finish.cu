@@ -319,8 +319,13 @@ int finish_config(int max_nodes, int* net_nodes) {
   if (e != cudaSuccess) return (int)e;
   const int room = (optin - 8 * 1024) / 8;  // static shared memory stays below 8 KB
   *net_nodes = max_nodes <= room ? max_nodes : 0;
+  // the limit is the most a CTA can have, so that one context's
+  // configuration never lowers it under another's
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, k_finish);
+  if (e != cudaSuccess) return (int)e;
   e = cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           *net_nodes * 8);
+                           optin - (int)fa.sharedSizeBytes);
   return (int)e;
 }
 

@@ -523,11 +523,18 @@ int push_config_t(int smem_nodes, int* warps, int* blocks_per_sm, size_t* smem_b
   const size_t fixed = sizeof(uint64_t) * kPushMaxWarps * kPushStages + sizeof(PushShared) + 1024;
   *warps = 0;
   *blocks_per_sm = 0;
+  // the kernel may use all the dynamic shared memory a CTA can have: every
+  // context's launches (of any grid size and shape) stay within that limit,
+  // so no context's configuration lowers it under another's
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, k_push<R>);
+  if (e != cudaSuccess) return (int)e;
+  e = cudaFuncSetAttribute(k_push<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - (int)fa.sharedSizeBytes);
+  if (e != cudaSuccess) return (int)e;
   for (int w = kPushMaxWarps; w >= 4; w -= 4) {
     const size_t bytes = (size_t)w * kPushStages * stage_bytes<R>() + (size_t)smem_nodes * 8;
     if (bytes + fixed > (size_t)optin) continue;
-    e = cudaFuncSetAttribute(k_push<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return (int)e;
     int bps = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_push<R>, w * 32, bytes);
     if (e != cudaSuccess) return (int)e;

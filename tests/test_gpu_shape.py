@@ -65,3 +65,40 @@ def test_autotune_keeps_the_results(slpic):
     assert_same_state(tuned, plain, len(items))
     tuned.close()
     plain.close()
+
+
+def test_more_warps_than_fit_beside_the_shared_grid_deposit_to_global_memory(slpic):
+    """With the 16384-cell gap in the batch, a particle-kernel CTA fits at
+    most 8 warps beside the shared charge grid; 12 and 16 warps deposit to
+    global memory instead.  The integers, and so every result, are the
+    same."""
+    items = batch_items()
+    assert max(spec["n_cells"] for spec, _, _ in items) == 16384
+    states = states_for(items, seed0=80)
+    ref = load_batch(slpic, items, states)
+    assert ref.launch_shape() == (8, 8)
+    ref.step(40)
+    for shape in ((16, 8), (12, 4)):
+        sim = load_batch(slpic, items, states)
+        sim.set_launch_shape(*shape)
+        assert sim.launch_shape() == shape
+        sim.step(40)
+        assert_same_state(ref, sim, len(items))
+        sim.close()
+    ref.close()
+
+
+def test_contexts_of_different_grids_live_side_by_side(slpic):
+    """A context with a large charge grid keeps stepping after a context
+    with a small one was configured in the same process (the kernels'
+    shared-memory limits are per process)."""
+    items = batch_items()
+    states = states_for(items, seed0=90)
+    big = load_batch(slpic, items, states)
+    big.step(3)
+    small = load_batch(slpic, items[:1], states[:1])
+    small.step(3)
+    big.step(3)
+    big.synchronize()
+    small.close()
+    big.close()
