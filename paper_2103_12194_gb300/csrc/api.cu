@@ -602,21 +602,31 @@ int run_small(slpic_ctx* c, int64_t n, int64_t* done,
   if (int e = small_config(c->fp64, max_pn, &smem, &bps))
     return cuda_fail(c, (cudaError_t)e, "small path configuration");
   if (bps == 0 || (c->n_inst > 1 && (int64_t)bps * c->sms < c->n_inst)) return SLPIC_OK;
+  // the grid barrier counts arrivals in 32 bits: launches of at most 2^30
+  // arrivals (steps x instances), one after another
+  const int64_t per_launch = std::max<int64_t>(1, (int64_t(1) << 30) / c->n_inst);
   const size_t off0 = offsetof(Control, small_bar);
-  CK(cudaMemsetAsync((char*)c->d_ctrl + off0, 0, offsetof(Control, small_done) + 8 - off0,
-                     c->stream),
-     "small path");
-  if (int e = launch_small(c->refs, n, c->small_limit, smem, c->stream))
-    return cuda_fail(c, (cudaError_t)e, "small path launch");
-  launch_finish(c->refs, 1, c->stream);  // the batched path's next step
-  CK(cudaGetLastError(), "small path");
-  CK(cudaStreamSynchronize(c->stream), "small path");
-  long long d = 0;
-  CK(cudaMemcpy(&d, &c->d_ctrl->small_done, sizeof d, cudaMemcpyDeviceToHost), "small path");
-  *done = d;
-  c->last_launches = 2;
-  if (d > 0) mark_stepped(c);
-  return device_error(c);
+  c->last_launches = 0;
+  while (*done < n) {
+    const int64_t k = std::min(n - *done, per_launch);
+    CK(cudaMemsetAsync((char*)c->d_ctrl + off0, 0, offsetof(Control, small_done) + 8 - off0,
+                       c->stream),
+       "small path");
+    if (int e = launch_small(c->refs, k, c->small_limit, smem, c->stream))
+      return cuda_fail(c, (cudaError_t)e, "small path launch");
+    launch_finish(c->refs, 1, c->stream);  // the batched path's next step
+    CK(cudaGetLastError(), "small path");
+    CK(cudaStreamSynchronize(c->stream), "small path");
+    long long d = 0;
+    CK(cudaMemcpy(&d, &c->d_ctrl->small_done, sizeof d, cudaMemcpyDeviceToHost),
+       "small path");
+    *done += d;
+    c->last_launches += 2;
+    if (d > 0) mark_stepped(c);
+    if (int rc = device_error(c)) return rc;
+    if (d < k) break;  // a store outgrew the path
+  }
+  return SLPIC_OK;
 }
 
 void drop_graph(slpic_ctx* c) {
