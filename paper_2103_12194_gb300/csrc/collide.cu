@@ -7,7 +7,8 @@
 // angles with the recoil loss, excitation removes its threshold and scatters
 // isotropically, ionization shares the excess energy between the primary and
 // a born electron and creates an Ar+ at the same position with the same flux
-// weight.  Each candidate is then deposited with its new density weight.
+// weight.  Each candidate is then deposited with its new density weight
+// (with an imposed field the deposit is formed from the markers when read).
 //
 // Work: chunks of kCollChunkTiles consecutive tiles (each warp kCollWarpTiles
 // of them; the warp numbers the candidates of its tiles in (tile, slot) order

@@ -3,8 +3,10 @@
 // k_collide appended every birth), decides whether a store is repacked,
 // publishes the step's deposit, solves the 1D Poisson equation for the next
 // step's field and commits the step's tallies; the last CTA plans the next
-// step.  k_move repacks the stores that became sparse.  Also: seeding, load
-// validation and the Philox self-check kernel.
+// step.  k_move repacks the stores that became sparse.  With an imposed
+// field the step deposits nothing and k_deposit forms the deposit from the
+// markers when it is read.  Also: seeding, load validation and the Philox
+// self-check kernel.
 #include <algorithm>
 
 #include "device_common.cuh"

@@ -4,7 +4,8 @@
 // (Sec. IV), the null-collision test of electrons against the majorant
 // probability (Sec. III; one Philox2x32-10 draw keyed by (id, step)),
 // in-place compaction of survivors, and the fixed-point deposit of
-// w_p = beta w_j (Eq. Ansatz).
+// w_p = beta w_j (Eq. Ansatz; with an imposed field the deposit is formed
+// from the markers when read, and the step deposits nothing).
 //
 // Work decomposition.  Every (instance, species) segment is a sequence of
 // tiles of kTile = 128 marker slots (tile k holds fill[k] markers), and every
@@ -263,8 +264,8 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
     if (d[0].sseg != cur_seg) {
       if (cur_seg >= 0) flush_segment(r, cur_seg, s_rho, cs, use_smem);
       cur_seg = d[0].sseg;
-      // with an imposed field the deposit is formed when it is read
-      // (deposit_markers), so nothing is deposited here
+      // with an imposed field the deposit is formed from the markers when it
+      // is read (k_deposit), so nothing is deposited here
       use_smem = r.inst[cur_seg >> 1].field_mode == 1 &&
                  r.inst[cur_seg >> 1].n_cells + 1 <= r.smem_nodes;
     }
