@@ -1,0 +1,55 @@
+"""The measured workloads follow their stated recipes (CPU only): the
+batched sweep's 32 instances and the Table tab:sims runs' time steps."""
+import math
+
+from paper_2103_12194_gb300 import inputs
+
+import bench
+
+
+def test_batched_sweep_recipe():
+    items = bench.batch_specs(inputs)
+    assert len(items) == 32
+    pds = [spec["p_Pa"] * 1.0 / inputs.TORR for spec, _ in items]  # d = 1 cm
+    assert math.isclose(pds[0], 0.1, rel_tol=1e-12) and math.isclose(pds[-1], 100.0, rel_tol=1e-12)
+    assert all(b > a for a, b in zip(pds, pds[1:]))
+    ns = [n for _, n in items]
+    assert ns[0] == 10_000 and ns[-1] == 4_000_000
+    cells = [spec["n_cells"] for spec, _ in items]
+    assert min(cells) == 128 and max(cells) == 16384
+    for (spec, _), pd in zip(items, pds):
+        assert spec["field_mode"] == 1 and spec["gamma_se"] == 0.07
+        if pd > 0.3:
+            # Eq. paschen with A = 11.5, B = 176, gamma = 0.07
+            v_b = 176.0 * pd / (math.log(11.5 * pd) - math.log(math.log(1.0 + 1.0 / 0.07)))
+            assert math.isclose(spec["V"], v_b, rel_tol=1e-12)
+        else:
+            assert spec["V"] == 1000.0
+
+
+def test_table_sims_time_steps():
+    """SLPIC: dt = dx / v0, so 30 ion crossings (2 d / v0 each) are
+    60 cells steps; PIC: dt = dx / v_max, sqrt(M / m_e) times shorter."""
+    for p, V, cells in bench.TAB_SIMS:
+        s = bench.tab_sims_spec(inputs, p, V, cells, False, seed=1)
+        q = bench.tab_sims_spec(inputs, p, V, cells, True, seed=1)
+        dx = 0.01 / cells
+        assert math.isclose(s["dt"], dx / inputs.ion_speed(V), rel_tol=1e-12)
+        assert math.isclose(s["vlim_e"], inputs.ion_speed(V), rel_tol=1e-12)
+        assert q["vlim_e"] == math.inf
+        assert math.isclose(s["dt"] / q["dt"], math.sqrt(inputs.M_AR / inputs.ME), rel_tol=1e-12)
+        steps = 30 * (2 * 0.01 / inputs.ion_speed(V)) / s["dt"]
+        assert math.isclose(steps, 60 * cells, rel_tol=1e-12)
+        assert s["emission_model"] == 1 and s["n_exc"] == 3
+
+
+def test_table_sims_rows_are_the_papers():
+    """The study's rows are Table tab:sims's (p, V, cells), from the golden
+    fixture transcribed from the paper."""
+    import os
+    import numpy as np
+    path = os.path.join(os.path.dirname(__file__), "golden", "table_sims.txt")
+    rows = np.loadtxt(path, comments="#", usecols=(0, 1, 2))
+    assert len(rows) == len(bench.TAB_SIMS)
+    for (p, V, cells), r in zip(bench.TAB_SIMS, rows):
+        assert (p, V, cells) == (r[0], r[1], int(r[2]))
