@@ -49,6 +49,7 @@ class OracleConfig(ctypes.Structure):
         ("sig_ex3", ctypes.POINTER(ctypes.c_float)),
         ("e_ex2", ctypes.c_double),
         ("e_ex3", ctypes.c_double),
+        ("kick_scheme", ctypes.c_int),
     ]
 
 
@@ -102,6 +103,7 @@ def lib():
         L.oracle_history.argtypes = [vp, vp]
         L.oracle_constants.argtypes = [vp, vp]
         L.oracle_xsec.argtypes = [vp, vp, i64, vp]
+        L.oracle_kick.argtypes = [vp, ctypes.c_int, i64, vp, vp, vp, vp, vp]
         L.oracle_philox.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, vp]
         L.oracle_philox_many.argtypes = [vp, i64, ctypes.c_uint32, ctypes.c_uint32, vp]
         L.oracle_philox2_many.argtypes = [vp, i64, ctypes.c_uint32, vp]
@@ -209,6 +211,7 @@ class Oracle:
         if n_exc >= 3:
             c.sig_ex3 = self._sig[4].ctypes.data_as(fp)
             c.e_ex3 = float(s["e_ex3"])
+        c.kick_scheme = int(s.get("kick_scheme", 0))
         self.precision = int(precision)
         self._cfg = c
         self._h = lib().oracle_create(ctypes.byref(c))
@@ -293,6 +296,16 @@ class Oracle:
         out = np.empty(3, np.float64)
         lib().oracle_constants(self._h, _ptr(out))
         return {"P0": out[0], "vb_cap": out[1], "ndt": out[2]}
+
+    def kick(self, species, vx, vy, vz, A):
+        """New v_x after one step's kick for arrays of velocities and
+        unlimited increments A = q E_x dt / m (the oracle's kick, in its
+        precision)."""
+        arrs = [np.ascontiguousarray(np.broadcast_to(a, np.shape(vx)), dtype=np.float64)
+                for a in (vx, vy, vz, A)]
+        out = np.empty(arrs[0].size, np.float64)
+        lib().oracle_kick(self._h, int(species), out.size, *[_ptr(a) for a in arrs], _ptr(out))
+        return out.reshape(np.shape(vx))
 
     def xsec(self, eps):
         eps = np.ascontiguousarray(eps, dtype=np.float64)

@@ -19,11 +19,14 @@
 // Readings of the paper that this file fixes (the paper is silent on them):
 //  * cathode at x = 0 with phi = 0, anode at x = d with phi = V (Sec. IV);
 //  * linear (cloud-in-cell) shape for gather and deposit (Eq. Ansatz);
-//  * leapfrog below the speed limit; across and above it the kick integrates
-//    Eq. slpicEOMv in the speed-limited time (the trapezoid rule, exact for
-//    motion along the field: the energy gained is q E_x times the distance
-//    moved); the drift uses beta of the post-kick speed (Eqs. slpicEOMx,
-//    slpicEOMv, betaAbrupt);
+//  * the kick solves Eq. slpicEOMv exactly over the step with E_x held at
+//    its gathered value (leapfrog below the speed limit; across and above it
+//    the motion is unlimited in the time tau = integral of beta dt, and the
+//    step's end follows from the elapsed time, a closed form in asinh); the
+//    drift uses beta of the post-kick speed (Eqs. slpicEOMx, slpicEOMv,
+//    betaAbrupt).  The FP64 reference evaluates that solution directly; the
+//    FP32 mirror restates the library's single-precision solution of the same
+//    equation;
 //  * collision probability of a marker per step = beta v dt / lambda_mfp
 //    = n_g sigma(eps) beta v dt (Sec. III, the d'/lambda_mfp rule and
 //    Eq. SLPICcollisionNumber with beta_n = 1, whole-marker collisions),
@@ -47,6 +50,7 @@
 #include <cstdint>
 #include <cstring>
 #include <limits>
+#include <type_traits>
 #include <vector>
 
 namespace {
@@ -160,6 +164,8 @@ typedef struct {
   const float* sig_ex2;
   const float* sig_ex3;
   double e_ex2, e_ex3;
+  int kick_scheme;      // 0: Eq. slpicEOMv solved exactly; 1: a planted
+                        // trapezoid-rule approximation (pins only)
 } oracle_config;
 
 // Per-step record of what happened (all sums over markers, in the step).
@@ -296,49 +302,243 @@ struct Sim {
   // beta(v) = min(1, vlim / v), Eq. betaAbrupt.
   R beta(R v, int s) const { return v > vlim[s] ? vlim[s] / v : (R)1; }
 
-  // New v_x after the kick of one step, A = q E_x dt / m (Eq. slpicEOMv:
-  // dv_x/dt = beta(|v|) q E_x / m; v_y, v_z unchanged).  Unlimited species,
-  // and a marker below the limit at both ends of the step: v_x + A
-  // (leapfrog).  Otherwise, with L the limit: the part of the step up to
-  // |v| = L is unlimited; over the rest (a fraction f of dt) the motion is
-  // unlimited in the time tau = integral of beta dt, u = v_1 + A tau / dt,
-  // and f dt = integral of |v| / L dtau, taken by the trapezoid rule:
-  // z (s_1 + s') = 2 f |A| L for the gain z of v_x along A, with s_1 and s'
-  // the speeds at the ends of that part.  Its root is taken by one Newton
-  // step from the root with v_y = v_z = 0.
+  // New v_x after the kick of one step, A = q E_x dt / m the unlimited
+  // velocity increment (Eq. slpicEOMv: dv_x/dt = beta(|v|) q E_x / m, with
+  // v_y and v_z unchanged and E_x held at its gathered value over the step).
+  // FP64 reference: the exact solution (kick_reference); FP32 mirror: the
+  // arithmetic of the library's kick, operation by operation (kick_mirror);
+  // kick_scheme 1 plants a trapezoid-rule approximation for the pins.
   R kick(const Marker<R>& m, R A, int s) const {
     if (!limited[s]) return m.vx + A;
-    const R L = vlim[s];
-    const R sp = std::sqrt(m.vx * m.vx + m.vy * m.vy + m.vz * m.vz);
+    if (cfg.kick_scheme == 1) return kick_trapezoid(m.vx, m.vy, m.vz, A, vlim[s]);
+    if constexpr (std::is_same<R, double>::value) {
+      return kick_reference(m.vx, m.vy, m.vz, A, vlim[s]);
+    } else {
+      return kick_mirror(m.vx, m.vy, m.vz, A, vlim[s]);
+    }
+  }
+
+  // Psi(w) = integral from 0 to w of max(L, sqrt(w'^2 + p^2)) dw', an odd
+  // function of w.  With sqrt(w^2 + p^2) >= L for |w| >= q = sqrt(L^2 - p^2)
+  // (q = 0 when p >= L):
+  //   |w| <= q:  L w;
+  //   |w| >  q:  sign(w) [L q + (Phi(|w|) - Phi(q)) / 2],
+  // Phi(x) = x sqrt(x^2 + p^2) + p^2 asinh(x / p), the antiderivative of
+  // 2 sqrt(x^2 + p^2) (Phi(x) = x^2 when p = 0).
+  static double psi(double w, double p, double L) {
+    const double a = std::fabs(w);
+    const double sg = w < 0.0 ? -1.0 : 1.0;
+    auto Phi = [p](double x) {
+      if (p == 0.0) return x * x;
+      return x * std::sqrt(x * x + p * p) + p * p * std::asinh(x / p);
+    };
+    const double q = p < L ? std::sqrt(L * L - p * p) : 0.0;
+    if (a <= q) return sg * L * a;
+    return sg * (L * q + 0.5 * (Phi(a) - Phi(q)));
+  }
+
+  // The exact kick (FP64 reference).  In the time tau = integral of beta dt
+  // the motion of Eq. slpicEOMv is unlimited: v_x = v_x0 + a tau, a = A / dt.
+  // The elapsed time is dt = integral of dtau / beta(|v|)
+  // = integral of max(1, |v| / L) dtau.  With w = v_x sign(A) the speed along
+  // the force and dtau = dw / |a|, the step's end w1 solves
+  //   Psi(w1) - Psi(w0) = L |a| dt = L |A|.
+  // Psi is increasing (slope max(L, |v|) >= L), and the root lies in
+  // [w0, w0 + |A|] (tau <= dt).  It is found by Newton steps kept inside
+  // that bracket (a bisection whenever a step would leave it), until the
+  // bracket or the step is at the last bits of w.  Below the limit at both
+  // ends of the step the motion is unlimited and the kick is v_x + A.
+  static double kick_reference(double vx, double vy, double vz, double A, double L) {
+    const double p2 = vy * vy + vz * vz;
+    const double vt = vx + A;
+    if (std::sqrt(vx * vx + p2) <= L && std::sqrt(vt * vt + p2) <= L) return vt;
+    if (A == 0.0) return vx;
+    const double g = A > 0.0 ? 1.0 : -1.0;
+    const double p = std::sqrt(p2);
+    const double w0 = g * vx;
+    const double target = psi(w0, p, L) + L * std::fabs(A);
+    double lo = w0, hi = w0 + std::fabs(A);
+    double w = 0.5 * (lo + hi);
+    for (int it = 0; it < 200; ++it) {
+      const double G = psi(w, p, L) - target;
+      if (G == 0.0) return g * w;
+      if (G < 0.0) lo = w;
+      else hi = w;
+      const double slope = std::max(L, std::sqrt(w * w + p2));
+      double wn = w - G / slope;
+      if (!(wn > lo && wn < hi)) wn = 0.5 * (lo + hi);
+      const double tol = 4.0 * std::numeric_limits<double>::epsilon() *
+                         std::max(std::fabs(w), std::max(L, p));
+      if (hi - lo <= tol || std::fabs(wn - w) <= 0.25 * tol) {
+        w = wn;
+        break;
+      }
+      w = wn;
+    }
+    return g * w;
+  }
+
+  // A planted mistake for the pins (kick_scheme 1): the elapsed time of the
+  // speed-limited part taken by the trapezoid rule from the two end speeds,
+  // solved by one Newton step, and a path that dips below the limit inside
+  // the step treated as limited throughout.  Its errors reach tens of per
+  // cent off the field axis.
+  static R kick_trapezoid(R vx, R vy, R vz, R A, R L) {
+    const R sp = std::sqrt(vx * vx + vy * vy + vz * vz);
     if (sp <= L) {
-      const R vt = m.vx + A;
-      if (std::sqrt(vt * vt + m.vy * m.vy + m.vz * m.vz) <= L) return vt;
+      const R vt = vx + A;
+      if (std::sqrt(vt * vt + vy * vy + vz * vz) <= L) return vt;
     }
     const R g = A > (R)0 ? (R)1 : (R)-1;
     const R aA = g * A;
-    const R p2 = m.vy * m.vy + m.vz * m.vz;
+    const R p2 = vy * vy + vz * vz;
     R f, s1, v1;
     if (sp < L) {
-      // reaches the limit inside the step, at speed L with v_x = g q
       const R q = std::sqrt(std::max((R)0, L * L - p2));
-      f = std::min((R)1, std::max((R)0, (R)1 - (q - g * m.vx) / aA));
+      f = std::min((R)1, std::max((R)0, (R)1 - (q - g * vx) / aA));
       s1 = L;
       v1 = q;
     } else {
       f = (R)1;
       s1 = sp;
-      v1 = g * m.vx;
+      v1 = g * vx;
     }
     const R K = (R)2 * f * aA * L;
     const R c = s1 + v1;
     R z = (std::sqrt(c * c + (R)4 * K) - c) * (R)0.5;
-    if (z * s1 > K) z = K / s1;  // the root is at most K / s_1
+    if (z * s1 > K) z = K / s1;
     const R w = v1 + z;
     const R sn = std::sqrt(w * w + p2);
     const R t = s1 + sn;
-    const R den = t * sn + z * w;  // sn times the slope of z (s_1 + s') - K
+    const R den = t * sn + z * w;
     if (den > (R)0) z = std::max((R)0, z - (z * t - K) * sn / den);
     return g * (v1 + z);
+  }
+
+  // ---- FP32 mirror of the library's kick --------------------------------
+  // The library solves the same equation as kick_reference with IEEE single
+  // operations only (+ - * / sqrt and fused multiply-adds), so that this
+  // restatement reproduces it bit for bit.  Along the force the path has up
+  // to three parts: limited and slowing (w < -q), unlimited (|w| <= q, the
+  // time-integral is L dw), limited and speeding up (w > q).  In a limited
+  // part, with m = |w| and D(m0, m) = integral of sqrt(x^2 + p^2) dx from
+  // m0 to m = [m s - m0 s0 + p^2 log((m + s) / (m0 + s0))] / 2, the end
+  // solves D(m0, m) = T (T = +-the remaining budget): a third-order series
+  // guess in X = T / s0^2 (beyond |X| = 1/2, sqrt(m0^2 + 2T)), then Halley
+  // steps kept inside a bracket until the step is below 2^-8 of the speed
+  // (the error left is then about the cube of that, under a float ulp).
+  static float mad32(float a, float b, float c) { return std::fmaf(a, b, c); }
+
+  // Natural logarithm of a positive normal float from IEEE operations:
+  // y = 2^k m with m in [sqrt(1/2), sqrt(2)), log m = 2 atanh(t),
+  // t = (m - 1) / (m + 1), |t| <= 0.1716, by the Taylor series of atanh to
+  // t^9 (the next term is below 2^-28 of the sum); log 2 split in two parts
+  // so that k log 2 keeps its precision.
+  static float log_mirror(float y) {
+    uint32_t b;
+    std::memcpy(&b, &y, 4);
+    const int32_t ix = (int32_t)b - (int32_t)0x3F3504F3;
+    const int32_t k = ix >> 23;
+    const uint32_t mb = (uint32_t)(ix & 0x7FFFFF) + 0x3F3504F3u;
+    float m;
+    std::memcpy(&m, &mb, 4);
+    const float f = m - 1.0f;
+    const float t = f / (m + 1.0f);
+    const float t2 = t * t;
+    float poly = mad32(t2, 1.0f / 9.0f, 1.0f / 7.0f);
+    poly = mad32(t2, poly, 1.0f / 5.0f);
+    poly = mad32(t2, poly, 1.0f / 3.0f);
+    poly = mad32(t2, poly, 1.0f);
+    const float kf = (float)k;
+    return mad32(kf, 0.693145751953125f, mad32(kf, 1.428606765330187e-06f, (t + t) * poly));
+  }
+
+  // End speed m >= 0 along the force with D(m0, m) = T, root in [lo, hi].
+  static float kick_solve_mirror(float m0, float T, float lo, float hi, float p2) {
+    const float s0 = std::sqrt(mad32(m0, m0, p2));
+    const float h0 = m0 + s0;
+    const float rr = 1.0f / (s0 * h0);
+    const float is0 = h0 * rr, ih0 = s0 * rr;
+    const float X = (T * is0) * is0;
+    const float c0 = m0 * is0;
+    float m;
+    if (std::fabs(X) <= 0.5f) {
+      const float c3 = mad32(4.0f * c0, c0, -1.0f) * (float)(1.0 / 6.0);
+      const float zh = X * mad32(X, mad32(X, c3, -0.5f * c0), 1.0f);
+      m = mad32(s0, zh, m0);
+    } else {
+      m = std::sqrt(std::max(0.0f, mad32(m0, m0, T + T)));
+    }
+    m = std::min(std::max(m, lo), hi);
+    const float hm0s0 = 0.5f * (m0 * s0);
+    const float hp2 = 0.5f * p2;
+    for (int it = 0; it < 24; ++it) {
+      const float s = std::sqrt(mad32(m, m, p2));
+      const float lg = p2 > 0.0f ? log_mirror((m + s) * ih0) : 0.0f;
+      const float F = mad32(hp2, lg, mad32(0.5f * m, s, -hm0s0)) - T;
+      if (F > 0.0f) hi = m;
+      else lo = m;
+      const float s2 = s * s;
+      const float dm = ((F + F) * s2) / mad32(s2 + s2, s, -(F * m));
+      float mn = m - dm;
+      if (!(mn >= lo && mn <= hi)) mn = 0.5f * (lo + hi);
+      const float step = m - mn;
+      m = mn;
+      if (std::fabs(step) <= 0.00390625f * s) break;
+    }
+    return m;
+  }
+
+  static float kick_mirror(float vx, float vy, float vz, float A, float L) {
+    const float L2 = L * L;
+    const float p2 = mad32(vy, vy, vz * vz);
+    const float vt = vx + A;
+    if (mad32(vx, vx, p2) <= L2 && mad32(vt, vt, p2) <= L2) return vt;
+    if (!(A != 0.0f)) return vx;
+    const float g = A > 0.0f ? 1.0f : -1.0f;
+    float W = L * (g * A);
+    float w = g * vx;
+    const float q2 = L2 - p2;
+    const float q = q2 > 0.0f ? std::sqrt(q2) : 0.0f;
+    float m0, T, lo, hi, sgn;
+    if (w < -q) {
+      // limited, slowing down: the cost of reaching the unlimited zone
+      // (or the axis) is D(q, |w|) >= L (|w| - q)
+      m0 = -w;
+      bool stay = W <= L * (m0 - q);
+      if (!stay) {
+        const float s0 = std::sqrt(mad32(m0, m0, p2));
+        const float sq = q > 0.0f ? L : std::sqrt(p2);
+        float C1 = 0.5f * (m0 * s0 - q * sq);
+        if (p2 > 0.0f) C1 = mad32(0.5f * p2, log_mirror((m0 + s0) / (q + sq)), C1);
+        stay = W < C1;
+        if (!stay) {
+          W = W - C1;
+          w = -q;
+        }
+      }
+      if (stay) {
+        T = -W;
+        lo = q;
+        hi = m0;
+        sgn = -1.0f;
+        return g * (sgn * kick_solve_mirror(m0, T, lo, hi, p2));
+      }
+    }
+    if (w < q) {
+      // unlimited zone
+      const float reach = L * (q - w);
+      if (W <= reach) return g * (w + W / L);
+      W = W - reach;
+      w = q;
+    }
+    // limited, speeding up; s >= s(w) along the way bounds the end
+    m0 = w;
+    T = W;
+    lo = w;
+    hi = w + W / std::sqrt(mad32(w, w, p2));
+    sgn = 1.0f;
+    return g * (sgn * kick_solve_mirror(m0, T, lo, hi, p2));
   }
 
   // Linear interpolation of the cumulative cross sections at eps.  Nodes sit
@@ -791,6 +991,24 @@ int oracle_step(void* hp, int64_t nsteps) {
   if (!h || nsteps < 0) return -1;
   visit(h, [&](auto& sim) {
     for (int64_t i = 0; i < nsteps; ++i) sim.one_step();
+  });
+  return 0;
+}
+
+// The kick of n markers of species s (tests): new v_x for velocities
+// (vx, vy, vz) and unlimited increments A, in the oracle's precision.
+int oracle_kick(void* hp, int s, int64_t n, const double* vx, const double* vy,
+                const double* vz, const double* A, double* out) {
+  Handle* h = (Handle*)hp;
+  if (!h || s < 0 || s > 1 || n < 0) return -1;
+  visit(h, [&](auto& sim) {
+    using R = decltype(sim.K_E);
+    for (int64_t i = 0; i < n; ++i) {
+      Marker<R> m;
+      m.cell = 0; m.off = 0; m.wj = 1; m.id = 0;
+      m.vx = (R)vx[i]; m.vy = (R)vy[i]; m.vz = (R)vz[i];
+      out[i] = (double)sim.kick(m, (R)A[i], s);
+    }
   });
   return 0;
 }

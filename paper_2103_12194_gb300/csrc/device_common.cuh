@@ -3,7 +3,8 @@
 //
 // The whole library is compiled with -fmad=false and IEEE division and square
 // root, so every expression below is evaluated with one rounding per
-// operation, in the order written.
+// operation, in the order written; a fused multiply-add appears only where
+// the source asks for one (mad, __fmaf_rn).
 #pragma once
 
 #include <cuda/atomic>
@@ -138,51 +139,158 @@ __device__ __forceinline__ R beta_of(R v, R vlim) {
   return r_min((R)1, vlim / v);
 }
 
+// Multiply-add in the marker type: fused (one rounding) in float, where the
+// kick spends its time; written out in double, the plain FP64 form.
+__device__ __forceinline__ float mad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double mad(double a, double b, double c) { return a * b + c; }
+
+// Natural logarithm of a positive normal float from IEEE operations only:
+// y = 2^k m with m in [sqrt(1/2), sqrt(2)), log m = 2 atanh(t) with
+// t = (m - 1) / (m + 1), |t| <= 0.1716, by the Taylor series of atanh up to
+// t^9 (the next term is below 2^-28 of the sum), and k log 2 with log 2
+// split in a 15-bit head and a tail so that the product keeps its precision.
+// In double the library's log is used.
+__device__ __forceinline__ float r_logk(float y) {
+  const int ix = (int)__float_as_uint(y) - 0x3F3504F3;
+  const int k = ix >> 23;
+  const float m = __uint_as_float((uint32_t)(ix & 0x7FFFFF) + 0x3F3504F3u);
+  const float f = m - 1.0f;
+  const float t = f / (m + 1.0f);
+  const float t2 = t * t;
+  float poly = __fmaf_rn(t2, 1.0f / 9.0f, 1.0f / 7.0f);
+  poly = __fmaf_rn(t2, poly, 1.0f / 5.0f);
+  poly = __fmaf_rn(t2, poly, 1.0f / 3.0f);
+  poly = __fmaf_rn(t2, poly, 1.0f);
+  const float kf = (float)k;
+  return __fmaf_rn(kf, 0.693145751953125f, __fmaf_rn(kf, 1.428606765330187e-06f, (t + t) * poly));
+}
+__device__ __forceinline__ double r_logk(double y) { return log(y); }
+
+// Halley steps of the kick stop once a step is below this fraction of the
+// speed; the error left is then about its cube.
+template <typename R>
+__device__ __forceinline__ R kick_tol();
+template <>
+__device__ __forceinline__ float kick_tol<float>() {
+  return 0.00390625f;  // 2^-8
+}
+template <>
+__device__ __forceinline__ double kick_tol<double>() {
+  return 3.814697265625e-06;  // 2^-18
+}
+
+// End speed m >= 0 along the force of a speed-limited part of the kick:
+// D(m0, m) = T with D(a, b) = integral from a to b of sqrt(x^2 + p2) dx
+//          = [b s_b - a s_a + p2 log((b + s_b) / (a + s_a))] / 2,
+// root in [lo, hi] (T > 0 speeding up, T < 0 slowing down).  A third-order
+// series guess in X = T / s0^2 (beyond |X| = 1/2, sqrt(m0^2 + 2 T)), then
+// Halley steps (D' = s, D'' = m / s) kept inside the bracket.
+template <typename R>
+__device__ __forceinline__ R kick_solve(R m0, R T, R lo, R hi, R p2) {
+  const R s0 = r_sqrt(mad(m0, m0, p2));
+  const R h0 = m0 + s0;
+  const R rr = (R)1 / (s0 * h0);
+  const R is0 = h0 * rr, ih0 = s0 * rr;
+  const R X = (T * is0) * is0;
+  const R c0 = m0 * is0;
+  R m;
+  if (r_abs(X) <= (R)0.5) {
+    const R c3 = mad((R)4 * c0, c0, (R)-1) * (R)(1.0 / 6.0);
+    const R zh = X * mad(X, mad(X, c3, (R)-0.5 * c0), (R)1);
+    m = mad(s0, zh, m0);
+  } else {
+    m = r_sqrt(r_max((R)0, mad(m0, m0, T + T)));
+  }
+  m = r_min(r_max(m, lo), hi);
+  const R hm0s0 = (R)0.5 * (m0 * s0);
+  const R hp2 = (R)0.5 * p2;
+  const R tau = kick_tol<R>();
+  for (int it = 0; it < 24; ++it) {
+    const R s = r_sqrt(mad(m, m, p2));
+    const R lg = p2 > (R)0 ? r_logk((m + s) * ih0) : (R)0;
+    const R F = mad(hp2, lg, mad((R)0.5 * m, s, -hm0s0)) - T;
+    if (F > (R)0) hi = m;
+    else lo = m;
+    const R s2 = s * s;
+    const R dm = ((F + F) * s2) / mad(s2 + s2, s, -(F * m));
+    R mn = m - dm;
+    if (!(mn >= lo && mn <= hi)) mn = (R)0.5 * (lo + hi);
+    const R step = m - mn;
+    m = mn;
+    if (r_abs(step) <= tau * s) break;
+  }
+  return m;
+}
+
 // Speed-limited kick over one step of a species with a finite limit L
-// (Eq. slpicEOMv: dv_x/dt = beta(|v|) q E_x / m, v_y and v_z unchanged).
-// A = q E_x dt / m is the unlimited velocity increment.  Returns the new v_x.
+// (Eq. slpicEOMv: dv_x/dt = beta(|v|) q E_x / m with E_x held at its gathered
+// value, v_y and v_z unchanged).  A = q E_x dt / m is the unlimited velocity
+// increment; returns the new v_x.
 //  - Below the limit at both ends of the step: the leapfrog kick v_x + A.
-//  - Otherwise the marker moves at the limit for a fraction f of the step
-//    (f < 1 when it starts below L: the first part, up to |v| = L, is an
-//    unlimited kick).  Along the speed-limited part, in the time
-//    tau = integral of beta dt the motion is unlimited (u = v_1 + (A / dt) tau
-//    along x), and f dt = integral of |v| / L dtau; the trapezoid rule for
-//    that integral gives z (s_1 + s') = K with z = u - v_1 (in the direction
-//    of A), K = 2 f |A| L, s_1 and s' the speeds at the ends.  Exact for
-//    motion along x (the energy gained is q E_x times the distance moved,
-//    as Eqs. slpicEOMx and slpicEOMv imply), second order otherwise.  Solved
-//    by one Newton step from its root for v_y = v_z = 0, an upper bound.
+//  - Otherwise the exact solution of the equation over the step.  In the
+//    time tau = integral of beta dt the motion is unlimited,
+//    v_x = v_x0 + (A / dt) tau, and dt = integral of max(1, |v| / L) dtau.
+//    With w = v_x sign(A) the speed along the force and p2 = v_y^2 + v_z^2,
+//    the step ends where the integral of max(L, sqrt(w^2 + p2)) dw from w0
+//    reaches W = L |A|.  Along the force the path has up to three parts:
+//    limited and slowing (w < -q), unlimited (|w| <= q, q^2 = L^2 - p2) and
+//    limited and speeding up (w > q); the end lies in the first part whose
+//    cost exhausts W.  Only + - * / sqrt (and fused multiply-adds in float)
+//    are used, so an FP32 restatement reproduces it bit for bit.
 template <typename R>
 __device__ __forceinline__ R limited_kick(R vx, R vy, R vz, R A, R L) {
-  const R sp = r_sqrt(vx * vx + vy * vy + vz * vz);
-  if (sp <= L) {
-    const R vt = vx + A;
-    if (r_sqrt(vt * vt + vy * vy + vz * vz) <= L) return vt;
-  }
+  const R L2 = L * L;
+  const R p2 = mad(vy, vy, vz * vz);
+  const R vt = vx + A;
+  if (mad(vx, vx, p2) <= L2 && mad(vt, vt, p2) <= L2) return vt;
+  if (!(A != (R)0)) return vx;
   const R g = A > (R)0 ? (R)1 : (R)-1;
-  const R aA = g * A;
-  const R p2 = vy * vy + vz * vz;
-  R f, s1, v1;
-  if (sp < L) {
-    const R q = r_sqrt(r_max((R)0, L * L - p2));
-    f = r_min((R)1, r_max((R)0, (R)1 - (q - g * vx) / aA));
-    s1 = L;
-    v1 = q;
-  } else {
-    f = (R)1;
-    s1 = sp;
-    v1 = g * vx;
+  R W = L * (g * A);
+  R w = g * vx;
+  const R q2 = L2 - p2;
+  const R q = q2 > (R)0 ? r_sqrt(q2) : (R)0;
+  R m0, T, lo, hi, sgn;
+  bool solved = false;
+  if (w < -q) {
+    // limited and slowing down: reaching the unlimited zone (or the axis,
+    // when p2 >= L2) costs D(q, |w|) >= L (|w| - q)
+    m0 = -w;
+    bool stay = W <= L * (m0 - q);
+    if (!stay) {
+      const R s0 = r_sqrt(mad(m0, m0, p2));
+      const R sq = q > (R)0 ? L : r_sqrt(p2);
+      R C1 = (R)0.5 * (m0 * s0 - q * sq);
+      if (p2 > (R)0) C1 = mad((R)0.5 * p2, r_logk((m0 + s0) / (q + sq)), C1);
+      stay = W < C1;
+      if (!stay) {
+        W = W - C1;
+        w = -q;
+      }
+    }
+    if (stay) {
+      T = -W;
+      lo = q;
+      hi = m0;
+      sgn = (R)-1;
+      solved = true;
+    }
   }
-  const R K = (R)2 * f * aA * L;
-  const R c = s1 + v1;
-  R z = (r_sqrt(c * c + (R)4 * K) - c) * (R)0.5;
-  if (z * s1 > K) z = K / s1;  // z <= K / s_1: the root's other bound
-  const R w = v1 + z;
-  const R s = r_sqrt(w * w + p2);
-  const R t = s1 + s;
-  const R den = t * s + z * w;  // s times the derivative of z (s_1 + s') - K
-  if (den > (R)0) z = r_max((R)0, z - (z * t - K) * s / den);
-  return g * (v1 + z);
+  if (!solved) {
+    if (w < q) {
+      // unlimited zone
+      const R reach = L * (q - w);
+      if (W <= reach) return g * (w + W / L);
+      W = W - reach;
+      w = q;
+    }
+    // limited and speeding up; s >= s(w) along the way bounds the end
+    m0 = w;
+    T = W;
+    lo = w;
+    hi = w + W / r_sqrt(mad(w, w, p2));
+    sgn = (R)1;
+  }
+  return g * (sgn * kick_solve(m0, T, lo, hi, p2));
 }
 
 // Direction with cos(theta) = 1 - 2 ua about x and azimuth 2 pi ub.

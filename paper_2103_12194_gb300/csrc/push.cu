@@ -350,8 +350,8 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
           a[j] = qmdt * (E0 + off[j] * (E1 - E0));
         }
         // speed-limited kick (limited_kick: leapfrog below the limit, the
-        // proper-time trapezoid rule across and above it) and drift (beta of
-        // the post-kick speed); an unlimited species has beta = 1 exactly
+        // exact solution of Eq. slpicEOMv across and above it) and drift
+        // (beta of the post-kick speed); an unlimited species has beta = 1
         if (limited) {
 #pragma unroll
           for (int j = 0; j < kPerLane; ++j) vx[j] = limited_kick(vx[j], vy[j], vz[j], a[j], vlim);

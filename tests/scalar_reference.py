@@ -87,39 +87,43 @@ class ScalarSim:
         return vl / v if v > vl else 1.0
 
     def kick(self, vx, vy, vz, A, sp):
-        """v_x after one step's kick, A = q E dt / m.  Below the speed limit
-        at both ends: v_x + A.  Else: the unlimited part up to |v| = L, then
-        the speed-limited part (fraction f of the step), where with
-        z = (v_x' - v_1) sign(A) the trapezoid rule for the elapsed time
-        gives z (s_1 + |v'|) = 2 f |A| L; z from the v_y = v_z = 0 root and
-        one Newton step."""
+        """v_x after one step's kick, A = q E dt / m (Eq. slpicEOMv with the
+        field held over the step).  In the time tau = integral of beta dt the
+        motion is unlimited, v_x(tau) = vx + (A / dt) tau, and the step's
+        elapsed time is the integral of 1 / beta(|v(tau)|) dtau.  The end is
+        the tau in [0, dt] where that integral reaches dt: the integral is
+        taken by adaptive quadrature (split where the speed crosses the limit,
+        where the integrand has a kink) and the root by Brent's method."""
         L = self.vl[sp]
         if not (L > 0 and math.isfinite(L)):
             return vx + A
-        speed = math.sqrt(vx * vx + vy * vy + vz * vz)
-        vt = vx + A
-        if speed <= L and math.sqrt(vt * vt + vy * vy + vz * vz) <= L:
-            return vt
-        sign = 1.0 if A > 0 else -1.0
-        mag = sign * A
+        if A == 0.0:
+            return vx
+        from scipy import integrate, optimize
         perp2 = vy * vy + vz * vz
-        if speed < L:
-            along = math.sqrt(max(0.0, L * L - perp2))
-            frac = min(1.0, max(0.0, 1.0 - (along - sign * vx) / mag))
-            s_a, u_a = L, along
-        else:
-            frac, s_a, u_a = 1.0, speed, sign * vx
-        K = 2.0 * frac * mag * L
-        c = s_a + u_a
-        z = (math.sqrt(c * c + 4.0 * K) - c) * 0.5
-        if z * s_a > K:
-            z = K / s_a
-        w = u_a + z
-        s_b = math.sqrt(w * w + perp2)
-        slope = (s_a + s_b) * s_b + z * w
-        if slope > 0:
-            z = max(0.0, z - (z * (s_a + s_b) - K) * s_b / slope)
-        return sign * (u_a + z)
+        dt = 1.0
+        a = A / dt
+
+        def inv_beta(tau):
+            u = vx + a * tau
+            return max(1.0, math.sqrt(u * u + perp2) / L)
+
+        # the speed crosses L where (vx + a tau)^2 = L^2 - perp2
+        kinks = []
+        if perp2 < L * L:
+            q = math.sqrt(L * L - perp2)
+            kinks = sorted(t for t in ((q - vx) / a, (-q - vx) / a) if 0.0 < t < dt)
+
+        def elapsed(tau):
+            pts = [0.0] + [k for k in kinks if k < tau] + [tau]
+            return sum(integrate.quad(inv_beta, x0, x1, epsabs=0.0, epsrel=1e-13, limit=200)[0]
+                       for x0, x1 in zip(pts[:-1], pts[1:]))
+
+        if elapsed(dt) <= dt * (1.0 + 1e-15):
+            return vx + A
+        tau = optimize.brentq(lambda t: elapsed(t) - dt, 0.0, dt, xtol=1e-16 * dt,
+                              rtol=1e-15, maxiter=200)
+        return vx + a * tau
 
     def draws(self, ident, step, sp, blk):
         c = [ident, step & MASK32, (self.s.get("instance", 0) * 2 + sp) & MASK32, blk]

@@ -1,13 +1,16 @@
 """The FP64 marker path (slpic_set_precision(ctx, 64)) against the FP64 oracle.
 
-The FP64 path runs the same kernels in double. Every decision of a step is
-made with + - * / sqrt, table lookups and Philox uniforms, which are exact in
-both, so counts, ids, cells and the deposit are bit-exact against the
-oracle.
+The FP64 path runs the same kernels in double. Without a speed limit every
+decision of a step is made with + - * / sqrt, table lookups and Philox
+uniforms, which are exact in both, so counts, ids, cells and the deposit are
+bit-exact against the oracle.
 
-Values that pass through an elementary function (scattering angles, seeding
-directions, Box-Muller) may differ by an ulp between CUDA's and the host
-library's double functions. They are compared to 1e-12 relative.
+The speed-limited kick is solved by Halley steps on the GPU and from its
+closed form (asinh) by the oracle; the two agree to rounding.  Values that
+pass through it, or through an elementary function (scattering angles,
+seeding directions, Box-Muller), may differ in the last bits; they are
+compared to 1e-12 relative, and a deposit rounded from them to the nearest
+fixed-point unit may differ by one unit now and then.
 """
 import math
 
@@ -41,15 +44,24 @@ def make_sim64(slpic, spec, cap=(1 << 20, 1 << 20)):
 
 
 def same_markers64(g, r, exact):
+    """Same markers in the same order.  exact: every field bit for bit.
+    Otherwise the position x = cell + offset to 1e-12 of a cell (a marker
+    that moves exactly one cell per step, as one speed-limited on the field
+    axis does, sits on a cell boundary, where a last-bit difference puts it at
+    offset 0 of cell k or offset 1 - 2^-53 of cell k - 1: the same position)
+    and velocities to 1e-12 relative."""
     assert np.array_equal(g["id"], r["id"].astype(np.uint32))
-    assert np.array_equal(g["cell"], r["cell"])
     assert g["off"].dtype == np.float64
     if exact:
+        assert np.array_equal(g["cell"], r["cell"])
         for k in ("off", "vx", "vy", "vz", "wj"):
             assert np.array_equal(g[k], r[k]), k
     else:
         assert np.array_equal(g["wj"], r["wj"])
-        assert np.allclose(g["off"], r["off"], rtol=0, atol=REL64)
+        xg, xr = g["cell"] + g["off"], r["cell"] + r["off"]
+        worst = int(np.argmax(np.abs(xg - xr))) if xg.size else 0
+        assert np.allclose(xg, xr, rtol=0, atol=REL64), (worst, xg[worst], xr[worst])
+        assert np.abs(g["cell"] - r["cell"]).max(initial=0) <= 1
         vg = np.stack([g["vx"], g["vy"], g["vz"]])
         vr = np.stack([r["vx"], r["vy"], r["vz"]])
         err = np.linalg.norm(vg - vr, axis=0) / np.maximum(np.linalg.norm(vr, axis=0), 1.0)
@@ -107,7 +119,12 @@ def test_fp64_deposit_bit_exact(slpic, oracle_mod):
 
 
 @pytest.mark.parametrize("vlim_e", [None, math.inf])
-def test_fp64_vacuum_steps_bit_exact(slpic, oracle_mod, vlim_e):
+def test_fp64_vacuum_steps_match_oracle(slpic, oracle_mod, vlim_e):
+    """Many steps without gas: bit-exact without a speed limit; with one,
+    ids and counts exact, positions and velocities to 1e-12 (the kick's two
+    solutions agree to rounding), the deposit to 1e-6 of each node's charge
+    and the total to 64 fixed-point units."""
+    exact = vlim_e == math.inf
     spec = inputs.gap_spec(n_cells=300, V=250.0, gamma_se=0.4, field_mode=0, vlim_e=vlim_e)
     spec["p_Pa"] = 0.0
     if vlim_e == math.inf:
@@ -123,8 +140,17 @@ def test_fp64_vacuum_steps_bit_exact(slpic, oracle_mod, vlim_e):
         sim.step(chunk)
         ref.step(chunk)
         for s in (0, 1):
-            same_markers64(sim.particles(0, s), ref.particles(s), exact=True)
-            assert np.array_equal(sim.charge(0, s), ref.charge(s))
+            same_markers64(sim.particles(0, s), ref.particles(s), exact=exact)
+            qg, qr = sim.charge(0, s), ref.charge(s)
+            if exact:
+                assert np.array_equal(qg, qr)
+            else:
+                # a marker on a cell boundary (above) moves about 2^-24 of its
+                # charge between two nodes (the electrons emitted at rest do
+                # so every step); a last-bit difference of beta moves one
+                # fixed-point unit
+                assert np.all(np.abs(qg - qr) <= 1e-6 * np.abs(qr) + 64)
+                assert abs(int(qg.sum()) - int(qr.sum())) <= 64
     hg, hr = sim.history(0), ref.history()
     for k in ("n_live", "n_abs", "n_see"):
         assert np.array_equal(hg[k], hr[k]), k

@@ -274,6 +274,148 @@ def test_speed_limited_energy_equals_work_from_rest(oracle_mod, precision):
         assert e == pytest.approx(e_want, rel=10 * tol)
 
 
+def _rk4_kick(vx, vy, vz, A, L, n=4000):
+    """v_x after one step of dv_x/dt = beta(|v|) A / dt (Eq. slpicEOMv with
+    the field held over the step, v_y and v_z fixed), by classical RK4 with n
+    substeps in units where dt = 1.  The right-hand side has a kink where the
+    speed crosses L; the substeps are split there so that each piece is
+    smooth."""
+    p2 = vy * vy + vz * vz
+
+    def f(u):
+        s = math.sqrt(u * u + p2)
+        return A * (L / s if s > L else 1.0)
+
+    # times at which the speed would cross L if it moved unlimited from vx are
+    # only a guide: locate the crossing along the integrated path instead, by
+    # halving a substep that straddles it
+    def rk4(u, h):
+        k1 = f(u)
+        k2 = f(u + 0.5 * h * k1)
+        k3 = f(u + 0.5 * h * k2)
+        k4 = f(u + h * k3)
+        return u + h * (k1 + 2 * k2 + 2 * k3 + k4) / 6.0
+
+    def above(u):
+        return u * u + p2 > L * L
+
+    t, u, h = 0.0, vx, 1.0 / n
+    while t < 1.0 - 1e-15:
+        h = min(h, 1.0 - t)
+        un = rk4(u, h)
+        if above(un) != above(u) and h > 1e-13:
+            # bisect the substep to the crossing, then continue from it
+            lo, hi = 0.0, h
+            for _ in range(60):
+                mid = 0.5 * (lo + hi)
+                if above(rk4(u, mid)) == above(u):
+                    lo = mid
+                else:
+                    hi = mid
+            u = rk4(u, hi)
+            t += hi
+            h = 1.0 / n
+            continue
+        u, t = un, t + h
+    return u
+
+
+def _kick_cases(n, seed):
+    """Off-axis velocities (speeds from 1e-3 to 1e3 v_lim in energy, every
+    direction) and kicks |A| from 1e-2 to 1e3 v_lim of either sign."""
+    rng = np.random.default_rng(seed)
+    L = 1.0e5
+    speed = L * 10.0 ** rng.uniform(-1.5, 1.5, n)
+    ct = rng.uniform(-1, 1, n)
+    st = np.sqrt(1 - ct * ct)
+    ph = rng.uniform(0, 2 * np.pi, n)
+    vx, vy, vz = speed * ct, speed * st * np.cos(ph), speed * st * np.sin(ph)
+    A = L * 10.0 ** rng.uniform(-2, 3, n) * rng.choice([-1.0, 1.0], n)
+    return L, vx, vy, vz, A
+
+
+def _kick_oracle(oracle_mod, L, precision, kick_scheme=0):
+    spec = inputs.gap_spec(n_cells=64, V=100.0, vlim_e=L, field_mode=0)
+    spec["kick_scheme"] = kick_scheme
+    return oracle_mod.Oracle(spec, precision)
+
+
+_RK4_CACHE = {}
+
+
+def _kick_errors(o, L, vx, vy, vz, A):
+    """Relative errors of the oracle's kick against RK4; the substeps shrink
+    with the kick so that each changes the speed by a small fraction of L."""
+    got = o.kick(0, vx, vy, vz, A)
+    key = (L,) + tuple(np.concatenate([vx, vy, vz, A]).tolist())
+    if key not in _RK4_CACHE:
+        _RK4_CACHE[key] = np.array([_rk4_kick(*c, L, n=int(max(4000, 64 * abs(c[3]) / L)))
+                                    for c in zip(vx, vy, vz, A)])
+    want = _RK4_CACHE[key]
+    scale = np.maximum(np.sqrt(want ** 2 + vy ** 2 + vz ** 2), L)
+    return np.abs(got - want) / scale
+
+
+def test_kick_matches_fine_integration_off_axis(oracle_mod):
+    """Eq. slpicEOMv over one step, off the field axis (v_y, v_z != 0), for
+    kicks from 1e-2 to 1e3 v_lim: the FP64 oracle's kick equals an RK4
+    integration of dv_x/dt = beta(|v|) q E_x / m (written here, with its
+    substeps split where the speed crosses the limit) to 1e-9 of the speed;
+    the FP32 mirror to 2e-6."""
+    L, vx, vy, vz, A = _kick_cases(300, seed=11)
+    err64 = _kick_errors(_kick_oracle(oracle_mod, L, 64), L, vx, vy, vz, A)
+    assert err64.max() < 1e-9, err64.max()
+    f32 = [np.float32(a).astype(np.float64) for a in (vx, vy, vz, A)]
+    err32 = _kick_errors(_kick_oracle(oracle_mod, L, 32), L, *f32)
+    assert err32.max() < 2e-6, err32.max()
+
+
+def test_planted_trapezoid_kick_fails_the_integration_pin(oracle_mod):
+    """The pin above catches a plausible mistake: the elapsed time of the
+    speed-limited part taken by the trapezoid rule and solved by one Newton
+    step (planted in the oracle with kick_scheme 1) misses the integration
+    by tens of per cent off the axis."""
+    L, vx, vy, vz, A = _kick_cases(300, seed=11)
+    err = _kick_errors(_kick_oracle(oracle_mod, L, 64, kick_scheme=1), L, vx, vy, vz, A)
+    assert err.max() > 0.05, err.max()
+    assert (err > 1e-9).mean() > 0.3
+
+
+def test_kick_on_the_field_axis_closed_forms(oracle_mod):
+    """On the field axis (v_y = v_z = 0) Eqs. slpicEOMx, slpicEOMv make the
+    energy gained equal to q E_x times the distance moved, and a limited
+    marker moves v_lim dt per step: from w0 >= L along the force,
+    w1^2 = w0^2 + 2 L |A|.  A marker moving against the force at w0 < -L first
+    slows to -L (cost (w0^2 - L^2) / 2 of the budget L |A|), crosses the
+    unlimited zone (cost 2 L^2) and speeds up beyond +L with the rest."""
+    L = 1.0e5
+    o64 = _kick_oracle(oracle_mod, L, 64)
+    o32 = _kick_oracle(oracle_mod, L, 32)
+    w0 = np.array([1.0, 1.5, 3.0, 10.0, 100.0]) * L
+    A = np.array([0.01, 1.0, 7.0, 50.0, 1e3]) * L
+    want = np.sqrt(w0 ** 2 + 2 * L * A)
+    for sign in (1.0, -1.0):
+        got = o64.kick(0, sign * w0, 0.0 * w0, 0.0 * w0, sign * A)
+        assert np.allclose(got, sign * want, rtol=1e-13)
+        got32 = o32.kick(0, sign * w0, 0.0 * w0, 0.0 * w0, sign * A)
+        assert np.allclose(got32, sign * want, rtol=3e-7)
+    # through the unlimited zone: from -b to beyond +L
+    b = np.array([1.2, 2.0, 5.0]) * L
+    A = np.array([20.0, 30.0, 60.0]) * L
+    rest = L * A - (b ** 2 - L ** 2) / 2 - 2 * L ** 2
+    assert np.all(rest > 0)
+    want = np.sqrt(L ** 2 + 2 * rest)
+    assert np.allclose(o64.kick(0, -b, 0 * b, 0 * b, A), want, rtol=1e-13)
+    # a kick too small to reach the zone slows the marker: w1^2 = w0^2 - 2 L |A|
+    b = np.array([3.0, 10.0]) * L
+    A = np.array([0.5, 20.0]) * L
+    want = -np.sqrt(b ** 2 - 2 * L * A)
+    assert np.allclose(o64.kick(0, -b, 0 * b, 0 * b, A), want, rtol=1e-13)
+    # below the limit at both ends of the step: unlimited leapfrog
+    assert o64.kick(0, np.array([0.2 * L]), np.array([0.1 * L]), np.array([0.0]),
+                    np.array([0.3 * L]))[0] == 0.5 * L
+
+
 def test_displacement_bounded_by_speed_limit(oracle_mod):
     """|dx| <= beta v dt <= v0 dt per step (Sec. II.B)."""
     spec, _ = inputs.small_gap_config()
