@@ -453,12 +453,15 @@ struct Sim {
     return mad32(kf, 0.693145751953125f, mad32(kf, 1.428606765330187e-06f, (t + t) * poly));
   }
 
-  // End speed m >= 0 along the force with D(m0, m) = T, root in [lo, hi].
-  static float kick_solve_mirror(float m0, float T, float lo, float hi, float p2) {
+  // End speed m >= 0 along the force with D(m0, m) = T, root in [lo, hi];
+  // speeding up (fwd), the upper end is m0 + T / s0 (s >= s0 along the way),
+  // with 1 / s0 from the reciprocal shared with 1 / (m0 + s0).
+  static float kick_solve_mirror(float m0, float T, float lo, float hi, float p2, bool fwd) {
     const float s0 = std::sqrt(mad32(m0, m0, p2));
     const float h0 = m0 + s0;
     const float rr = 1.0f / (s0 * h0);
     const float is0 = h0 * rr, ih0 = s0 * rr;
+    if (fwd) hi = mad32(T, is0, m0);
     const float X = (T * is0) * is0;
     const float c0 = m0 * is0;
     float m;
@@ -522,7 +525,7 @@ struct Sim {
         lo = q;
         hi = m0;
         sgn = -1.0f;
-        return g * (sgn * kick_solve_mirror(m0, T, lo, hi, p2));
+        return g * (sgn * kick_solve_mirror(m0, T, lo, hi, p2, false));
       }
     }
     if (w < q) {
@@ -532,13 +535,13 @@ struct Sim {
       W = W - reach;
       w = q;
     }
-    // limited, speeding up; s >= s(w) along the way bounds the end
+    // limited, speeding up
     m0 = w;
     T = W;
     lo = w;
-    hi = w + W / std::sqrt(mad32(w, w, p2));
+    hi = 0.0f;  // set by the solve
     sgn = 1.0f;
-    return g * (sgn * kick_solve_mirror(m0, T, lo, hi, p2));
+    return g * (sgn * kick_solve_mirror(m0, T, lo, hi, p2, true));
   }
 
   // Linear interpolation of the cumulative cross sections at eps.  Nodes sit

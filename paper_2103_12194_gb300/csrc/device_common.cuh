@@ -179,53 +179,10 @@ __device__ __forceinline__ double kick_tol<double>() {
   return 3.814697265625e-06;  // 2^-18
 }
 
-// End speed m >= 0 along the force of a speed-limited part of the kick:
-// D(m0, m) = T with D(a, b) = integral from a to b of sqrt(x^2 + p2) dx
-//          = [b s_b - a s_a + p2 log((b + s_b) / (a + s_a))] / 2,
-// root in [lo, hi] (T > 0 speeding up, T < 0 slowing down).  A third-order
-// series guess in X = T / s0^2 (beyond |X| = 1/2, sqrt(m0^2 + 2 T)), then
-// Halley steps (D' = s, D'' = m / s) kept inside the bracket.
-template <typename R>
-__device__ __forceinline__ R kick_solve(R m0, R T, R lo, R hi, R p2) {
-  const R s0 = r_sqrt(mad(m0, m0, p2));
-  const R h0 = m0 + s0;
-  const R rr = (R)1 / (s0 * h0);
-  const R is0 = h0 * rr, ih0 = s0 * rr;
-  const R X = (T * is0) * is0;
-  const R c0 = m0 * is0;
-  R m;
-  if (r_abs(X) <= (R)0.5) {
-    const R c3 = mad((R)4 * c0, c0, (R)-1) * (R)(1.0 / 6.0);
-    const R zh = X * mad(X, mad(X, c3, (R)-0.5 * c0), (R)1);
-    m = mad(s0, zh, m0);
-  } else {
-    m = r_sqrt(r_max((R)0, mad(m0, m0, T + T)));
-  }
-  m = r_min(r_max(m, lo), hi);
-  const R hm0s0 = (R)0.5 * (m0 * s0);
-  const R hp2 = (R)0.5 * p2;
-  const R tau = kick_tol<R>();
-  for (int it = 0; it < 24; ++it) {
-    const R s = r_sqrt(mad(m, m, p2));
-    const R lg = p2 > (R)0 ? r_logk((m + s) * ih0) : (R)0;
-    const R F = mad(hp2, lg, mad((R)0.5 * m, s, -hm0s0)) - T;
-    if (F > (R)0) hi = m;
-    else lo = m;
-    const R s2 = s * s;
-    const R dm = ((F + F) * s2) / mad(s2 + s2, s, -(F * m));
-    R mn = m - dm;
-    if (!(mn >= lo && mn <= hi)) mn = (R)0.5 * (lo + hi);
-    const R step = m - mn;
-    m = mn;
-    if (r_abs(step) <= tau * s) break;
-  }
-  return m;
-}
-
 // Speed-limited kick over one step of a species with a finite limit L
 // (Eq. slpicEOMv: dv_x/dt = beta(|v|) q E_x / m with E_x held at its gathered
-// value, v_y and v_z unchanged).  A = q E_x dt / m is the unlimited velocity
-// increment; returns the new v_x.
+// value, v_y and v_z unchanged), for the N slots a lane advances.  A is the
+// unlimited velocity increment q E_x dt / m; vx is replaced by the new v_x.
 //  - Below the limit at both ends of the step: the leapfrog kick v_x + A.
 //  - Otherwise the exact solution of the equation over the step.  In the
 //    time tau = integral of beta dt the motion is unlimited,
@@ -235,62 +192,139 @@ __device__ __forceinline__ R kick_solve(R m0, R T, R lo, R hi, R p2) {
 //    reaches W = L |A|.  Along the force the path has up to three parts:
 //    limited and slowing (w < -q), unlimited (|w| <= q, q^2 = L^2 - p2) and
 //    limited and speeding up (w > q); the end lies in the first part whose
-//    cost exhausts W.  Only + - * / sqrt (and fused multiply-adds in float)
-//    are used, so an FP32 restatement reproduces it bit for bit.
-template <typename R>
-__device__ __forceinline__ R limited_kick(R vx, R vy, R vz, R A, R L) {
+//    cost exhausts W.
+//  - In a limited part the end speed m >= 0 solves D(m0, m) = T, where
+//    D(a, b) = integral from a to b of sqrt(x^2 + p2) dx
+//            = [b s_b - a s_a + p2 log((b + s_b) / (a + s_a))] / 2
+//    and T = +W (speeding up) or -W (slowing down): a third-order series
+//    guess in X = T / s0^2 (beyond |X| = 1/2, sqrt(m0^2 + 2 T)), then Halley
+//    steps (D' = s, D'' = m / s) kept inside a bracket until a step is below
+//    kick_tol of the speed.
+// The slots take their Halley steps together, one step of every unfinished
+// slot per round, so that their dependency chains interleave; each slot's
+// arithmetic is that of a kick computed alone.  Only + - * / sqrt (and fused
+// multiply-adds in float) are used, so an FP32 restatement reproduces it bit
+// for bit.
+template <typename R, int N>
+__device__ __forceinline__ void limited_kick_n(R (&vx)[N], const R (&vy)[N], const R (&vz)[N],
+                                               const R (&A)[N], R L) {
   const R L2 = L * L;
-  const R p2 = mad(vy, vy, vz * vz);
-  const R vt = vx + A;
-  if (mad(vx, vx, p2) <= L2 && mad(vt, vt, p2) <= L2) return vt;
-  if (!(A != (R)0)) return vx;
-  const R g = A > (R)0 ? (R)1 : (R)-1;
-  R W = L * (g * A);
-  R w = g * vx;
-  const R q2 = L2 - p2;
-  const R q = q2 > (R)0 ? r_sqrt(q2) : (R)0;
-  R m0, T, lo, hi, sgn;
-  bool solved = false;
-  if (w < -q) {
-    // limited and slowing down: reaching the unlimited zone (or the axis,
-    // when p2 >= L2) costs D(q, |w|) >= L (|w| - q)
-    m0 = -w;
-    bool stay = W <= L * (m0 - q);
-    if (!stay) {
-      const R s0 = r_sqrt(mad(m0, m0, p2));
-      const R sq = q > (R)0 ? L : r_sqrt(p2);
-      R C1 = (R)0.5 * (m0 * s0 - q * sq);
-      if (p2 > (R)0) C1 = mad((R)0.5 * p2, r_logk((m0 + s0) / (q + sq)), C1);
-      stay = W < C1;
+  const R tau = kick_tol<R>();
+  R m[N], m0[N], T[N], lo[N], hi[N], p2[N], ih0[N], hm0s0[N], gs[N];
+  bool act[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    act[j] = false;
+    p2[j] = mad(vy[j], vy[j], vz[j] * vz[j]);
+    const R sp2 = mad(vx[j], vx[j], p2[j]);
+    const R vt = vx[j] + A[j];
+    if (sp2 <= L2 && mad(vt, vt, p2[j]) <= L2) {
+      vx[j] = vt;
+      continue;
+    }
+    if (!(A[j] != (R)0)) continue;
+    const R g = A[j] > (R)0 ? (R)1 : (R)-1;
+    R W = L * (g * A[j]);
+    R w = g * vx[j];
+    const R q2 = L2 - p2[j];
+    const R q = q2 > (R)0 ? r_sqrt(q2) : (R)0;
+    bool fwd = true, done = false;
+    R s0;
+    if (w < -q) {
+      // limited and slowing down: reaching the unlimited zone (or the axis,
+      // when p2 >= L2) costs D(q, |w|) >= L (|w| - q)
+      m0[j] = -w;
+      s0 = r_sqrt(sp2);
+      bool stay = W <= L * (m0[j] - q);
       if (!stay) {
-        W = W - C1;
-        w = -q;
+        const R sq = q > (R)0 ? L : r_sqrt(p2[j]);
+        R C1 = (R)0.5 * (m0[j] * s0 - q * sq);
+        if (p2[j] > (R)0) C1 = mad((R)0.5 * p2[j], r_logk((m0[j] + s0) / (q + sq)), C1);
+        stay = W < C1;
+        if (!stay) {
+          W = W - C1;
+          w = -q;
+        }
+      }
+      if (stay) {
+        T[j] = -W;
+        lo[j] = q;
+        hi[j] = m0[j];
+        gs[j] = -g;
+        fwd = false;
       }
     }
-    if (stay) {
-      T = -W;
-      lo = q;
-      hi = m0;
-      sgn = (R)-1;
-      solved = true;
+    if (fwd) {
+      if (w < q) {
+        // unlimited zone
+        const R reach = L * (q - w);
+        if (W <= reach) {
+          vx[j] = g * (w + W / L);
+          done = true;
+        } else {
+          W = W - reach;
+          w = q;
+        }
+      }
+      if (!done) {
+        // limited and speeding up
+        m0[j] = w;
+        s0 = w == g * vx[j] ? r_sqrt(sp2) : r_sqrt(mad(w, w, p2[j]));
+        T[j] = W;
+        lo[j] = w;
+        gs[j] = g;
+      }
+    }
+    if (done) continue;
+    // the solve's constants and its starting guess
+    const R h0 = m0[j] + s0;
+    const R rr = (R)1 / (s0 * h0);
+    const R is0 = h0 * rr;
+    ih0[j] = s0 * rr;
+    if (fwd) hi[j] = mad(T[j], is0, m0[j]);  // s >= s0 along the way
+    const R X = (T[j] * is0) * is0;
+    const R c0 = m0[j] * is0;
+    R mg;
+    if (r_abs(X) <= (R)0.5) {
+      const R c3 = mad((R)4 * c0, c0, (R)-1) * (R)(1.0 / 6.0);
+      const R zh = X * mad(X, mad(X, c3, (R)-0.5 * c0), (R)1);
+      mg = mad(s0, zh, m0[j]);
+    } else {
+      mg = r_sqrt(r_max((R)0, mad(m0[j], m0[j], T[j] + T[j])));
+    }
+    m[j] = r_min(r_max(mg, lo[j]), hi[j]);
+    hm0s0[j] = (R)0.5 * (m0[j] * s0);
+    act[j] = true;
+  }
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < N; ++j) any |= act[j];
+  for (int it = 0; it < 24 && any; ++it) {
+    any = false;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      if (!act[j]) continue;
+      const R s = r_sqrt(mad(m[j], m[j], p2[j]));
+      const R lg = p2[j] > (R)0 ? r_logk((m[j] + s) * ih0[j]) : (R)0;
+      const R F = mad((R)0.5 * p2[j], lg, mad((R)0.5 * m[j], s, -hm0s0[j])) - T[j];
+      if (F > (R)0) hi[j] = m[j];
+      else lo[j] = m[j];
+      const R s2 = s * s;
+      const R dm = ((F + F) * s2) / mad(s2 + s2, s, -(F * m[j]));
+      R mn = m[j] - dm;
+      if (!(mn >= lo[j] && mn <= hi[j])) mn = (R)0.5 * (lo[j] + hi[j]);
+      const R step = m[j] - mn;
+      m[j] = mn;
+      if (r_abs(step) <= tau * s) {
+        act[j] = false;
+        vx[j] = gs[j] * m[j];
+      }
+      any |= act[j];
     }
   }
-  if (!solved) {
-    if (w < q) {
-      // unlimited zone
-      const R reach = L * (q - w);
-      if (W <= reach) return g * (w + W / L);
-      W = W - reach;
-      w = q;
-    }
-    // limited and speeding up; s >= s(w) along the way bounds the end
-    m0 = w;
-    T = W;
-    lo = w;
-    hi = w + W / r_sqrt(mad(w, w, p2));
-    sgn = (R)1;
-  }
-  return g * (sgn * kick_solve(m0, T, lo, hi, p2));
+#pragma unroll
+  for (int j = 0; j < N; ++j)
+    if (act[j]) vx[j] = gs[j] * m[j];  // the iteration cap (the bracket holds the root)
 }
 
 // Direction with cos(theta) = 1 - 2 ua about x and azimuth 2 pi ub.

@@ -215,29 +215,31 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
   __syncthreads();
   volatile int* abort_flag = &cs.abort;
 
-  // descriptors of rounds m .. m + 3 (the fill of round m + 3 is loaded a
-  // round before the bulk loads that need it are issued)
   SegCursor cursor;
   cursor.seg = 0;
   cursor.q_begin = 1u;  // empty range: the first look-up searches
   cursor.q_end = 0u;
   cursor.n_tiles = 0u;
   cursor.fill = nullptr;
-  WarpTile d[4];
+  // descriptors of rounds m .. m + kPushStages (the bulk loads of a round
+  // are issued kPushStages - 1 rounds ahead, and its fill is read a round
+  // before that)
+  constexpr int kAhead = kPushStages - 1;
+  WarpTile d[kPushStages + 1];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j <= kPushStages; ++j) {
     d[j].valid = false;
     d[j].fill = 0u;
     d[j].sseg = 0;
     d[j].k = 0u;
   }
 #pragma unroll
-  for (int j = 0; j < 3; ++j)
+  for (int j = 0; j < kPushStages; ++j)
     if (j < n_rounds) d[j] = tile_of(r, cursor, q0 + j, warp);
   uint32_t phase = 0;    // parity bit per stage
   uint32_t pending = 0;  // stages with a bulk load not yet waited for
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
+  for (int j = 0; j < kAhead; ++j) {
     if (d[j].valid && d[j].fill) {
       if (lane == 0) load_tile<R>(r, d[j], stages + j * kSB, &bars[j]);
       pending |= 1u << j;
@@ -247,16 +249,16 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
   int cur_seg = -1;
   bool use_smem = false;
   for (int m = 0; m < n_rounds; ++m) {
-    // ---- 0. descriptors ahead; bulk loads of round m + 2 ---------------------
-    if (m + 3 < n_rounds) d[3] = tile_of(r, cursor, q0 + m + 3, warp);
-    const int sc = m % kPushStages;        // stage of round m
-    const int sn = (m + 2) % kPushStages;  // stage of round m + 2
+    // ---- 0. descriptors ahead; bulk loads of round m + kAhead ---------------
+    if (m + kPushStages < n_rounds) d[kPushStages] = tile_of(r, cursor, q0 + m + kPushStages, warp);
+    const int sc = m % kPushStages;             // stage of round m
+    const int sn = (m + kAhead) % kPushStages;  // stage of round m + kAhead
     const bool aborted = *abort_flag != 0;
-    if (m + 2 < n_rounds && d[2].valid && d[2].fill && !aborted) {
+    if (m + kAhead < n_rounds && d[kAhead].valid && d[kAhead].fill && !aborted) {
       if (lane == 0) {
         // the stage's last bulk stores (round m - 1) must have read it
         bulk_wait_read_all();
-        load_tile<R>(r, d[2], stages + sn * kSB, &bars[sn]);
+        load_tile<R>(r, d[kAhead], stages + sn * kSB, &bars[sn]);
       }
       pending |= 1u << sn;
     }
@@ -310,24 +312,6 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
         }
       }
       if (t.fill && ok) {
-        // slots past the fill are read (stage memory) but never used; their
-        // cell is taken as 0 so that the gather stays in range
-        int cell[kPerLane];
-        R off[kPerLane], vx[kPerLane], vy[kPerLane], vz[kPerLane], wj[kPerLane];
-        uint32_t id[kPerLane];
-        bool live[kPerLane];
-#pragma unroll
-        for (int j = 0; j < kPerLane; ++j) {
-          const int i = j * 32 + lane;
-          live[j] = i < (int)t.fill;
-          cell[j] = live[j] ? st_cell[i] : 0;
-          off[j] = st_off[i];
-          vx[j] = st_vx[i];
-          vy[j] = st_vy[i];
-          vz[j] = st_vz[i];
-          wj[j] = st_wj[i];
-          id[j] = st_id[i];
-        }
         unsigned long long* rho = use_smem ? s_rho : P.rho_acc[sp];
         const uint32_t step = r.istate[inst].step;
         const StepConsts<R>& K = consts<R>(P);
@@ -338,136 +322,168 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
         const bool electrons = sp == kElectron;
         const bool limited = vlim < (R)INFINITY;  // beta = 1 for an unlimited species
         const bool dep = P.field_mode == 1;       // deposit during the step
-
-        // ---- 4. advance the lane's slots ---------------------------------------
-        // straight-line over the kPerLane slots so that their dependency chains
-        // interleave
-        R a[kPerLane], b1[kPerLane];
+        // The lane's slots are advanced in kHalves passes of kPerHalf slots
+        // (lane l, pass h: slots (h kPerHalf + j) 32 + l), so that one pass's
+        // state fits the registers of a CTA of kPushMaxWarps warps.  Ranks of
+        // survivors and events run on across the passes, in slot order.
+#pragma unroll 1
+        for (int h = 0; h < kHalves; ++h) {
+          const int i0 = h * kPerHalf * 32;
+          if (i0 >= (int)t.fill) break;
+          // slots past the fill are read (stage memory) but never used; their
+          // cell is taken as 0 so that the gather stays in range
+          int cell[kPerHalf];
+          R off[kPerHalf], vx[kPerHalf], vy[kPerHalf], vz[kPerHalf], wj[kPerHalf];
+          uint32_t id[kPerHalf];
+          bool live[kPerHalf];
 #pragma unroll
-        for (int j = 0; j < kPerLane; ++j) {
-          // gather (linear between the cell's nodes)
-          const R E0 = __ldg(Enode + cell[j]), E1 = __ldg(Enode + cell[j] + 1);
-          a[j] = qmdt * (E0 + off[j] * (E1 - E0));
-        }
-        // speed-limited kick (limited_kick: leapfrog below the limit, the
-        // exact solution of Eq. slpicEOMv across and above it) and drift
-        // (beta of the post-kick speed); an unlimited species has beta = 1
-        if (limited) {
-#pragma unroll
-          for (int j = 0; j < kPerLane; ++j) vx[j] = limited_kick(vx[j], vy[j], vz[j], a[j], vlim);
-#pragma unroll
-          for (int j = 0; j < kPerLane; ++j)
-            b1[j] = beta_of(r_sqrt(vx[j] * vx[j] + vy[j] * vy[j] + vz[j] * vz[j]), vlim);
-        } else {
-#pragma unroll
-          for (int j = 0; j < kPerLane; ++j) {
-            vx[j] = vx[j] + a[j];
-            b1[j] = (R)1;
+          for (int j = 0; j < kPerHalf; ++j) {
+            const int i = i0 + j * 32 + lane;
+            live[j] = i < (int)t.fill;
+            cell[j] = live[j] ? st_cell[i] : 0;
+            off[j] = st_off[i];
+            vx[j] = st_vx[i];
+            vy[j] = st_vy[i];
+            vz[j] = st_vz[i];
+            wj[j] = st_wj[i];
+            id[j] = st_id[i];
           }
-        }
+          // ---- 4. advance the slots -------------------------------------------
+          R a[kPerHalf], b1[kPerHalf];
 #pragma unroll
-        for (int j = 0; j < kPerLane; ++j) {
-          R o = off[j] + b1[j] * (vx[j] * dtdx);
-          const R fl = r_floor(o);
-          int c = cell[j] + (int)fl;
-          o = o - fl;
-          if (o >= (R)1) {
-            o = (R)0;
-            c += 1;
+          for (int j = 0; j < kPerHalf; ++j) {
+            // gather (linear between the cell's nodes)
+            const R E0 = __ldg(Enode + cell[j]), E1 = __ldg(Enode + cell[j] + 1);
+            a[j] = qmdt * (E0 + off[j] * (E1 - E0));
           }
-          cell[j] = c;
-          off[j] = o;
-        }
-        // ---- 5. electrodes (rare, out of line), candidate draws, deposit -------
-        bool alive[kPerLane], event[kPerLane];
+          // speed-limited kick (limited_kick_n: leapfrog below the limit, the
+          // exact solution of Eq. slpicEOMv across and above it) and drift
+          // (beta of the post-kick speed); an unlimited species has beta = 1
+          if (limited) {
 #pragma unroll
-        for (int j = 0; j < kPerLane; ++j) {
-          alive[j] = live[j] && (uint32_t)cell[j] < N;
-          event[j] = false;
-        }
+            for (int j = 0; j < kPerHalf; ++j) {
+              R x1[1] = {vx[j]};
+              const R y1[1] = {vy[j]}, z1[1] = {vz[j]}, a1[1] = {a[j]};
+              limited_kick_n<R, 1>(x1, y1, z1, a1, vlim);
+              vx[j] = x1[0];
+            }
 #pragma unroll
-        for (int j = 0; j < kPerLane; ++j) {
-          if (live[j] && !alive[j])
-            event[j] = absorb<R>(P, sp, cell[j] < 0 ? 0 : 1, wj[j], id[j], step, cs.s_acc,
-                                 vx[j], vy[j], vz[j]);
-        }
-        if (electrons) {
-          const uint32_t key2 = P.key2;
+            for (int j = 0; j < kPerHalf; ++j)
+              b1[j] = beta_of(r_sqrt(vx[j] * vx[j] + vy[j] * vy[j] + vz[j] * vz[j]), vlim);
+          } else {
 #pragma unroll
-          for (int j = 0; j < kPerLane; ++j) {
-            const uint2 rr = philox2x32_10(make_uint2(id[j], step), key2);
-            event[j] = alive[j] && uniform01r<R>(rr.x) < P0;
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < kPerLane; ++j) {
-          // deposit w_p = beta w_j now unless a collision may change v
-          if (dep && alive[j] && !event[j]) {
-            const long long Q = fixed_charge(b1[j] * wj[j], wscale);
-            const long long right = right_share(Q, off[j]);
-            atomicAdd(rho + cell[j], (unsigned long long)(Q - right));
-            atomicAdd(rho + cell[j] + 1, (unsigned long long)right);
-          }
-        }
-
-        // ---- 6. rank survivors and events ------------------------------------
-        uint32_t b_alive[kPerLane], b_event[kPerLane];
-        uint32_t pre_alive[kPerLane], pre_event[kPerLane];
-#pragma unroll
-        for (int j = 0; j < kPerLane; ++j) {
-          b_alive[j] = __ballot_sync(0xFFFFFFFFu, alive[j]);
-          b_event[j] = __ballot_sync(0xFFFFFFFFu, event[j]);
-          pre_alive[j] = n_surv;
-          pre_event[j] = n_event;
-          n_surv += __popc(b_alive[j]);
-          n_event += __popc(b_event[j]);
-        }
-        // ---- 7. events: emissions to staging, candidates to the queue ----------
-#pragma unroll
-        for (int j = 0; j < kPerLane; ++j) {
-          if (event[j]) {
-            const uint32_t e = pre_event[j] + (uint32_t)__popc(b_event[j] & lanemask_lt);
-            if (electrons) {
-              // the candidate's slot after compaction = its rank among survivors
-              const uint32_t r_a = pre_alive[j] + (uint32_t)__popc(b_alive[j] & lanemask_lt);
-              S.cand[tbase + e] = (uint16_t)r_a;
-            } else if (dep) {
-              stage_emission<R>(P, tbase + e, wj[j]);
-            } else {
-              stage_emission<R, false>(P, tbase + e, wj[j]);
+            for (int j = 0; j < kPerHalf; ++j) {
+              vx[j] = vx[j] + a[j];
+              b1[j] = (R)1;
             }
           }
-        }
-        // ---- 8. write the survivors back to the stage: in place, or compacted
-        // in order when a marker left (every lane holds its slots in registers,
-        // so one warp barrier separates the reads from the writes)
-        compact = n_surv != t.fill;
-        if (!compact) {
 #pragma unroll
-          for (int j = 0; j < kPerLane; ++j) {
-            const int i = j * 32 + lane;
-            if (alive[j]) {
-              st_cell[i] = cell[j];
-              st_off[i] = off[j];
-              st_vx[i] = vx[j];
+          for (int j = 0; j < kPerHalf; ++j) {
+            R o = off[j] + b1[j] * (vx[j] * dtdx);
+            const R fl = r_floor(o);
+            int c = cell[j] + (int)fl;
+            o = o - fl;
+            if (o >= (R)1) {
+              o = (R)0;
+              c += 1;
+            }
+            cell[j] = c;
+            off[j] = o;
+          }
+          // ---- 5. electrodes (rare, out of line), candidate draws, deposit -----
+          bool alive[kPerHalf], event[kPerHalf];
+#pragma unroll
+          for (int j = 0; j < kPerHalf; ++j) {
+            alive[j] = live[j] && (uint32_t)cell[j] < N;
+            event[j] = false;
+          }
+#pragma unroll
+          for (int j = 0; j < kPerHalf; ++j) {
+            if (live[j] && !alive[j])
+              event[j] = absorb<R>(P, sp, cell[j] < 0 ? 0 : 1, wj[j], id[j], step, cs.s_acc,
+                                   vx[j], vy[j], vz[j]);
+          }
+          if (electrons) {
+            const uint32_t key2 = P.key2;
+#pragma unroll
+            for (int j = 0; j < kPerHalf; ++j) {
+              const uint2 rr = philox2x32_10(make_uint2(id[j], step), key2);
+              event[j] = alive[j] && uniform01r<R>(rr.x) < P0;
             }
           }
-        } else {
+#pragma unroll
+          for (int j = 0; j < kPerHalf; ++j) {
+            // deposit w_p = beta w_j now unless a collision may change v
+            if (dep && alive[j] && !event[j]) {
+              const long long Q = fixed_charge(b1[j] * wj[j], wscale);
+              const long long right = right_share(Q, off[j]);
+              atomicAdd(rho + cell[j], (unsigned long long)(Q - right));
+              atomicAdd(rho + cell[j] + 1, (unsigned long long)right);
+            }
+          }
+          // ---- 6. rank survivors and events ----------------------------------
+          uint32_t b_alive[kPerHalf], b_event[kPerHalf];
+          uint32_t pre_alive[kPerHalf], pre_event[kPerHalf];
+#pragma unroll
+          for (int j = 0; j < kPerHalf; ++j) {
+            b_alive[j] = __ballot_sync(0xFFFFFFFFu, alive[j]);
+            b_event[j] = __ballot_sync(0xFFFFFFFFu, event[j]);
+            pre_alive[j] = n_surv;
+            pre_event[j] = n_event;
+            n_surv += __popc(b_alive[j]);
+            n_event += __popc(b_event[j]);
+          }
+          // ---- 7. events: emissions to staging, candidates to the queue --------
+#pragma unroll
+          for (int j = 0; j < kPerHalf; ++j) {
+            if (event[j]) {
+              const uint32_t e = pre_event[j] + (uint32_t)__popc(b_event[j] & lanemask_lt);
+              if (electrons) {
+                // the candidate's slot after compaction = its rank among survivors
+                const uint32_t r_a = pre_alive[j] + (uint32_t)__popc(b_alive[j] & lanemask_lt);
+                S.cand[tbase + e] = (uint16_t)r_a;
+              } else if (dep) {
+                stage_emission<R>(P, tbase + e, wj[j]);
+              } else {
+                stage_emission<R, false>(P, tbase + e, wj[j]);
+              }
+            }
+          }
+          // ---- 8. write the pass's survivors back to the stage: in place while
+          // no marker of the tile has left, else compacted in order (every lane
+          // holds the pass's slots in registers, so one warp barrier separates
+          // the reads from the writes; the compacted slots lie below the pass's
+          // own, which every lane has read)
+          const uint32_t live_so_far = min(t.fill, (uint32_t)(i0 + kPerHalf * 32));
+          if (n_surv == live_so_far) {
+#pragma unroll
+            for (int j = 0; j < kPerHalf; ++j) {
+              const int i = i0 + j * 32 + lane;
+              if (alive[j]) {
+                st_cell[i] = cell[j];
+                st_off[i] = off[j];
+                st_vx[i] = vx[j];
+              }
+            }
+          } else {
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < kPerHalf; ++j) {
+              if (alive[j]) {
+                const uint32_t r_a = pre_alive[j] + (uint32_t)__popc(b_alive[j] & lanemask_lt);
+                st_cell[r_a] = cell[j];
+                st_off[r_a] = off[j];
+                st_vx[r_a] = vx[j];
+                st_vy[r_a] = vy[j];
+                st_vz[r_a] = vz[j];
+                st_wj[r_a] = wj[j];
+                st_id[r_a] = id[j];
+              }
+            }
+          }
           __syncwarp();
-#pragma unroll
-          for (int j = 0; j < kPerLane; ++j) {
-            if (alive[j]) {
-              const uint32_t r_a = pre_alive[j] + (uint32_t)__popc(b_alive[j] & lanemask_lt);
-              st_cell[r_a] = cell[j];
-              st_off[r_a] = off[j];
-              st_vx[r_a] = vx[j];
-              st_vy[r_a] = vy[j];
-              st_vz[r_a] = vz[j];
-              st_wj[r_a] = wj[j];
-              st_id[r_a] = id[j];
-            }
-          }
         }
+        compact = n_surv != t.fill;
       }
       // ---- 9. store the tile to its own slots ---------------------------------
       // position and vx change every step; vy, vz, w_j and the id only move
@@ -497,9 +513,9 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
       }
     }
 #pragma unroll
-    for (int j = 0; j < 3; ++j) d[j] = d[j + 1];
-    d[3].valid = false;
-    d[3].fill = 0u;
+    for (int j = 0; j < kPushStages; ++j) d[j] = d[j + 1];
+    d[kPushStages].valid = false;
+    d[kPushStages].fill = 0u;
   }
   if (n_rounds > 0) flush_segment(r, cur_seg, s_rho, cs, use_smem);
   if (lane == 0) {

@@ -20,8 +20,11 @@ constexpr uint32_t kSeedStep = 0xFFFFFFFFu;
 // shared-memory stages.
 constexpr int kTile = 128;
 constexpr int kPerLane = kTile / 32;
-constexpr int kPushMaxWarps = 16;
-constexpr int kPushStages = 3;
+constexpr int kPushMaxWarps = 24;
+constexpr int kPushStages = 2;
+// The particle kernel advances a lane's kPerLane slots in kHalves passes.
+constexpr int kHalves = 2;
+constexpr int kPerHalf = kPerLane / kHalves;
 // Shared-memory stage of one tile: cell and id (4 bytes each), then the five
 // real streams (off, vx, vy, vz, w_j) of sizeof(R) bytes.
 template <typename R>

@@ -252,8 +252,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(DeviceRefs r, long l
           a[j] = qmdt * (E0 + off[j] * (E1 - E0));
         }
         if (limited) {
-#pragma unroll
-          for (int j = 0; j < kPerLane; ++j) vx[j] = limited_kick(vx[j], vy[j], vz[j], a[j], vlim);
+          limited_kick_n<R, kPerLane>(vx, vy, vz, a, vlim);
 #pragma unroll
           for (int j = 0; j < kPerLane; ++j)
             b1[j] = beta_of(r_sqrt(vx[j] * vx[j] + vy[j] * vy[j] + vz[j] * vz[j]), vlim);
