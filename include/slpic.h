@@ -363,8 +363,24 @@ int slpic_paschen_bisect(slpic_ctx* ctx, const slpic_paschen_spec* spec, double*
 int slpic_ion_trend(slpic_ctx* ctx, int64_t steps_per_window, int n_windows, double* means,
                     int* above);
 
+/* Multiplication per ion transit (Sec. V: the population over windows of
+ * one ion crossing time sqrt(2 M d / (e E))).  Advances every instance by
+ * n_windows windows of steps_per_window steps (the single-CTA path while the
+ * stores are small, then the batched kernels) and writes:
+ * - see [n_inst * n_windows] (instance-major): the flux weight of the
+ *   electrons emitted at the cathode in each window (the sum of their w_j,
+ *   Eq. j), from the FP64 running totals the step keeps on the device;
+ * - M [n_inst * (n_windows - 1)] (may be NULL): the multiplication of each
+ *   window over the one before, see_k / see_{k-1} (NaN after a window with
+ *   no emission).
+ * Below breakdown M < 1 and the emission dies out; above it M > 1.  The
+ * caller sizes the stores for the growth it expects: a store that
+ * overflows ends the call with SLPIC_ERR_CAPACITY, as slpic_step does. */
+int slpic_multiplication(slpic_ctx* ctx, int64_t steps_per_window, int n_windows, double* see,
+                         double* M);
+
 /* Launch shape of the step: warps per CTA of the particle kernel (a
- * multiple of 4, at most 16; each warp owns a 128-slot tile) and CTAs per
+ * multiple of 4, at most 24; each warp owns a 128-slot tile) and CTAs per
  * SM of the collision kernel (1..32).  While the warps' stages leave room
  * for the largest instance's charge grid in shared memory the kernel
  * deposits there; with more warps it deposits to global memory.  The

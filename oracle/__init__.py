@@ -297,6 +297,19 @@ class Oracle:
         lib().oracle_constants(self._h, _ptr(out))
         return {"P0": out[0], "vb_cap": out[1], "ndt": out[2]}
 
+    def multiplication(self, steps_per_window, n_windows):
+        """Multiplication per ion transit (Sec. V): the flux weight of the
+        electrons emitted at the cathode in each of n_windows windows of
+        steps_per_window steps, and the ratio of each window's to the one
+        before (NaN after a window with no emission).  Steps the oracle."""
+        start = len(self.history())
+        self.step(int(steps_per_window) * int(n_windows))
+        w = self.history()["w_see"][start:].reshape(int(n_windows), int(steps_per_window))
+        see = w.sum(axis=1)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            M = np.where(see[:-1] > 0, see[1:] / np.where(see[:-1] > 0, see[:-1], 1.0), np.nan)
+        return see, M
+
     def kick(self, species, vx, vy, vz, A):
         """New v_x after one step's kick for arrays of velocities and
         unlimited increments A = q E_x dt / m (the oracle's kick, in its

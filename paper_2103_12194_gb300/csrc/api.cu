@@ -1766,6 +1766,57 @@ extern "C" int slpic_paschen_bisect(slpic_ctx* c, const slpic_paschen_spec* ps, 
 // ---------------------------------------------------------------------------
 // The paper's breakdown test (Sec. V): the trend of the ion population.
 // ---------------------------------------------------------------------------
+// Advance every instance by n steps: the single-CTA path while it applies,
+// then the batched kernels.
+int advance(slpic_ctx* c, int64_t n) {
+  for (int64_t done = 0; done < n;) {
+    int64_t k = 0;
+    if (int rc = run_small(c, n - done, &k)) return rc;
+    if (k == 0) {
+      k = n - done;
+      if (int rc = slpic_step(c, k)) return rc;
+    }
+    done += k;
+  }
+  return SLPIC_OK;
+}
+
+extern "C" int slpic_multiplication(slpic_ctx* c, int64_t steps_per_window, int n_windows,
+                                    double* see, double* M) {
+  if (!c) return SLPIC_ERR_INVALID_ARG;
+  if (!see || steps_per_window < 1 || n_windows < 1)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "multiplication: need see, steps_per_window >= 1 "
+                                          "and n_windows >= 1");
+  if (int rc = prepare(c)) return rc;
+  const int n = c->n_inst;
+  // flux weight emitted at the cathode so far, from the step's FP64 totals
+  std::vector<double> w0(n), w1(n);
+  auto read_see = [&](std::vector<double>& out) -> int {
+    for (int i = 0; i < n; ++i) {
+      slpic_tallies t;
+      if (int rc = slpic_read_tallies(c, i, &t)) return rc;
+      out[i] = t.w_see;
+    }
+    return SLPIC_OK;
+  };
+  if (int rc = read_see(w0)) return rc;
+  for (int w = 0; w < n_windows; ++w) {
+    if (int rc = advance(c, steps_per_window)) return rc;
+    if (int rc = read_see(w1)) return rc;
+    for (int i = 0; i < n; ++i) see[(size_t)i * n_windows + w] = w1[i] - w0[i];
+    w0 = w1;
+  }
+  if (M) {
+    for (int i = 0; i < n; ++i) {
+      const double* S = see + (size_t)i * n_windows;
+      for (int k = 1; k < n_windows; ++k)
+        M[(size_t)i * (n_windows - 1) + k - 1] =
+            S[k - 1] > 0.0 ? S[k] / S[k - 1] : std::numeric_limits<double>::quiet_NaN();
+    }
+  }
+  return SLPIC_OK;
+}
+
 extern "C" int slpic_ion_trend(slpic_ctx* c, int64_t steps_per_window, int n_windows,
                                double* means, int* above) {
   if (!c) return SLPIC_ERR_INVALID_ARG;

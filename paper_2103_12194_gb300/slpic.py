@@ -117,6 +117,7 @@ def lib():
         "slpic_set_cross_sections_levels": ([vp, i32, i32, i32, i32, vp, i32, vp, vp, vp,
                                              f64], i32),
         "slpic_ion_trend": ([vp, i64, i32, vp, vp], i32),
+        "slpic_multiplication": ([vp, i64, i32, vp, vp], i32),
         "slpic_set_launch_shape": ([vp, i32, i32], i32),
         "slpic_get_launch_shape": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
         "slpic_autotune": ([vp, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
@@ -399,6 +400,14 @@ class Simulation:
         self._ck(self._L.slpic_ion_trend(self._h, int(steps_per_window), int(n_windows),
                                          _ptr(means), _ptr(above)))
         return means, above.astype(bool)
+
+    def multiplication(self, steps_per_window, n_windows):
+        """slpic_multiplication: (see[n_inst, n_windows], M[n_inst, n_windows - 1])."""
+        see = np.empty((self.n_instances, int(n_windows)))
+        M = np.empty((self.n_instances, max(int(n_windows) - 1, 0)))
+        self._ck(self._L.slpic_multiplication(self._h, int(steps_per_window), int(n_windows),
+                                              _ptr(see), _ptr(M)))
+        return see, M
 
     def set_launch_shape(self, push_warps, collide_ctas_per_sm):
         self._ck(self._L.slpic_set_launch_shape(self._h, int(push_warps),

@@ -6,7 +6,12 @@
 - The ion-population trend (stepping over 30 ion crossing times) classifies
   voltages the same way as the Townsend gain G >= 1. The voltages are well
   away from V_b.
+- With the paper's setup, the trend classifies every seed as the oracle's
+  own trend does, and the ions per window agree with the oracle's within two
+  standard errors over 16 seeds a side.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -102,3 +107,53 @@ def test_pic_and_slpic_classify_alike(slpic):
         got[pic] = (list(above), means)
         sim.close()
     assert got[False][0] == got[True][0] == [False, True], got
+
+
+def test_ion_trend_matches_oracle_over_seeds(slpic):
+    """Sec. V with the paper's setup (Sec. IV): 100 electrons at rest at the
+    cathode, the Eq. sey yield, five processes, v_lim = v0, dt = dx / v0;
+    1 Torr cm, 96 cells, 30 ion crossing times in 15 windows.  Below
+    breakdown (115 V) and above (260 V), 16 seeds on the GPU and 16 in the
+    oracle: every seed is classified alike on both sides, and the live ions
+    summed over the windows every run completed agree within two standard
+    errors.  A run whose live markers pass 20000 stops as above, on both
+    sides."""
+    from . import oracle_ensemble as ens
+    table_levels, cells, n_runs, n_win = 3, 96, 16, 15
+    spw = 60 * cells // n_win
+    volts = (115.0, 260.0)
+    stop = 20000
+
+    def kw(V, seed, instance=0):
+        v0 = inputs.ion_speed(V)
+        return dict(n_cells=cells, V=V, pd_torr_cm=1.0, gamma_se=0.07, field_mode=0,
+                    vlim_e=v0, dt=0.01 / cells / v0, seed=seed, instance=instance,
+                    table_levels=table_levels, emission_model=1)
+
+    sim = slpic.Simulation(len(volts) * n_runs)
+    for a, V in enumerate(volts):
+        for k in range(n_runs):
+            i = a * n_runs + k
+            spec = ens._spec(kw(V, 4000 + i, instance=i))
+            # the trend stops an instance past a third of its smaller store
+            sim.configure(i, spec, capacity=(3 * stop, 3 * stop))
+            sim.seed(i, slpic.ELECTRON, 100, slpic.SEED_REST)
+    means, above = sim.ion_trend(spw, n_win)
+    sim.close()
+    ref = ens.pool_map(ens.ion_trend, [(kw(V, 8000 + 53 * a + k), 100, spw, n_win, stop)
+                                       for a, V in enumerate(volts) for k in range(n_runs)])
+    r_means = np.array([m for m, _ in ref]).reshape(len(volts), n_runs, n_win)
+    r_above = np.array([g for _, g in ref]).reshape(len(volts), n_runs)
+    g_means = means.reshape(len(volts), n_runs, n_win)
+    g_above = above.reshape(len(volts), n_runs)
+    assert not g_above[0].any() and not r_above[0].any(), (g_above, r_above)
+    assert g_above[1].all() and r_above[1].all(), (g_above, r_above)
+    for a in range(len(volts)):
+        done = (g_means[a] >= 0).all(axis=0) & (r_means[a] >= 0).all(axis=0)
+        n_done = int(np.argmin(done)) if not done.all() else n_win
+        assert n_done >= 1, a
+        g_sum = g_means[a][:, :n_done].sum(axis=1)
+        r_sum = r_means[a][:, :n_done].sum(axis=1)
+        d = abs(g_sum.mean() - r_sum.mean())
+        s = math.hypot(g_sum.std(ddof=1), r_sum.std(ddof=1)) / math.sqrt(n_runs)
+        assert d <= 2.0 * s, (volts[a], n_done, g_sum.mean(), r_sum.mean(), s)

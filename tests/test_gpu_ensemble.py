@@ -1,0 +1,191 @@
+"""Long-run ensemble quantities on the GPU against the FP64 oracle: the
+Townsend coefficient alpha(E/N), the multiplication per ion transit and the
+breakdown voltage (Sec. II.A, Townsend criterion; Sec. V), each over at least
+16 independent seeds per side.
+
+The two sides run the same physics in different precisions and draw
+different seeds, so single runs differ; their means agree within two
+standard errors of the difference (each side's standard error from the
+scatter of its runs).  The oracle runs on a process pool of the host's
+cores.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2103_12194_gb300 import inputs
+
+from . import oracle_ensemble as ens
+
+pytestmark = pytest.mark.gpu
+
+N_RUNS = 16
+
+
+@pytest.fixture(scope="module")
+def slpic():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_12194_gb300 import build
+    build.build()
+    from paper_2103_12194_gb300 import slpic as mod
+    return mod
+
+
+def se(x):
+    x = np.asarray(x, float)
+    return x.std(ddof=1) / math.sqrt(x.size)
+
+
+def agree(a, b):
+    """|mean a - mean b| <= 2 standard errors of the difference."""
+    d = abs(np.mean(a) - np.mean(b))
+    return d <= 2.0 * math.hypot(se(a), se(b)), (np.mean(a), np.mean(b), se(a), se(b))
+
+
+def gap_kw(pd, cells, V, seed, instance=0, gamma=0.0, **extra):
+    # d = 1 cm, imposed uniform field, v_lim = 4 sqrt(2 e V / M), dt = dx / v_lim
+    kw = dict(n_cells=cells, V=V, pd_torr_cm=pd, gamma_se=gamma, field_mode=0, seed=seed,
+              instance=instance)
+    kw.update(extra)
+    return kw
+
+
+def test_townsend_alpha_matches_oracle_within_two_sigma(slpic):
+    """alpha(E/N) at three reduced fields (1 Torr cm; 150, 200 and 260 V over
+    1 cm): avalanches from electrons at rest at the cathode, no emission;
+    the flux weight reaching the anode per seed electron is e^(alpha d)."""
+    volts = (150.0, 200.0, 260.0)
+    n_gpu, n_ref = 1000, 100
+    sim = slpic.Simulation(len(volts) * N_RUNS)
+    for a, V in enumerate(volts):
+        for k in range(N_RUNS):
+            i = a * N_RUNS + k
+            sim.configure(i, inputs.gap_spec(**gap_kw(1.0, 128, V, seed=1000 + i, instance=i)),
+                          capacity=(1 << 19, 1 << 19))
+            sim.seed(i, slpic.ELECTRON, n_gpu, slpic.SEED_REST)
+    for _ in range(400):
+        sim.step(64)
+        if all(sim.count(i, 0) == 0 for i in range(sim.n_instances)):
+            break
+    gpu = np.array([sim.tallies(i)["w_abs"][0][1] / n_gpu
+                    for i in range(sim.n_instances)]).reshape(len(volts), N_RUNS)
+    sim.close()
+    ref = np.array(ens.pool_map(ens.anode_electrons_per_seed,
+                                [(gap_kw(1.0, 128, V, seed=5000 + 97 * a + k), n_ref)
+                                 for a, V in enumerate(volts) for k in range(N_RUNS)]))
+    ref = ref.reshape(len(volts), N_RUNS)
+    alpha = []
+    for a in range(len(volts)):
+        ok, info = agree(gpu[a], ref[a])
+        assert ok, (volts[a], info)
+        alpha.append(math.log(gpu[a].mean()) / 0.01)
+    # alpha grows with E/N, and the three fields are distinct regimes
+    assert alpha[0] < alpha[1] < alpha[2]
+    assert gpu[2].mean() > 2.5 * gpu[0].mean()
+
+
+def test_multiplication_per_ion_transit_matches_oracle_within_two_sigma(slpic):
+    """Sec. V: electrons at rest at the cathode, gamma = 0.07, windows of one
+    ion crossing time (8 x 128 steps here).  Per run the multiplication over
+    windows 2..4 (after the first transit) is the ratio of their emitted
+    weight to that of windows 1..3; its mean over runs agrees, and so does
+    the emitted weight per seed in each window."""
+    V, n_win, spw = 165.0, 5, 8 * 128
+    n_gpu, n_ref = 2000, 400
+    sim = slpic.Simulation(N_RUNS)
+    for k in range(N_RUNS):
+        sim.configure(k, inputs.gap_spec(**gap_kw(1.0, 128, V, seed=2000 + k, instance=k,
+                                                  gamma=ens.GAMMA)),
+                      capacity=(1 << 20, 1 << 21))
+        sim.seed(k, slpic.ELECTRON, n_gpu, slpic.SEED_REST)
+    see, M = sim.multiplication(spw, n_win)
+    sim.close()
+    assert np.allclose(M, see[:, 1:] / see[:, :-1])
+    gpu = see / n_gpu
+    ref = np.array(ens.pool_map(ens.multiplication,
+                                [(gap_kw(1.0, 128, V, seed=7000 + k, gamma=ens.GAMMA), n_ref,
+                                  spw, n_win) for k in range(N_RUNS)]))
+
+    def pooled(s):
+        return s[:, 2:].sum(axis=1) / s[:, 1:-1].sum(axis=1)
+
+    m_gpu, m_ref = pooled(gpu), pooled(ref)
+    ok, info = agree(m_gpu, m_ref)
+    assert ok, info
+    assert 0.3 < m_gpu.mean() < 0.95  # below breakdown: the emission dies out
+    for w in range(n_win):
+        ok, info = agree(gpu[:, w], ref[:, w])
+        assert ok, (w, info)
+
+
+def test_breakdown_voltage_matches_oracle_crossing(slpic):
+    """Sec. V breakdown voltages at three pd points (0.6, 1 and 3 Torr cm):
+    the batched bisection's bracket against the oracle's G = 1 crossing,
+    found from its mean gains at 7 % either side of the bracket (ln G is
+    linear in V over that span), with the crossing's standard error from the
+    gains' scatter.  The bracket's centre lies within two standard errors
+    (both sides) plus half the bracket of the oracle's crossing."""
+    points = ((0.6, 64), (1.0, 128), (3.0, 256))
+    n_v, n_seed = 4, 2000
+    sim = slpic.Simulation(len(points) * n_v)
+    for p, (pd, cells) in enumerate(points):
+        for j in range(n_v):
+            i = p * n_v + j
+            sim.configure(i, inputs.gap_spec(**gap_kw(pd, cells, 300.0, seed=3000 + i,
+                                                      instance=i, gamma=ens.GAMMA)),
+                          capacity=(256 * n_seed, 512 * n_seed))
+    lo, hi, _ = sim.paschen_bisect([100.0] * 3, [500.0] * 3, n_v=n_v, rounds=3, n_seed=n_seed,
+                                   e0=1.0, vlim_factor=4.0)
+    sim.close()
+    n_ref, n_b = 200, 8
+    args = []
+    for p, (pd, cells) in enumerate(points):
+        mid = 0.5 * (lo[p] + hi[p])
+        for f in (0.93, 1.07):
+            for b in range(n_b):
+                args.append((gap_kw(pd, cells, f * mid, seed=9000 + 131 * p + 17 * b +
+                                    (0 if f < 1 else 7)), n_ref))
+    g = np.array(ens.pool_map(ens.gain, args)).reshape(len(points), 2, n_b)
+    for p in range(len(points)):
+        mid = 0.5 * (lo[p] + hi[p])
+        v1, v2 = 0.93 * mid, 1.07 * mid
+        m1, m2 = g[p, 0].mean(), g[p, 1].mean()
+        assert m1 < 1.0 < m2, (points[p], lo[p], hi[p], m1, m2)
+        l1, l2 = math.log(m1), math.log(m2)
+        s1, s2 = se(g[p, 0]) / m1, se(g[p, 1]) / m2  # standard errors of ln G
+        slope = (l2 - l1) / (v2 - v1)
+        vb = v1 - l1 / slope
+        # crossing error from the two ln G errors (linear interpolation)
+        w1, w2 = (v2 - vb) / (v2 - v1), (vb - v1) / (v2 - v1)
+        s_ref = math.hypot(w1 * s1, w2 * s2) / slope
+        # the GPU's gains carry the same relative scatter at 2000 seeds
+        s_gpu = 0.5 * (s1 + s2) * math.sqrt(n_ref / n_seed) / slope
+        tol = 2.0 * math.hypot(s_ref, s_gpu) + 0.5 * (hi[p] - lo[p])
+        assert abs(mid - vb) <= tol, (points[p], lo[p], hi[p], vb, s_ref, s_gpu)
+
+
+def test_multiplication_windows_count_ion_arrivals(slpic, oracle_mod):
+    """slpic_multiplication's windows on a case with a closed form: ions at
+    rest in a vacuum gap, gamma = 1, so each window's emitted weight is the
+    number of ions whose leapfrog arrival step falls in it.  The GPU equals
+    the FP32 mirror exactly, and the closed form to within two ions per
+    window (an FP32 position on an arrival boundary may land a step early or
+    late)."""
+    from .test_oracle_pins import ion_arrival_case
+    spec, ions, arrive = ion_arrival_case()
+    spw, n_win = 100, 5
+    sim = slpic.Simulation(1)
+    sim.configure(0, spec, capacity=(1 << 16, 1 << 16))
+    sim.load(0, 1, ions)
+    see, M = sim.multiplication(spw, n_win)
+    sim.close()
+    ref = oracle_mod.Oracle(spec, precision=32)
+    ref.load(1, ions)
+    see32, _ = ref.multiplication(spw, n_win)
+    assert np.array_equal(see[0], see32)
+    want = np.bincount(arrive // spw, minlength=n_win)[:n_win].astype(float)
+    assert np.abs(see[0] - want).max() <= 2
+    assert np.allclose(M[0, :3], see[0, 1:4] / see[0, :3])

@@ -12,7 +12,10 @@ launch. Bars:
   limit of tiles, at the same step for every instance of a batch, and the
   batched path carries on from there with the same results;
 - the paper's ion-population test gives the same window means with and
-  without it.
+  without it;
+- against the oracle's FP32 mirror directly: many vacuum steps bit for bit,
+  and one dense step with every collision process (counts, ids and cells
+  bit-exact, velocities after scattering to 1e-5).
 """
 import math
 
@@ -208,3 +211,63 @@ def test_ion_trend_is_the_same_with_and_without_the_small_path(slpic):
     assert np.array_equal(m1[ok], m0[ok])
     for j in np.flatnonzero(ok):
         assert t1[j].tobytes() == t0[j].tobytes()
+
+
+def test_small_path_matches_fp32_mirror_in_vacuum(slpic, oracle_mod):
+    """No gas, imposed field, emission on: every operation of the step is
+    + - * / sqrt, so the single-CTA path and the FP32 mirror agree bit for bit
+    over many steps (speed-limited electrons, ions reaching the cathode,
+    emitted electrons, compaction)."""
+    from .test_gpu_parity import assert_same_markers
+    spec = inputs.gap_spec(n_cells=219, V=170.0, pd_torr_cm=1.0, gamma_se=0.4, field_mode=0,
+                           vlim_e=inputs.ion_speed(170.0), dt=0.01 / 219 / inputs.ion_speed(170.0))
+    spec["p_Pa"] = 0.0
+    e, i = mixed_state(spec, 2500, 1500, seed=71)
+    sim = slpic.Simulation(1)
+    sim.configure(0, spec, capacity=(1 << 18, 1 << 18))
+    sim.load(0, 0, e)
+    sim.load(0, 1, i)
+    ref = oracle_mod.Oracle(spec, precision=32)
+    ref.load(0, e)
+    ref.load(1, i)
+    total = 0
+    for chunk in (1, 7, 40, 200):
+        done = sim.step_small(chunk)
+        assert done == chunk
+        ref.step(chunk)
+        total += chunk
+        for s in (0, 1):
+            assert_same_markers(sim.particles(0, s), ref.particles(s), spec["vlim_e"], True)
+            assert np.array_equal(sim.charge(0, s), ref.charge(s))
+    hg, hr = sim.history(0), ref.history()
+    assert len(hg) == len(hr) == total
+    for k in ("n_live", "n_abs", "n_see", "marker_steps"):
+        assert np.array_equal(hg[k], hr[k]), k
+    assert hr["n_see"].sum() > 50
+    sim.close()
+
+
+def test_small_path_matches_fp32_mirror_in_one_dense_step(slpic, oracle_mod):
+    """One step with every collision process through the single-CTA path:
+    counts, ids and cells bit-exact against the FP32 mirror; velocities (which
+    pass through the elementary functions of the scattering) to 1e-5."""
+    from .test_gpu_parity import assert_same_markers
+    spec = inputs.gap_spec(n_cells=256, V=300.0, pd_torr_cm=30.0, gamma_se=0.5, field_mode=0,
+                           table=inputs.make_table(levels=3))
+    e, i = mixed_state(spec, 3500, 1200, seed=73)
+    sim = slpic.Simulation(1)
+    sim.configure(0, spec, capacity=(1 << 18, 1 << 18))
+    sim.load(0, 0, e)
+    sim.load(0, 1, i)
+    assert sim.step_small(1) == 1
+    ref = oracle_mod.Oracle(spec, precision=32)
+    ref.load(0, e)
+    ref.load(1, i)
+    ref.step(1)
+    hg, hr = sim.history(0)[-1], ref.history()[-1]
+    for k in ("n_live", "n_coll", "n_candidates", "n_abs", "n_see", "n_clamp", "marker_steps"):
+        assert np.array_equal(hg[k], hr[k]), (k, hg[k], hr[k])
+    assert min(hr["n_coll"]) > 10 and hr["n_see"] > 10
+    for s in (0, 1):
+        assert_same_markers(sim.particles(0, s), ref.particles(s), spec["vlim_e"], False)
+    sim.close()

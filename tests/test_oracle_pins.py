@@ -904,3 +904,64 @@ def test_slpic_deficit_comes_from_the_per_step_collision_probability(oracle_mod)
     assert p - s1 > 0.05 * p and p - s1 > 3.0 * math.hypot(ep, e1), (s1, p)
     assert abs(s4 - p) < 0.05 * p and abs(s4 - p) < p - s1, (s4, s1, p)
 
+
+
+# ---------------------------------------------------------------------------
+# Multiplication per ion transit (Sec. V)
+# ---------------------------------------------------------------------------
+
+def ion_arrival_case(n=5000, cells=64, V=100.0, crossing_steps=400, seed=3):
+    """Ions at rest uniform in a vacuum gap, a uniform field, every ion that
+    reaches the cathode emitting one electron (gamma = 1).  Returns the spec,
+    the ions, and each ion's arrival step from the leapfrog closed form:
+    x_k = x_0 - a dt^2 k (k + 1) / 2 in cell units, the ion leaves in the
+    first step k with x_k < 0 (history index k - 1)."""
+    d = 0.01
+    dx = d / cells
+    a = inputs.QE * V / d / inputs.M_AR  # toward the cathode
+    dt = math.sqrt(2.0 * dx * cells / (a * crossing_steps ** 2))
+    spec = vacuum(inputs.gap_spec(n_cells=cells, V=V, gamma_se=1.0, field_mode=0, dt=dt))
+    rng = np.random.default_rng(seed)
+    ions = inputs.rest_state(n)
+    ions["cell"] = rng.integers(0, cells, n).astype(np.int32)
+    ions["off"] = np.minimum(rng.random(n, dtype=np.float32),
+                             np.float32(np.nextafter(np.float32(1), np.float32(0))))
+    x0 = ions["cell"] + ions["off"].astype(np.float64)
+    step_cells = a * dt * dt / dx
+    k = np.ceil((-1.0 + np.sqrt(1.0 + 8.0 * x0 / step_cells)) / 2.0).astype(np.int64)
+    k[k * (k + 1) / 2.0 * step_cells <= x0] += 1  # strictly past the cathode
+    return spec, ions, k - 1
+
+
+def test_multiplication_windows_count_ion_arrivals(oracle_mod):
+    """The windowed emission tally counts, window by window, the ions that
+    reach the cathode: with gamma = 1 each emits exactly one electron, so the
+    emitted weight per window equals the number of ions whose leapfrog
+    arrival step (closed form) falls in it, and M is the ratio of successive
+    windows."""
+    spec, ions, arrive = ion_arrival_case()
+    spw, n_win = 100, 5
+    o = oracle_mod.Oracle(spec, 64)
+    o.load(1, ions)
+    see, M = o.multiplication(spw, n_win)
+    want = np.bincount(arrive // spw, minlength=n_win)[:n_win].astype(float)
+    assert want[:4].min() > 300 and want[4] == 0
+    assert np.array_equal(see, want)
+    assert np.allclose(M[:3], want[1:4] / want[:3])
+    assert M[3] == 0.0  # every ion has arrived: no emission in the last window
+
+
+def test_multiplication_follows_the_townsend_criterion(oracle_mod):
+    """Sec. II.A: the emission grows from one ion transit to the next where the
+    first-generation gain G = gamma (e^(alpha d) - 1) exceeds 1 and dies out
+    where it is below 1 (1 Torr cm: G is about 0.5 at 150 V and 4 at 250 V in
+    this gas).  Windows of one ion crossing time, 8 x 128 steps here."""
+    def late_M(V, n_seed):
+        spec = inputs.gap_spec(n_cells=128, V=V, pd_torr_cm=1.0, gamma_se=0.07, field_mode=0,
+                               seed=17)
+        o = oracle_mod.Oracle(spec, 64)
+        o.seed(0, n_seed, 1)
+        see, _ = o.multiplication(8 * 128, 3)
+        return see[2] / see[1]
+    assert late_M(150.0, 150) < 0.8
+    assert late_M(250.0, 25) > 1.5
