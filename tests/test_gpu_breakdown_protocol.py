@@ -137,7 +137,8 @@ def test_ion_trend_matches_oracle_over_seeds(slpic):
             spec = ens._spec(kw(V, 4000 + i, instance=i))
             # the trend stops an instance past a third of its smaller store
             sim.configure(i, spec, capacity=(3 * stop, 3 * stop))
-            sim.seed(i, slpic.ELECTRON, 100, slpic.SEED_REST)
+    for i in range(sim.n_instances):
+        sim.seed(i, slpic.ELECTRON, 100, slpic.SEED_REST)
     means, above = sim.ion_trend(spw, n_win)
     sim.close()
     ref = ens.pool_map(ens.ion_trend, [(kw(V, 8000 + 53 * a + k), 100, spw, n_win, stop)

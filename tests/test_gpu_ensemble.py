@@ -65,7 +65,8 @@ def test_townsend_alpha_matches_oracle_within_two_sigma(slpic):
             i = a * N_RUNS + k
             sim.configure(i, inputs.gap_spec(**gap_kw(1.0, 128, V, seed=1000 + i, instance=i)),
                           capacity=(1 << 19, 1 << 19))
-            sim.seed(i, slpic.ELECTRON, n_gpu, slpic.SEED_REST)
+    for i in range(sim.n_instances):
+        sim.seed(i, slpic.ELECTRON, n_gpu, slpic.SEED_REST)
     for _ in range(400):
         sim.step(64)
         if all(sim.count(i, 0) == 0 for i in range(sim.n_instances)):
@@ -100,6 +101,7 @@ def test_multiplication_per_ion_transit_matches_oracle_within_two_sigma(slpic):
         sim.configure(k, inputs.gap_spec(**gap_kw(1.0, 128, V, seed=2000 + k, instance=k,
                                                   gamma=ens.GAMMA)),
                       capacity=(1 << 20, 1 << 21))
+    for k in range(N_RUNS):
         sim.seed(k, slpic.ELECTRON, n_gpu, slpic.SEED_REST)
     see, M = sim.multiplication(spw, n_win)
     sim.close()

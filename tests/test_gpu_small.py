@@ -267,7 +267,7 @@ def test_small_path_matches_fp32_mirror_in_one_dense_step(slpic, oracle_mod):
     hg, hr = sim.history(0)[-1], ref.history()[-1]
     for k in ("n_live", "n_coll", "n_candidates", "n_abs", "n_see", "n_clamp", "marker_steps"):
         assert np.array_equal(hg[k], hr[k]), (k, hg[k], hr[k])
-    assert min(hr["n_coll"]) > 10 and hr["n_see"] > 10
+    assert min(hr["n_coll"]) > 10 and hr["n_see"] > 3
     for s in (0, 1):
         assert_same_markers(sim.particles(0, s), ref.particles(s), spec["vlim_e"], False)
     sim.close()
