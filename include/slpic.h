@@ -436,8 +436,9 @@ int slpic_philox2x32(int device, uint32_t key, const uint32_t* ctr, int64_t n,
 /* slpic_philox without any device allocation.  A library utility; the method
  * has no counterpart.  Same arguments and results as slpic_philox, but the
  * counters and outputs are staged in one fixed device array that the library
- * owns (SLPIC_PHILOX_STATIC_MAX counters, reserved when the library is
- * loaded), so the call makes no cudaMalloc or cudaFree.  It is for callers
+ * owns (SLPIC_PHILOX_STATIC_MAX counters and as many outputs, 1 MiB, held on
+ * every device that loads the library's device code until the process
+ * exits), so the call makes no cudaMalloc or cudaFree.  It is for callers
  * that must not allocate device memory at the time of the call: a process
  * whose memory pool already holds all of the device, or one that checks the
  * random stream while a simulation runs on another stream of the same device
@@ -446,19 +447,23 @@ int slpic_philox2x32(int device, uint32_t key, const uint32_t* ctr, int64_t n,
  *  - n > SLPIC_PHILOX_STATIC_MAX, n < 0 or a NULL array: SLPIC_ERR_INVALID_ARG
  *    before anything runs; the message is in slpic_last_error(NULL).  CUDA
  *    failures return SLPIC_ERR_CUDA with the message there too.
+ *  - Set-up, once per device and context, with that device current: the
+ *    array's address (cudaGetSymbolAddress), a private non-blocking stream,
+ *    and the load of the library's device code that holds the array and the
+ *    kernel.  CUDA loads device code lazily, and that first load reserves the
+ *    1 MiB: slpic_create does the set-up for its device, and otherwise the
+ *    first call on a device does it.  Create a context (or make one call) on
+ *    each device before filling a memory pool or beginning a stream capture
+ *    there.  After cudaDeviceReset the next call sets up again.
+ *  - The copies and the kernel run on the private non-blocking stream: the
+ *    call neither waits for nor delays work on other streams, and returns
+ *    once out is written.  It makes `device` current for the calling thread.
  *  - Nothing in the scratch has to start at zero: each call copies its n
  *    counters in before the kernel reads them, and copies back only the n
  *    outputs the kernel has written.
  *  - There is one scratch array per device in a process: calls that overlap
  *    on one device (made from several host threads) race on it and return
- *    wrong words; serialise them.
- *  - The first call on each device looks up the scratch address
- *    (cudaGetSymbolAddress, with that device current) and caches it.  As this
- *    setup happens lazily, make the first call on a device before any stream
- *    capture begins on it.
- *  - Like slpic_philox, the call makes `device` current for the calling
- *    thread and runs on the legacy default stream; it returns when out is
- *    written. */
+ *    wrong words; serialise them. */
 int slpic_philox_static(int device, uint64_t seed, const uint32_t* ctr, int64_t n,
                         uint32_t* out);
 

@@ -2,6 +2,7 @@
 // and stores the configuration, derives the single-precision constants of
 // the step, owns the device memory, and launches the step (directly or as a
 // replayed CUDA graph of several steps).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -739,6 +740,8 @@ const char* slpic_last_error(const slpic_ctx* c) {
   return c ? c->err.c_str() : g_create_error.c_str();
 }
 
+int philox_static_setup_for(int device);
+
 int slpic_create(slpic_ctx** out, int device, int n_instances) {
   if (!out) return fail(nullptr, SLPIC_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -748,6 +751,9 @@ int slpic_create(slpic_ctx** out, int device, int n_instances) {
   cudaError_t e = cudaGetDeviceCount(&n);
   if (e != cudaSuccess) return fail(nullptr, SLPIC_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
   if (device < 0 || device >= n) return fail(nullptr, SLPIC_ERR_INVALID_ARG, "bad device %d", device);
+  // slpic_philox_static's set-up for this device now, while memory is free
+  // and before any stream capture (the caller's current device is kept)
+  if (int rc = philox_static_setup_for(device)) return rc;
   slpic_ctx* c = new slpic_ctx;
   c->device = device;
   c->n_inst = n_instances;
@@ -1906,18 +1912,76 @@ extern "C" int slpic_ion_trend(slpic_ctx* c, int64_t steps_per_window, int n_win
 // ---------------------------------------------------------------------------
 // slpic_philox_static: the Philox self-check without device allocation.  The
 // counters (first half) and the outputs (second half) live in one file-scope
-// device array of the module, whose address is looked up once per device.
-// Callers that cannot allocate: a process whose memory pool already holds the
-// whole device, or one checking the random stream while a simulation runs on
-// another stream (cudaFree would synchronise the device under it).
+// device array of the module.  Callers that cannot allocate: a process whose
+// memory pool already holds the whole device, or one checking the random
+// stream while a simulation runs on another stream (the cudaFree of
+// slpic_philox would synchronise the device under it).
 
 static __device__ __align__(256) uint32_t g_philox_scratch[2 * 4 * SLPIC_PHILOX_STATIC_MAX];
 
 namespace {
 constexpr int kStaticMaxDevices = 64;
+
+// Per device: the array's address and a private non-blocking stream, valid in
+// the context they were made in.
+struct StaticScratch {
+  CUcontext ctx = nullptr;
+  uint32_t* ptr = nullptr;
+  cudaStream_t stream = nullptr;
+};
 std::mutex g_scratch_mu;
-uint32_t* g_scratch_ptr[kStaticMaxDevices];
+StaticScratch g_scratch[kStaticMaxDevices];
+
+// The driver's cuCtxGetCurrent, found through the runtime (no link to the
+// driver library).
+using CtxGetCurrent = CUresult (*)(CUcontext*);
+CtxGetCurrent ctx_get_current() {
+  static CtxGetCurrent fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<CtxGetCurrent>(f);
+  }();
+  return fn;
+}
 }  // namespace
+
+// Set-up for `device`, which must be current: the array's address
+// (cudaGetSymbolAddress, which loads the module's device data if CUDA has not
+// yet done so), a private non-blocking stream, and the load of the Philox
+// kernel's module.  Cached per device, and redone when the device's current
+// context differs from the one the cache was made in (after cudaDeviceReset);
+// the stream of a context that is gone is not touched again.
+int philox_static_setup(int device, StaticScratch* out) {
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  CUcontext cur = nullptr;
+  CtxGetCurrent get = ctx_get_current();
+  if (!get || get(&cur) != CUDA_SUCCESS || !cur)
+    return fail(nullptr, SLPIC_ERR_CUDA, "slpic_philox_static: no current context on device %d",
+                device);
+  StaticScratch& s = g_scratch[device];
+  if (!(s.ptr && s.ctx == cur)) {
+    uint32_t* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void**)&p, g_philox_scratch);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "slpic_philox_static: cudaGetSymbolAddress");
+    cudaStream_t st = nullptr;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "slpic_philox_static: stream");
+    e = (cudaError_t)philox_preload();
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(st);
+      return cuda_fail(nullptr, e, "slpic_philox_static: kernel load");
+    }
+    s.ctx = cur;
+    s.ptr = p;
+    s.stream = st;
+  }
+  *out = s;
+  return SLPIC_OK;
+}
 
 extern "C" int slpic_philox_static(int device, uint64_t seed, const uint32_t* ctr, int64_t n,
                                    uint32_t* out) {
@@ -1934,28 +1998,35 @@ extern "C" int slpic_philox_static(int device, uint64_t seed, const uint32_t* ct
   if (n == 0) return SLPIC_OK;
   cudaError_t e = cudaSetDevice(device);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "slpic_philox_static: cudaSetDevice");
-  uint32_t* scratch = nullptr;
-  {
-    // once per device, with that device current; later calls reuse it
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[device]) {
-      uint32_t* p = nullptr;
-      e = cudaGetSymbolAddress((void**)&p, g_philox_scratch);
-      if (e != cudaSuccess)
-        return cuda_fail(nullptr, e, "slpic_philox_static: cudaGetSymbolAddress");
-      g_scratch_ptr[device] = p;
-    }
-    scratch = g_scratch_ptr[device];
-  }
-  uint32_t* dctr = scratch;
-  uint32_t* dout = scratch + 4 * (size_t)SLPIC_PHILOX_STATIC_MAX;
+  StaticScratch sc;
+  if (int rc = philox_static_setup(device, &sc)) return rc;
+  uint32_t* dctr = sc.ptr;
+  uint32_t* dout = sc.ptr + 4 * (size_t)SLPIC_PHILOX_STATIC_MAX;
   const size_t b = (size_t)n * 16;
-  e = cudaMemcpy(dctr, ctr, b, cudaMemcpyHostToDevice);
+  e = cudaMemcpyAsync(dctr, ctr, b, cudaMemcpyHostToDevice, sc.stream);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "slpic_philox_static: counters to device");
-  launch_philox((uint32_t)seed, (uint32_t)(seed >> 32), dctr, dout, n, 0);
+  launch_philox((uint32_t)seed, (uint32_t)(seed >> 32), dctr, dout, n, sc.stream);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "slpic_philox_static: launch");
-  e = cudaMemcpy(out, dout, b, cudaMemcpyDeviceToHost);
+  e = cudaMemcpyAsync(out, dout, b, cudaMemcpyDeviceToHost, sc.stream);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "slpic_philox_static: outputs to host");
+  e = cudaStreamSynchronize(sc.stream);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "slpic_philox_static: synchronise");
   return SLPIC_OK;
+}
+
+
+// slpic_philox_static's set-up for `device` from slpic_create; the calling
+// thread's current device is restored.
+int philox_static_setup_for(int device) {
+  if (device < 0 || device >= kStaticMaxDevices) return SLPIC_OK;
+  int prev = 0;
+  cudaError_t e = cudaGetDevice(&prev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "slpic_create: cudaGetDevice");
+  e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "slpic_create: cudaSetDevice");
+  StaticScratch sc;
+  int rc = philox_static_setup(device, &sc);
+  cudaSetDevice(prev);
+  return rc;
 }

@@ -565,6 +565,13 @@ void launch_philox2(uint32_t k, const uint32_t* ctr, uint32_t* out, long long n,
                                                    reinterpret_cast<uint2*>(out), n);
 }
 
+// Load the Philox kernel's module now (CUDA loads modules lazily, and the
+// load can reserve device memory).
+int philox_preload() {
+  cudaFuncAttributes a;
+  return (int)cudaFuncGetAttributes(&a, k_philox);
+}
+
 void launch_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, uint32_t* out, long long n,
                    cudaStream_t s) {
   if (n <= 0) return;

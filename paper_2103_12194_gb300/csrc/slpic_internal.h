@@ -314,6 +314,7 @@ void launch_seed(const DeviceRefs& r, int inst, int species, uint32_t base, uint
                  cudaStream_t s);
 void launch_validate(int fp64, const SoA& d, uint32_t n, int N, int shift, unsigned int* bad,
                      unsigned long long* wsum, cudaStream_t s);
+int philox_preload();
 void launch_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, uint32_t* out,
                    long long n, cudaStream_t s);
 void launch_philox2(uint32_t k, const uint32_t* ctr, uint32_t* out, long long n,

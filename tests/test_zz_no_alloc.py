@@ -50,3 +50,51 @@ def test_small_and_empty_calls_and_rejection_leave_it_usable():
         slpic.philox_static(_counters(rng, slpic.PHILOX_STATIC_MAX + 1), 5)
     ctr = _counters(rng, 3)
     np.testing.assert_array_equal(slpic.philox_static(ctr, 5), slpic.philox(ctr, 5))
+
+
+@pytest.mark.gpu
+def test_calls_leave_free_device_memory_unchanged():
+    """The entry point allocates nothing: free device memory is the same
+    before and after a call, for the first call after a context was created
+    on the device (slpic_create did the set-up) and for later calls."""
+    torch = pytest.importorskip("torch")
+    slpic = _slpic()
+    torch.cuda.mem_get_info(0)  # the process's own context exists
+    sim = slpic.Simulation(1, device=0)
+    rng = np.random.default_rng(11)
+    ctr = _counters(rng, 4096)
+    for _ in range(2):
+        free0, _ = torch.cuda.mem_get_info(0)
+        got = slpic.philox_static(ctr, 77)
+        free1, _ = torch.cuda.mem_get_info(0)
+        assert free1 == free0
+    np.testing.assert_array_equal(got, slpic.philox(ctr, 77))
+    sim.close()
+
+
+@pytest.mark.gpu
+def test_call_returns_while_a_simulation_runs_on_another_stream():
+    """The call's copies and kernel use a private non-blocking stream: it
+    returns with the right words while steps queued on a simulation's
+    non-blocking stream are still running."""
+    torch = pytest.importorskip("torch")
+    slpic = _slpic()
+    from paper_2103_12194_gb300 import inputs
+    stream = torch.cuda.Stream(device=0)
+    sim = slpic.Simulation(1, device=0, stream=stream)
+    spec = inputs.gap_spec(n_cells=4096, V=300.0, pd_torr_cm=1.0, field_mode=1)
+    sim.configure(0, spec, capacity=(1 << 23, 1 << 22))
+    sim.seed(0, slpic.ELECTRON, 4_000_000, 2)
+    sim.step(40)
+    sim.synchronize()
+    rng = np.random.default_rng(12)
+    ctr = _counters(rng, 2048)
+    want = slpic.philox(ctr, 9)
+    slpic.philox_static(ctr, 9)
+    sim.step(800)  # queued on the simulation's stream
+    got = slpic.philox_static(ctr, 9)
+    busy = not stream.query()
+    sim.synchronize()
+    np.testing.assert_array_equal(got, want)
+    assert busy, "the simulation's steps had finished before the call returned"
+    sim.close()
