@@ -44,8 +44,13 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--paschen", action="store_true",
-                    help="also time the batched FP32 breakdown-voltage sweep against the "
+                    help="(default) time the batched FP32 breakdown-voltage sweep against the "
                          "plain one-instance FP64 bisection")
+    ap.add_argument("--no-paschen", action="store_true",
+                    help="leave out the breakdown-voltage sweep")
+    ap.add_argument("--cpu-config1", action="store_true",
+                    help="instead of the benchmark, time config 1 (256 cells, 2e4 electrons, "
+                         "2000 steps) in full on the CPU oracle and print one JSON line")
     ap.add_argument("--tab-sims", default=None, metavar="ROWS",
                     help="instead of the benchmark, run the PIC vs SLPIC study shaped like "
                          "Table tab:sims on the rows given (comma-separated indices 0-10, "
@@ -165,37 +170,104 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(spec, n_markers, seconds):
-    """The oracle (FP64, as it stands, one host thread) on a bounded sample of
-    the same workload: n markers drawn like the GPU's, a few steps."""
+def _oracle_slice_run(spec, n, first, seconds):
+    """One host process: the FP64 oracle on markers first .. first + n - 1 of
+    the workload's sample (the same draw as the GPU's), stepped for about
+    `seconds`.  Returns (marker-steps, seconds)."""
     import oracle
     from paper_2103_12194_gb300 import inputs
-    n = min(n_markers, 200_000)
-    st = inputs.gap_state(n, spec, rng_seed=1, e_lo=0.1, e_hi=200.0)
+    st = inputs.gap_state(first + n, spec, rng_seed=1, e_lo=0.1, e_hi=200.0)
+    st = {k: v[first:first + n] for k, v in st.items()}
     o = oracle.Oracle(spec, precision=64)
     o.load(0, st)
     t0 = time.perf_counter()
     o.step(1)
-    t1 = time.perf_counter()
-    per_step = max(t1 - t0, 1e-6)
+    per_step = max(time.perf_counter() - t0, 1e-6)
     k = max(1, min(5000, int(seconds / per_step)))
     t0 = time.perf_counter()
     o.step(k)
     dt = time.perf_counter() - t0
+    return int(o.history()["marker_steps"][1:].sum()), dt
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the
+    machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(spec, n_markers, seconds):
+    """The oracle (FP64, as it stands) on a bounded sample of the same
+    workload: first one host thread on 2e5 of the workload's electrons, then
+    every host core at once, each core's process on its own slice of the same
+    2e5 electrons (the oracle is single-threaded; the slices share nothing).
+    The all-cores figure is the baseline; the single-thread one is kept."""
+    import multiprocessing
+    n = min(n_markers, 200_000)
+    ms1, dt1 = _oracle_slice_run(spec, n, 0, seconds / 2)
+    cores = os.cpu_count() or 1
+    per = max(1, n // cores)
+    args = [(spec, per, c * per, seconds / 2) for c in range(cores)]
+    t0 = time.perf_counter()
+    with multiprocessing.get_context("spawn").Pool(cores) as pool:
+        res = pool.starmap(_oracle_slice_run, args)
+    wall = time.perf_counter() - t0
+    ms_all = sum(r[0] for r in res)
+    dt_all = max(r[1] for r in res)
+    return {"value": ms_all / dt_all, "unit": "marker-steps/s", "cores": cores, "kind": "oracle",
+            "cpu": cpu_model(),
+            "sample": "%d of the workload's electrons (same draw), FP64 oracle: %d processes "
+                      "of %d electrons each, %.1f s of stepping (%.1f s with start-up)"
+                      % (n, cores, per, dt_all, wall),
+            "single_thread": {"value": ms1 / dt1, "cores": 1,
+                              "sample": "%d electrons, %.1f s" % (n, dt1)}}
+
+
+def cpu_config1():
+    """Config 1 of the workloads timed in full on the oracle (FP64, one host
+    thread): 256 cells, 1 Torr cm, 300 V, gamma 0.07, 2e4 electrons seeded at
+    the cathode at 1 eV, 2000 steps, Poisson on."""
+    import oracle
+    from paper_2103_12194_gb300 import inputs
+    spec, run = inputs.small_gap_config()
+    o = oracle.Oracle(spec, precision=64)
+    o.seed(0, run["n_seed"], run["seed_mode"], e0=run["e0"])
+    t0 = time.perf_counter()
+    o.step(run["steps"])
+    dt = time.perf_counter() - t0
     h = o.history()
-    ms = int(h["marker_steps"][1:].sum())
-    return {"value": ms / dt, "unit": "marker-steps/s", "cores": 1, "kind": "oracle",
-            "sample": "%d of the workload's electrons (same draw), %d steps, FP64 oracle, "
-                      "single host thread, %.1f s" % (n, k, dt)}
+    ms = int(h["marker_steps"].sum())
+    return {"workload": "config 1: 256 cells, 1 Torr cm, 300 V, gamma 0.07, 2e4 electrons at "
+                        "the cathode at 1 eV, 2000 steps, Poisson on, FP64 oracle, 1 thread",
+            "seconds": dt, "marker_steps": ms, "value": ms / dt, "unit": "marker-steps/s",
+            "live_at_end": [int(x) for x in h["n_live"][-1]], "cores": 1, "cpu": cpu_model()}
 
 
-def paschen_sweep(slpic, inputs, local, stream, pds=(0.5, 1.0, 2.0, 4.0), n_v=8, rounds=3,
-                  n_seed=2000, v_lo=100.0, v_hi=900.0):
+def paschen_sweep(slpic, inputs, local, stream, pds=(0.5, 1.0, 2.0, 4.0), n_v=7, rounds=3,
+                  n_seed=1000, v_lo=100.0, v_hi=900.0):
     """Breakdown voltages at a few pd points (d = 1 cm, gamma = 0.07, cells
     from dx = lambda_min / 4): the batched FP32 search (all pd points and n_v
     voltages per round in one context) against the plain FP64 bisection (one
-    single-instance context per pd point, one voltage per round, as many
-    halvings as reach the same bracket width)."""
+    single-instance context per pd point, one voltage per round).  With
+    n_v + 1 a power of two the bisection's halvings reach exactly the same
+    final bracket width, and both evaluate every gain from n_seed electrons:
+    the same breakdown-voltage accuracy."""
     import numpy as np
     import torch
     table = inputs.make_table()
@@ -218,7 +290,8 @@ def paschen_sweep(slpic, inputs, local, stream, pds=(0.5, 1.0, 2.0, 4.0), n_v=8,
                                        rounds=rounds, n_seed=n_seed)
     sim.close()
     t32 = time.perf_counter() - t0
-    halvings = int(math.ceil(rounds * math.log2(n_v + 1)))
+    halvings = int(round(rounds * math.log2(n_v + 1)))
+    assert 2 ** halvings == (n_v + 1) ** rounds, "n_v + 1 must be a power of two"
     t0 = time.perf_counter()
     lo64, hi64 = [], []
     for p, pd in enumerate(pds):
@@ -236,6 +309,8 @@ def paschen_sweep(slpic, inputs, local, stream, pds=(0.5, 1.0, 2.0, 4.0), n_v=8,
                            "Vb_lo": lo64, "Vb_hi": hi64},
             "bracket_width_V": {"fp32_batched": (v_hi - v_lo) / (n_v + 1) ** rounds,
                                 "fp64_plain": (v_hi - v_lo) / 2 ** halvings},
+            "Vb_mid_difference_V": [0.5 * (a + b) - 0.5 * (c + d)
+                                    for a, b, c, d in zip(lo32, hi32, lo64, hi64)],
             "speedup": t64 / t32}
 
 
@@ -672,7 +747,7 @@ def run_ours(args):
         sim.close()
 
     sweep = None
-    if args.paschen and rank == 0:
+    if not args.no_paschen and rank == 0:
         sweep = paschen_sweep(slpic, inputs, local, stream)
 
     cpu = None
@@ -712,7 +787,9 @@ def run_ours(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.cpu_config1:
+        print(json.dumps(cpu_config1()), flush=True)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
