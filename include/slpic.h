@@ -363,6 +363,42 @@ int slpic_paschen_bisect(slpic_ctx* ctx, const slpic_paschen_spec* spec, double*
 int slpic_ion_trend(slpic_ctx* ctx, int64_t steps_per_window, int n_windows, double* means,
                     int* above);
 
+/* Checkpoint and resume.  slpic_save writes the context's state to a host
+ * buffer: per instance the live markers of both species in store order and
+ * their next serial numbers, the step counters (step index, steps done,
+ * seeded and live weights, live-ion sum), the tally totals and the history
+ * ring, the node field (phi and E) and the last deposit.  The configuration
+ * (gap, gas, tables, species, emission, dt, seed, capacities) is not in it.
+ * With buf = NULL only *size_out (the snapshot's bytes) is written; with a
+ * buffer smaller than that, SLPIC_ERR_CAPACITY.  Synchronises.
+ * slpic_load restores such a snapshot into a context configured as the
+ * saved one was (same instance count, precision, cells and ring length,
+ * capacities holding the markers; else SLPIC_ERR_INVALID_ARG or
+ * SLPIC_ERR_CAPACITY).  Steps after a load give, bit for bit, the results
+ * the saved context would have given.  A library utility; the method has no
+ * counterpart. */
+int slpic_save(slpic_ctx* ctx, void* buf, size_t capacity, size_t* size_out);
+int slpic_load(slpic_ctx* ctx, const void* buf, size_t size);
+
+/* Bounded waits: every wait of a kernel on data another thread block
+ * produces (bulk-copy barriers, the ordered scans' look-back, the single-CTA
+ * path's grid barrier) gives up after this many polls, latches
+ * SLPIC_ERR_TIMEOUT and lets the kernel return; the next synchronising call
+ * returns the error and steps are no-ops until slpic_clear_error.  0 restores
+ * the default (2^22 polls, seconds).  A library utility; the method has no
+ * counterpart. */
+int slpic_set_spin_limit(slpic_ctx* ctx, uint32_t polls);
+/* Test hook for the bounded waits: once, in a launch of the single-CTA path
+ * with more than one instance, the thread block of instance `inst` leaves
+ * out its arrival at grid barrier `barrier` (the barrier taken after
+ * barrier - 1 steps of the launch; 1 = before its first step).  Every
+ * block's wait at that barrier then runs out after the spin limit, the
+ * launch ends there, and the call that stepped returns SLPIC_ERR_TIMEOUT.
+ * inst = -1 switches the hook off.  After the timeout, slpic_clear_error and
+ * a fresh load or seed make the context usable again.  A library utility;
+ * the method has no counterpart. */
+int slpic_test_skip_barrier(slpic_ctx* ctx, int inst, int64_t barrier);
+
 /* Multiplication per ion transit (Sec. V: the population over windows of
  * one ion crossing time sqrt(2 M d / (e E))).  Advances every instance by
  * n_windows windows of steps_per_window steps (the single-CTA path while the

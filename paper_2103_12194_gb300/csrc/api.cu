@@ -81,6 +81,7 @@ struct slpic_ctx {
   InstState* d_istate = nullptr;
   SpeciesState* d_sstate = nullptr;
   Control* d_ctrl = nullptr;
+  unsigned int spin_limit = 0;  // bounded waits' polls (0: the default)
   Transfer* d_xfer = nullptr;
   unsigned int* d_seg = nullptr;
   unsigned int* d_scratch = nullptr;  // 16 bytes for small device results
@@ -469,6 +470,9 @@ int commit(slpic_ctx* c) {
   c->refs.sstate = c->d_sstate;
   c->refs.xfer = c->d_xfer;
   c->refs.ctrl = c->d_ctrl;
+  CK(cudaMemcpy(&c->d_ctrl->spin_limit, &c->spin_limit, sizeof c->spin_limit,
+                cudaMemcpyHostToDevice),
+     "control");
   c->refs.seg_start = c->d_seg;
   c->refs.n_inst = c->n_inst;
   // the whole charge grid of the largest instance goes to shared memory when
@@ -1784,6 +1788,223 @@ int advance(slpic_ctx* c, int64_t n) {
     }
     done += k;
   }
+  return SLPIC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint and resume.  A snapshot is a host byte buffer:
+//   header  "SLPICSV1", version, precision, n_inst;
+//   per instance: its record (cells, ring length, whether it has stepped,
+//     the counters of InstState, the tally totals, live markers and next id
+//     per species), then the history ring, phi, E (FP64), E (FP32), the last
+//     deposit of both species, and the live markers of each species in store
+//     order as seven arrays (cell, offset, vx, vy, vz, w_j, id), every array
+//     padded to 8 bytes.
+namespace {
+struct SnapHeader {
+  char magic[8];
+  int32_t version;
+  int32_t fp64;
+  int32_t n_inst;
+  int32_t pad;
+};
+struct SnapInst {
+  int32_t n_cells;
+  int32_t ring_len;
+  int32_t stepped;
+  int32_t pad;
+  InstState is;
+  TallyRec total;
+  uint64_t n_live[2];
+  uint32_t next_id[2];
+};
+constexpr char kSnapMagic[8] = {'S', 'L', 'P', 'I', 'C', 'S', 'V', '1'};
+size_t pad8(size_t b) { return (b + 7) & ~size_t(7); }
+
+// Bytes of instance i's part of a snapshot (the live counts are read).
+int snap_inst_bytes(slpic_ctx* c, int i, const SpeciesState st[2], size_t* bytes) {
+  const InstDev& P = c->h_inst[i];
+  const size_t nn = (size_t)P.n_cells + 1;
+  size_t b = pad8(sizeof(SnapInst)) + pad8(sizeof(TallyRec) * P.ring_len) + 2 * nn * 8 +
+             pad8(nn * 4) + 2 * nn * 8;
+  for (int s = 0; s < 2; ++s)
+    for (int k = 0; k < 7; ++k) b += pad8(field_bytes(c, k, st[s].n_live));
+  *bytes = b;
+  return SLPIC_OK;
+}
+}  // namespace
+
+extern "C" int slpic_save(slpic_ctx* c, void* buf, size_t capacity, size_t* size_out) {
+  if (!c || !size_out) return SLPIC_ERR_INVALID_ARG;
+  if (int rc = prepare(c)) return rc;
+  if (int rc = sync(c)) return rc;
+  const int n = c->n_inst;
+  std::vector<SpeciesState> st(2 * (size_t)n);
+  size_t total = pad8(sizeof(SnapHeader));
+  for (int i = 0; i < n; ++i) {
+    // the deposit and phi as a read would form them
+    if (int rc = materialize_deposit(c, i)) return rc;
+    if (c->h_inst[i].field_mode == 1 && c->stepped[i]) {
+      launch_phi(c->refs, i, c->stream);
+      CK(cudaGetLastError(), "save");
+    }
+    for (int s = 0; s < 2; ++s)
+      if (int rc = read_state(c, i, s, &st[2 * i + s])) return rc;
+    size_t b = 0;
+    snap_inst_bytes(c, i, &st[2 * i], &b);
+    total += b;
+  }
+  CK(cudaStreamSynchronize(c->stream), "save");
+  *size_out = total;
+  if (!buf) return SLPIC_OK;
+  if (capacity < total)
+    return fail(c, SLPIC_ERR_CAPACITY, "save: the snapshot takes %zu bytes, the buffer %zu",
+                total, capacity);
+  char* o = static_cast<char*>(buf);
+  SnapHeader h{};
+  std::memcpy(h.magic, kSnapMagic, 8);
+  h.version = 1;
+  h.fp64 = c->fp64;
+  h.n_inst = n;
+  std::memcpy(o, &h, sizeof h);
+  o += pad8(sizeof h);
+  for (int i = 0; i < n; ++i) {
+    const InstDev& P = c->h_inst[i];
+    const size_t nn = (size_t)P.n_cells + 1;
+    SnapInst r{};
+    r.n_cells = P.n_cells;
+    r.ring_len = P.ring_len;
+    r.stepped = c->stepped[i];
+    CK(cudaMemcpy(&r.is, c->d_istate + i, sizeof r.is, cudaMemcpyDeviceToHost), "save");
+    CK(cudaMemcpy(&r.total, P.total, sizeof r.total, cudaMemcpyDeviceToHost), "save");
+    for (int s = 0; s < 2; ++s) {
+      r.n_live[s] = st[2 * i + s].n_live;
+      r.next_id[s] = st[2 * i + s].next_id;
+    }
+    std::memcpy(o, &r, sizeof r);
+    o += pad8(sizeof r);
+    CK(cudaMemcpy(o, P.ring, sizeof(TallyRec) * P.ring_len, cudaMemcpyDeviceToHost), "save");
+    o += pad8(sizeof(TallyRec) * P.ring_len);
+    CK(cudaMemcpy(o, P.phi, nn * 8, cudaMemcpyDeviceToHost), "save");
+    o += nn * 8;
+    CK(cudaMemcpy(o, P.E64, nn * 8, cudaMemcpyDeviceToHost), "save");
+    o += nn * 8;
+    CK(cudaMemcpy(o, P.E32, nn * 4, cudaMemcpyDeviceToHost), "save");
+    o += pad8(nn * 4);
+    for (int s = 0; s < 2; ++s) {
+      CK(cudaMemcpy(o, P.rho_last[s], nn * 8, cudaMemcpyDeviceToHost), "save");
+      o += nn * 8;
+    }
+    for (int s = 0; s < 2; ++s) {
+      const int64_t nl = st[2 * i + s].n_live;
+      Arrays a{};
+      a.fp64 = c->fp64;
+      char* base = o;
+      for (int k = 0; k < 7; ++k) {
+        a.f[k] = base;
+        base += pad8(field_bytes(c, k, nl));
+      }
+      int64_t got = 0;
+      if (int rc = read_common(c, i, s, a, nl, &got)) return rc;
+      o = base;
+    }
+  }
+  return SLPIC_OK;
+}
+
+extern "C" int slpic_load(slpic_ctx* c, const void* buf, size_t size) {
+  if (!c || !buf) return SLPIC_ERR_INVALID_ARG;
+  const char* o = static_cast<const char*>(buf);
+  const char* end = o + size;
+  SnapHeader h;
+  if (size < sizeof h) return fail(c, SLPIC_ERR_INVALID_ARG, "load: not a snapshot");
+  std::memcpy(&h, o, sizeof h);
+  if (std::memcmp(h.magic, kSnapMagic, 8) != 0 || h.version != 1)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "load: not a snapshot of this library");
+  if (h.fp64 != c->fp64 || h.n_inst != c->n_inst)
+    return fail(c, SLPIC_ERR_INVALID_ARG,
+                "load: snapshot of %d instances in FP%d, context of %d in FP%d", h.n_inst,
+                h.fp64 ? 64 : 32, c->n_inst, c->fp64 ? 64 : 32);
+  if (int rc = prepare(c)) return rc;
+  if (int rc = sync(c)) return rc;
+  o += pad8(sizeof h);
+  for (int i = 0; i < c->n_inst; ++i) {
+    const InstDev& P = c->h_inst[i];
+    const size_t nn = (size_t)P.n_cells + 1;
+    SnapInst r;
+    if (end - o < (ptrdiff_t)sizeof r) return fail(c, SLPIC_ERR_INVALID_ARG, "load: truncated");
+    std::memcpy(&r, o, sizeof r);
+    if (r.n_cells != P.n_cells || r.ring_len != P.ring_len)
+      return fail(c, SLPIC_ERR_INVALID_ARG,
+                  "load: instance %d has %d cells in the snapshot, %d in the context", i,
+                  r.n_cells, P.n_cells);
+    SpeciesState st[2];
+    for (int s = 0; s < 2; ++s) st[s].n_live = (uint32_t)r.n_live[s];
+    size_t b = 0;
+    snap_inst_bytes(c, i, st, &b);
+    if ((size_t)(end - o) < b) return fail(c, SLPIC_ERR_INVALID_ARG, "load: truncated");
+    o += pad8(sizeof r);
+    const char* ring = o;
+    o += pad8(sizeof(TallyRec) * P.ring_len);
+    const char* phi = o;
+    o += nn * 8;
+    const char* e64 = o;
+    o += nn * 8;
+    const char* e32 = o;
+    o += pad8(nn * 4);
+    const char* rho[2];
+    for (int s = 0; s < 2; ++s) {
+      rho[s] = o;
+      o += nn * 8;
+    }
+    for (int s = 0; s < 2; ++s) {
+      const int64_t nl = (int64_t)r.n_live[s];
+      Arrays a{};
+      a.fp64 = c->fp64;
+      for (int k = 0; k < 7; ++k) {
+        a.f[k] = const_cast<char*>(o);
+        o += pad8(field_bytes(c, k, nl));
+      }
+      if (int rc = load_common(c, i, s, a, nl, r.next_id[s], cudaMemcpyHostToDevice)) return rc;
+    }
+    // the counters, tallies, field and deposit as saved (the loads above
+    // set the seeded and live weights from the markers)
+    CK(cudaMemcpy(c->d_istate + i, &r.is, sizeof r.is, cudaMemcpyHostToDevice), "load");
+    CK(cudaMemcpy(P.total, &r.total, sizeof r.total, cudaMemcpyHostToDevice), "load");
+    CK(cudaMemcpy(P.ring, ring, sizeof(TallyRec) * P.ring_len, cudaMemcpyHostToDevice), "load");
+    CK(cudaMemcpy(P.phi, phi, nn * 8, cudaMemcpyHostToDevice), "load");
+    CK(cudaMemcpy(P.E64, e64, nn * 8, cudaMemcpyHostToDevice), "load");
+    CK(cudaMemcpy(P.E32, e32, nn * 4, cudaMemcpyHostToDevice), "load");
+    for (int s = 0; s < 2; ++s)
+      CK(cudaMemcpy(P.rho_last[s], rho[s], nn * 8, cudaMemcpyHostToDevice), "load");
+    c->stepped[i] = (char)r.stepped;
+    c->dep_dirty[i] = 0;
+  }
+  if (int rc = replan(c)) return rc;
+  return sync(c);
+}
+
+extern "C" int slpic_set_spin_limit(slpic_ctx* c, uint32_t polls) {
+  if (!c) return SLPIC_ERR_INVALID_ARG;
+  c->spin_limit = polls;
+  if (!c->d_ctrl) return SLPIC_OK;
+  if (int rc = set_device(c)) return rc;
+  CK(cudaStreamSynchronize(c->stream), "spin limit");
+  CK(cudaMemcpy(&c->d_ctrl->spin_limit, &polls, sizeof polls, cudaMemcpyHostToDevice),
+     "spin limit");
+  return SLPIC_OK;
+}
+
+extern "C" int slpic_test_skip_barrier(slpic_ctx* c, int inst, int64_t barrier) {
+  if (!c) return SLPIC_ERR_INVALID_ARG;
+  if (inst < -1 || inst >= c->n_inst || barrier < 0)
+    return fail(c, SLPIC_ERR_INVALID_ARG, "skip barrier: instance in [-1, n_inst), barrier >= 0");
+  if (int rc = prepare(c)) return rc;
+  CK(cudaStreamSynchronize(c->stream), "skip barrier");
+  const int cta = inst + 1;
+  const long long b = inst < 0 ? 0 : (long long)barrier;
+  CK(cudaMemcpy(&c->d_ctrl->skip_cta, &cta, sizeof cta, cudaMemcpyHostToDevice), "skip barrier");
+  CK(cudaMemcpy(&c->d_ctrl->skip_barrier, &b, sizeof b, cudaMemcpyHostToDevice), "skip barrier");
   return SLPIC_OK;
 }
 

@@ -464,6 +464,13 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 
 namespace slpic {
 
+// Polls a bounded wait makes before it gives up: the context's limit, or
+// kSpinLimit.
+__device__ __forceinline__ uint32_t spin_limit(const Control* ctrl) {
+  const uint32_t l = *((volatile const unsigned int*)&ctrl->spin_limit);
+  return l ? l : kSpinLimit;
+}
+
 // Ordered scan over chunks taken in increasing order (decoupled look-back),
 // called by all 32 lanes of one warp: chunk c of a scan whose first chunk is
 // `first` publishes its aggregate, then reads the records of up to 32
@@ -489,6 +496,7 @@ __device__ __forceinline__ uint32_t chunk_lookback(ChunkStatus* st, unsigned int
     return 0;
   }
   if (lane == 0) chunk_publish(st + c, agg, false, epoch);
+  const uint32_t limit = spin_limit(ctrl);
   uint32_t excl = 0;
   long long top = (long long)c - 1;  // nearest predecessor not yet added
   bool timed_out = false;
@@ -501,7 +509,7 @@ __device__ __forceinline__ uint32_t chunk_lookback(ChunkStatus* st, unsigned int
       cuda::atomic_ref<unsigned int, cuda::thread_scope_device> f(st[j].flag);
       fv = f.load(cuda::memory_order_acquire);
       while ((fv >> 2) != epoch || (fv & 3u) == 0u) {
-        if (++polls > kSpinLimit || *((volatile int*)&ctrl->error) == kErrTimeout) {
+        if (++polls > limit || *((volatile int*)&ctrl->error) == kErrTimeout) {
           timed_out = true;
           break;
         }

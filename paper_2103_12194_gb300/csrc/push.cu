@@ -197,6 +197,7 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
 
   Control* ctrl = r.ctrl;
   if (*((volatile int*)&ctrl->error)) return;
+  const uint32_t limit = spin_limit(ctrl);
   // this CTA's contiguous range of super-tiles (equal weight per CTA)
   const unsigned long long wt = ctrl->w_total;
   const unsigned int q0 =
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
       if (t.fill) {
         uint32_t polls = 0;
         while (!mbar_try_wait(&bars[sc], (phase >> sc) & 1u)) {
-          if (++polls > kSpinLimit) {
+          if (++polls > limit) {
             set_error(ctrl, kErrTimeout);
             *abort_flag = 1;
             ok = false;

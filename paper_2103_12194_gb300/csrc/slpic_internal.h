@@ -43,7 +43,8 @@ constexpr int kErrTimeout = 2;
 constexpr int kErrIdWrap = 3;
 
 // Bounded waits: polls before a wait gives up with kErrTimeout (each poll of
-// an mbarrier suspends the thread for up to about a microsecond).
+// an mbarrier suspends the thread for up to about a microsecond), unless the
+// context sets another limit (Control::spin_limit).
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 // Per-step accumulators of one instance (integer; weights in fixed point).
@@ -247,6 +248,9 @@ struct Control {
   unsigned int small_bar;    // single-CTA path: arrivals at its grid barriers
   int small_stop;            // single-CTA path: a store outgrew it
   long long small_done;      // single-CTA path: steps run by the last launch
+  unsigned int spin_limit;   // polls before a bounded wait gives up (0: kSpinLimit)
+  int skip_cta;              // test hook: CTA + 1 of the single-CTA path that skips
+  long long skip_barrier;    //   its arrival at this grid barrier (0: none)
 };
 
 // Look-back record of one chunk of an ordered scan.

@@ -187,11 +187,17 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(DeviceRefs r, long l
         // grid barrier b = done: arrive, then wait (bounded) for every CTA
         if (stop) atomicOr(&ctrl->small_stop, 1);
         __threadfence();
-        atomicAdd(&ctrl->small_bar, 1u);
+        // test hook: one CTA leaves out its arrival at one barrier, so that
+        // every CTA's bounded wait there runs out (its own included)
+        const bool skip = *((volatile int*)&ctrl->skip_cta) == (int)blockIdx.x + 1 &&
+                          *((volatile long long*)&ctrl->skip_barrier) == done + 1;
+        if (skip) *((volatile int*)&ctrl->skip_cta) = 0;  // once
+        else atomicAdd(&ctrl->small_bar, 1u);
         const unsigned int target = (unsigned int)(done + 1) * gridDim.x;
+        const uint32_t limit = spin_limit(ctrl);
         uint32_t polls = 0;
         while (*((volatile unsigned int*)&ctrl->small_bar) < target) {
-          if (++polls > kSpinLimit) {
+          if (++polls > limit) {
             atomicCAS(&ctrl->error, 0, kErrTimeout);
             stop = 1;
             break;

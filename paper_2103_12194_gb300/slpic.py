@@ -118,6 +118,10 @@ def lib():
                                              f64], i32),
         "slpic_ion_trend": ([vp, i64, i32, vp, vp], i32),
         "slpic_multiplication": ([vp, i64, i32, vp, vp], i32),
+        "slpic_set_spin_limit": ([vp, u32], i32),
+        "slpic_save": ([vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], i32),
+        "slpic_load": ([vp, vp, ctypes.c_size_t], i32),
+        "slpic_test_skip_barrier": ([vp, i32, i64], i32),
         "slpic_set_launch_shape": ([vp, i32, i32], i32),
         "slpic_get_launch_shape": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
         "slpic_autotune": ([vp, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
@@ -408,6 +412,26 @@ class Simulation:
         self._ck(self._L.slpic_multiplication(self._h, int(steps_per_window), int(n_windows),
                                               _ptr(see), _ptr(M)))
         return see, M
+
+    def save(self):
+        """slpic_save: the context's state as bytes."""
+        n = ctypes.c_size_t(0)
+        self._ck(self._L.slpic_save(self._h, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._ck(self._L.slpic_save(self._h, buf, n.value, ctypes.byref(n)))
+        return buf.raw[:n.value]
+
+    def restore(self, snapshot):
+        """slpic_load: restore a state saved by save() into this context,
+        configured as the saved one was."""
+        buf = ctypes.create_string_buffer(bytes(snapshot), len(snapshot))
+        self._ck(self._L.slpic_load(self._h, buf, len(snapshot)))
+
+    def set_spin_limit(self, polls):
+        self._ck(self._L.slpic_set_spin_limit(self._h, int(polls)))
+
+    def test_skip_barrier(self, inst, barrier):
+        self._ck(self._L.slpic_test_skip_barrier(self._h, int(inst), int(barrier)))
 
     def set_launch_shape(self, push_warps, collide_ctas_per_sm):
         self._ck(self._L.slpic_set_launch_shape(self._h, int(push_warps),
