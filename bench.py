@@ -459,11 +459,20 @@ def batch_specs(inputs, n_inst=32):
     return out
 
 
-def batch_bench(slpic, inputs, steps, warmup, local, stream):
+def batch_bench(slpic, inputs, steps, warmup, local, stream, world=1, rank=0):
     """All 32 instances of the sweep workload advanced by the same launches:
-    aggregate marker-steps/s and the particle kernel's roofline."""
+    aggregate marker-steps/s and the particle kernel's roofline.  With
+    several ranks the instances are shared among them by markers x steps
+    (ranks.partition) and each rank steps its own in one context; rank 0
+    gathers the per-instance marker-steps, and the job's rate is their sum
+    over the slowest rank's time."""
     import torch
-    items = batch_specs(inputs)
+    from paper_2103_12194_gb300 import ranks
+    all_items = batch_specs(inputs)
+    mine = ranks.partition([n for _, n in all_items], world)[rank]
+    items = [all_items[k] for k in mine]
+    for j, (spec, _) in enumerate(items):
+        spec["instance"] = j
     sim = slpic.Simulation(len(items), device=local, stream=stream)
     for k, (spec, n) in enumerate(items):
         # avalanches above breakdown grow the ions about 4x in 400 steps
@@ -491,18 +500,25 @@ def batch_bench(slpic, inputs, steps, warmup, local, stream):
     ms3 = sum(int(sim.tallies(k)["marker_steps"]) for k in range(len(items)))
     sim.set_profiling(False)
     live = [[sim.count(k, 0), sim.count(k, 1)] for k in range(len(items))]
+    per_inst = {mine[k]: (int(sim.tallies(k)["marker_steps"]), live[k]) for k in range(len(items))}
     sim.close()
     peak, peak_kind = peaks()
     achieved = BYTES_PER_MARKER_STEP * (ms3 - ms2) / (push_ms / 1e3) / 1e9
-    return {"value": (ms1 - ms0) / (wall_ms / 1e3), "unit": "marker-steps/s", "steps": steps,
-            "ms_per_step": wall_ms / steps, "instances": len(items),
-            "markers_seeded": sum(n for _, n in items),
-            "cells": [spec["n_cells"] for spec, _ in items],
+    t_job, work_job = combine_ranks(wall_ms, ms1 - ms0, world, "cuda")
+    gathered = ranks.gather(per_inst, world, rank)
+    if gathered is not None and sorted(gathered) != list(range(len(all_items))):
+        raise RuntimeError("the ranks did not cover every instance")
+    return {"value": work_job / t_job, "unit": "marker-steps/s", "steps": steps,
+            "ms_per_step": t_job * 1e3 / steps, "instances": len(all_items),
+            "instances_per_rank": len(items), "ranks": world,
+            "markers_seeded": sum(n for _, n in all_items),
+            "cells": [spec["n_cells"] for spec, _ in all_items],
             "launch_shape": {"push_warps_per_cta": shape[0], "collide_ctas_per_sm": shape[1]},
             "roofline": {"bound": "hbm", "kernel": "k_push", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                          "push_share_of_step": push_ms / ((ms3 - ms2) / (ms1 - ms0) * wall_ms)},
-            "live_at_end": live}
+            "live_at_end": ([gathered[k][1] for k in range(len(all_items))]
+                            if gathered is not None else None)}
 
 
 def small_pop(slpic, inputs, steps, local, stream, V=171.5):
@@ -592,11 +608,13 @@ def run_ours(args):
     build.build()
     stream = torch.cuda.current_stream()
     if args.batch:
+        res = batch_bench(slpic, inputs, args.steps if args.steps != 1000 else 100,
+                          args.warmup, local, stream, world, rank)
         if rank == 0:
-            res = batch_bench(slpic, inputs, args.steps if args.steps != 1000 else 100,
-                              args.warmup, local, stream)
             res["study"] = ("32 uneven instances, pd 0.1-100 Torr cm, 1e4-4e6 electrons each, "
-                            "Poisson on, one context")
+                            "Poisson on, one context per rank, instances shared among the "
+                            "ranks by markers x steps")
+            res["scaling"] = "strong" if world > 1 else None
             print(json.dumps(res), flush=True)
         return
     if args.small_pop:
