@@ -224,76 +224,59 @@ __device__ __forceinline__ void limited_kick_n(R (&vx)[N], const R (&vy)[N], con
     }
     if (!(A[j] != (R)0)) continue;
     const R g = A[j] > (R)0 ? (R)1 : (R)-1;
-    R W = L * (g * A[j]);
-    R w = g * vx[j];
-    const R q2 = L2 - p2[j];
-    const R q = q2 > (R)0 ? r_sqrt(q2) : (R)0;
-    bool fwd = true, done = false;
-    R s0;
-    if (w < -q) {
-      // limited and slowing down: reaching the unlimited zone (or the axis,
-      // when p2 >= L2) costs D(q, |w|) >= L (|w| - q)
-      m0[j] = -w;
-      s0 = r_sqrt(sp2);
-      bool stay = W <= L * (m0[j] - q);
-      if (!stay) {
-        const R sq = q > (R)0 ? L : r_sqrt(p2[j]);
-        R C1 = (R)0.5 * (m0[j] * s0 - q * sq);
-        if (p2[j] > (R)0) C1 = mad((R)0.5 * p2[j], r_logk((m0[j] + s0) / (q + sq)), C1);
-        stay = W < C1;
-        if (!stay) {
-          W = W - C1;
-          w = -q;
-        }
+    const R W = L * (g * A[j]);
+    const R w = g * vx[j];
+    // the unlimited zone |w| <= q (empty when p2 >= L2)
+    const R q = r_sqrt(r_max(L2 - p2[j], (R)0));
+    const R s0 = r_sqrt(sp2);
+    const R a0 = -w;
+    // Limited and slowing down (w < -q): reaching the zone (or the axis,
+    // when p2 >= L2) costs C1 = D(q, |w|) >= L (|w| - q).  Every lane forms
+    // C1, so that the common paths run without divergence; it is used only
+    // by the lanes that start there.
+    const bool regI = w < -q;
+    const R sq = q > (R)0 ? L : r_sqrt(p2[j]);
+    R C1 = (R)0.5 * (a0 * s0 - q * sq);
+    if (p2[j] > (R)0) C1 = mad((R)0.5 * p2[j], r_logk((a0 + s0) / (q + sq)), C1);
+    const bool stay = regI && (W <= L * (a0 - q) || W < C1);
+    // otherwise the limited part that speeds up starts at wf with budget Wf
+    R wf = regI ? -q : w;
+    R Wf = regI ? W - C1 : W;
+    R s0f = s0;
+    if (!stay && wf < q) {
+      // the unlimited zone (rare in a warp): the step may end inside it
+      const R reach = L * (q - wf);
+      if (Wf <= reach) {
+        vx[j] = g * (wf + Wf / L);
+        continue;
       }
-      if (stay) {
-        T[j] = -W;
-        lo[j] = q;
-        hi[j] = m0[j];
-        gs[j] = -g;
-        fwd = false;
-      }
+      Wf = Wf - reach;
+      wf = q;
     }
-    if (fwd) {
-      if (w < q) {
-        // unlimited zone
-        const R reach = L * (q - w);
-        if (W <= reach) {
-          vx[j] = g * (w + W / L);
-          done = true;
-        } else {
-          W = W - reach;
-          w = q;
-        }
-      }
-      if (!done) {
-        // limited and speeding up
-        m0[j] = w;
-        s0 = w == g * vx[j] ? r_sqrt(sp2) : r_sqrt(mad(w, w, p2[j]));
-        T[j] = W;
-        lo[j] = w;
-        gs[j] = g;
-      }
-    }
-    if (done) continue;
+    if (!stay && wf != w) s0f = r_sqrt(mad(wf, wf, p2[j]));
+    m0[j] = stay ? a0 : wf;
+    T[j] = stay ? -W : Wf;
+    lo[j] = stay ? q : wf;
+    gs[j] = stay ? -g : g;
+    const R s0s = stay ? s0 : s0f;
     // the solve's constants and its starting guess
-    const R h0 = m0[j] + s0;
-    const R rr = (R)1 / (s0 * h0);
+    const R h0 = m0[j] + s0s;
+    const R rr = (R)1 / (s0s * h0);
     const R is0 = h0 * rr;
-    ih0[j] = s0 * rr;
-    if (fwd) hi[j] = mad(T[j], is0, m0[j]);  // s >= s0 along the way
+    ih0[j] = s0s * rr;
+    hi[j] = stay ? a0 : mad(T[j], is0, m0[j]);  // speeding up: s >= s0 along the way
     const R X = (T[j] * is0) * is0;
     const R c0 = m0[j] * is0;
     R mg;
     if (r_abs(X) <= (R)0.5) {
       const R c3 = mad((R)4 * c0, c0, (R)-1) * (R)(1.0 / 6.0);
       const R zh = X * mad(X, mad(X, c3, (R)-0.5 * c0), (R)1);
-      mg = mad(s0, zh, m0[j]);
+      mg = mad(s0s, zh, m0[j]);
     } else {
       mg = r_sqrt(r_max((R)0, mad(m0[j], m0[j], T[j] + T[j])));
     }
     m[j] = r_min(r_max(mg, lo[j]), hi[j]);
-    hm0s0[j] = (R)0.5 * (m0[j] * s0);
+    hm0s0[j] = (R)0.5 * (m0[j] * s0s);
     act[j] = true;
   }
   bool any = false;
