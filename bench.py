@@ -48,6 +48,10 @@ def parse():
                          "plain one-instance FP64 bisection")
     ap.add_argument("--no-paschen", action="store_true",
                     help="leave out the breakdown-voltage sweep")
+    ap.add_argument("--paschen-full", action="store_true",
+                    help="instead of the benchmark, run the full breakdown search (24 pd points "
+                         "over 0.05-200 Torr cm, 8 voltages each, SLPIC at three v_lim and PIC) "
+                         "and print one JSON line")
     ap.add_argument("--cpu-config1", action="store_true",
                     help="instead of the benchmark, time config 1 (256 cells, 2e4 electrons, "
                          "2000 steps) in full on the CPU oracle and print one JSON line")
@@ -312,6 +316,93 @@ def paschen_sweep(slpic, inputs, local, stream, pds=(0.5, 1.0, 2.0, 4.0), n_v=7,
             "Vb_mid_difference_V": [0.5 * (a + b) - 0.5 * (c + d)
                                     for a, b, c, d in zip(lo32, hi32, lo64, hi64)],
             "speedup": t64 / t32}
+
+
+def paschen_full(slpic, inputs, local, stream, n_pd=12, pd_lo=0.1, pd_hi=100.0, max_cells=2048,
+                 n_v=8, rounds=3, n_seed=1000, pic_max=2.0, fp64_points=4):
+    """The full breakdown search of the sweep workloads, in a bounded form:
+    n_pd pd points log-spaced over [pd_lo, pd_hi] Torr cm (d = 1 cm,
+    gamma = 0.07, cells from dx = lambda_min / 4 clamped to 128-max_cells),
+    each bracketed by a batched
+    section search over n_v voltages per round (n_pd * n_v instances live in
+    one context per method).  Methods: SLPIC with v_lim = 1, 4 and 16 times
+    v0 = sqrt(2 e V / M), and standard PIC (no limit, dt = dx / v_max) for
+    pd <= pic_max (Sec. V ran PIC up to 4 Torr).  Then the plain FP64 form
+    (one single-instance context per pd point, bisection at the same final
+    bracket width) for SLPIC at 4 v0 on fp64_points of the points."""
+    import numpy as np
+    import torch
+    table = inputs.make_table()
+    smax = float(np.max(table["sig_el"].astype(np.float64) + table["sig_ex"] + table["sig_io"]))
+    pds = [pd_lo * (pd_hi / pd_lo) ** (k / (n_pd - 1)) for k in range(n_pd)]
+
+    def spec_for(pd, inst):
+        n_g = pd * inputs.TORR / (inputs.KB * 300.0)
+        cells = int(min(max_cells, max(128, math.ceil(4 * 0.01 * n_g * smax))))
+        return inputs.gap_spec(n_cells=cells, V=300.0, pd_torr_cm=pd, gamma_se=0.07,
+                               field_mode=0, seed=31 + inst, instance=inst)
+
+    def v_guess(pd):
+        # Paschen's law with the Lieberman constants of Sec. V (A = 11.5,
+        # B = 176, gamma = 0.07) above its left asymptote, else 1000 V
+        if pd <= 0.3:
+            return 1000.0
+        return 176.0 * pd / (math.log(11.5 * pd) - math.log(math.log(1 + 1 / 0.07)))
+
+    cap = (2 * 16 * n_seed, 32 * n_seed)
+    out = {"pd_torr_cm": pds, "n_v": n_v, "rounds": rounds, "n_seed": n_seed,
+           "initial_bracket": "[0.5, 3] x Paschen's law (A = 11.5, B = 176, gamma = 0.07), "
+                              "1000 V below 0.3 Torr cm",
+           "bracket_width_fraction_of_initial": 1.0 / (n_v + 1) ** rounds, "methods": {}}
+    for name, f, pmax in (("SLPIC v_lim=1 v0", 1.0, None), ("SLPIC v_lim=4 v0", 4.0, None),
+                          ("SLPIC v_lim=16 v0", 16.0, None), ("PIC", 0.0, pic_max)):
+        pts = [p for p in pds if pmax is None or p <= pmax * 1.0001]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim = slpic.Simulation(len(pts) * n_v, device=local, stream=stream)
+        for a, pd in enumerate(pts):
+            for j in range(n_v):
+                sim.configure(a * n_v + j, spec_for(pd, a * n_v + j), capacity=cap)
+        lo, hi, _ = sim.paschen_bisect([0.5 * v_guess(p) for p in pts],
+                                       [3.0 * v_guess(p) for p in pts], n_v=n_v,
+                                       rounds=rounds, n_seed=n_seed, vlim_factor=f,
+                                       max_steps=2_000_000)
+        sim.close()
+        out["methods"][name] = {"s": time.perf_counter() - t0, "instances": len(pts) * n_v,
+                                "pd_torr_cm": pts, "Vb_lo": [float(x) for x in lo],
+                                "Vb_hi": [float(x) for x in hi]}
+        print("# " + json.dumps({name: out["methods"][name]}), file=sys.stderr, flush=True)
+    # the plain FP64 form on a subset, at the same final bracket width
+    # (n_v + 1 = 8 voltages a round, 3 rounds = 9 halvings)
+    sub = [pds[k] for k in np.linspace(1, n_pd - 2, fp64_points).round().astype(int)]
+    lo32, hi32, t32 = [], [], 0.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim = slpic.Simulation(len(sub) * 7, device=local, stream=stream)
+    for a, pd in enumerate(sub):
+        for j in range(7):
+            sim.configure(a * 7 + j, spec_for(pd, a * 7 + j), capacity=cap)
+    lo, hi, _ = sim.paschen_bisect([0.5 * v_guess(p) for p in sub],
+                                   [3.0 * v_guess(p) for p in sub], n_v=7, rounds=3,
+                                   n_seed=n_seed, vlim_factor=4.0, max_steps=2_000_000)
+    sim.close()
+    t32 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    lo64, hi64 = [], []
+    for pd in sub:
+        sim = slpic.Simulation(1, device=local, stream=stream, precision=64)
+        sim.configure(0, spec_for(pd, 0), capacity=cap)
+        l, h, _ = sim.paschen_bisect([0.5 * v_guess(pd)], [3.0 * v_guess(pd)], n_v=1, rounds=9,
+                                     n_seed=n_seed, vlim_factor=4.0, max_steps=2_000_000)
+        sim.close()
+        lo64.append(float(l[0]))
+        hi64.append(float(h[0]))
+    t64 = time.perf_counter() - t0
+    out["fp32_batched_vs_fp64_plain"] = {
+        "method": "SLPIC v_lim=4 v0", "pd_torr_cm": sub, "bracket_width_fraction_of_initial": 1 / 512,
+        "fp32_batched": {"s": t32, "Vb_lo": [float(x) for x in lo], "Vb_hi": [float(x) for x in hi]},
+        "fp64_plain": {"s": t64, "Vb_lo": lo64, "Vb_hi": hi64}, "speedup": t64 / t32}
+    return out
 
 
 # Table tab:sims: pressure [Torr] at d = 1 cm, voltage [V] near the paper's
@@ -615,6 +706,13 @@ def run_ours(args):
                             "Poisson on, one context per rank, instances shared among the "
                             "ranks by markers x steps")
             res["scaling"] = "strong" if world > 1 else None
+            print(json.dumps(res), flush=True)
+        return
+    if args.paschen_full:
+        if rank == 0:
+            res = paschen_full(slpic, inputs, local, stream)
+            res["study"] = ("breakdown-voltage search over a Paschen curve, batched FP32 on one "
+                            "GB300, SLPIC at three speed limits and PIC")
             print(json.dumps(res), flush=True)
         return
     if args.small_pop:

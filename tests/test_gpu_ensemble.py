@@ -124,13 +124,14 @@ def test_multiplication_per_ion_transit_matches_oracle_within_two_sigma(slpic):
 
 
 def test_breakdown_voltage_matches_oracle_crossing(slpic):
-    """Sec. V breakdown voltages at three pd points (0.6, 1 and 3 Torr cm):
+    """Sec. V breakdown voltages at six pd points (0.3-6 Torr cm, at reduced
+    cell and marker counts):
     the batched bisection's bracket against the oracle's G = 1 crossing,
     found from its mean gains at 7 % either side of the bracket (ln G is
     linear in V over that span), with the crossing's standard error from the
     gains' scatter.  The bracket's centre lies within two standard errors
     (both sides) plus half the bracket of the oracle's crossing."""
-    points = ((0.6, 64), (1.0, 128), (3.0, 256))
+    points = ((0.3, 64), (0.6, 64), (1.0, 128), (2.0, 192), (3.0, 256), (6.0, 384))
     n_v, n_seed = 4, 2000
     sim = slpic.Simulation(len(points) * n_v)
     for p, (pd, cells) in enumerate(points):
@@ -139,7 +140,8 @@ def test_breakdown_voltage_matches_oracle_crossing(slpic):
             sim.configure(i, inputs.gap_spec(**gap_kw(pd, cells, 300.0, seed=3000 + i,
                                                       instance=i, gamma=ens.GAMMA)),
                           capacity=(256 * n_seed, 512 * n_seed))
-    lo, hi, _ = sim.paschen_bisect([100.0] * 3, [500.0] * 3, n_v=n_v, rounds=3, n_seed=n_seed,
+    lo, hi, _ = sim.paschen_bisect([100.0] * len(points), [600.0] * len(points), n_v=n_v,
+                                   rounds=3, n_seed=n_seed,
                                    e0=1.0, vlim_factor=4.0)
     sim.close()
     n_ref, n_b = 200, 8
