@@ -99,12 +99,23 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def _code_only(text):
+    """C++ source without its comments and whitespace (string literals in
+    these kernel files hold no comment markers)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return re.sub(r"\s+", "", text)
+
+
 def push_source_hash():
-    """Hash of the particle kernel's sources (the kernel and its headers)."""
+    """Hash of the particle kernel's code (the kernel and its headers, with
+    comments and whitespace left out): a recorded traffic figure stays valid
+    through comment edits and lapses with any change of code."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2103_12194_gb300", "csrc")
     for name in ("push.cu", "device_common.cuh", "slpic_internal.h", "step_ops.cuh"):
-        h.update(open(os.path.join(csrc, name), "rb").read())
+        h.update(_code_only(open(os.path.join(csrc, name)).read()).encode())
     return h.hexdigest()[:16]
 
 
