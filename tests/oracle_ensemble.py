@@ -89,6 +89,23 @@ def ion_trend(kw, n_seed, steps_per_window, n_windows, stop_markers):
     return means, bool(grows)
 
 
+def space_charge(kw, n, W, steps):
+    """The space-charge run of the Poisson-feedback test: a quasi-neutral
+    plasma of n electron and n ion markers of flux weight W, stepped
+    `steps` steps with the Poisson solve on.  Returns (phi, live counts)."""
+    import oracle
+    from paper_2103_12194_gb300 import inputs
+    spec = _spec(kw)
+    e = inputs.gap_state(n, spec, rng_seed=81, e_lo=1.0, e_hi=5.0, wj=W)
+    i = inputs.gap_state(n, spec, rng_seed=82, e_lo=0.02, e_hi=0.05, species=1, wj=W,
+                         first_id=0)
+    o = oracle.Oracle(spec, precision=64)
+    o.load(0, e)
+    o.load(1, i)
+    o.step(steps)
+    return o.field()[0], [o.count(0), o.count(1)]
+
+
 def pool_map(fn, args):
     """fn(*a) for every a in args, on a spawn-started process pool."""
     n = min(len(args), os.cpu_count() or 1, 16)

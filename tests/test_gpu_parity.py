@@ -174,6 +174,14 @@ def test_one_step_matches_fp32_mirror(slpic, oracle_mod):
     for s in (0, 1):
         qg, qr = sim.charge(0, s), ref.charge(s)
         assert np.allclose(qg, qr, rtol=REL, atol=REL * 2**32)
+    # and it is exactly the FP32 mirror's deposit of the GPU's own markers
+    dep = oracle_mod.Oracle(spec, precision=32)
+    for s in (0, 1):
+        g = sim.particles(0, s)
+        dep.load(s, {k: (g[k] if k in ("cell", "id") else g[k].astype(np.float32)) for k in g})
+    dep.deposit()
+    for s in (0, 1):
+        assert np.array_equal(sim.charge(0, s), dep.charge(s))
     sim.close()
 
 
