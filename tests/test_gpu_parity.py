@@ -318,6 +318,81 @@ def test_kick_matches_mirror_and_fp64_reference(slpic, oracle_mod, regime):
     sim.close()
 
 
+def degenerate_kick_state(L, n_cells, rng_seed=7):
+    """Velocities at the kick's boundaries: at rest; exactly at the limit
+    along +x, -x and across; the perpendicular speed at, just below and just
+    above the limit; on the axis just inside and outside it; and speeds from
+    1e-3 to 1e3 v_lim in every direction."""
+    f32 = np.float32
+    L32 = f32(L)
+    up, dn = np.nextafter(L32, f32(np.inf)), np.nextafter(L32, f32(0))
+    v = [(0, 0, 0), (L32, 0, 0), (-L32, 0, 0), (0, L32, 0), (0, 0, -L32),
+         (0, up, 0), (0, dn, 0), (0.3 * L32, L32, 0), (-0.3 * L32, dn, 0),
+         (up, 0, 0), (dn, 0, 0), (-up, 0, 0), (-dn, 0, 0), (f32(1e-30), 0, 0),
+         (0.6 * L32, 0.8 * L32, 0)]
+    rng = np.random.default_rng(rng_seed)
+    n_r = 4000
+    sp = L * 10.0 ** rng.uniform(-3, 3, n_r)
+    ct = rng.uniform(-1, 1, n_r)
+    st = np.sqrt(1 - ct * ct)
+    ph = rng.uniform(0, 2 * np.pi, n_r)
+    v += list(zip(sp * ct, sp * st * np.cos(ph), sp * st * np.sin(ph)))
+    v = np.array(v, np.float32)
+    n = len(v)
+    return {"cell": (np.arange(n) % n_cells).astype(np.int32),
+            "off": np.full(n, 0.5, np.float32),
+            "vx": v[:, 0].copy(), "vy": v[:, 1].copy(), "vz": v[:, 2].copy(),
+            "wj": np.ones(n, np.float32), "id": np.arange(n, dtype=np.uint32)}
+
+
+def test_kick_degenerate_cases_match_mirror_and_fp64_reference(slpic, oracle_mod):
+    """The kick's edge cases, one vacuum step: no field (A = 0), kicks from
+    1e-6 to about 1e4 v_lim, markers exactly at the limit or one ulp either
+    side, at rest, on the axis, and with the perpendicular speed at the
+    limit (where the unlimited zone closes).  Bit-exact against the FP32
+    mirror; within 2e-6 of max(|v|, v_lim) of the FP64 oracle."""
+    L = 1.5e5
+    N = 64
+    base = dict(n_cells=N, pd_torr_cm=1.0, field_mode=0, vlim_e=L, gamma_se=0.0)
+    dx = 0.01 / N
+    # A = e (V / d) dt / m_e; choose dt for |A| / L = 0 (V = 0), 1e-6, 1e-2, 1, 50, 1e4
+    ratios = (0.0, 1e-6, 1e-2, 1.0, 50.0, 1e4)
+    specs = []
+    for k, r in enumerate(ratios):
+        V = 100.0 if r else 0.0
+        a = inputs.QE * (V / 0.01) / inputs.ME
+        dt = r * L / a if r else dx / L
+        spec = inputs.gap_spec(V=V, dt=dt, seed=11 + k, instance=k, **base)
+        spec["p_Pa"] = 0.0
+        specs.append(spec)
+    sim = slpic.Simulation(len(specs))
+    for k, spec in enumerate(specs):
+        sim.configure(k, spec, capacity=(1 << 14, 1 << 12))
+    st = degenerate_kick_state(L, N)
+    for k in range(len(specs)):
+        sim.load(k, 0, st)
+    sim.step(1)
+    for k, spec in enumerate(specs):
+        g = sim.particles(k, 0)
+        r32 = oracle_mod.Oracle(spec, precision=32)
+        r32.load(0, st)
+        r32.step(1)
+        assert_same_markers(g, r32.particles(0), L, exact_values=True)
+        r64 = oracle_mod.Oracle(spec, precision=64)
+        r64.load(0, st)
+        r64.step(1)
+        r = r64.particles(0)
+        ids, ig, ir = np.intersect1d(g["id"], r["id"], return_indices=True)
+        assert ids.size >= min(g["id"].size, r["id"].size) - 2, k
+        vg = np.stack([g[q][ig] for q in ("vx", "vy", "vz")]).astype(np.float64)
+        vr = np.stack([r[q][ir] for q in ("vx", "vy", "vz")])
+        err = np.abs(vg[0] - vr[0]) / np.maximum(np.linalg.norm(vr, axis=0), L)
+        assert err.max() <= 2e-6, (ratios[k], err.max(), ids[np.argmax(err)])
+        if ratios[k] == 0.0:
+            assert np.array_equal(g["vx"], st["vx"][g["id"]])  # no field: no kick
+    sim.close()
+
+
 # ---------------------------------------------------------------------------
 # Field solve
 # ---------------------------------------------------------------------------

@@ -370,6 +370,36 @@ def test_kick_matches_fine_integration_off_axis(oracle_mod):
     assert err32.max() < 2e-6, err32.max()
 
 
+def test_kick_boundary_cases_match_fine_integration(oracle_mod):
+    """The kick at its boundaries against the RK4 integration: at rest,
+    exactly at the limit along and across the field, the perpendicular
+    speed at the limit (where the unlimited zone closes) or one part in 1e7
+    either side, on the axis just inside and outside the limit, for kicks of
+    1e-2, 1 and 50 v_lim of either sign; and no field at all.  FP64 within
+    1e-9 of the speed, the FP32 mirror within 5e-7."""
+    L = 1.0e5
+    e = 1e-7
+    cases = [(0, 0, 0), (L, 0, 0), (-L, 0, 0), (0, L, 0), (0, L * (1 + e), 0),
+             (0, L * (1 - e), 0), (0.3 * L, L, 0), (-0.3 * L, L * (1 - e), 0),
+             (L * (1 + e), 0, 0), (-L * (1 - e), 0, 0), (0.6 * L, 0.8 * L, 0),
+             (-2 * L, 0.5 * L, 0.1 * L)]
+    vx, vy, vz, A = [], [], [], []
+    for r in (1e-2, 1.0, 50.0):
+        for sgn in (1.0, -1.0):
+            for c in cases:
+                vx.append(c[0]), vy.append(c[1]), vz.append(c[2]), A.append(sgn * r * L)
+    vx, vy, vz, A = map(np.array, (vx, vy, vz, A))
+    err64 = _kick_errors(_kick_oracle(oracle_mod, L, 64), L, vx, vy, vz, A)
+    assert err64.max() < 1e-9, err64.max()
+    f32 = [np.float32(a).astype(np.float64) for a in (vx, vy, vz, A)]
+    err32 = _kick_errors(_kick_oracle(oracle_mod, L, 32), L, *f32)
+    assert err32.max() < 5e-7, err32.max()
+    # no field: no kick, above or below the limit
+    o = _kick_oracle(oracle_mod, L, 64)
+    got = o.kick(0, vx, vy, vz, 0.0 * A)
+    assert np.array_equal(got, vx)
+
+
 def test_planted_trapezoid_kick_fails_the_integration_pin(oracle_mod):
     """The pin above catches a plausible mistake: the elapsed time of the
     speed-limited part taken by the trapezoid rule and solved by one Newton
