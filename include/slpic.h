@@ -416,7 +416,7 @@ int slpic_multiplication(slpic_ctx* ctx, int64_t steps_per_window, int n_windows
                          double* M);
 
 /* Launch shape of the step: warps per CTA of the particle kernel (a
- * multiple of 4, at most 24; each warp owns a 128-slot tile) and CTAs per
+ * multiple of 4, at most 20; each warp owns a 128-slot tile) and CTAs per
  * SM of the collision kernel (1..32).  While the warps' stages leave room
  * for the largest instance's charge grid in shared memory the kernel
  * deposits there; with more warps it deposits to global memory.  The

@@ -20,7 +20,7 @@ constexpr uint32_t kSeedStep = 0xFFFFFFFFu;
 // shared-memory stages.
 constexpr int kTile = 128;
 constexpr int kPerLane = kTile / 32;
-constexpr int kPushMaxWarps = 24;
+constexpr int kPushMaxWarps = 20;
 constexpr int kPushStages = 2;
 // The particle kernel advances a lane's kPerLane slots in kHalves passes.
 constexpr int kHalves = 2;

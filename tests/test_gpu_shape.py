@@ -33,11 +33,11 @@ def assert_same_state(a, b, n_inst):
 
 
 def test_results_do_not_depend_on_launch_shape(slpic):
-    items = batch_items()[:4]  # the grids fit next to 24 warps' stages
+    items = batch_items()[:4]  # the grids fit next to 20 warps' stages
     states = states_for(items, seed0=60)
     ref = load_batch(slpic, items, states)
     w0, c0 = ref.launch_shape()
-    assert w0 == 24 and c0 == 8
+    assert w0 == 20 and c0 == 8
     ref.step(40)
     for shape in ((8, 4), (4, 16), (12, 1), (20, 2)):
         sim = load_batch(slpic, items, states)
@@ -56,7 +56,7 @@ def test_autotune_keeps_the_results(slpic):
     states = states_for(items, seed0=70)
     tuned = load_batch(slpic, items, states)
     w, cc = tuned.autotune(steps_each=8)
-    assert w % 4 == 0 and 4 <= w <= 24 and cc in (2, 4, 8, 16)
+    assert w % 4 == 0 and 4 <= w <= 20 and cc in (2, 4, 8, 16)
     assert tuned.launch_shape() == (w, cc)
     steps = len(tuned.history(0))
     assert steps >= 8 * 6
@@ -69,7 +69,7 @@ def test_autotune_keeps_the_results(slpic):
 
 def test_more_warps_than_fit_beside_the_shared_grid_deposit_to_global_memory(slpic):
     """With the 16384-cell gap in the batch, a particle-kernel CTA fits at
-    most 12 warps beside the shared charge grid; 16 and 24 warps deposit to
+    most 12 warps beside the shared charge grid; 16 and 20 warps deposit to
     global memory instead.  The integers, and so every result, are the
     same."""
     items = batch_items()
@@ -78,7 +78,7 @@ def test_more_warps_than_fit_beside_the_shared_grid_deposit_to_global_memory(slp
     ref = load_batch(slpic, items, states)
     assert ref.launch_shape() == (12, 8)
     ref.step(40)
-    for shape in ((16, 8), (24, 4)):
+    for shape in ((16, 8), (20, 4)):
         sim = load_batch(slpic, items, states)
         sim.set_launch_shape(*shape)
         assert sim.launch_shape() == shape
