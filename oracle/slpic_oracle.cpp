@@ -429,28 +429,44 @@ struct Sim {
   // (the error left is then about the cube of that, under a float ulp).
   static float mad32(float a, float b, float c) { return std::fmaf(a, b, c); }
 
-  // Natural logarithm of a positive normal float from IEEE operations:
-  // y = 2^k m with m in [sqrt(1/2), sqrt(2)), log m = 2 atanh(t),
-  // t = (m - 1) / (m + 1), |t| <= 0.1716, by the Taylor series of atanh to
-  // t^9 (the next term is below 2^-28 of the sum); log 2 split in two parts
-  // so that k log 2 keeps its precision.
+  // Natural logarithm of a positive normal float by Tang's table-driven
+  // method (ACM TOMS 16, 1990), from IEEE operations and a table:
+  // y = 2^k m with m's bit pattern in [0x3F350000, 0x3FB50000) (about
+  // [0.707, 1.414)); interval j of m (the top 6 bits of its offset from the
+  // lower end) has centre c_j = the float at 0x3F350000 + 2^17 j + 2^16;
+  // r_j = 1 / c_j rounded to float, n_j = -log(r_j) rounded to float;
+  // f = m r_j - 1 in one rounding (|f| < 2^-7); log(1 + f) by its Taylor
+  // series to f^4; log y = k log 2 + n_j + log(1 + f), with log 2 split in
+  // two parts so that k log 2 keeps its precision.
+  struct LogTable {
+    float r[64], n[64];
+    LogTable() {
+      for (int j = 0; j < 64; ++j) {
+        const uint32_t cb = 0x3F350000u + ((uint32_t)j << 17) + (1u << 16);
+        float c;
+        std::memcpy(&c, &cb, 4);
+        r[j] = 1.0f / c;
+        n[j] = (float)(-std::log((double)r[j]));
+      }
+    }
+  };
   static float log_mirror(float y) {
+    static const LogTable tab;
     uint32_t b;
     std::memcpy(&b, &y, 4);
-    const int32_t ix = (int32_t)b - (int32_t)0x3F3504F3;
+    const int32_t ix = (int32_t)b - (int32_t)0x3F350000;
     const int32_t k = ix >> 23;
-    const uint32_t mb = (uint32_t)(ix & 0x7FFFFF) + 0x3F3504F3u;
+    const uint32_t mb = (uint32_t)ix & 0x7FFFFFu;
+    const uint32_t bits = mb + 0x3F350000u;
     float m;
-    std::memcpy(&m, &mb, 4);
-    const float f = m - 1.0f;
-    const float t = f / (m + 1.0f);
-    const float t2 = t * t;
-    float poly = mad32(t2, 1.0f / 9.0f, 1.0f / 7.0f);
-    poly = mad32(t2, poly, 1.0f / 5.0f);
-    poly = mad32(t2, poly, 1.0f / 3.0f);
-    poly = mad32(t2, poly, 1.0f);
+    std::memcpy(&m, &bits, 4);
+    const int j = (int)(mb >> 17);
+    const float f = mad32(m, tab.r[j], -1.0f);
+    float q = mad32(f, -0.25f, 1.0f / 3.0f);
+    q = mad32(f, q, -0.5f);
+    const float lp = mad32(f * f, q, f);
     const float kf = (float)k;
-    return mad32(kf, 0.693145751953125f, mad32(kf, 1.428606765330187e-06f, (t + t) * poly));
+    return mad32(kf, 0.693145751953125f, mad32(kf, 1.428606765330187e-06f, tab.n[j] + lp));
   }
 
   // End speed m >= 0 along the force with D(m0, m) = T, root in [lo, hi];

@@ -144,25 +144,51 @@ __device__ __forceinline__ R beta_of(R v, R vlim) {
 __device__ __forceinline__ float mad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double mad(double a, double b, double c) { return a * b + c; }
 
-// Natural logarithm of a positive normal float from IEEE operations only:
-// y = 2^k m with m in [sqrt(1/2), sqrt(2)), log m = 2 atanh(t) with
-// t = (m - 1) / (m + 1), |t| <= 0.1716, by the Taylor series of atanh up to
-// t^9 (the next term is below 2^-28 of the sum), and k log 2 with log 2
-// split in a 15-bit head and a tail so that the product keeps its precision.
+// Natural logarithm of a positive normal float by Tang's table-driven method
+// (P. T. P. Tang, "Table-driven implementation of the logarithm function in
+// IEEE floating-point arithmetic", ACM TOMS 16, 1990), from IEEE operations
+// and one table read, with no division:
+//  - y = 2^k m with m in [0x3F350000, 0x3FB50000) as bit patterns
+//    (about [0.707, 1.414)); the top 6 bits of m's offset from the lower end
+//    pick interval j, whose centre c_j is the float at bit pattern
+//    0x3F350000 + 2^17 j + 2^16 (c_37 = 1 exactly);
+//  - kLogTab[j] = {r_j, n_j} with r_j = 1 / c_j rounded to float and n_j =
+//    -log(r_j) rounded to nearest float (r_37 = 1, n_37 = 0);
+//  - f = m r_j - 1 in one rounding (|f| < 2^-7), log(1 + f) by its Taylor
+//    series to f^4 (the next term is below 2^-28 of the sum), and
+//    log y = k log 2 + n_j + log(1 + f), with log 2 split in a 15-bit head
+//    and a tail so that the product keeps its precision.
 // In double the library's log is used.
+__device__ const float2 kLogTab[64] = {
+    {1.4065934e+00f, -3.411708e-01f}, {1.3913044e+00f, -3.302417e-01f}, {1.3763441e+00f, -3.1943077e-01f}, {1.3617021e+00f, -3.0873546e-01f},
+    {1.3473685e+00f, -2.981534e-01f}, {1.3333334e+00f, -2.8768212e-01f}, {1.3195876e+00f, -2.7731925e-01f}, {1.3061224e+00f, -2.6706275e-01f},
+    {1.2929293e+00f, -2.569104e-01f}, {1.28e+00f, -2.4686006e-01f}, {1.2673267e+00f, -2.3690973e-01f}, {1.254902e+00f, -2.2705749e-01f},
+    {1.2427185e+00f, -2.1730128e-01f}, {1.2307693e+00f, -2.076394e-01f}, {1.2190477e+00f, -1.9806994e-01f}, {1.2075472e+00f, -1.8859118e-01f},
+    {1.1962616e+00f, -1.792014e-01f}, {1.1851852e+00f, -1.6989905e-01f}, {1.1743119e+00f, -1.6068234e-01f}, {1.1636363e+00f, -1.5154986e-01f},
+    {1.1531532e+00f, -1.4250009e-01f}, {1.1428572e+00f, -1.3353144e-01f}, {1.1327434e+00f, -1.2464244e-01f}, {1.122807e+00f, -1.1583182e-01f},
+    {1.1130434e+00f, -1.0709809e-01f}, {1.1034483e+00f, -9.8440066e-02f}, {1.0940171e+00f, -8.985638e-02f}, {1.0847458e+00f, -8.134564e-02f},
+    {1.0756303e+00f, -7.290682e-02f}, {1.0666667e+00f, -6.4538576e-02f}, {1.0578512e+00f, -5.6239676e-02f}, {1.0491803e+00f, -4.8009165e-02f},
+    {1.0406504e+00f, -3.9845873e-02f}, {1.032258e+00f, -3.1748667e-02f}, {1.024e+00f, -2.3716575e-02f}, {1.0158731e+00f, -1.5748415e-02f},
+    {1.007874e+00f, -7.843174e-03f}, {1.e+00f, 0.e+00f}, {9.846154e-01f, 1.5504186e-02f}, {9.69697e-01f, 3.0771628e-02f},
+    {9.5522386e-01f, 4.580956e-02f}, {9.411765e-01f, 6.0624618e-02f}, {9.2753625e-01f, 7.52234e-02f}, {9.142857e-01f, 8.9612156e-02f},
+    {9.0140843e-01f, 1.0379681e-01f}, {8.888889e-01f, 1.17783025e-01f}, {8.767123e-01f, 1.3157636e-01f}, {8.648649e-01f, 1.4518198e-01f},
+    {8.5333335e-01f, 1.5860501e-01f}, {8.4210527e-01f, 1.7185025e-01f}, {8.3116883e-01f, 1.8492234e-01f}, {8.2051283e-01f, 1.9782573e-01f},
+    {8.101266e-01f, 2.1056475e-01f}, {8.e-01f, 2.2314353e-01f}, {7.9012346e-01f, 2.3556606e-01f}, {7.804878e-01f, 2.478362e-01f},
+    {7.710843e-01f, 2.5995755e-01f}, {7.619048e-01f, 2.719337e-01f}, {7.529412e-01f, 2.8376815e-01f}, {7.4418604e-01f, 2.9546422e-01f},
+    {7.356322e-01f, 3.0702505e-01f}, {7.2727275e-01f, 3.184537e-01f}, {7.1910113e-01f, 3.2975328e-01f}, {7.111111e-01f, 3.4092656e-01f},
+};
 __device__ __forceinline__ float r_logk(float y) {
-  const int ix = (int)__float_as_uint(y) - 0x3F3504F3;
+  const int ix = (int)__float_as_uint(y) - 0x3F350000;
   const int k = ix >> 23;
-  const float m = __uint_as_float((uint32_t)(ix & 0x7FFFFF) + 0x3F3504F3u);
-  const float f = m - 1.0f;
-  const float t = f / (m + 1.0f);
-  const float t2 = t * t;
-  float poly = __fmaf_rn(t2, 1.0f / 9.0f, 1.0f / 7.0f);
-  poly = __fmaf_rn(t2, poly, 1.0f / 5.0f);
-  poly = __fmaf_rn(t2, poly, 1.0f / 3.0f);
-  poly = __fmaf_rn(t2, poly, 1.0f);
+  const uint32_t mb = (uint32_t)ix & 0x7FFFFFu;
+  const float m = __uint_as_float(mb + 0x3F350000u);
+  const float2 t = __ldg(&kLogTab[mb >> 17]);
+  const float f = __fmaf_rn(m, t.x, -1.0f);
+  float q = __fmaf_rn(f, -0.25f, 1.0f / 3.0f);
+  q = __fmaf_rn(f, q, -0.5f);
+  const float lp = __fmaf_rn(f * f, q, f);
   const float kf = (float)k;
-  return __fmaf_rn(kf, 0.693145751953125f, __fmaf_rn(kf, 1.428606765330187e-06f, (t + t) * poly));
+  return __fmaf_rn(kf, 0.693145751953125f, __fmaf_rn(kf, 1.428606765330187e-06f, t.y + lp));
 }
 __device__ __forceinline__ double r_logk(double y) { return log(y); }
 
