@@ -417,8 +417,9 @@ int commit(slpic_ctx* c) {
       const size_t cand_slots = s == kElectron ? slots : 0;
       const size_t arr = ((size_t)cap_tiles[s] + 1) * 4 + 256;
       const size_t rsz = c->fp64 ? 8 : 4;
+      const size_t crsz = c->fp64 ? sizeof(CandRec<double>) : sizeof(CandRec<float>);
       size_t b = 2 * soa_bytes(slots, rsz) + soa_bytes(stage_b, rsz) + 4 * arr +
-                 cand_slots * (2 + rsz) + 512;
+                 cand_slots * crsz + 512;
       void* sb;
       if (int rc = dmalloc(c, &sb, b, "marker buffers")) return rc;
       char* q = (char*)sb;
@@ -430,8 +431,7 @@ int commit(slpic_ctx* c) {
       S.fill[1] = carve<uint32_t>(q, cap_tiles[s] + 1);
       S.births = carve<uint32_t>(q, cap_tiles[s] + 1);
       S.n_cand = carve<uint32_t>(q, cap_tiles[s] + 1);
-      S.cand = cand_slots ? carve<uint16_t>(q, cand_slots) : nullptr;
-      S.esec = cand_slots ? (void*)carve<char>(q, cand_slots * rsz) : nullptr;
+      S.crec = cand_slots ? (void*)carve<char>(q, cand_slots * crsz) : nullptr;
       CK(cudaMemset(S.fill[0], 0, ((size_t)cap_tiles[s] + 1) * 4), "fills");
       CK(cudaMemset(S.fill[1], 0, ((size_t)cap_tiles[s] + 1) * 4), "fills");
       total_tiles += cap_tiles[s];

@@ -12,7 +12,9 @@
 //
 // Work: chunks of kCollChunkTiles consecutive tiles (each warp kCollWarpTiles
 // of them; the warp numbers the candidates of its tiles in (tile, slot) order
-// and takes them 32 at a time, one lane each), handed out in order (electron
+// and takes them 32 at a time, one lane each, reading each candidate's
+// record -- its state and slot, one 32-byte sector in float -- and writing
+// only the new velocity to its slot), handed out in order (electron
 // tiles of an instance, then its ion tiles).  The births of a chunk (ionizations; for ion chunks the
 // electrons the particle kernel staged for emission) get their slots from an
 // ordered scan over the chunks (decoupled look-back), so they are appended
@@ -86,7 +88,6 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
     const SoAT<R> me = soa_as<R>(E.buf[se.cur]);
     const StepConsts<R>& K = consts<R>(P);
     const R kv = K.K_V[kElectron], vlim = K.vlim[kElectron];
-    R* esec = reinterpret_cast<R*>(E.esec);
     // events of the tiles (electron chunks: queued candidates; ion chunks:
     // electrons emitted at the cathode) and their exclusive prefix: the
     // warp's events are numbered in (tile, slot) order
@@ -123,12 +124,12 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
         bool ionized = false;
         if (ce < total) {
           const size_t base = (size_t)(kw + j) * kTile;
-          const uint32_t a = E.cand[base + q];
-          const size_t o = base + a;
-          const int cell = me.cell[o];
-          const R off = me.off[o], wj = me.wj[o];
-          const uint32_t id = me.id[o];
-          R vx = me.vx[o], vy = me.vy[o], vz = me.vz[o];
+          const CandRec<R> cr = get_cand<R>(E.crec, base + q);
+          const size_t o = base + cr.slot;
+          const int cell = cr.cell;
+          const R off = cr.off, wj = cr.wj;
+          const uint32_t id = cr.id;
+          R vx = cr.vx, vy = cr.vy, vz = cr.vz;
           const R s1 = vx * vx + vy * vy + vz * vz;
           const R v1 = r_sqrt(s1);
           const uint4 rr =
@@ -145,9 +146,11 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
             me.vy[o] = vy;
             me.vz[o] = vz;
             if (proc == 2) {
+              // mark for pass 2, with the secondary's energy in place of vx
               ionized = true;
-              E.cand[base + q] = (uint16_t)(a | 0x8000u);  // mark for pass 2
-              esec[base + q] = es;
+              CandRec<R>* w = reinterpret_cast<CandRec<R>*>(E.crec) + base + q;
+              w->slot = cr.slot | kIonizedMark;
+              w->vx = es;
             }
           }
           if (P.field_mode == 1)  // imposed field: the deposit is formed when read
@@ -186,22 +189,23 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
           uint32_t q;
           const int j = locate_event(ce < total ? ce : total - 1, q);
           const size_t base = (size_t)(kw + j) * kTile;
-          const uint32_t a = ce < total ? E.cand[base + q] : 0u;
-          const bool ionized = ce < total && (a & 0x8000u);
+          const CandRec<R>* rp = reinterpret_cast<const CandRec<R>*>(E.crec) + base + q;
+          const uint32_t a = ce < total ? rp->slot : 0u;
+          const bool ionized = ce < total && (a & kIonizedMark);
           const uint32_t b = __ballot_sync(0xFFFFFFFFu, ionized);
           if (ionized) {
             const uint32_t rank = off_w + ranked + __popc(b & lanemask_lt);
-            const size_t o = base + (a & 0x7FFFu);
+            const CandRec<R> cr = *rp;
             const uint32_t pe = app_e + rank, pi = app_i + rank;
             if (pe >= cap_e || pi >= cap_i) {
               atomicCAS(&ctrl->error, 0, kErrCapacity);
             } else {
               if (P.field_mode == 1)
-                born_pair<R>(P, me, mi, pe, pi, me.cell[o], me.off[o], me.wj[o], me.id[o], step,
-                             esec[base + q], se.next_id + rank, si.next_id + rank);
+                born_pair<R>(P, me, mi, pe, pi, cr.cell, cr.off, cr.wj, cr.id, step, cr.vx,
+                             se.next_id + rank, si.next_id + rank);
               else
-                born_pair<R, false>(P, me, mi, pe, pi, me.cell[o], me.off[o], me.wj[o], me.id[o],
-                                    step, esec[base + q], se.next_id + rank, si.next_id + rank);
+                born_pair<R, false>(P, me, mi, pe, pi, cr.cell, cr.off, cr.wj, cr.id, step, cr.vx,
+                                    se.next_id + rank, si.next_id + rank);
             }
           }
           ranked += __popc(b);
@@ -239,6 +243,6 @@ void launch_collide(const DeviceRefs& r, int grid, cudaStream_t s) {
 
 static_assert(kCollThreads == 32 * kCollWarps, "kCollWarps warps per chunk");
 static_assert(kCollWarpTiles <= 32, "per-tile counts live one per lane");
-static_assert(kTile <= 0x8000, "candidate slots leave the top bit for the ionization mark");
+static_assert((uint32_t)kTile < kIonizedMark, "candidate slots leave the top bit for the ionization mark");
 
 }  // namespace slpic

@@ -26,8 +26,9 @@
 //     when a marker left the tile, and lane 0 stores the fields that changed
 //     to the tile's own slots with bulk copies.
 // Collision candidates (the electrons that drew u < P0) are not scattered
-// here: their final slots are queued per tile and k_collide scatters them
-// all at once, so the long, rare scattering path never stalls the stream.
+// here: their states and final slots are queued per tile as 32-byte records
+// and k_collide scatters them all at once, so the long, rare scattering path
+// never stalls the stream and reads each candidate with one sector.
 // The shared charge grid is added to global memory with integer atomics when
 // the CTA moves to another segment (a CTA-wide barrier, taken by all warps at
 // the same round) or finishes, so the deposit is exact and independent of the
@@ -442,7 +443,8 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
               if (electrons) {
                 // the candidate's slot after compaction = its rank among survivors
                 const uint32_t r_a = pre_alive[j] + (uint32_t)__popc(b_alive[j] & lanemask_lt);
-                S.cand[tbase + e] = (uint16_t)r_a;
+                put_cand(S.crec, tbase + e, cell[j], off[j], vx[j], vy[j], vz[j], wj[j], id[j],
+                         r_a);
               } else if (dep) {
                 stage_emission<R>(P, tbase + e, wj[j]);
               } else {

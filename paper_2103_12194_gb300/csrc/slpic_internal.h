@@ -171,17 +171,38 @@ struct Transfer {
   uint32_t pad;
 };
 
+// A null-collision candidate as the particle kernel leaves it: the electron's
+// state after its push and its slot in the tile after compaction (the top bit
+// marks an ionization once it has collided; vx then holds the energy given to
+// the secondary).  One record fills a 32-byte sector in float, so the
+// collision kernel reads a candidate with one sector instead of one per field.
+template <typename R>
+struct CandRec;
+template <>
+struct alignas(32) CandRec<float> {
+  int cell;
+  float off, vx, vy, vz, wj;
+  uint32_t id, slot;
+};
+template <>
+struct alignas(16) CandRec<double> {
+  int cell;
+  uint32_t id;
+  double off, vx, vy, vz, wj;
+  uint32_t slot, pad;
+};
+static_assert(sizeof(CandRec<float>) == 32, "one sector per float record");
+constexpr uint32_t kIonizedMark = 0x80000000u;
+
 // Configuration of one species of one instance (constant during a run).
 struct SpeciesDev {
   SoA buf[2];         // tiled marker store (cap_tiles * kTile slots each)
   uint32_t* fill[2];  // [cap_tiles] live markers per tile of each buffer
   SoA stage_b;        // electrons only: emission births, slot = ion tile * kTile + rank
   uint32_t* births;   // ions: [cap_tiles] electrons emitted by each tile in the step
-  uint16_t* cand;     // electrons: [cap_tiles * kTile] slots of the tile's
-                      // null-collision candidates, in slot order
+  void* crec;         // electrons: [cap_tiles * kTile] CandRec<R>, the tile's
+                      // null-collision candidates in slot order
   uint32_t* n_cand;   // electrons: [cap_tiles] candidates per tile
-  void* esec;         // electrons: [cap_tiles * kTile] energy (type R) given
-                      // to the secondary by an ionizing candidate
   uint32_t cap_tiles;
   uint32_t pad;
 };

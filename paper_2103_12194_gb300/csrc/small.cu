@@ -319,7 +319,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(DeviceRefs r, long l
             const uint32_t e = pre_event[j] + (uint32_t)__popc(b_event[j] & lanemask_lt);
             if (electrons) {
               const uint32_t r_a = pre_alive[j] + (uint32_t)__popc(b_alive[j] & lanemask_lt);
-              S.cand[tbase + e] = (uint16_t)r_a;
+              put_cand(S.crec, tbase + e, cell[j], off[j], vx[j], vy[j], vz[j], wj[j], id[j],
+                       r_a);
             } else {
               stage_emission<R, false>(P, tbase + e, wj[j]);
             }
@@ -385,17 +386,18 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(DeviceRefs r, long l
         const int j = tile_of_event(sh.pre[0], (int)se.n_tiles, c);
         const uint32_t q = c - sh.pre[0][j];
         const size_t base = (size_t)j * kTile;
-        const size_t o = base + E.cand[base + q];
+        const CandRec<R> cr = get_cand<R>(E.crec, base + q);
+        const size_t o = base + cr.slot;
         slot[u] = (uint32_t)o;
-        const uint32_t id = me.id[o];
-        R vx = me.vx[o], vy = me.vy[o], vz = me.vz[o];
+        const uint32_t id = cr.id;
+        R vx = cr.vx, vy = cr.vy, vz = cr.vz;
         const R s1 = vx * vx + vy * vy + vz * vz;
         const R v1 = r_sqrt(s1);
         const uint4 rr = philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u, 0u), P.key0, P.key1);
         int proc;
         R e2 = (R)0;
         const Velocity<R> nv = collide<R>(P, kv, vlim, vx, vy, vz, v1, s1, rr, id, step,
-                                          me.wj[o], sh.acc, &e2, &proc);
+                                          cr.wj, sh.acc, &e2, &proc);
         if (proc < 3) {
           me.vx[o] = nv.vx;
           me.vy[o] = nv.vy;

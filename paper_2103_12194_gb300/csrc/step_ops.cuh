@@ -284,6 +284,36 @@ __device__ __forceinline__ void write_marker(const SoAT<R>& d, size_t o, int cel
   d.id[o] = id;
 }
 
+// Record of null-collision candidate i of an electron store (the tile's
+// queue slot tbase + rank): in float two 16-byte stores of one sector.
+__device__ __forceinline__ void put_cand(void* crec, size_t i, int cell, float off, float vx,
+                                         float vy, float vz, float wj, uint32_t id,
+                                         uint32_t slot) {
+  float4* p = reinterpret_cast<float4*>(reinterpret_cast<CandRec<float>*>(crec) + i);
+  p[0] = make_float4(__int_as_float(cell), off, vx, vy);
+  p[1] = make_float4(vz, wj, __uint_as_float(id), __uint_as_float(slot));
+}
+__device__ __forceinline__ void put_cand(void* crec, size_t i, int cell, double off, double vx,
+                                         double vy, double vz, double wj, uint32_t id,
+                                         uint32_t slot) {
+  CandRec<double> c;
+  c.cell = cell;
+  c.id = id;
+  c.off = off;
+  c.vx = vx;
+  c.vy = vy;
+  c.vz = vz;
+  c.wj = wj;
+  c.slot = slot;
+  c.pad = 0u;
+  reinterpret_cast<CandRec<double>*>(crec)[i] = c;
+}
+
+template <typename R>
+__device__ __forceinline__ CandRec<R> get_cand(const void* crec, size_t i) {
+  return reinterpret_cast<const CandRec<R>*>(crec)[i];
+}
+
 constexpr int kFinThreads = 1024;
 
 __device__ __forceinline__ long long shfl_up(long long v, int o) {
