@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
   __shared__ uint32_t s_births[kCollWarps];
   __shared__ uint32_t s_prefix;
   __shared__ unsigned int s_chunk;
+  step_kernel_entry();
   Control* ctrl = r.ctrl;
   if (*((volatile int*)&ctrl->error)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -237,8 +238,8 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
 }
 
 void launch_collide(const DeviceRefs& r, int grid, cudaStream_t s) {
-  if (r.fp64) k_collide<double><<<grid, kCollThreads, 0, s>>>(r);
-  else k_collide<float><<<grid, kCollThreads, 0, s>>>(r);
+  if (r.fp64) launch_step_kernel(k_collide<double>, grid, kCollThreads, 0, s, r);
+  else launch_step_kernel(k_collide<float>, grid, kCollThreads, 0, s, r);
 }
 
 static_assert(kCollThreads == 32 * kCollWarps, "kCollWarps warps per chunk");

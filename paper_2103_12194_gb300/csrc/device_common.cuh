@@ -15,6 +15,34 @@
 
 namespace slpic {
 
+// Programmatic dependent launch between the kernels of a step: each kernel
+// lets the next one be scheduled at once (its CTAs take SMs as this grid's
+// CTAs leave) and waits, before its first read of global memory, until the
+// previous grid has completed and its writes are visible.  Launched without
+// the attribute, the wait returns at once.
+__device__ __forceinline__ void step_kernel_entry() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Launch a step kernel with programmatic stream serialization (see
+// step_kernel_entry); errors surface through cudaGetLastError like <<<>>>.
+template <typename... P, typename... A>
+inline void launch_step_kernel(void (*kernel)(P...), int grid, int threads, size_t smem,
+                               cudaStream_t s, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned int)grid);
+  cfg.blockDim = dim3((unsigned int)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  (void)cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
+}
+
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each two
 // 32x32 -> 64-bit products of counter words 0 and 2 with the round
 // multipliers, the high halves mixed with the other words and the round key;

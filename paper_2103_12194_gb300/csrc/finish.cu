@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode, 
   __shared__ __int128 s_i128[32];
   __shared__ unsigned long long s_acc[ACC_COUNT];
   __shared__ int s_flag;
+  step_kernel_entry();
   Control* ctrl = r.ctrl;
   const int t = threadIdx.x;
   if (mode == 1) {
@@ -334,7 +335,7 @@ int finish_config(int max_nodes, int* net_nodes) {
 void launch_finish(const DeviceRefs& r, int mode, cudaStream_t s) {
   const int grid = mode == 1 ? 1 : r.n_inst;
   const int nodes = mode == 1 ? 0 : r.finish_net_nodes;
-  k_finish<<<grid, kFinThreads, (size_t)nodes * 8, s>>>(r, mode, nodes);
+  launch_step_kernel(k_finish, grid, kFinThreads, (size_t)nodes * 8, s, r, mode, nodes);
 }
 
 // ---------------------------------------------------------------------------
@@ -350,6 +351,7 @@ __global__ void __launch_bounds__(kMoveThreads) k_move(DeviceRefs r) {
   __shared__ uint32_t s_pre[kMoveChunkTiles];
   __shared__ unsigned int s_chunk;
   constexpr int kPerLaneTiles = kMoveChunkTiles / 32;
+  step_kernel_entry();
   Control* ctrl = r.ctrl;
   if (*((volatile int*)&ctrl->error)) return;
   const unsigned int n_chunks = ctrl->n_move_chunks;
@@ -425,8 +427,8 @@ __global__ void __launch_bounds__(kMoveThreads) k_move(DeviceRefs r) {
 }
 
 void launch_move(const DeviceRefs& r, int grid, cudaStream_t s) {
-  if (r.fp64) k_move<double><<<grid, kMoveThreads, 0, s>>>(r);
-  else k_move<float><<<grid, kMoveThreads, 0, s>>>(r);
+  if (r.fp64) launch_step_kernel(k_move<double>, grid, kMoveThreads, 0, s, r);
+  else launch_step_kernel(k_move<float>, grid, kMoveThreads, 0, s, r);
 }
 
 // ---------------------------------------------------------------------------

@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(kPushMaxWarps * 32, 1) k_push(DeviceRefs r) {
       reinterpret_cast<unsigned long long*>(smem_raw + (size_t)W * kPushStages * kSB);
   uint64_t* bars = s_bar[warp];
 
+  step_kernel_entry();
   Control* ctrl = r.ctrl;
   if (*((volatile int*)&ctrl->error)) return;
   const uint32_t limit = spin_limit(ctrl);
@@ -589,11 +590,11 @@ void launch_push(const DeviceRefs& r, int grid, cudaStream_t s) {
   if (r.fp64) {
     const size_t bytes = (size_t)r.push_warps * kPushStages * stage_bytes<double>() +
                          (size_t)r.smem_nodes * 8;
-    k_push<double><<<grid, r.push_warps * 32, bytes, s>>>(r);
+    launch_step_kernel(k_push<double>, grid, r.push_warps * 32, bytes, s, r);
   } else {
     const size_t bytes = (size_t)r.push_warps * kPushStages * stage_bytes<float>() +
                          (size_t)r.smem_nodes * 8;
-    k_push<float><<<grid, r.push_warps * 32, bytes, s>>>(r);
+    launch_step_kernel(k_push<float>, grid, r.push_warps * 32, bytes, s, r);
   }
 }
 
