@@ -358,7 +358,7 @@ int commit(slpic_ctx* c) {
     if (c->fp64) bytes += (tab_n * sizeof(TabNode64) + 255) & ~size_t(255);
     bytes += ((nn * 4 + 255) & ~size_t(255));
     bytes += 2 * ((nn * 8 + 255) & ~size_t(255));
-    bytes += 4 * ((nn * 8 + 255) & ~size_t(255));
+    bytes += 5 * ((nn * 8 + 255) & ~size_t(255)) + 256;
     bytes += 256 + ((sizeof(TallyRec) * kRingLen + 255) & ~size_t(255)) + 256;
     void* blk;
     if (int rc = dmalloc(c, &blk, bytes, "instance arrays")) return rc;
@@ -375,6 +375,8 @@ int commit(slpic_ctx* c) {
     P.rho_acc[1] = carve<unsigned long long>(p, nn);
     P.rho_last[0] = carve<long long>(p, nn);
     P.rho_last[1] = carve<long long>(p, nn);
+    P.pois_I = carve<long long>(p, nn);
+    P.pois_D1 = carve<double>(p, 1);
     P.acc = carve<unsigned long long>(p, ACC_COUNT);
     P.ring = carve<TallyRec>(p, kRingLen);
     P.total = carve<TallyRec>(p, 1);

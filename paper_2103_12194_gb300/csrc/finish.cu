@@ -2,8 +2,9 @@
 // from the step's exact counters (the particle kernel compacted every tile,
 // k_collide appended every birth), decides whether a store is repacked,
 // publishes the step's deposit, solves the 1D Poisson equation for the next
-// step's field and commits the step's tallies; the last CTA plans the next
-// step.  k_move repacks the stores that became sparse.  With an imposed
+// step's field (its exact integer sums) and commits the step's tallies; the
+// last CTA plans the next step.  k_move evaluates the field from those sums
+// over the whole grid and repacks the stores that became sparse.  With an imposed
 // field the step deposits nothing and k_deposit forms the deposit from the
 // markers when it is read.  Also: seeding, load validation and the Philox
 // self-check kernel.
@@ -184,34 +185,20 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode, 
   // and phi[N] = V fixes D_1 = (V + C J_N) / N, J_N = sum_{0<i<=N} I_i.
   // The node field is the centred difference of phi, written with the exact
   // integer sums: E_k = -(D_k + D_{k+1}) / (2 dx) = -(2 D_1 - C (I_k + I_{k+1}))
-  // / (2 dx), one-sided at the electrodes; phi itself is formed on demand
-  // (k_phi) when it is read.
+  // / (2 dx), one-sided at the electrodes.  This CTA leaves I_k and D_1; k_move,
+  // which follows every step on many SMs, evaluates E in FP64 (poisson_field),
+  // and phi is formed on demand (k_phi) when it is read.
   if (P.field_mode == 1) {
     const int chunk = (N + kFinThreads - 1) / kFinThreads;  // over k = 1..N
     const int k0 = 1 + t * chunk;
     long long I0;
     const double D1 = poisson_d1(P, s_net, k0, chunk, s_i64, s_i128, &I0);
-    const double C = P.pois_C;
-    const double inv2dx = 1.0 / (2.0 * P.dx);
-    const double twoD1 = D1 + D1;
     long long Ik = I0;
     for (int k = k0; k < k0 + chunk && k <= N; ++k) {
-      double e;
-      if (k <= N - 1) {
-        const long long Ik1 = Ik + net_at(P, s_net, k);
-        e = -(twoD1 - C * (double)(Ik + Ik1)) * inv2dx;
-        Ik = Ik1;
-      } else {
-        e = -(D1 - C * (double)Ik) / P.dx;  // k = N
-      }
-      P.E64[k] = e;
-      P.E32[k] = (float)e;
+      P.pois_I[k] = Ik;
+      if (k <= N - 1) Ik += net_at(P, s_net, k);
     }
-    if (t == 0) {
-      const double e0 = -D1 / P.dx;  // I_1 = 0: D_1
-      P.E64[0] = e0;
-      P.E32[0] = (float)e0;
-    }
+    if (t == 0) *P.pois_D1 = D1;
   }
 
   // ---- tallies: one thread per 8-byte slot of the record ---------------------
@@ -354,6 +341,10 @@ __global__ void __launch_bounds__(kMoveThreads) k_move(DeviceRefs r) {
   step_kernel_entry();
   Control* ctrl = r.ctrl;
   if (*((volatile int*)&ctrl->error)) return;
+  // the field of the step's Poisson solves, node by node over the grid
+  for (int i = 0; i < r.n_inst; ++i)
+    if (r.inst[i].field_mode == 1)
+      poisson_field(r.inst[i], blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
   const unsigned int n_chunks = ctrl->n_move_chunks;
   if (n_chunks == 0) return;
   const unsigned int epoch = ctrl->epoch;

@@ -231,6 +231,8 @@ struct InstDev {
   float* E32;                   // node field used by the FP32 push
   double* phi;                  // node potential
   double* E64;                  // node field
+  long long* pois_I;            // [nn] I_k = sum_{0<j<k} net_j of the last solve
+  double* pois_D1;              // [1] D_1 of the last solve
   unsigned long long* rho_acc[2];  // fixed-point deposit of the current step
   long long* rho_last[2];          // deposit of the last finished step
   unsigned long long* acc;         // ACC_COUNT per-step accumulators

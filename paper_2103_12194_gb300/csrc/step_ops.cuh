@@ -377,12 +377,37 @@ __device__ double poisson_d1(const InstDev& P, const long long* s_net, int k0, i
     if (k <= N - 1) Ik += net_at(P, s_net, k);
   }
   const __int128 incJ = block_incl_scan<__int128, kThreads>(locJ, s_i128);
-  __shared__ __int128 s_JN;
-  if (threadIdx.x == kThreads - 1) s_JN = incJ;
+  // one thread forms D_1 (FP64 is scarce on this part) and shares it
+  __shared__ double s_D1;
+  if (threadIdx.x == kThreads - 1) s_D1 = (P.V + P.pois_C * (double)incJ) / (double)N;
   __syncthreads();
-  const __int128 JN = s_JN;
+  const double D1 = s_D1;
   __syncthreads();
-  return (P.V + P.pois_C * (double)JN) / (double)N;
+  return D1;
+}
+
+// The node field of instance P's last Poisson solve from its exact integer
+// sums (k_finish leaves I_k and D_1): the centred difference of phi,
+// E_k = -(2 D_1 - C (I_k + I_{k+1})) / (2 dx), one-sided at the electrodes,
+// for the nodes k = k0, k0 + stride, ...
+__device__ __forceinline__ void poisson_field(const InstDev& P, int k0, int stride) {
+  const int N = P.n_cells;
+  const double D1 = *P.pois_D1;
+  const double C = P.pois_C;
+  const double inv2dx = 1.0 / (2.0 * P.dx);
+  const double twoD1 = D1 + D1;
+  for (int k = k0; k <= N; k += stride) {
+    double e;
+    if (k == 0) {
+      e = -D1 / P.dx;  // I_1 = 0: D_1
+    } else if (k <= N - 1) {
+      e = -(twoD1 - C * (double)(P.pois_I[k] + P.pois_I[k + 1])) * inv2dx;
+    } else {
+      e = -(D1 - C * (double)P.pois_I[k]) / P.dx;  // k = N
+    }
+    P.E64[k] = e;
+    P.E32[k] = (float)e;
+  }
 }
 
 // Record of one step (TallyRec) from its accumulators q: thread t < kTallySlots
