@@ -34,7 +34,7 @@ constexpr int kCollThreads = 256;
 }  // namespace
 
 template <typename R>
-__global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
+__global__ void __launch_bounds__(kCollThreads, 4) k_collide(DeviceRefs r) {
   __shared__ unsigned long long s_acc[ACC_COUNT];
   __shared__ uint32_t s_births[kCollWarps];
   __shared__ uint32_t s_prefix;
@@ -116,29 +116,42 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
     };
 
     // ---- pass 1: scatter this warp's candidates, count the births ------------
+    // Rounds of 32 candidates, one per lane; the records of the next round are
+    // read while this round scatters, so their load latency overlaps it.
     uint32_t warp_births = 0;
-    if (!ion_chunk) {
+    if (!ion_chunk && total) {
+      const uint32_t ctr2 = P.ctr_inst * 2u, key0 = P.key0, key1 = P.key1;
+      const bool dep = P.field_mode == 1;  // imposed field: the deposit is formed when read
+      unsigned long long* rho_e = P.rho_acc[kElectron];
+      const R wscale = K.wscale;
+      uint32_t qn;
+      int jn = locate_event(lane < total ? lane : total - 1, qn);
+      CandRec<R> nx = {};
+      if (lane < total) nx = get_cand<R>(E.crec, (size_t)(kw + jn) * kTile + qn);
+      uint32_t n_proc[3] = {0u, 0u, 0u};
       for (uint32_t c0 = 0; c0 < total; c0 += 32) {
         const uint32_t ce = c0 + lane;
-        uint32_t q;
-        const int j = locate_event(ce < total ? ce : total - 1, q);
+        const int j = jn;
+        const uint32_t q = qn;
+        const CandRec<R> cr = nx;
+        if (c0 + 32 < total) {
+          const uint32_t cn = ce + 32;
+          jn = locate_event(cn < total ? cn : total - 1, qn);
+          if (cn < total) nx = get_cand<R>(E.crec, (size_t)(kw + jn) * kTile + qn);
+        }
         bool ionized = false;
+        int proc = 3;
         if (ce < total) {
           const size_t base = (size_t)(kw + j) * kTile;
-          const CandRec<R> cr = get_cand<R>(E.crec, base + q);
           const size_t o = base + cr.slot;
-          const int cell = cr.cell;
-          const R off = cr.off, wj = cr.wj;
           const uint32_t id = cr.id;
           R vx = cr.vx, vy = cr.vy, vz = cr.vz;
           const R s1 = vx * vx + vy * vy + vz * vz;
           const R v1 = r_sqrt(s1);
-          const uint4 rr =
-              philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u, 0u), P.key0, P.key1);
-          int proc;
+          const uint4 rr = philox4x32_10(make_uint4(id, step, ctr2, 0u), key0, key1);
           R es = (R)0;
           const Velocity<R> nv =
-              collide<R>(P, kv, vlim, vx, vy, vz, v1, s1, rr, id, step, wj, s_acc, &es, &proc);
+              collide<R>(P, kv, vlim, vx, vy, vz, v1, s1, rr, id, step, cr.wj, s_acc, &es, &proc);
           if (proc < 3) {
             vx = nv.vx;
             vy = nv.vy;
@@ -154,14 +167,23 @@ __global__ void __launch_bounds__(kCollThreads) k_collide(DeviceRefs r) {
               w->vx = es;
             }
           }
-          if (P.field_mode == 1)  // imposed field: the deposit is formed when read
-            deposit(P.rho_acc[kElectron], cell, off,
-                    fixed_charge(beta_of(r_sqrt(vx * vx + vy * vy + vz * vz), vlim) * wj,
-                                 K.wscale));
+          if (dep)
+            deposit(rho_e, cr.cell, cr.off,
+                    fixed_charge(beta_of(r_sqrt(vx * vx + vy * vy + vz * vz), vlim) * cr.wj,
+                                 wscale));
         }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) n_proc[k] += __popc(__ballot_sync(0xFFFFFFFFu, proc == k));
         warp_births += __popc(__ballot_sync(0xFFFFFFFFu, ionized));
       }
-    } else {
+      // the warp's candidates and collisions, counted once
+      if (lane == 0) {
+        atomicAdd(&s_acc[ACC_CAND], (unsigned long long)total);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          if (n_proc[k]) atomicAdd(&s_acc[ACC_COLL0 + k], (unsigned long long)n_proc[k]);
+      }
+    } else if (ion_chunk) {
       warp_births = total;
     }
     if (lane == 0) s_births[warp] = warp_births;

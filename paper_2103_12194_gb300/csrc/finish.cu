@@ -341,10 +341,18 @@ __global__ void __launch_bounds__(kMoveThreads) k_move(DeviceRefs r) {
   step_kernel_entry();
   Control* ctrl = r.ctrl;
   if (*((volatile int*)&ctrl->error)) return;
-  // the field of the step's Poisson solves, node by node over the grid
-  for (int i = 0; i < r.n_inst; ++i)
-    if (r.inst[i].field_mode == 1)
-      poisson_field(r.inst[i], blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  // the field of the step's Poisson solves: CTA b takes part b / n_inst of
+  // instance b % n_inst (every instance gets gridDim / n_inst CTAs, at least
+  // one), node by node
+  {
+    const int n_inst = r.n_inst;
+    const int parts = max(1, (int)gridDim.x / n_inst);
+    for (int b = blockIdx.x; b < n_inst * parts; b += gridDim.x) {
+      const InstDev& P = r.inst[b % n_inst];
+      if (P.field_mode == 1)
+        poisson_field(P, (b / n_inst) * blockDim.x + threadIdx.x, parts * blockDim.x);
+    }
+  }
   const unsigned int n_chunks = ctrl->n_move_chunks;
   if (n_chunks == 0) return;
   const unsigned int epoch = ctrl->epoch;

@@ -398,6 +398,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(DeviceRefs r, long l
         R e2 = (R)0;
         const Velocity<R> nv = collide<R>(P, kv, vlim, vx, vy, vz, v1, s1, rr, id, step,
                                           cr.wj, sh.acc, &e2, &proc);
+        atomicAdd(&sh.acc[ACC_CAND], 1ull);
+        if (proc < 3) atomicAdd(&sh.acc[ACC_COLL0 + proc], 1ull);
         if (proc < 3) {
           me.vx[o] = nv.vx;
           me.vy[o] = nv.vy;

@@ -143,6 +143,8 @@ struct Velocity {
 // (u[0] is unused: the candidate test drew from Philox2x32).
 // Returns the new velocity; *proc_out = 0 elastic, 1 excitation,
 // 2 ionization, 3 null (velocity unchanged).
+// (The caller counts the candidate and its process: ACC_CAND and
+// ACC_COLL0 + proc for proc < 3.)
 template <typename R>
 __device__ Velocity<R> collide(const InstDev& P, R kv, R vlim, R vx, R vy, R vz, R v1, R s1,
                                uint4 rr, uint32_t id, uint32_t step, R wj,
@@ -150,7 +152,6 @@ __device__ Velocity<R> collide(const InstDev& P, R kv, R vlim, R vx, R vy, R vz,
   const StepConsts<R>& K = consts<R>(P);
   R u[4];
   uniform4<R>(rr, u);
-  atomicAdd(&acc[ACC_CAND], 1ull);
   R vb = v1 > vlim ? vlim : v1;
   if (vb > K.vb_cap) {
     vb = K.vb_cap;
@@ -170,7 +171,6 @@ __device__ Velocity<R> collide(const InstDev& P, R kv, R vlim, R vx, R vy, R vz,
   *proc_out = proc;
   Velocity<R> o = {vx, vy, vz};
   if (proc == 3) return o;
-  atomicAdd(&acc[ACC_COLL0 + proc], 1ull);
   if (proc == 0) {
     // Vahedi-Surendra: cos chi = (2 + eps - 2 (1 + eps)^u) / eps, with
     // 1 - cos chi and 1 + cos chi each formed without cancellation so that
