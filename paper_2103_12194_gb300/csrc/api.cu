@@ -509,6 +509,8 @@ int commit(slpic_ctx* c) {
       return cuda_fail(c, (cudaError_t)e2, "finish kernel configuration");
     c->refs.finish_net_nodes = net_nodes;
   }
+  if (int e2 = collide_config())
+    return cuda_fail(c, (cudaError_t)e2, "collision kernel configuration");
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device), "attributes");
   c->sms = sms;

@@ -30,11 +30,32 @@ namespace slpic {
 namespace {
 
 constexpr int kCollThreads = 256;
+constexpr int kQ = 64;  // entries of each queue (a round adds at most 32 to one below 32)
+
+// One warp's collision queues in shared memory (structure of arrays, one
+// entry per lane of a drain).  Elastic collisions keep the incident velocity;
+// excitations and ionizations (rare; one queue) only the energy.  idx packs
+// the candidate's tile in the warp's range (5 bits), its rank among the
+// tile's candidates (7 bits) and its slot in the tile (7 bits).
+template <typename R>
+struct CollQueues {
+  uint32_t e_idx[kQ];
+  int32_t e_cell[kQ];
+  R e_off[kQ], e_wj[kQ], e_vx[kQ], e_vy[kQ], e_vz[kQ], e_eps[kQ], e_u2[kQ], e_u3[kQ];
+  uint32_t n_idx[kQ], n_id[kQ], n_k[kQ];
+  int32_t n_cell[kQ];
+  R n_off[kQ], n_wj[kQ], n_eps[kQ], n_u2[kQ], n_u3[kQ];
+};
+
+__host__ __device__ constexpr uint32_t pack_idx(uint32_t j, uint32_t q, uint32_t slot) {
+  return j | (q << 5) | (slot << 12);
+}
 
 }  // namespace
 
 template <typename R>
 __global__ void __launch_bounds__(kCollThreads, 4) k_collide(DeviceRefs r) {
+  extern __shared__ __align__(16) unsigned char coll_smem[];
   __shared__ unsigned long long s_acc[ACC_COUNT];
   __shared__ uint32_t s_births[kCollWarps];
   __shared__ uint32_t s_prefix;
@@ -116,18 +137,99 @@ __global__ void __launch_bounds__(kCollThreads, 4) k_collide(DeviceRefs r) {
     };
 
     // ---- pass 1: scatter this warp's candidates, count the births ------------
-    // Rounds of 32 candidates, one per lane; the records of the next round are
-    // read while this round scatters, so their load latency overlaps it.
+    // Rounds of 32 candidates, one per lane: each lane draws its candidate's
+    // process (the records of the next round load meanwhile); null collisions
+    // are deposited at once, the others queued by kind and scattered 32 at a
+    // time with every lane on the same path.  Each collision's arithmetic is
+    // that of collide(); the deposits and counters are integer sums, so the
+    // order of the scatterings does not matter.
     uint32_t warp_births = 0;
     if (!ion_chunk && total) {
+      CollQueues<R>& Q = reinterpret_cast<CollQueues<R>*>(coll_smem)[warp];
       const uint32_t ctr2 = P.ctr_inst * 2u, key0 = P.key0, key1 = P.key1;
       const bool dep = P.field_mode == 1;  // imposed field: the deposit is formed when read
       unsigned long long* rho_e = P.rho_acc[kElectron];
       const R wscale = K.wscale;
+      CandRec<R>* crec = reinterpret_cast<CandRec<R>*>(E.crec);
+      const size_t kbase = (size_t)kw * kTile;
+      // the new velocity of slot o, and the deposit with it
+      auto finish_one = [&](uint32_t o, int cell, R off, R wj, const Velocity<R>& nv) {
+        me.vx[o] = nv.vx;
+        me.vy[o] = nv.vy;
+        me.vz[o] = nv.vz;
+        if (dep)
+          deposit(rho_e, cell, off,
+                  fixed_charge(beta_of(r_sqrt(nv.vx * nv.vx + nv.vy * nv.vy + nv.vz * nv.vz),
+                                       vlim) * wj, wscale));
+      };
+      uint32_t e_head = 0, e_tail = 0, n_head = 0, n_tail = 0;
+      // scatter the n <= 32 oldest elastic (inelastic) entries, lane l the l-th
+      auto drain_elastic = [&](uint32_t n) {
+        const uint32_t i = (e_head + lane) & (kQ - 1);
+        const bool on = lane < n;
+        uint32_t idx = 0;
+        int cell = 0;
+        R off = 0, wj = 0, vx = 0, vy = 0, vz = 0, eps = 0, u2 = 0, u3 = 0;
+        if (on) {
+          idx = Q.e_idx[i];
+          cell = Q.e_cell[i];
+          off = Q.e_off[i];
+          wj = Q.e_wj[i];
+          vx = Q.e_vx[i];
+          vy = Q.e_vy[i];
+          vz = Q.e_vz[i];
+          eps = Q.e_eps[i];
+          u2 = Q.e_u2[i];
+          u3 = Q.e_u3[i];
+        }
+        __syncwarp();  // the entries are read before the next round refills them
+        if (on) {
+          const R v1 = r_sqrt(vx * vx + vy * vy + vz * vz);
+          const Velocity<R> nv = scatter_elastic<R>(K, kv, vx, vy, vz, v1, eps, u2, u3);
+          finish_one((uint32_t)(kbase + (idx & 31u) * kTile + (idx >> 12)), cell, off, wj, nv);
+        }
+        e_head += n;
+      };
+      auto drain_inelastic = [&](uint32_t n) {
+        const uint32_t i = (n_head + lane) & (kQ - 1);
+        const bool on = lane < n;
+        uint32_t idx = 0, id = 0, k = 0;
+        int cell = 0;
+        R off = 0, wj = 0, eps = 0, u2 = 0, u3 = 0;
+        if (on) {
+          idx = Q.n_idx[i];
+          id = Q.n_id[i];
+          k = Q.n_k[i];
+          cell = Q.n_cell[i];
+          off = Q.n_off[i];
+          wj = Q.n_wj[i];
+          eps = Q.n_eps[i];
+          u2 = Q.n_u2[i];
+          u3 = Q.n_u3[i];
+        }
+        __syncwarp();
+        if (on) {
+          const size_t base = kbase + (idx & 31u) * kTile;
+          const uint32_t slot = idx >> 12;
+          Velocity<R> nv;
+          if ((int)k <= P.n_exc) {
+            nv = scatter_excitation<R>(K, kv, eps, (int)k, u2, u3, s_acc);
+          } else {
+            R es;
+            nv = scatter_ionization<R>(P, kv, eps, u2, u3, id, step, wj, s_acc, &es);
+            // mark for pass 2, with the secondary's energy in place of vx
+            CandRec<R>* w = crec + base + ((idx >> 5) & 127u);
+            w->slot = slot | kIonizedMark;
+            w->vx = es;
+          }
+          finish_one((uint32_t)(base + slot), cell, off, wj, nv);
+        }
+        n_head += n;
+      };
       uint32_t qn;
       int jn = locate_event(lane < total ? lane : total - 1, qn);
       CandRec<R> nx = {};
-      if (lane < total) nx = get_cand<R>(E.crec, (size_t)(kw + jn) * kTile + qn);
+      if (lane < total) nx = get_cand<R>(E.crec, kbase + (size_t)jn * kTile + qn);
       uint32_t n_proc[3] = {0u, 0u, 0u};
       for (uint32_t c0 = 0; c0 < total; c0 += 32) {
         const uint32_t ce = c0 + lane;
@@ -137,45 +239,59 @@ __global__ void __launch_bounds__(kCollThreads, 4) k_collide(DeviceRefs r) {
         if (c0 + 32 < total) {
           const uint32_t cn = ce + 32;
           jn = locate_event(cn < total ? cn : total - 1, qn);
-          if (cn < total) nx = get_cand<R>(E.crec, (size_t)(kw + jn) * kTile + qn);
+          if (cn < total) nx = get_cand<R>(E.crec, kbase + (size_t)jn * kTile + qn);
         }
-        bool ionized = false;
-        int proc = 3;
+        int proc = 3, kx = 0;
+        R u[4] = {0, 0, 0, 0}, eps = 0;
         if (ce < total) {
-          const size_t base = (size_t)(kw + j) * kTile;
-          const size_t o = base + cr.slot;
-          const uint32_t id = cr.id;
-          R vx = cr.vx, vy = cr.vy, vz = cr.vz;
-          const R s1 = vx * vx + vy * vy + vz * vz;
+          const R s1 = cr.vx * cr.vx + cr.vy * cr.vy + cr.vz * cr.vz;
           const R v1 = r_sqrt(s1);
-          const uint4 rr = philox4x32_10(make_uint4(id, step, ctr2, 0u), key0, key1);
-          R es = (R)0;
-          const Velocity<R> nv =
-              collide<R>(P, kv, vlim, vx, vy, vz, v1, s1, rr, id, step, cr.wj, s_acc, &es, &proc);
-          if (proc < 3) {
-            vx = nv.vx;
-            vy = nv.vy;
-            vz = nv.vz;
-            me.vx[o] = vx;
-            me.vy[o] = vy;
-            me.vz[o] = vz;
-            if (proc == 2) {
-              // mark for pass 2, with the secondary's energy in place of vx
-              ionized = true;
-              CandRec<R>* w = reinterpret_cast<CandRec<R>*>(E.crec) + base + q;
-              w->slot = cr.slot | kIonizedMark;
-              w->vx = es;
-            }
-          }
-          if (dep)
-            deposit(rho_e, cr.cell, cr.off,
-                    fixed_charge(beta_of(r_sqrt(vx * vx + vy * vy + vz * vz), vlim) * cr.wj,
-                                 wscale));
+          const uint4 rr = philox4x32_10(make_uint4(cr.id, step, ctr2, 0u), key0, key1);
+          proc = choose_process<R>(P, vlim, v1, s1, rr, s_acc, u, eps, kx);
+          if (proc == 3 && dep)  // null: the velocity is kept
+            deposit(rho_e, cr.cell, cr.off, fixed_charge(beta_of(v1, vlim) * cr.wj, wscale));
         }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) n_proc[k] += __popc(__ballot_sync(0xFFFFFFFFu, proc == k));
-        warp_births += __popc(__ballot_sync(0xFFFFFFFFu, ionized));
+        const uint32_t be = __ballot_sync(0xFFFFFFFFu, proc == 0);
+        const uint32_t bn = __ballot_sync(0xFFFFFFFFu, proc == 1 || proc == 2);
+        const uint32_t bi = __ballot_sync(0xFFFFFFFFu, proc == 2);
+        n_proc[0] += __popc(be);
+        n_proc[1] += __popc(bn & ~bi);
+        n_proc[2] += __popc(bi);
+        warp_births += __popc(bi);
+        const uint32_t idx = pack_idx((uint32_t)j, q, cr.slot);
+        if (proc == 0) {
+          const uint32_t i = (e_tail + __popc(be & lanemask_lt)) & (kQ - 1);
+          Q.e_idx[i] = idx;
+          Q.e_cell[i] = cr.cell;
+          Q.e_off[i] = cr.off;
+          Q.e_wj[i] = cr.wj;
+          Q.e_vx[i] = cr.vx;
+          Q.e_vy[i] = cr.vy;
+          Q.e_vz[i] = cr.vz;
+          Q.e_eps[i] = eps;
+          Q.e_u2[i] = u[2];
+          Q.e_u3[i] = u[3];
+        } else if (proc != 3) {
+          const uint32_t i = (n_tail + __popc(bn & lanemask_lt)) & (kQ - 1);
+          Q.n_idx[i] = idx;
+          Q.n_id[i] = cr.id;
+          Q.n_k[i] = (uint32_t)kx;
+          Q.n_cell[i] = cr.cell;
+          Q.n_off[i] = cr.off;
+          Q.n_wj[i] = cr.wj;
+          Q.n_eps[i] = eps;
+          Q.n_u2[i] = u[2];
+          Q.n_u3[i] = u[3];
+        }
+        e_tail += __popc(be);
+        n_tail += __popc(bn);
+        __syncwarp();
+        if (e_tail - e_head >= 32u) drain_elastic(32u);
+        if (n_tail - n_head >= 32u) drain_inelastic(32u);
       }
+      if (e_tail != e_head) drain_elastic(e_tail - e_head);
+      if (n_tail != n_head) drain_inelastic(n_tail - n_head);
+      __syncwarp();
       // the warp's candidates and collisions, counted once
       if (lane == 0) {
         atomicAdd(&s_acc[ACC_CAND], (unsigned long long)total);
@@ -260,12 +376,28 @@ __global__ void __launch_bounds__(kCollThreads, 4) k_collide(DeviceRefs r) {
 }
 
 void launch_collide(const DeviceRefs& r, int grid, cudaStream_t s) {
-  if (r.fp64) launch_step_kernel(k_collide<double>, grid, kCollThreads, 0, s, r);
-  else launch_step_kernel(k_collide<float>, grid, kCollThreads, 0, s, r);
+  if (r.fp64)
+    launch_step_kernel(k_collide<double>, grid, kCollThreads,
+                       kCollWarps * sizeof(CollQueues<double>), s, r);
+  else
+    launch_step_kernel(k_collide<float>, grid, kCollThreads,
+                       kCollWarps * sizeof(CollQueues<float>), s, r);
+}
+
+// The collision queues' shared memory (above the static 48 KB in FP64).
+int collide_config() {
+  cudaError_t e = cudaFuncSetAttribute(k_collide<float>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(kCollWarps * sizeof(CollQueues<float>)));
+  if (e != cudaSuccess) return (int)e;
+  e = cudaFuncSetAttribute(k_collide<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kCollWarps * sizeof(CollQueues<double>)));
+  return (int)e;
 }
 
 static_assert(kCollThreads == 32 * kCollWarps, "kCollWarps warps per chunk");
 static_assert(kCollWarpTiles <= 32, "per-tile counts live one per lane");
+static_assert(kTile <= 128 && kCollWarpTiles <= 32, "pack_idx: 5 bits of tile, 7 of rank, 7 of slot");
 static_assert((uint32_t)kTile < kIonizedMark, "candidate slots leave the top bit for the ionization mark");
 
 }  // namespace slpic

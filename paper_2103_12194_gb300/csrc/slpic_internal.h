@@ -333,6 +333,7 @@ void launch_phi(const DeviceRefs& r, int inst, cudaStream_t s);
 void launch_deposit(const DeviceRefs& r, int inst, int n_tiles, cudaStream_t s);
 // Scatter the null-collision candidates queued by the particle kernel.
 void launch_collide(const DeviceRefs& r, int grid, cudaStream_t s);
+int collide_config();
 // Seeding: n markers written contiguously from slot `base` of the current
 // buffer; mode 0/1/2 as SLPIC_SEED_*; for mode 3 (thermal) e0 carries the
 // thermal speed sqrt(k T / m).

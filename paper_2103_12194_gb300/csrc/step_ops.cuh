@@ -139,18 +139,17 @@ struct Velocity {
   R vx, vy, vz;
 };
 
-// Choose the process with u[1] against the cumulative rates and scatter
-// (u[0] is unused: the candidate test drew from Philox2x32).
-// Returns the new velocity; *proc_out = 0 elastic, 1 excitation,
-// 2 ionization, 3 null (velocity unchanged).
-// (The caller counts the candidate and its process: ACC_CAND and
-// ACC_COLL0 + proc for proc < 3.)
+// Process of a null-collision candidate (speed v1, v1^2 = s1): u = the four
+// uniforms of its Philox4x32 block rr (u[0] is unused: the candidate test drew
+// from Philox2x32); u[1] P0 is compared with the cumulative rates
+// n_g sigma_k(eps) beta v dt.  Returns 0 elastic, 1 excitation, 2 ionization,
+// 3 null, with eps the candidate's energy and k its index in the cumulative
+// list (excitation level k for proc 1).
 template <typename R>
-__device__ Velocity<R> collide(const InstDev& P, R kv, R vlim, R vx, R vy, R vz, R v1, R s1,
-                               uint4 rr, uint32_t id, uint32_t step, R wj,
-                               unsigned long long* acc, R* e_sec_out, int* proc_out) {
+__device__ __forceinline__ int choose_process(const InstDev& P, R vlim, R v1, R s1, uint4 rr,
+                                              unsigned long long* acc, R (&u)[4], R& eps,
+                                              int& k_out) {
   const StepConsts<R>& K = consts<R>(P);
-  R u[4];
   uniform4<R>(rr, u);
   R vb = v1 > vlim ? vlim : v1;
   if (vb > K.vb_cap) {
@@ -158,7 +157,7 @@ __device__ Velocity<R> collide(const InstDev& P, R kv, R vlim, R vx, R vy, R vz,
     atomicAdd(&acc[ACC_MAJ], 1ull);
   }
   const R c = K.ndt * vb;
-  const R eps = s1 * K.K_E;
+  eps = s1 * K.K_E;
   R xs[kMaxProc];
   xsec(P, eps, xs);
   const R rsel = u[1] * K.P0;
@@ -167,54 +166,90 @@ __device__ Velocity<R> collide(const InstDev& P, R kv, R vlim, R vx, R vy, R vz,
   const int n_proc = P.n_exc + 2;
   int k = 0;
   while (k < n_proc && !(rsel < c * xs[k])) ++k;
-  const int proc = k == n_proc ? 3 : (k == 0 ? 0 : (k <= P.n_exc ? 1 : 2));
-  *proc_out = proc;
-  Velocity<R> o = {vx, vy, vz};
-  if (proc == 3) return o;
-  if (proc == 0) {
-    // Vahedi-Surendra: cos chi = (2 + eps - 2 (1 + eps)^u) / eps, with
-    // 1 - cos chi and 1 + cos chi each formed without cancellation so that
-    // sin chi keeps its relative precision at both ends
-    const R L = r_log1p(eps);
-    const R em = r_expm1(u[2] * L);
-    const R ep = -r_expm1(-((R)1 - u[2]) * L);
-    R omc = (em + em) / eps;
-    R opc = (((R)1 + eps) * (ep + ep)) / eps;
-    omc = r_min((R)2, r_max((R)0, omc));
-    opc = r_min((R)2, r_max((R)0, opc));
-    const R cc = omc <= (R)1 ? (R)1 - omc : opc - (R)1;
-    const R sc = r_sqrt(omc * opc);
-    const R ph = K.two_pi * u[3];
-    const R cp = r_cos(ph), sn = r_sin(ph);
-    const R e_new = eps * ((R)1 - K.R2 * omc);
-    R ux = vx / v1, uy = vy / v1, uz = vz / v1;
-    rotate(ux, uy, uz, cc, sc, cp, sn);
-    const R vn = r_sqrt(e_new * kv);
-    o.vx = vn * ux;
-    o.vy = vn * uy;
-    o.vz = vn * uz;
-  } else if (proc == 1) {
-    R e_new = eps - K.e_ex[k - 1];
-    if (e_new < (R)0) {
-      e_new = (R)0;
-      atomicAdd(&acc[ACC_CLAMP], 1ull);
-    }
-    isotropic(r_sqrt(e_new * kv), u[2], u[3], K.two_pi, o.vx, o.vy, o.vz);
-  } else {
-    R e_av = eps - K.e_io;
-    if (e_av < (R)0) {
-      e_av = (R)0;
-      atomicAdd(&acc[ACC_CLAMP], 1ull);
-    }
-    atomicAdd(&acc[ACC_WIONZ], (unsigned long long)fixed_charge(wj, K.wscale));
-    const uint4 r1 =
-        philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u, 1u), P.key0, P.key1);
-    const R es = uniform01r<R>(r1.x) * e_av;
-    const R ep = e_av - es;
-    isotropic(r_sqrt(ep * kv), u[2], u[3], K.two_pi, o.vx, o.vy, o.vz);
-    *e_sec_out = es;
+  k_out = k;
+  return k == n_proc ? 3 : (k == 0 ? 0 : (k <= P.n_exc ? 1 : 2));
+}
+
+// Elastic scattering of an electron of velocity v (speed v1, energy eps) by
+// the Vahedi-Surendra angles (u2: polar, u3: azimuth) with the recoil loss.
+template <typename R>
+__device__ __forceinline__ Velocity<R> scatter_elastic(const StepConsts<R>& K, R kv, R vx, R vy,
+                                                       R vz, R v1, R eps, R u2, R u3) {
+  // Vahedi-Surendra: cos chi = (2 + eps - 2 (1 + eps)^u) / eps, with
+  // 1 - cos chi and 1 + cos chi each formed without cancellation so that
+  // sin chi keeps its relative precision at both ends
+  const R L = r_log1p(eps);
+  const R em = r_expm1(u2 * L);
+  const R ep = -r_expm1(-((R)1 - u2) * L);
+  R omc = (em + em) / eps;
+  R opc = (((R)1 + eps) * (ep + ep)) / eps;
+  omc = r_min((R)2, r_max((R)0, omc));
+  opc = r_min((R)2, r_max((R)0, opc));
+  const R cc = omc <= (R)1 ? (R)1 - omc : opc - (R)1;
+  const R sc = r_sqrt(omc * opc);
+  const R ph = K.two_pi * u3;
+  const R cp = r_cos(ph), sn = r_sin(ph);
+  const R e_new = eps * ((R)1 - K.R2 * omc);
+  R ux = vx / v1, uy = vy / v1, uz = vz / v1;
+  rotate(ux, uy, uz, cc, sc, cp, sn);
+  const R vn = r_sqrt(e_new * kv);
+  return {vn * ux, vn * uy, vn * uz};
+}
+
+// Excitation of level k: the threshold removed, an isotropic direction.
+template <typename R>
+__device__ __forceinline__ Velocity<R> scatter_excitation(const StepConsts<R>& K, R kv, R eps, int k,
+                                                          R u2, R u3, unsigned long long* acc) {
+  R e_new = eps - K.e_ex[k - 1];
+  if (e_new < (R)0) {
+    e_new = (R)0;
+    atomicAdd(&acc[ACC_CLAMP], 1ull);
   }
+  Velocity<R> o;
+  isotropic(r_sqrt(e_new * kv), u2, u3, K.two_pi, o.vx, o.vy, o.vz);
   return o;
+}
+
+// Ionization: the excess energy shared between the primary (isotropic) and
+// the secondary (*es_out, block 1 of the primary's draws), the flux weight
+// of the pair tallied.
+template <typename R>
+__device__ __forceinline__ Velocity<R> scatter_ionization(const InstDev& P, R kv, R eps, R u2,
+                                                          R u3, uint32_t id, uint32_t step, R wj,
+                                                          unsigned long long* acc, R* es_out) {
+  const StepConsts<R>& K = consts<R>(P);
+  R e_av = eps - K.e_io;
+  if (e_av < (R)0) {
+    e_av = (R)0;
+    atomicAdd(&acc[ACC_CLAMP], 1ull);
+  }
+  atomicAdd(&acc[ACC_WIONZ], (unsigned long long)fixed_charge(wj, K.wscale));
+  const uint4 r1 =
+      philox4x32_10(make_uint4(id, step, P.ctr_inst * 2u, 1u), P.key0, P.key1);
+  const R es = uniform01r<R>(r1.x) * e_av;
+  const R ep = e_av - es;
+  Velocity<R> o;
+  isotropic(r_sqrt(ep * kv), u2, u3, K.two_pi, o.vx, o.vy, o.vz);
+  *es_out = es;
+  return o;
+}
+
+// Choose the process and scatter (Sec. III and IV).  Returns the new
+// velocity; *proc_out = 0 elastic, 1 excitation, 2 ionization, 3 null
+// (velocity unchanged).  The caller counts the candidate and its process
+// (ACC_CAND, ACC_COLL0 + proc for proc < 3).
+template <typename R>
+__device__ Velocity<R> collide(const InstDev& P, R kv, R vlim, R vx, R vy, R vz, R v1, R s1,
+                               uint4 rr, uint32_t id, uint32_t step, R wj,
+                               unsigned long long* acc, R* e_sec_out, int* proc_out) {
+  R u[4], eps;
+  int k;
+  const int proc = choose_process<R>(P, vlim, v1, s1, rr, acc, u, eps, k);
+  *proc_out = proc;
+  if (proc == 0) return scatter_elastic<R>(consts<R>(P), kv, vx, vy, vz, v1, eps, u[2], u[3]);
+  if (proc == 1) return scatter_excitation<R>(consts<R>(P), kv, eps, k, u[2], u[3], acc);
+  if (proc == 2) return scatter_ionization<R>(P, kv, eps, u[2], u[3], id, step, wj, acc, e_sec_out);
+  return {vx, vy, vz};
 }
 
 // Write the electron and Ar+ born by an ionization at slots pe (electron
