@@ -441,15 +441,15 @@ int commit(slpic_ctx* c) {
   }
   void* blk;
   const size_t nseg = 2 * (size_t)c->n_inst;
-  // ordered-scan records: at most one chunk per kCollChunkTiles (kMoveChunkTiles)
-  // tiles of every store, plus one partial chunk per store
-  const size_t coll_chunks = total_tiles / kCollChunkTiles + nseg + 2;
+  // ordered-scan records: at most one chunk per kCollMinChunkTiles
+  // (kMoveChunkTiles) tiles of every store, plus one partial chunk per store
+  const size_t coll_chunks = total_tiles / kCollMinChunkTiles + nseg + 2;
   const size_t move_chunks = total_tiles / kMoveChunkTiles + nseg + 2;
   size_t bytes = ((sizeof(InstDev) * c->n_inst + 255) & ~size_t(255)) +
                  ((sizeof(InstState) * c->n_inst + 255) & ~size_t(255)) +
                  ((sizeof(SpeciesState) * nseg + 255) & ~size_t(255)) +
                  ((sizeof(Transfer) * nseg + 255) & ~size_t(255)) + 256 +
-                 4 * ((4 * (nseg + 1) + 255) & ~size_t(255)) + 256 +
+                 5 * ((4 * (nseg + 1) + 255) & ~size_t(255)) + 256 +
                  ((sizeof(ChunkStatus) * coll_chunks + 255) & ~size_t(255)) +
                  ((sizeof(ChunkStatus) * move_chunks + 255) & ~size_t(255));
   if (int rc = dmalloc(c, &blk, bytes, "control")) return rc;
@@ -465,6 +465,7 @@ int commit(slpic_ctx* c) {
   c->refs.seg_wstart = carve<unsigned int>(p, nseg + 1);
   c->refs.coll_start = carve<unsigned int>(p, nseg + 1);
   c->refs.move_start = carve<unsigned int>(p, nseg + 1);
+  c->refs.coll_tiles = carve<unsigned int>(p, nseg + 1);
   c->refs.coll_scan = carve<ChunkStatus>(p, coll_chunks);
   c->refs.move_scan = carve<ChunkStatus>(p, move_chunks);
   c->refs.inst = c->d_inst;
@@ -475,6 +476,11 @@ int commit(slpic_ctx* c) {
   CK(cudaMemcpy(&c->d_ctrl->spin_limit, &c->spin_limit, sizeof c->spin_limit,
                 cudaMemcpyHostToDevice),
      "control");
+  {
+    const std::vector<unsigned int> t(c->n_inst, (unsigned int)kCollMaxChunkTiles);
+    CK(cudaMemcpy(c->refs.coll_tiles, t.data(), t.size() * 4, cudaMemcpyHostToDevice),
+       "control");
+  }
   c->refs.seg_start = c->d_seg;
   c->refs.n_inst = c->n_inst;
   // the whole charge grid of the largest instance goes to shared memory when

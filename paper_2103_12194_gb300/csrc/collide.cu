@@ -10,8 +10,8 @@
 // weight.  Each candidate is then deposited with its new density weight
 // (with an imposed field the deposit is formed from the markers when read).
 //
-// Work: chunks of kCollChunkTiles consecutive tiles (each warp kCollWarpTiles
-// of them; the warp numbers the candidates of its tiles in (tile, slot) order
+// Work: chunks of consecutive tiles (each warp an eighth of them, at most
+// 32; the warp numbers the candidates of its tiles in (tile, slot) order
 // and takes them 32 at a time, one lane each, reading each candidate's
 // record -- its state and slot, one 32-byte sector in float -- and writing
 // only the new velocity to its slot), handed out in order (electron
@@ -101,12 +101,14 @@ __global__ void __launch_bounds__(kCollThreads, 4) k_collide(DeviceRefs r) {
     const uint32_t step = r.istate[inst].step;
     const unsigned int first = r.coll_start[inst];
     const unsigned int local = c - first;
-    const unsigned int e_chunks = (se.n_tiles + kCollChunkTiles - 1) / kCollChunkTiles;
+    const uint32_t Te = r.coll_tiles[inst];
+    const unsigned int e_chunks = (se.n_tiles + Te - 1) / Te;
     const bool ion_chunk = local >= e_chunks;
     const uint32_t nt = ion_chunk ? si.n_tiles : se.n_tiles;
-    // this warp's tiles: kCollWarpTiles consecutive ones, tile kw + j at lane j
-    const uint32_t kw = (ion_chunk ? local - e_chunks : local) * kCollChunkTiles +
-                        warp * kCollWarpTiles;
+    // this warp's tiles: wt consecutive ones, tile kw + j at lane j
+    const uint32_t T = ion_chunk ? (uint32_t)kCollMaxChunkTiles : Te;
+    const uint32_t wt = T / kCollWarps;
+    const uint32_t kw = (ion_chunk ? local - e_chunks : local) * T + warp * wt;
     const SoAT<R> me = soa_as<R>(E.buf[se.cur]);
     const StepConsts<R>& K = consts<R>(P);
     const R kv = K.K_V[kElectron], vlim = K.vlim[kElectron];
@@ -114,7 +116,7 @@ __global__ void __launch_bounds__(kCollThreads, 4) k_collide(DeviceRefs r) {
     // electrons emitted at the cathode) and their exclusive prefix: the
     // warp's events are numbered in (tile, slot) order
     uint32_t cnt = 0;
-    if (lane < kCollWarpTiles && kw + lane < nt) cnt = ion_chunk ? I.births[kw + lane] : E.n_cand[kw + lane];
+    if (lane < wt && kw + lane < nt) cnt = ion_chunk ? I.births[kw + lane] : E.n_cand[kw + lane];
     uint32_t excl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -396,8 +398,12 @@ int collide_config() {
 }
 
 static_assert(kCollThreads == 32 * kCollWarps, "kCollWarps warps per chunk");
-static_assert(kCollWarpTiles <= 32, "per-tile counts live one per lane");
-static_assert(kTile <= 128 && kCollWarpTiles <= 32, "pack_idx: 5 bits of tile, 7 of rank, 7 of slot");
+static_assert(kCollMaxChunkTiles / kCollWarps <= 32, "per-tile counts live one per lane");
+static_assert(kTile <= 128 && kCollMaxChunkTiles / kCollWarps <= 32,
+              "pack_idx: 5 bits of tile, 7 of rank, 7 of slot");
+static_assert((kCollMinChunkTiles & (kCollMinChunkTiles - 1)) == 0 &&
+                  kCollMinChunkTiles % kCollWarps == 0,
+              "chunk sizes are powers of two of whole warps");
 static_assert((uint32_t)kTile < kIonizedMark, "candidate slots leave the top bit for the ionization mark");
 
 }  // namespace slpic

@@ -59,9 +59,11 @@ __device__ void plan_next(const DeviceRefs& r, long long* s_buf) {
   for (int base = 0; base < r.n_inst; base += kFinThreads) {
     const int i = base + t;
     long long nc = 0;
-    if (i < r.n_inst)
-      nc = ((long long)r.sstate[2 * i].n_tiles + kCollChunkTiles - 1) / kCollChunkTiles +
-           ((long long)r.sstate[2 * i + 1].n_tiles + kCollChunkTiles - 1) / kCollChunkTiles;
+    if (i < r.n_inst) {
+      const long long T = r.coll_tiles[i];
+      nc = ((long long)r.sstate[2 * i].n_tiles + T - 1) / T +
+           ((long long)r.sstate[2 * i + 1].n_tiles + kCollMaxChunkTiles - 1) / kCollMaxChunkTiles;
+    }
     const long long i_nc = block_incl_scan<long long>(nc, s_buf);
     if (i < r.n_inst) r.coll_start[i] = (unsigned int)(s_carry[3] + i_nc - nc);
     __syncthreads();
@@ -162,6 +164,18 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode, 
     x.n_new = n_new;
     x.tail = tail;
     x.end = end;
+    if (sp == kElectron) {
+      // electron collision chunks of the next step: the largest power of two
+      // (tiles) with about kCollTargetPerWarp candidates per warp at this
+      // step's candidates per tile
+      const unsigned long long cand = s_acc[ACC_CAND];
+      const unsigned long long room =
+          cand ? (unsigned long long)kCollTargetPerWarp * kCollWarps * s0.n_tiles / cand
+               : (unsigned long long)kCollMaxChunkTiles;
+      unsigned int T = kCollMaxChunkTiles;
+      while (T > (unsigned int)kCollMinChunkTiles && T > room) T >>= 1;
+      r.coll_tiles[inst] = T;
+    }
     SpeciesState s1;
     s1.cur = x.dst;
     s1.n_live = n_new;

@@ -284,11 +284,17 @@ struct ChunkStatus {
   unsigned int pad;
 };
 
-// Collision chunks: kCollWarps warps of kCollWarpTiles consecutive tiles
-// each; repacking chunks: kMoveChunkTiles tiles.
+// Collision chunks: kCollWarps warps of T / kCollWarps consecutive tiles
+// each.  Electron chunks have T = coll_tiles[inst] tiles, a power of two in
+// [kCollMinChunkTiles, kCollMaxChunkTiles] chosen from the instance's last
+// step so that a warp meets about kCollTargetPerWarp candidates (many
+// collisions per step: small chunks, more warps); ion chunks (the electrons
+// emitted at the cathode, rare) have kCollMaxChunkTiles.  Repacking chunks:
+// kMoveChunkTiles tiles.
 constexpr int kCollWarps = 8;
-constexpr int kCollWarpTiles = 32;
-constexpr int kCollChunkTiles = kCollWarps * kCollWarpTiles;
+constexpr int kCollMaxChunkTiles = kCollWarps * 32;
+constexpr int kCollMinChunkTiles = kCollWarps;
+constexpr int kCollTargetPerWarp = 256;
 constexpr int kMoveChunkTiles = 128;
 // Single-CTA path (small.cu): at most this many tiles per store and instance
 // when a step starts.
@@ -303,6 +309,7 @@ struct DeviceRefs {
   unsigned int* seg_start;   // [n_seg + 1] first super-tile of each segment
   unsigned int* seg_wstart;  // [n_seg + 1] summed super-tile weights before each segment
   unsigned int* coll_start;  // [n_inst + 1] first collision chunk of each instance
+  unsigned int* coll_tiles;  // [n_inst] tiles per electron collision chunk
   unsigned int* move_start;  // [n_seg + 1] first repacking chunk of each segment
   ChunkStatus* coll_scan;    // [max collision chunks]
   ChunkStatus* move_scan;    // [max repacking chunks]
