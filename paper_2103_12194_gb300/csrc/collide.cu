@@ -324,19 +324,20 @@ __global__ void __launch_bounds__(kCollThreads, 4) k_collide(DeviceRefs r) {
       const uint32_t cap_e = E.cap_tiles * (uint32_t)kTile, cap_i = I.cap_tiles * (uint32_t)kTile;
       const SoAT<R> mi = soa_as<R>(I.buf[si.cur]);
       if (!ion_chunk) {
-        uint32_t ranked = 0;
-        for (uint32_t c0 = 0; c0 < total; c0 += 32) {
-          const uint32_t ce = c0 + lane;
-          uint32_t q;
-          const int j = locate_event(ce < total ? ce : total - 1, q);
-          const size_t base = (size_t)(kw + j) * kTile;
-          const CandRec<R>* rp = reinterpret_cast<const CandRec<R>*>(E.crec) + base + q;
-          const uint32_t a = ce < total ? rp->slot : 0u;
-          const bool ionized = ce < total && (a & kIonizedMark);
-          const uint32_t b = __ballot_sync(0xFFFFFFFFu, ionized);
-          if (ionized) {
-            const uint32_t rank = off_w + ranked + __popc(b & lanemask_lt);
-            const CandRec<R> cr = *rp;
+        // the ionized candidates in candidate order, queued (in the elastic
+        // queue's index array, free after pass 1) and placed 32 at a time:
+        // the n-th of the warp gets rank off_w + n
+        uint32_t* bq = reinterpret_cast<CollQueues<R>*>(coll_smem)[warp].e_idx;
+        const CandRec<R>* crec = reinterpret_cast<const CandRec<R>*>(E.crec);
+        const size_t kbase = (size_t)kw * kTile;
+        uint32_t b_head = 0, b_tail = 0;
+        auto drain_births = [&](uint32_t n) {
+          const bool on = lane < n;
+          const uint32_t ri = on ? bq[(b_head + lane) & (kQ - 1)] : 0u;
+          __syncwarp();
+          if (on) {
+            const uint32_t rank = off_w + b_head + lane;
+            const CandRec<R> cr = crec[kbase + ri];
             const uint32_t pe = app_e + rank, pi = app_i + rank;
             if (pe >= cap_e || pi >= cap_i) {
               atomicCAS(&ctrl->error, 0, kErrCapacity);
@@ -349,8 +350,29 @@ __global__ void __launch_bounds__(kCollThreads, 4) k_collide(DeviceRefs r) {
                                     se.next_id + rank, si.next_id + rank);
             }
           }
-          ranked += __popc(b);
+          b_head += n;
+        };
+        // the slots (with the ionization mark) of the next round load meanwhile
+        uint32_t qn;
+        int jn = locate_event(lane < total ? lane : total - 1, qn);
+        uint32_t an = lane < total ? crec[kbase + (size_t)jn * kTile + qn].slot : 0u;
+        for (uint32_t c0 = 0; c0 < total && b_tail < warp_births; c0 += 32) {
+          const uint32_t ce = c0 + lane;
+          const int j = jn;
+          const uint32_t q = qn, a = an;
+          if (c0 + 32 < total) {
+            const uint32_t cn = ce + 32;
+            jn = locate_event(cn < total ? cn : total - 1, qn);
+            an = cn < total ? crec[kbase + (size_t)jn * kTile + qn].slot : 0u;
+          }
+          const bool ionized = ce < total && (a & kIonizedMark);
+          const uint32_t b = __ballot_sync(0xFFFFFFFFu, ionized);
+          if (ionized) bq[(b_tail + __popc(b & lanemask_lt)) & (kQ - 1)] = (uint32_t)j * kTile + q;
+          b_tail += __popc(b);
+          __syncwarp();
+          if (b_tail - b_head >= 32u) drain_births(32u);
         }
+        if (b_tail != b_head) drain_births(b_tail - b_head);
       } else {
         // electrons emitted at the cathode, after every ionization electron
         const SoAT<R> sb = soa_as<R>(E.stage_b);
