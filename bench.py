@@ -62,6 +62,11 @@ def parse():
     ap.add_argument("--batch", action="store_true",
                     help="instead of the benchmark, time the batched sweep workload: 32 uneven "
                          "instances (pd 0.1-100 Torr cm, 1e4-4e6 electrons) in one context")
+    ap.add_argument("--dense", action="store_true",
+                    help="instead of the benchmark, time one collision-dense instance: the "
+                         "batched sweep's instance 26 (about 33 Torr cm, dx = lambda_min / 4, "
+                         "6339 cells) with 4e6 electrons, a quarter of them null-collision "
+                         "candidates per step")
     ap.add_argument("--small-pop", action="store_true",
                     help="instead of the benchmark, time the paper's breakdown run at 1 Torr cm "
                          "(Table tab:sims row 4) with and without the single-CTA path")
@@ -623,6 +628,47 @@ def batch_bench(slpic, inputs, steps, warmup, local, stream, world=1, rank=0):
                             if gathered is not None else None)}
 
 
+def dense_bench(slpic, inputs, steps, warmup, local, stream, n=4_000_000):
+    """One collision-dense instance (the batched sweep's instance 26: about
+    33 Torr cm at the paper's resolution, dx = lambda_min / 4, dt = dx /
+    v_lim), n electrons log-uniform over 0.1-200 eV, Poisson on: about a
+    quarter of the electrons are null-collision candidates each step, so the
+    collision kernel carries a large share of the step.  Whole steps timed
+    with CUDA events, then the particle kernel alone on the same state."""
+    import torch
+    spec, _ = batch_specs(inputs)[26]
+    spec["instance"] = 0
+    sim = slpic.Simulation(1, device=local, stream=stream)
+    sim.configure(0, spec, capacity=(4 * n + 65536, 4 * n + 65536))
+    sim.seed(0, slpic.ELECTRON, n, slpic.SEED_GAP, e_lo=0.1, e_hi=200.0)
+    sim.step(warmup)
+    sim.synchronize()
+    t0 = sim.tallies(0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall_ms = e0.elapsed_time(e1)
+    t1 = sim.tallies(0)
+    sim.set_profiling(True)
+    sim.step(steps)
+    sim.synchronize()
+    push_ms, _ = sim.profile()
+    t2 = sim.tallies(0)
+    sim.set_profiling(False)
+    sim.close()
+    ms = int(t1["marker_steps"]) - int(t0["marker_steps"])
+    cand = int(t1["n_candidates"]) - int(t0["n_candidates"])
+    prof_ms = int(t2["marker_steps"]) - int(t1["marker_steps"])
+    return {"value": ms / (wall_ms / 1e3), "unit": "marker-steps/s", "steps": steps,
+            "warmup": warmup, "ms_per_step": wall_ms / steps, "cells": spec["n_cells"],
+            "electrons_seeded": n, "live_at_end": [int(x) for x in t2["n_live"]],
+            "candidates_per_marker_step": cand / ms if ms else None,
+            "push_share_of_step": (push_ms / (prof_ms / ms * wall_ms)) if ms and prof_ms else None}
+
+
 def small_pop(slpic, inputs, steps, local, stream, V=171.5):
     """The paper's breakdown run at 1 Torr cm (219 cells, V near this gas's
     V_b, SLPIC with v_lim = v0, 100 electrons at rest, Eq. sey yield, five
@@ -724,6 +770,14 @@ def run_ours(args):
             res = paschen_full(slpic, inputs, local, stream)
             res["study"] = ("breakdown-voltage search over a Paschen curve, batched FP32 on one "
                             "GB300, SLPIC at three speed limits and PIC")
+            print(json.dumps(res), flush=True)
+        return
+    if args.dense:
+        if rank == 0:
+            res = dense_bench(slpic, inputs, args.steps if args.steps != 1000 else 20,
+                              args.warmup, local, stream)
+            res["study"] = ("one collision-dense instance (the batched sweep's instance 26, "
+                            "4e6 electrons, Poisson on)")
             print(json.dumps(res), flush=True)
         return
     if args.small_pop:

@@ -477,7 +477,16 @@ int commit(slpic_ctx* c) {
                 cudaMemcpyHostToDevice),
      "control");
   {
-    const std::vector<unsigned int> t(c->n_inst, (unsigned int)kCollMaxChunkTiles);
+    // first step's electron collision chunks from the majorant probability:
+    // about P0 kTile candidates per full tile
+    std::vector<unsigned int> t(c->n_inst, (unsigned int)kCollMaxChunkTiles);
+    for (int i = 0; i < c->n_inst; ++i) {
+      const double P0 = c->fp64 ? c->h_inst[i].c64.P0 : (double)c->h_inst[i].c32.P0;
+      const double per_tile = P0 * kTile;
+      while (t[i] > (unsigned int)kCollMinChunkTiles &&
+             t[i] / kCollWarps * per_tile > kCollTargetPerWarp)
+        t[i] >>= 1;
+    }
     CK(cudaMemcpy(c->refs.coll_tiles, t.data(), t.size() * 4, cudaMemcpyHostToDevice),
        "control");
   }
