@@ -20,6 +20,98 @@ namespace {
 
 constexpr int kMoveThreads = 256;
 
+// Segments a single warp plans (kPlanPerLane consecutive ones per lane; an
+// instance's two segments stay in one lane).
+constexpr int kPlanPerLane = 8;
+
+__device__ __forceinline__ long long warp_incl_scan(long long v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(0xFFFFFFFFu, v, o);
+    if (lane >= o) v += y;
+  }
+  return v;
+}
+
+// Write the plan's totals and reset the step's counters (one thread).
+__device__ __forceinline__ void plan_totals(const DeviceRefs& r, int n_seg, unsigned int start,
+                                            unsigned int wstart, unsigned int move,
+                                            unsigned int coll) {
+  r.seg_start[n_seg] = start;
+  r.seg_wstart[n_seg] = wstart;
+  r.coll_start[r.n_inst] = coll;
+  r.move_start[n_seg] = move;
+  r.ctrl->n_super = start;
+  r.ctrl->w_total = wstart;
+  r.ctrl->n_seg = n_seg;
+  r.ctrl->n_coll_chunks = coll;
+  r.ctrl->coll_counter = 0;
+  r.ctrl->n_move_chunks = move;
+  r.ctrl->move_counter = 0;
+  r.ctrl->epoch = (r.ctrl->epoch + 1u) & 0x3FFFFFFFu;
+  r.ctrl->finish_done = 0;
+}
+
+// The plan below by one warp (n_seg <= 32 kPlanPerLane), with shuffle scans
+// and no block barrier.
+__device__ void plan_next_warp(const DeviceRefs& r) {
+  const int lane = threadIdx.x & 31;
+  const int n_seg = r.n_inst * 2;
+  const long long W = r.push_warps;
+  long long ns[kPlanPerLane], w[kPlanPerLane], mv[kPlanPerLane], nc[kPlanPerLane / 2];
+  long long s_ns = 0, s_w = 0, s_mv = 0, s_nc = 0;
+#pragma unroll
+  for (int j = 0; j < kPlanPerLane; ++j) {
+    const int sg = lane * kPlanPerLane + j;
+    ns[j] = w[j] = mv[j] = 0;
+    if (sg < n_seg) {
+      ns[j] = ((long long)r.sstate[sg].n_tiles + W - 1) / W;
+      w[j] = ns[j] * ((sg & 1) ? kWeightIon : kWeightElectron);
+      const Transfer& x = r.xfer[sg];
+      if (x.compact) mv[j] = ((long long)x.n_tiles_old + kMoveChunkTiles - 1) / kMoveChunkTiles;
+    }
+    s_ns += ns[j];
+    s_w += w[j];
+    s_mv += mv[j];
+  }
+#pragma unroll
+  for (int j = 0; j < kPlanPerLane / 2; ++j) {
+    const int i = lane * (kPlanPerLane / 2) + j;
+    nc[j] = 0;
+    if (i < r.n_inst) {
+      const long long T = r.coll_tiles[i];
+      nc[j] = ((long long)r.sstate[2 * i].n_tiles + T - 1) / T +
+              ((long long)r.sstate[2 * i + 1].n_tiles + kCollMaxChunkTiles - 1) /
+                  kCollMaxChunkTiles;
+    }
+    s_nc += nc[j];
+  }
+  const long long i_ns = warp_incl_scan(s_ns, lane), i_w = warp_incl_scan(s_w, lane);
+  const long long i_mv = warp_incl_scan(s_mv, lane), i_nc = warp_incl_scan(s_nc, lane);
+  long long e_ns = i_ns - s_ns, e_w = i_w - s_w, e_mv = i_mv - s_mv, e_nc = i_nc - s_nc;
+#pragma unroll
+  for (int j = 0; j < kPlanPerLane; ++j) {
+    const int sg = lane * kPlanPerLane + j;
+    if (sg < n_seg) {
+      r.seg_start[sg] = (unsigned int)e_ns;
+      r.seg_wstart[sg] = (unsigned int)e_w;
+      r.move_start[sg] = (unsigned int)e_mv;
+    }
+    e_ns += ns[j];
+    e_w += w[j];
+    e_mv += mv[j];
+  }
+#pragma unroll
+  for (int j = 0; j < kPlanPerLane / 2; ++j) {
+    const int i = lane * (kPlanPerLane / 2) + j;
+    if (i < r.n_inst) r.coll_start[i] = (unsigned int)e_nc;
+    e_nc += nc[j];
+  }
+  if (lane == 31)
+    plan_totals(r, n_seg, (unsigned int)i_ns, (unsigned int)i_w, (unsigned int)i_mv,
+                (unsigned int)i_nc);
+}
+
 // Plan the next step from the tiles in use (all threads of one CTA):
 // particle-kernel super-tiles (push_warps tiles each) and their weights per
 // segment, repacking chunks per segment and collision chunks per instance,
@@ -27,6 +119,10 @@ constexpr int kMoveThreads = 256;
 __device__ void plan_next(const DeviceRefs& r, long long* s_buf) {
   __shared__ long long s_carry[4];
   const int n_seg = r.n_inst * 2;
+  if (n_seg <= 32 * kPlanPerLane) {
+    if (threadIdx.x < 32) plan_next_warp(r);
+    return;
+  }
   const long long W = r.push_warps;
   const int t = threadIdx.x;
   if (t < 4) s_carry[t] = 0;
@@ -70,23 +166,9 @@ __device__ void plan_next(const DeviceRefs& r, long long* s_buf) {
     if (t == kFinThreads - 1) s_carry[3] += i_nc;
     __syncthreads();
   }
-  if (t == 0) {
-    const unsigned int start = (unsigned int)s_carry[0], wstart = (unsigned int)s_carry[1];
-    const unsigned int move = (unsigned int)s_carry[2], coll = (unsigned int)s_carry[3];
-    r.seg_start[n_seg] = start;
-    r.seg_wstart[n_seg] = wstart;
-    r.coll_start[r.n_inst] = coll;
-    r.move_start[n_seg] = move;
-    r.ctrl->n_super = start;
-    r.ctrl->w_total = wstart;
-    r.ctrl->n_seg = n_seg;
-    r.ctrl->n_coll_chunks = coll;
-    r.ctrl->coll_counter = 0;
-    r.ctrl->n_move_chunks = move;
-    r.ctrl->move_counter = 0;
-    r.ctrl->epoch = (r.ctrl->epoch + 1u) & 0x3FFFFFFFu;
-    r.ctrl->finish_done = 0;
-  }
+  if (t == 0)
+    plan_totals(r, n_seg, (unsigned int)s_carry[0], (unsigned int)s_carry[1],
+                (unsigned int)s_carry[2], (unsigned int)s_carry[3]);
 }
 
 }  // namespace
@@ -125,14 +207,25 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode, 
   }
   // (with an imposed field nothing was deposited: the deposit is formed from
   // the markers when it is read)
-  for (int k = t; k < nn && P.field_mode == 1; k += kFinThreads) {
-    const long long qe = (long long)P.rho_acc[kElectron][k];
-    const long long qi = (long long)P.rho_acc[kIon][k];
-    P.rho_last[kElectron][k] = qe;
-    P.rho_last[kIon][k] = qi;
-    P.rho_acc[kElectron][k] = 0ull;
-    P.rho_acc[kIon][k] = 0ull;
-    if (s_net) s_net[k] = qi - qe;
+  // (four nodes per thread at a time: their loads are issued before any store)
+  for (int k0 = t; k0 < nn && P.field_mode == 1; k0 += 4 * kFinThreads) {
+    long long qe[4], qi[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = k0 + u * kFinThreads;
+      qe[u] = k < nn ? (long long)P.rho_acc[kElectron][k] : 0ll;
+      qi[u] = k < nn ? (long long)P.rho_acc[kIon][k] : 0ll;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = k0 + u * kFinThreads;
+      if (k >= nn) break;
+      P.rho_last[kElectron][k] = qe[u];
+      P.rho_last[kIon][k] = qi[u];
+      P.rho_acc[kElectron][k] = 0ull;
+      P.rho_acc[kIon][k] = 0ull;
+      if (s_net) s_net[k] = qi[u] - qe[u];
+    }
   }
   __syncthreads();
 

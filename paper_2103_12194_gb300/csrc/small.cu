@@ -377,6 +377,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(DeviceRefs r, long l
       uint32_t slot[kSmallCandRows];
       R es[kSmallCandRows];
       unsigned __int128 flags = 0;  // 16-bit ionization count per row
+      uint32_t n_proc[3] = {0u, 0u, 0u};  // this thread's collisions by kind
 #pragma unroll
       for (int u = 0; u < kSmallCandRows; ++u) {
         const uint32_t c = (uint32_t)t + (uint32_t)u * kSmallThreads;
@@ -398,8 +399,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(DeviceRefs r, long l
         R e2 = (R)0;
         const Velocity<R> nv = collide<R>(P, kv, vlim, vx, vy, vz, v1, s1, rr, id, step,
                                           cr.wj, sh.acc, &e2, &proc);
-        atomicAdd(&sh.acc[ACC_CAND], 1ull);
-        if (proc < 3) atomicAdd(&sh.acc[ACC_COLL0 + proc], 1ull);
+        if (proc < 3) ++n_proc[proc];
         if (proc < 3) {
           me.vx[o] = nv.vx;
           me.vy[o] = nv.vy;
@@ -410,6 +410,14 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(DeviceRefs r, long l
           }
         }
       }
+      // the step's candidates and collisions, counted once per warp (C by
+      // one thread) instead of an atomic per candidate on shared counters
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const uint32_t nw = __reduce_add_sync(0xFFFFFFFFu, n_proc[k]);
+        if ((t & 31) == 0 && nw) atomicAdd(&sh.acc[ACC_COLL0 + k], (unsigned long long)nw);
+      }
+      if (t == 0 && C) atomicAdd(&sh.acc[ACC_CAND], (unsigned long long)C);
       // ranks of the ionizations in candidate order: c = t + kSmallThreads u,
       // so row u precedes row u + 1 and inside a row the threads are in order
       // (the scan is skipped in the many steps without an ionization)

@@ -237,9 +237,12 @@ __device__ __forceinline__ Velocity<R> scatter_ionization(const InstDev& P, R kv
 // Choose the process and scatter (Sec. III and IV).  Returns the new
 // velocity; *proc_out = 0 elastic, 1 excitation, 2 ionization, 3 null
 // (velocity unchanged).  The caller counts the candidate and its process
-// (ACC_CAND, ACC_COLL0 + proc for proc < 3).
+// (ACC_CAND, ACC_COLL0 + proc for proc < 3).  Kept out of line: the
+// single-CTA path calls it from several unrolled rows, and one copy of the
+// long scattering code keeps that latency-bound kernel's instruction
+// footprint small.
 template <typename R>
-__device__ Velocity<R> collide(const InstDev& P, R kv, R vlim, R vx, R vy, R vz, R v1, R s1,
+__device__ __noinline__ Velocity<R> collide(const InstDev& P, R kv, R vlim, R vx, R vy, R vz, R v1, R s1,
                                uint4 rr, uint32_t id, uint32_t step, R wj,
                                unsigned long long* acc, R* e_sec_out, int* proc_out) {
   R u[4], eps;
