@@ -185,6 +185,49 @@ def test_one_step_matches_fp32_mirror(slpic, oracle_mod):
     sim.close()
 
 
+def test_collision_dense_steps_match_fp32_mirror(slpic, oracle_mod):
+    """The collision kernel in the breakdown regime and beyond: every
+    electron a null-collision candidate, 15 % of them ionizing (electrons of
+    60-400 eV in a 30 Torr cm gap of 512 cells), so that a warp's elastic and
+    inelastic queues fill and drain 32 at a time, its births are placed 32
+    at a time, and the chunks are sized small (first from P0, then from the
+    first step's candidates).  Two steps against the FP32 mirror: counts
+    bit-exact; ids, cells and weights bit-exact; velocities within the
+    elementary functions' rounding, and so the second step's offsets within
+    1e-5 of a cell."""
+    spec = dense_spec(n_cells=512, pd=30.0)
+    e = inputs.gap_state(200_000, spec, rng_seed=9, e_lo=60.0, e_hi=400.0, wj_spread=1.0)
+    sim = make_sim(slpic, spec)
+    sim.load(0, 0, e)
+    sim.step(2)
+    ref = oracle_mod.Oracle(spec, precision=32)
+    ref.load(0, e)
+    ref.step(2)
+    hg, hr = sim.history(0)[-2:], ref.history()[-2:]
+    for k in ("n_live", "n_coll", "n_candidates", "n_abs", "n_see", "n_clamp", "n_majorant",
+              "marker_steps"):
+        assert np.array_equal(hg[k], hr[k]), (k, hg[k], hr[k])
+    first = hr[0]
+    assert first["n_candidates"] > 0.9 * 200_000
+    assert first["n_coll"][2] > 0.1 * first["n_candidates"]
+    for k in ("w_live", "w_abs", "w_see", "w_ionz"):
+        assert np.allclose(hg[k], hr[k], rtol=1e-12), k
+    vl = spec["vlim_e"]
+    for s in (0, 1):
+        g, r = sim.particles(0, s), ref.particles(s)
+        assert np.array_equal(g["id"], r["id"].astype(np.uint32))
+        assert np.array_equal(g["cell"], r["cell"])
+        assert np.array_equal(g["wj"].astype(np.float64), r["wj"])
+        # the second step drifts markers whose first collision left the last
+        # bits of CUDA's and the host's elementary functions in their velocity
+        assert np.abs(g["off"].astype(np.float64) - r["off"]).max() < 1e-5
+        vg = np.stack([g["vx"], g["vy"], g["vz"]]).astype(np.float64)
+        vr = np.stack([r["vx"], r["vy"], r["vz"]]).astype(np.float64)
+        err = np.linalg.norm(vg - vr, axis=0) / np.maximum(np.linalg.norm(vr, axis=0), vl)
+        assert err.max() <= REL, err.max()
+    sim.close()
+
+
 def test_one_step_matches_fp64_oracle(slpic, oracle_mod):
     """Against FP64: positions to 1e-5 of a cell; energies to 1e-5 of the
     marker's energy scale (an FP32 velocity carries its energy to ~1e-7
