@@ -911,8 +911,10 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sim.reset_counters(0)
-        sim.load(0, slpic.ELECTRON, pinned)
-        sim.load(0, slpic.ION, {k: v[:0] for k, v in pinned.items()})
+        # the serial numbers are 0 .. n - 1: the next one is passed, as a
+        # caller who knows its markers does (else the binding scans the ids)
+        sim.load(0, slpic.ELECTRON, pinned, next_id=n)
+        sim.load(0, slpic.ION, {k: v[:0] for k, v in pinned.items()}, next_id=0)
         sim.step(args.steps)
         hist = sim.history(0, capacity=args.steps)
         dens = sim.density(0, slpic.ELECTRON)

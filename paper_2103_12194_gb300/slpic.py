@@ -276,6 +276,10 @@ class Simulation:
                                     float(e_lo), float(e_hi), float(wj)))
 
     def load(self, i, species, state, next_id=None):
+        """Load the markers of one species from host arrays (the seven fields;
+        pinned memory copies fastest).  next_id is the next serial number the
+        instance hands out; left out, it is formed from the ids here, one pass
+        over them on the host."""
         n = len(state["cell"])
         arrs = {k: np.ascontiguousarray(state[k], dtype=DTYPES.get(k, self._real))
                 for k in FIELDS}
