@@ -162,7 +162,11 @@ int slpic_set_cross_sections_levels(slpic_ctx* ctx, int inst, int lo_exp2,
 /* Species: mass [kg], charge [C], speed limit v_lim [m/s] of Eq. betaAbrupt
  * (beta = min(1, v_lim/|v|); v_lim <= 0 or +inf gives beta = 1, i.e. PIC),
  * capacity = maximum live markers (rounded up to whole tiles of 128 markers,
- * plus one tile).  Only electrons collide (Sec. IV). */
+ * plus one tile).  Only electrons collide (Sec. IV).  Device memory per slot
+ * of capacity: two buffers of the seven marker fields (56 B in FP32, 96 B in
+ * FP64), and for electrons a null-collision candidate record (32 B in FP32,
+ * 64 B in FP64) and the staging of emitted electrons (28 B or 48 B per ion
+ * slot). */
 int slpic_set_species(slpic_ctx* ctx, int inst, int species, double mass,
                       double charge, double v_lim, int64_t capacity);
 /* Ion-induced secondary-electron yield gamma at the cathode (constant; the
