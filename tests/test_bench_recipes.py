@@ -53,3 +53,30 @@ def test_table_sims_rows_are_the_papers():
     assert len(rows) == len(bench.TAB_SIMS)
     for (p, V, cells), r in zip(bench.TAB_SIMS, rows):
         assert (p, V, cells) == (r[0], r[1], int(r[2]))
+
+
+def test_reference_arm_prints_the_line():
+    """`bench.py --impl reference` times the CPU oracle on a bounded sample of
+    the benchmark workload (no GPU) and prints one JSON line with the keys a
+    reader of the bench expects: the metric and value, the reference marker,
+    the CPU baseline's description and an end-to-end entry with no copies."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                          "--steps", "2", "--warmup", "1", "--cpu-seconds", "3"],
+                         capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1, out.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    assert d["metric"] == "marker-steps/s" and d["unit"] == "marker-steps/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True
+    assert d["steps"] == 2 and d["warmup"] == 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["e2e"]["value"] == d["value"]
