@@ -285,14 +285,18 @@ __device__ __forceinline__ void limited_kick_n(R (&vx)[N], const R (&vy)[N], con
     const R s0 = r_sqrt(sp2);
     const R a0 = -w;
     // Limited and slowing down (w < -q): reaching the zone (or the axis,
-    // when p2 >= L2) costs C1 = D(q, |w|) >= L (|w| - q).  Every lane forms
-    // C1, so that the common paths run without divergence; it is used only
-    // by the lanes that start there.
+    // when p2 >= L2) costs C1 = D(q, |w|) >= L (|w| - q).  C1 is formed only
+    // by the lanes whose budget exceeds that lower bound (a warp with none
+    // skips it); the others stay in the slowing part, or start elsewhere.
     const bool regI = w < -q;
-    const R sq = q > (R)0 ? L : r_sqrt(p2[j]);
-    R C1 = (R)0.5 * (a0 * s0 - q * sq);
-    if (p2[j] > (R)0) C1 = mad((R)0.5 * p2[j], r_logk((a0 + s0) / (q + sq)), C1);
-    const bool stay = regI && (W <= L * (a0 - q) || W < C1);
+    const bool near = regI && !(W <= L * (a0 - q));
+    R C1 = (R)0;
+    if (near) {
+      const R sq = q > (R)0 ? L : r_sqrt(p2[j]);
+      C1 = (R)0.5 * (a0 * s0 - q * sq);
+      if (p2[j] > (R)0) C1 = mad((R)0.5 * p2[j], r_logk((a0 + s0) / (q + sq)), C1);
+    }
+    const bool stay = regI && (!near || W < C1);
     // otherwise the limited part that speeds up starts at wf with budget Wf
     R wf = regI ? -q : w;
     R Wf = regI ? W - C1 : W;
