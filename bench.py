@@ -334,9 +334,9 @@ def paschen_sweep(slpic, inputs, local, stream, pds=(0.5, 1.0, 2.0, 4.0), n_v=7,
             "speedup": t64 / t32}
 
 
-def paschen_full(slpic, inputs, local, stream, n_pd=12, pd_lo=0.1, pd_hi=100.0, max_cells=2048,
-                 n_v=8, rounds=3, n_seed=1000, pic_max=2.0, fp64_points=4):
-    """The full breakdown search of the sweep workloads, in a bounded form:
+def paschen_full(slpic, inputs, local, stream, n_pd=24, pd_lo=0.05, pd_hi=200.0, max_cells=2048,
+                 n_v=8, rounds=3, n_seed=1000, pic_max=4.0, fp64_points=4):
+    """The full breakdown search of the sweep workloads, with the cells capped:
     n_pd pd points log-spaced over [pd_lo, pd_hi] Torr cm (d = 1 cm,
     gamma = 0.07, cells from dx = lambda_min / 4 clamped to 128-max_cells),
     each bracketed by a batched
