@@ -10,17 +10,23 @@
 // weight.  Each candidate is then deposited with its new density weight
 // (with an imposed field the deposit is formed from the markers when read).
 //
-// Work: chunks of consecutive tiles (each warp an eighth of them, at most
-// 32; the warp numbers the candidates of its tiles in (tile, slot) order
-// and takes them 32 at a time, one lane each, reading each candidate's
-// record -- its state and slot, one 32-byte sector in float -- and writing
-// only the new velocity to its slot), handed out in order (electron
-// tiles of an instance, then its ion tiles).  The births of a chunk (ionizations; for ion chunks the
-// electrons the particle kernel staged for emission) get their slots from an
-// ordered scan over the chunks (decoupled look-back), so they are appended
-// after the last live marker in (tile, slot) order -- ionization electrons
-// first, emitted electrons after -- with their final serial numbers, whatever
-// the scheduling.
+// Work: chunks of consecutive tiles handed out in order (electron tiles of an
+// instance, then its ion tiles); each warp takes an eighth of a chunk (at
+// most 32 tiles).  An instance's electron chunks are sized from its last
+// step's candidates per tile (about 256 candidates per warp), so a
+// collision-dense instance gets small chunks and many CTAs.  A warp numbers
+// the candidates of its tiles in (tile, slot) order and takes them 32 at a
+// time, one lane each: it reads each candidate's record (its state and slot,
+// one 32-byte sector in float; the next round's records load meanwhile),
+// draws the process, deposits null collisions at once and queues the others
+// by kind in shared memory, scattered 32 at a time on one code path; only
+// the new velocity is written to the candidate's slot.  The births of a
+// chunk (ionizations; for ion chunks the electrons the particle kernel
+// staged for emission) get their slots from an ordered scan over the chunks
+// (decoupled look-back), so they are appended after the last live marker in
+// (tile, slot) order -- ionization electrons first, emitted electrons after
+// -- with their final serial numbers, whatever the scheduling; they are
+// placed 32 at a time.
 #include "device_common.cuh"
 #include "slpic_internal.h"
 #include "step_ops.cuh"
