@@ -251,6 +251,7 @@ def cpu_baseline(spec, n_markers, seconds):
     ms_all = sum(r[0] for r in res)
     dt_all = max(r[1] for r in res)
     return {"value": ms_all / dt_all, "unit": "marker-steps/s", "cores": cores, "kind": "oracle",
+            "stepping_s": dt_all,
             "cpu": cpu_model(),
             "sample": "%d of the workload's electrons (same draw), FP64 oracle: %d processes "
                       "of %d electrons each, %.1f s of stepping (%.1f s with start-up)"
@@ -737,6 +738,9 @@ def run_reference(args):
             "config": {"workload": "push+MCC microbenchmark gap (CPU oracle sample)",
                        "markers": args.markers, "cells": 4096},
             "cpu_baseline": cb,
+            # each of the K steps is a bounded sample of the workload: the
+            # all-cores stepping time spread over them
+            "ms_per_step": cb["stepping_s"] * 1e3 / max(1, args.steps),
             "e2e": {"value": cb["value"], "unit": "marker-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -80,3 +80,4 @@ def test_reference_arm_prints_the_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"]
+    assert 0 < d["ms_per_step"] * d["steps"] < 600e3
