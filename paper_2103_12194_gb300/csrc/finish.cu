@@ -247,9 +247,12 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(DeviceRefs r, int mode, 
     const uint32_t end = tail + nb;
     const uint32_t n_new = surv + nb;
     const uint32_t nt = (end + kTile - 1) / kTile;
-    // repack when under three quarters of the slots in use are live
+    // repack when under 15/16 of the slots in use are live: tiles with holes
+    // cost the particle kernel nearly as much as full ones, and a growing
+    // avalanche leaves many (at 3/4 a 1000-step run of the benchmark ran at
+    // half the rate in its last steps)
     const uint32_t compact =
-        (nt > 2 && (unsigned long long)n_new * 4 < (unsigned long long)nt * kTile * 3) ? 1u : 0u;
+        (nt > 2 && (unsigned long long)n_new * 16 < (unsigned long long)nt * kTile * 15) ? 1u : 0u;
     x.compact = compact;
     x.src = s0.cur;
     x.dst = compact ? s0.cur ^ 1u : s0.cur;
