@@ -81,3 +81,21 @@ def test_reference_arm_prints_the_line():
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"]
     assert 0 < d["ms_per_step"] * d["steps"] < 600e3
+
+
+def test_recorded_push_traffic_matches_the_kernel_source():
+    """The bench reports the particle kernel's DRAM traffic only while the
+    ncu record in profiles/push_traffic.json was taken on the kernel's
+    current code (a digest of its sources without comments and whitespace).
+    A change to that code needs a new capture: this fails until it is
+    recorded, instead of the bench line silently losing its traffic."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "profiles", "push_traffic.json")
+    with open(path) as f:
+        rec = json.load(f)
+    assert rec["push_source_sha256_16"] == bench.push_source_hash(), (
+        "k_push's code changed since the traffic capture: rerun the ncu capture of "
+        "profiles/k_push_microbench_8e6.md and update push_traffic.json")
+    assert 0 < bench.push_traffic() < 48.0
